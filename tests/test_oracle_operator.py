@@ -1,0 +1,154 @@
+"""Pins of the oracle's stiffness/mass matrices, Dirichlet elimination and transfers.
+
+Closed forms used: the assembled P1 Kuhn stiffness equals h times the 7-point
+finite-difference Laplacian, hence D^-1 A has the known cosine spectrum;
+element matrices are symmetric with zero row sums and permute with their
+vertices; P reproduces polynomials of the element degree; P^T A_f P = A_c.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import fe_oracle as O
+import fe_inputs as I
+
+
+def _perm_local_dofs(k, pi):
+    """Local dof permutation induced by relabelling tet vertices by pi."""
+    if k == 1:
+        return list(pi)
+    out = list(pi)
+    for a, b in O.P2_EDGES:
+        pa, pb = sorted((pi[a], pi[b]))
+        out.append(4 + O.P2_EDGES.index((pa, pb)))
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_element_stiffness_invariants(k):
+    m = O.Mesh(2)
+    kap = I.grf_kappa(m.centroids(), seed=3)
+    A = O.element_stiffness(m, k, kap)
+    assert np.allclose(A, A.transpose(0, 2, 1), atol=1e-15)
+    assert np.abs(A.sum(axis=2)).max() < 1e-13
+    ev = np.linalg.eigvalsh(A)
+    assert ev[:, 0].min() > -1e-13 and (ev[:, 1] > 1e-6).all()  # kernel = constants only
+    # relabelling the vertices of a tet permutes its element matrix
+    for pi in itertools.permutations(range(4)):
+        if pi == (0, 1, 2, 3):
+            continue
+        m2 = O.Mesh(2)
+        inv = np.argsort(pi)
+        m2.cells = m.cells[:, inv]
+        A2 = O.element_stiffness(m2, k, kap)
+        perm = _perm_local_dofs(k, inv)
+        assert np.allclose(A2, A[:, perm][:, :, perm], atol=1e-14)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_p1_stiffness_is_h_times_7_point_laplacian(N):
+    L = O.Level(N, 1)
+    A = L.A_free.toarray()
+    h = 1.0 / N
+    lat = L.space.dof_lattice
+    interior = np.nonzero(~L.space.boundary)[0]
+    for i in interior:
+        row = A[i]
+        assert abs(row[i] - 6 * h) < 1e-14
+        for j in np.nonzero(np.abs(row) > 1e-14)[0]:
+            if j == i:
+                continue
+            d = np.abs(lat[j] - lat[i])
+            assert d.sum() == 1 and abs(row[j] + h) < 1e-14
+
+
+def test_p1_jacobi_spectrum_closed_form():
+    N = 6
+    L = O.Level(N, 1)
+    inter = ~L.space.boundary
+    A = L.A.toarray()[np.ix_(inter, inter)]
+    d = np.diag(A)
+    ev = np.sort(np.linalg.eigvalsh(A / np.sqrt(np.outer(d, d))))
+    h = 1.0 / N
+    j = np.arange(1, N)
+    expect = np.sort([1 - (np.cos(a * np.pi * h) + np.cos(b * np.pi * h) + np.cos(c * np.pi * h)) / 3
+                      for a in j for b in j for c in j])
+    assert np.allclose(ev, expect, atol=1e-13)
+    # and the Lanczos estimate used for the Chebyshev interval reaches 1 + cos(pi h)
+    assert abs(O.estimate_lambda_max(L.A, L.diag, 30) - (1 + np.cos(np.pi * h))) < 1e-8
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_global_matrix_invariants(k):
+    L = O.Level(3, k, I.grf_kappa(O.Mesh(3).centroids()))
+    A = L.A_free
+    assert abs(A - A.T).max() < 1e-14
+    assert np.abs(A @ np.ones(L.n)).max() < 1e-12
+    Abc = L.A.toarray()
+    assert np.linalg.eigvalsh(Abc).min() > 0
+    bd = L.space.boundary
+    assert np.allclose(Abc[bd][:, bd], np.eye(bd.sum()))
+    assert np.abs(Abc[bd][:, ~bd]).max() == 0
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_mass_matrix(k):
+    L = O.Level(3, k)
+    M = L.M
+    one = np.ones(L.n)
+    assert abs(one @ (M @ one) - 1.0) < 1e-13  # |Omega| = 1
+    x = L.space.coords
+    # int x dx = 1/2, int x*y dx = 1/4 (x, y in the P1 and P2 spaces)
+    assert abs(one @ (M @ x[:, 0]) - 0.5) < 1e-13
+    assert abs(x[:, 0] @ (M @ x[:, 1]) - 0.25) < 1e-13
+    assert abs(M - M.T).max() < 1e-16
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_apply_rows_matches_assembled(k):
+    L = O.Level(4, k, I.grf_kappa(O.Mesh(4).centroids()))
+    x = I.random_vector(L.n, 5)
+    rows = np.random.default_rng(1).choice(L.n, 40, replace=False)
+    assert np.allclose(O.apply_rows(L.space, L.kappa, x, rows), (L.A @ x)[rows], atol=1e-14)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_prolongation_reproduces_polynomials(k):
+    c, f = O.Level(2, k), O.Level(4, k)
+    P = O.prolongation(c, f)
+    assert np.allclose(P @ np.ones(c.n), 1.0, atol=1e-15)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        a = rng.normal(size=10)
+
+        def p(X):
+            x, y, z = X[:, 0], X[:, 1], X[:, 2]
+            val = a[0] + a[1] * x + a[2] * y + a[3] * z
+            if k == 2:
+                val = val + a[4] * x * x + a[5] * y * y + a[6] * z * z + a[7] * x * y + a[8] * x * z + a[9] * y * z
+            return val
+
+        assert np.allclose(P @ p(c.space.coords), p(f.space.coords), atol=1e-13)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_galerkin_identity(k):
+    c, f = O.Level(2, k), O.Level(4, k)
+    P = O.prolongation(c, f)
+    G = (P.T @ f.A_free @ P).toarray()
+    assert np.abs(G - c.A_free.toarray()).max() < 1e-13
+    # with the boundary eliminated, on the interior block
+    ic, fi = ~c.space.boundary, ~f.space.boundary
+    Pi = P[fi][:, ic]
+    Gi = (Pi.T @ f.A[fi][:, fi] @ Pi).toarray()
+    assert np.abs(Gi - c.A.toarray()[np.ix_(ic, ic)]).max() < 1e-13
+
+
+def test_coarsen_kappa_has_eight_children():
+    c, f = O.Mesh(2), O.Mesh(4)
+    parent, _ = O.locate_in_mesh(c, f.centroids())
+    assert np.all(np.bincount(parent, minlength=c.n_cells) == 8)
+    kf = I.grf_kappa(f.centroids())
+    kc = O.coarsen_kappa(c, f, kf)
+    assert np.allclose(kc, np.bincount(parent, kf) / 8)

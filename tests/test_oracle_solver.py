@@ -1,0 +1,150 @@
+"""Pins of the oracle's solvers: brute force, patch tests, convergence rates,
+the Chebyshev polynomial identity, the coarse Cholesky solve and the adjoint.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fe_oracle as O
+import fe_inputs as I
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("N", [2, 4])
+def test_brute_force_dense_solve(k, N):
+    h = O.Hierarchy(max(1, N // 2), 1, k)
+    L = h.fine
+    b = O.load_vector(L, I.sin_product_rhs(L.space.coords))
+    dense = np.linalg.solve(L.A.toarray(), b)
+    for pc in ("gmg", "jacobi"):
+        u, it, hist = O.solve(h, b, rtol=1e-14, precond=pc)
+        assert np.linalg.norm(u - dense) <= 1e-12 * np.linalg.norm(dense)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_patch_test_exact(k):
+    """Linear (P1) / quadratic (P2) solutions with matching Dirichlet data are nodally exact."""
+    h = O.Hierarchy(2, 1, k)
+    L = h.fine
+    X = L.space.coords
+    if k == 1:
+        u = 1 + 2 * X[:, 0] - 3 * X[:, 1] + 0.5 * X[:, 2]
+        f = np.zeros(L.n)
+    else:
+        u = X[:, 0] ** 2 + 2 * X[:, 1] ** 2 - X[:, 2] ** 2 + X[:, 0] * X[:, 1] - X[:, 1] * X[:, 2] + 3 * X[:, 0]
+        f = np.full(L.n, -4.0)  # -Laplace(u)
+    b = O.load_vector(L, f, bc_values=u)
+    uh, it, hist = O.solve(h, b, rtol=1e-14)
+    assert np.abs(uh - u).max() < 1e-12
+
+
+@pytest.mark.parametrize("k,Ns,order", [(1, (8, 16), 2.0), (2, (8, 16), 3.0)])
+def test_convergence_rates(k, Ns, order):
+    errs = []
+    for N in Ns:
+        h = O.Hierarchy(N // 4, 2, k)
+        L = h.fine
+        b = O.load_vector(L, I.sin_product_rhs(L.space.coords))
+        u, it, hist = O.solve(h, b, rtol=1e-12)
+        errs.append(O.l2_error(L.space, u, I.sin_product))
+    rate = np.log2(errs[0] / errs[1])
+    assert abs(rate - order) < 0.15, (errs, rate)
+
+
+def test_paper_manufactured_pair():
+    """The paper's printed f is -Laplace of its printed u (Section 2, Eqs. 2-3)."""
+    rng = np.random.default_rng(0)
+    X = rng.uniform(0.05, 0.95, size=(20, 3))
+    h = 1e-4
+    lap = np.zeros(20)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        lap += (I.paper_solution(X + e) - 2 * I.paper_solution(X) + I.paper_solution(X - e)) / h ** 2
+    assert np.allclose(-lap, I.paper_rhs(X), rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3])
+def test_chebyshev_polynomial_identity(steps):
+    """x_k - x* = p_k(D^-1 A)(x_0 - x*), p_k(t) = T_k((theta-t)/delta) / T_k(theta/delta)."""
+    L = O.Level(2, 2, I.grf_kappa(O.Mesh(2).centroids()))
+    A = L.A.toarray()
+    d = L.diag
+    rng = np.random.default_rng(1)
+    b, x0 = rng.normal(size=L.n), rng.normal(size=L.n)
+    xs = np.linalg.solve(A, b)
+    lo, hi = 0.3, 2.1
+    xk = O.chebyshev(lambda v: A @ v, d, b, x0, lo, hi, steps)
+    # D^-1 A = D^-1/2 S D^1/2 with S symmetric
+    Dh = np.sqrt(d)
+    S = A / np.outer(Dh, Dh)
+    lam, V = np.linalg.eigh(S)
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+    Tk = np.polynomial.chebyshev.Chebyshev.basis(steps)
+    pk = Tk((theta - lam) / delta) / Tk(theta / delta)
+    e0 = Dh * (x0 - xs)
+    ek = (V @ (pk * (V.T @ e0))) / Dh
+    assert np.allclose(xk - xs, ek, atol=1e-11)
+
+
+def test_coarse_cholesky_solve():
+    h = O.Hierarchy(3, 1, 2)
+    c = h.levels[0]
+    b = np.random.default_rng(2).normal(size=c.n)
+    x = h.coarse_solve(b)
+    assert np.linalg.norm(c.A @ x - b) < 1e-12 * np.linalg.norm(b)
+
+
+def test_gmg_pcg_is_mesh_independent():
+    its = []
+    for nref in (1, 2, 3):
+        h = O.Hierarchy(2, nref, 2)
+        L = h.fine
+        b = O.load_vector(L, I.sin_product_rhs(L.space.coords))
+        _, it, _ = O.solve(h, b, rtol=1e-8)
+        its.append(it)
+    assert max(its) <= 12 and its[-1] - its[0] <= 3, its
+
+
+def _J_direct(N, k, kappa, f_fn, ud_fn):
+    L = O.Level(N, k, kappa)
+    b = O.load_vector(L, f_fn(L.space.coords))
+    u = spla.spsolve(L.A.tocsc(), b)
+    return O.objective(L, u, ud_fn(L.space.coords))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_adjoint_gradient_vs_central_differences(k):
+    N = 2
+    mesh = O.Mesh(N)
+    kappa = I.grf_kappa(mesh.centroids(), seed=7)
+    f_fn = lambda X: np.ones(X.shape[0])
+    h = O.Hierarchy(1, 1, k, kappa)
+    L = h.fine
+    b = O.load_vector(L, f_fn(L.space.coords))
+    ud = I.target_field(L.space.coords)
+    J, g, u, lam = O.adjoint_gradient(h, b, ud)
+    assert abs(J - _J_direct(N, k, kappa, f_fn, I.target_field)) < 1e-12 * abs(J)
+    cells = np.random.default_rng(0).choice(mesh.n_cells, 12, replace=False)
+    for c in cells:
+        eps = 1e-5 * kappa[c]
+        kp, km = kappa.copy(), kappa.copy()
+        kp[c] += eps
+        km[c] -= eps
+        fd = (_J_direct(N, k, kp, f_fn, I.target_field) - _J_direct(N, k, km, f_fn, I.target_field)) / (2 * eps)
+        assert abs(fd - g[c]) <= 1e-6 * np.abs(g).max(), (c, fd, g[c])
+
+
+def test_adjoint_taylor_remainder_is_second_order():
+    N = 4
+    mesh = O.Mesh(N)
+    kappa = I.grf_kappa(mesh.centroids(), seed=9)
+    f_fn = lambda X: np.ones(X.shape[0])
+    h = O.Hierarchy(2, 1, 1, kappa)
+    L = h.fine
+    J, g, u, lam = O.adjoint_gradient(h, O.load_vector(L, f_fn(L.space.coords)), I.target_field(L.space.coords))
+    dk = np.random.default_rng(3).normal(size=mesh.n_cells) * kappa
+    rem = []
+    for t in (1e-2, 5e-3):
+        rem.append(abs(_J_direct(N, 1, kappa + t * dk, f_fn, I.target_field) - J - t * (g @ dk)))
+    assert 3.0 < rem[0] / rem[1] < 5.0  # O(t^2): halving t divides the remainder by ~4
