@@ -1,0 +1,226 @@
+/*
+ * fe.h -- C ABI of the GB300 matrix-free finite element Poisson library.
+ *
+ * The library solves -div(kappa grad u) = f on the unit cube with Dirichlet
+ * conditions on all six faces, discretised with continuous Lagrange P1 or P2
+ * elements on a tetrahedral UnitCubeMesh, by conjugate gradients preconditioned
+ * with a geometric multigrid V-cycle over a nested mesh hierarchy.  This is the
+ * Poisson model problem of the paper (Section 2, Eqs. 1-4: mesh, function
+ * space, Dirichlet BCs, right-hand side, bilinear form; Section 3: multigrid
+ * with two Chebyshev smoothing iterations per level and a direct coarse solve).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Return value: FE_OK (0) on success, a negative FE_ERR_* code on failure; no
+ *   entry point aborts or throws.  fe_last_error() returns a message for the
+ *   last failure on the calling thread.
+ * Vectors: every double/float pointer argument may point to HOST memory
+ *   (pageable or pinned) or to DEVICE memory of the current CUDA device.  The
+ *   library detects which (cudaPointerGetAttributes) and stages host data
+ *   through its own device buffers; results are complete in host memory when
+ *   the call returns.  Device data is read/written in stream order on
+ *   `stream` (a cudaStream_t, NULL = the legacy default stream); the call may
+ *   return before device-side work finishes unless stated otherwise.
+ * Ownership: handles are created and owned by the library and released with
+ *   the matching *_destroy.  Vectors are owned by the caller.  A hierarchy
+ *   holds device workspace; calls on the same hierarchy must not run
+ *   concurrently (from several host threads or on several streams at once).
+ * Mesh: UnitCubeMesh(N,N,N), vertex (i,j,k) at (i,j,k)/N with index
+ *   i + (N+1)(j + (N+1)k); cube (ci,cj,ck) has index q = ci + N(cj + N ck) and
+ *   is split into the six Kuhn tetrahedra 6q..6q+5 that share its main
+ *   diagonal (the paper does not state the split; this is the reading taken).
+ *   Level l of a hierarchy is the same construction with N0 * 2^l cubes.
+ * Degrees of freedom: P1 dofs are the vertices.  P2 dofs are the points of
+ *   the 2N lattice (2N+1 per axis); dofs 0..(N+1)^3-1 are the vertices in
+ *   vertex order, followed by edge midpoints grouped by the parity class of
+ *   their lattice coordinates in the order (1,0,0),(0,1,0),(0,0,1),(1,1,0),
+ *   (1,0,1),(0,1,1),(1,1,1); inside a class the sub-lattice (L - parity)/2 is
+ *   numbered x fastest.  Use fe_dof_coordinates() to evaluate fields.
+ * Boundary: a dof is a boundary dof if any lattice coordinate is 0 or kN.  The
+ *   operator is the symmetric elimination of the Dirichlet dofs: boundary
+ *   rows and columns of A are replaced by the identity.
+ * Coefficient: kappa is one FP64 value per fine cell (NULL means kappa = 1);
+ *   coarse levels use the arithmetic mean of the 8 child cells.
+ */
+#ifndef FE_GB300_H
+#define FE_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FE_OK 0
+#define FE_ERR_ARG (-1)             /* invalid argument (null handle, bad size, level out of range) */
+#define FE_ERR_CUDA (-2)            /* a CUDA runtime call or kernel launch failed */
+#define FE_ERR_NOMEM (-3)           /* device or host allocation failed */
+#define FE_ERR_NO_CONVERGENCE (-4)  /* the iteration limit was reached before the tolerance */
+#define FE_ERR_NAN (-5)             /* a residual norm became NaN or Inf */
+#define FE_ERR_TIMEOUT (-6)         /* a bounded device-side wait gave up */
+#define FE_ERR_UNSUPPORTED (-7)     /* valid request that this build does not support */
+
+/* ---- arithmetic types of an operator application ---- */
+#define FE_F64 0   /* vectors double, arithmetic FP64 */
+#define FE_F32 1   /* vectors float, arithmetic FP32 */
+#define FE_BF16 2  /* vectors float; dofs rounded to bf16 and contracted on the tensor cores, FP32 accumulation */
+
+/* ---- preconditioners and precision modes of fe_solve_poisson ---- */
+#define FE_PC_JACOBI 0
+#define FE_PC_GMG 1
+#define FE_PREC_F64 0         /* everything FP64 */
+#define FE_PREC_MIXED_F32 1   /* FP64 iterative refinement around an FP32 GMG-PCG */
+#define FE_PREC_MIXED_BF16 2  /* as FE_PREC_MIXED_F32 with bf16 tensor-core smoother applications */
+
+/* ---- right-hand side kinds ---- */
+#define FE_RHS_LOAD 0     /* rhs is the assembled load vector b (boundary entries = Dirichlet values) */
+#define FE_RHS_NODAL_F 1  /* rhs holds nodal values of f; b = M f on interior rows, 0 on the boundary */
+
+typedef struct fe_mesh fe_mesh;
+typedef struct fe_hierarchy fe_hierarchy;
+
+typedef struct fe_solver_opts {
+  double rtol;        /* stop when ||b - A u||_2 <= rtol ||b||_2 (unpreconditioned 2-norm) */
+  int max_it;         /* CG iteration limit (outer refinement steps for mixed precision) */
+  int precond;        /* FE_PC_JACOBI or FE_PC_GMG */
+  int precision;      /* FE_PREC_* */
+  int cheb_steps;     /* Chebyshev iterations per smoothing (2 in the paper's options) */
+  double cheb_lo;     /* Chebyshev interval [cheb_lo, cheb_hi] * lambda_max(D^-1 A) */
+  double cheb_hi;
+  double inner_rtol;  /* mixed precision: inner FP32 solve tolerance */
+  int inner_max_it;   /* mixed precision: inner iteration limit per refinement step */
+  int use_graph;      /* nonzero: replay each V-cycle from a captured CUDA graph */
+} fe_solver_opts;
+
+typedef struct fe_solve_stats {
+  int iterations;        /* CG iterations (sum of inner iterations for mixed precision) */
+  int outer_iterations;  /* refinement steps (mixed precision), else 1 */
+  double rel_residual;   /* final ||b - A u|| / ||b|| in FP64 */
+  double bnorm;          /* ||b||_2 */
+  double solve_ms;       /* host wall time of the solve */
+  int fine_applies_f64;  /* FP64 fine-level operator applications */
+  int fine_applies_low;  /* FP32/bf16 fine-level operator applications */
+} fe_solve_stats;
+
+/* Fill `opts` with the defaults: rtol 1e-8, max_it 500, GMG, FP64,
+ * 2 Chebyshev steps on [0.1, 1.1] lambda_max, inner_rtol 1e-4, inner_max_it 60,
+ * graphs on. */
+void fe_default_opts(fe_solver_opts* opts);
+
+/* Message of the last failure on this thread ("" if none).  The string is
+ * owned by the library and valid until the next call on this thread. */
+const char* fe_last_error(void);
+
+/* Number of visible CUDA devices (0 without a GPU); never fails. */
+int fe_device_count(void);
+
+/* ---- mesh and hierarchy (paper Section 2: UnitCubeMesh, MeshHierarchy, FunctionSpace) ---- */
+
+/* Create UnitCubeMesh(nx, ny, nz).  This build supports cubes only:
+ * nx == ny == nz >= 1, else FE_ERR_UNSUPPORTED / FE_ERR_ARG.  Host-only. */
+int fe_mesh_create(int nx, int ny, int nz, fe_mesh** out);
+void fe_mesh_destroy(fe_mesh* mesh);
+
+/* Refine `coarse` uniformly `nrefine` times (0..8) and build the degree-1 or
+ * degree-2 Lagrange space on every level, uploading the levels to the current
+ * CUDA device.  Level 0 is the coarse mesh, level nrefine the finest.  The
+ * coefficient is kappa = 1 until fe_set_coefficient() is called. */
+int fe_hierarchy_refine(const fe_mesh* coarse, int nrefine, int degree, fe_hierarchy** out);
+void fe_hierarchy_destroy(fe_hierarchy* h);
+
+/* Number of levels (nrefine + 1), or a negative code. */
+int fe_num_levels(const fe_hierarchy* h);
+
+/* Sizes of `level`: cubes per axis N, dofs n = (kN+1)^3, cells 6 N^3. */
+int fe_level_sizes(const fe_hierarchy* h, int level, int* N, long long* n_dofs, long long* n_cells);
+
+/* Coordinates of the dofs of `level`: xyz[3*i + a], n_dofs x 3 doubles. */
+int fe_dof_coordinates(const fe_hierarchy* h, int level, double* xyz);
+
+/* Centroids of the cells of `level`: xyz[3*c + a], n_cells x 3 doubles. */
+int fe_cell_centroids(const fe_hierarchy* h, int level, double* xyz);
+
+/* Boundary flags of the dofs of `level` (1 = Dirichlet dof), n_dofs bytes. */
+int fe_boundary_mask(const fe_hierarchy* h, int level, unsigned char* mask);
+
+/* Set the cell coefficient kappa (n_cells of the finest level, FP64; NULL =
+ * 1) and rebuild everything that depends on it on every level: per-cell
+ * geometric factors, Jacobi diagonals, Chebyshev eigenvalue estimates and the
+ * coarse Cholesky factor.  Synchronises `stream`. */
+int fe_set_coefficient(fe_hierarchy* h, const double* kappa_cells, void* stream);
+
+/* ---- operator application (paper Section 2, Eq. 4: the bilinear form) ---- */
+
+/* y = A_l x on `level`, matrix-free: for every tet K, y_K += kappa_K
+ * int_K grad(u) . grad(v) applied to the gathered dofs x_K, scatter-added
+ * into y; boundary rows give y_i = x_i and boundary entries of x are treated
+ * as 0 in interior rows.  dtype FE_F64: x, y double.  FE_F32: float.
+ * FE_BF16: float vectors, x rounded to bf16 and contracted on the tensor
+ * cores with FP32 accumulation.  x and y must not overlap. */
+int fe_apply_operator(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, void* stream);
+
+/* y = M_l x with the consistent mass matrix (all dofs, no boundary change). */
+int fe_apply_mass(const fe_hierarchy* h, int level, const double* x, double* y, void* stream);
+
+/* diag = diagonal of A_l (boundary entries 1), n_dofs doubles. */
+int fe_diagonal(const fe_hierarchy* h, int level, double* diag, void* stream);
+
+/* Largest eigenvalue estimate of D^-1 A_l used by the Chebyshev smoother. */
+int fe_lambda_max(const fe_hierarchy* h, int level, double* lmax);
+
+/* ---- multigrid components (paper Section 3: MG with Chebyshev smoothing, direct coarse solve) ---- */
+
+/* xf (+)= P xc: prolongation from level_fine-1 to level_fine by exact
+ * interpolation of the coarse Lagrange function at the fine nodes.
+ * accumulate != 0 adds to xf.  FP64. */
+int fe_prolong(const fe_hierarchy* h, int level_fine, const double* xc, double* xf, int accumulate, void* stream);
+
+/* rc = P^T rf: restriction from level_fine to level_fine-1 (the transpose of
+ * fe_prolong).  zero_boundary != 0 sets the coarse boundary entries to 0. */
+int fe_restrict(const fe_hierarchy* h, int level_fine, const double* rf, double* rc, int zero_boundary, void* stream);
+
+/* `steps` Chebyshev iterations for A_l x = b with the Jacobi preconditioner
+ * on [cheb_lo, cheb_hi] * lambda_max, starting from x (in/out).  dtype
+ * FE_F64 (double vectors) or FE_F32/FE_BF16 (float vectors). */
+int fe_smooth(const fe_hierarchy* h, int level, const void* b, void* x, int steps, double cheb_lo, double cheb_hi,
+              int dtype, void* stream);
+
+/* x = A_0^-1 b on the coarsest level with the FP64 Cholesky factor of its
+ * interior block (x_bd = b_bd). */
+int fe_coarse_solve(const fe_hierarchy* h, const double* b, double* x, void* stream);
+
+/* x = V(b): one V-cycle on the finest level (pre-smoothing from 0, residual,
+ * restriction, recursion, coarse Cholesky solve, prolongation,
+ * post-smoothing).  dtype as fe_smooth; the coarse solve is FP64. */
+int fe_vcycle(const fe_hierarchy* h, const void* b, void* x, int dtype, void* stream);
+
+/* ---- solves ---- */
+
+/* b = M f on interior rows and b_bd = 0, from nodal values f (n_dofs). */
+int fe_load_vector(const fe_hierarchy* h, const double* f_nodal, double* b, void* stream);
+
+/* Solve A u = b on the finest level by PCG (Jacobi or GMG V-cycle), or by
+ * FP64 iterative refinement around a reduced-precision GMG-PCG.  rhs:
+ * FE_RHS_LOAD or FE_RHS_NODAL_F (see above).  u: in = initial guess
+ * (ignored, taken as 0), out = solution.  Synchronises `stream`.  Returns
+ * FE_ERR_NO_CONVERGENCE if max_it is reached (u holds the last iterate) and
+ * FE_ERR_NAN on a non-finite residual.  opts NULL = defaults; stats may be NULL. */
+int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_solver_opts* opts, double* u,
+                     fe_solve_stats* stats, void* stream);
+
+/* Adjoint gradient of J(kappa) = (u - u_d)^T M (u - u_d) = int (u_h - I_h u_d)^2
+ * where A(kappa) u = b: solves A u = b (unless u_ckpt != NULL, which is taken
+ * as the checkpointed forward solution), then A lambda = -2 M (u - u_d) with
+ * lambda_bd = 0, and returns dJ_dkappa[K] = int_K grad(lambda) . grad(u) for
+ * every fine cell (n_cells doubles) and J (one double, may be NULL).  u_out
+ * (may be NULL) receives u.  rhs as in fe_solve_poisson. */
+int fe_adjoint_gradient(fe_hierarchy* h, const double* rhs, int rhs_kind, const double* u_d, const double* u_ckpt,
+                        const fe_solver_opts* opts, double* dJ_dkappa, double* J, double* u_out, void* stream);
+
+/* J = (u - u_d)^T M (u - u_d) on the finest level (the objective whose
+ * gradient fe_adjoint_gradient returns); J is one double in host memory. */
+int fe_objective(const fe_hierarchy* h, const double* u, const double* u_d, double* J, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_GB300_H */

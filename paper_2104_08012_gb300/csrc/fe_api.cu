@@ -1,0 +1,1058 @@
+// C ABI of the library (include/fe.h): mesh and hierarchy construction,
+// coefficient setup, and the host orchestration of the multigrid V-cycle,
+// preconditioned CG, mixed-precision iterative refinement and the adjoint
+// gradient.  Every arithmetic step runs in the CUDA kernels of fe_kernels.cu,
+// fe_blas.cu, fe_coarse.cu and fe_tc.cu; the host only sequences launches and
+// tests convergence.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+
+#include "fe_internal.cuh"
+
+void upload_mass_tables();
+void launch_fill64(size_t n, double v, double* p, cudaStream_t s);
+
+// ------------------------------------------------------------- errors
+static thread_local std::string g_err;
+void fe_set_error(const std::string& m) { g_err = m; }
+
+#define API_BEGIN try {
+#define API_END                                   \
+  }                                               \
+  catch (const FeError& e) {                      \
+    fe_set_error(e.msg);                          \
+    return e.code;                                \
+  }                                               \
+  catch (const std::bad_alloc&) {                 \
+    fe_set_error("host allocation failed");       \
+    return FE_ERR_NOMEM;                          \
+  }                                               \
+  catch (...) {                                   \
+    fe_set_error("unexpected C++ exception");     \
+    return FE_ERR_CUDA;                           \
+  }                                               \
+  return FE_OK;
+
+// ----------------------------------------------------------- numbering
+Numbering make_numbering(int N, int deg) {
+  Numbering nb{};
+  nb.N = N;
+  nb.deg = deg;
+  nb.m = deg * N;
+  if (deg == 1) {
+    const int n = (N + 1) * (N + 1) * (N + 1);
+    nb.off[0] = 0;
+    for (int k = 1; k < 9; ++k) nb.off[k] = n;
+    for (int k = 0; k < 8; ++k) nb.sx[k] = nb.sy[k] = nb.sz[k] = N + 1;
+    return nb;
+  }
+  int acc = 0;
+  for (int c = 0; c < 8; ++c) {
+    nb.sx[c] = N + 1 - class_parity_x(c);
+    nb.sy[c] = N + 1 - class_parity_y(c);
+    nb.sz[c] = N + 1 - class_parity_z(c);
+    nb.off[c] = acc;
+    acc += nb.sx[c] * nb.sy[c] * nb.sz[c];
+  }
+  nb.off[8] = acc;
+  return nb;
+}
+
+// ------------------------------------------------- host pointer staging
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void* stage_buf(fe_hierarchy* h, int slot, size_t bytes) {
+  DBuf<unsigned char>& b = h->stage[slot];
+  if (b.n < bytes) b.alloc(bytes);
+  return b.p;
+}
+
+template <typename T>
+static const T* stage_in(fe_hierarchy* h, int slot, const T* p, size_t n, cudaStream_t s) {
+  if (!p || is_device_ptr(p)) return p;
+  T* d = (T*)stage_buf(h, slot, n * sizeof(T));
+  CUDA_CHECK(cudaMemcpyAsync(d, p, n * sizeof(T), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+template <typename T>
+static T* stage_out(fe_hierarchy* h, int slot, T* p, size_t n) {
+  if (!p || is_device_ptr(p)) return p;
+  return (T*)stage_buf(h, slot, n * sizeof(T));
+}
+
+template <typename T>
+static void finish_out(T* user, const T* dev, size_t n, cudaStream_t s) {
+  if (user && user != dev) {
+    CUDA_CHECK(cudaMemcpyAsync(user, dev, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+  }
+}
+
+static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+// -------------------------------------------------- transfer stencils
+// Prolongation class o in [0,2k)^3 of a fine lattice point (position o/(2k)
+// inside its coarse cube): the containing Kuhn tet is found by sorting the
+// position's coordinates, its barycentrics are exact dyadic numbers, and the
+// coarse basis functions of that tet give the stencil weights.
+static void build_transfer_tables(TransferTables& t, int deg) {
+  const int K2 = 2 * deg;
+  t.deg = deg;
+  t.n_pro_class = K2 * K2 * K2;
+  t.h_pro_start.assign(1, 0);
+  t.h_pro_off.clear();
+  t.h_pro_w.clear();
+  struct Ent { int o[3]; int d[3]; double w; };
+  std::vector<Ent> all;
+  for (int oz = 0; oz < K2; ++oz)
+    for (int oy = 0; oy < K2; ++oy)
+      for (int ox = 0; ox < K2; ++ox) {
+        const int o[3] = {ox, oy, oz};
+        const double s[3] = {ox / (double)K2, oy / (double)K2, oz / (double)K2};
+        int sig[3] = {0, 1, 2};
+        std::stable_sort(sig, sig + 3, [&](int a, int b) { return s[a] > s[b]; });
+        const double lam[4] = {1.0 - s[sig[0]], s[sig[0]] - s[sig[1]], s[sig[1]] - s[sig[2]], s[sig[2]]};
+        int v[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {1, 1, 1}};
+        v[1][sig[0]] = 1;
+        v[2][sig[0]] = 1;
+        v[2][sig[1]] = 1;
+        auto push = [&](const int d[3], double w) {
+          if (w == 0.0) return;
+          t.h_pro_off.push_back(make_int4(d[0], d[1], d[2], 0));
+          t.h_pro_w.push_back(w);
+          all.push_back(Ent{{o[0], o[1], o[2]}, {d[0], d[1], d[2]}, w});
+        };
+        if (deg == 1) {
+          for (int i = 0; i < 4; ++i) push(v[i], lam[i]);
+        } else {
+          for (int i = 0; i < 4; ++i) {
+            const int d[3] = {2 * v[i][0], 2 * v[i][1], 2 * v[i][2]};
+            push(d, lam[i] * (2.0 * lam[i] - 1.0));
+          }
+          for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b) {
+              const int d[3] = {v[a][0] + v[b][0], v[a][1] + v[b][1], v[a][2] + v[b][2]};
+              push(d, 4.0 * lam[a] * lam[b]);
+            }
+        }
+        t.h_pro_start.push_back((int)t.h_pro_off.size());
+      }
+  // Restriction: coarse point Lc receives w * r_f(2 Lc + o - 2 d) from every
+  // entry (o, d, w) with d = Lc (mod k); classes indexed by the parity code of Lc.
+  t.n_res_class = deg == 2 ? 8 : 1;
+  t.h_res_start.assign(1, 0);
+  t.h_res_off.clear();
+  t.h_res_w.clear();
+  for (int cls = 0; cls < t.n_res_class; ++cls) {
+    for (const Ent& e : all) {
+      if (deg == 2) {
+        const int code = (e.d[0] & 1) | ((e.d[1] & 1) << 1) | ((e.d[2] & 1) << 2);
+        if (code != cls) continue;
+      }
+      t.h_res_off.push_back(make_int4(e.o[0] - 2 * e.d[0], e.o[1] - 2 * e.d[1], e.o[2] - 2 * e.d[2], 0));
+      t.h_res_w.push_back(e.w);
+    }
+    t.h_res_start.push_back((int)t.h_res_off.size());
+  }
+  auto up = [](auto& dbuf, const auto& vec) {
+    using T = typename std::decay_t<decltype(vec)>::value_type;
+    dbuf.alloc(vec.size());
+    CUDA_CHECK(cudaMemcpy(dbuf.p, vec.data(), sizeof(T) * vec.size(), cudaMemcpyHostToDevice));
+  };
+  up(t.pro_start, t.h_pro_start);
+  up(t.pro_off, t.h_pro_off);
+  up(t.pro_w, t.h_pro_w);
+  up(t.res_start, t.h_res_start);
+  up(t.res_off, t.h_res_off);
+  up(t.res_w, t.h_res_w);
+}
+
+// The 8 children of each coarse Kuhn type: (subcube code, fine type) whose
+// centroid lies in it (the Kuhn meshes at N and 2N are nested).
+static std::vector<int> build_children() {
+  std::vector<int> ch(48, -1), cnt(6, 0);
+  for (int code = 0; code < 8; ++code)
+    for (int t = 0; t < 6; ++t) {
+      int p0, p1, p2;
+      kuhn_perm(t, p0, p1, p2);
+      double c[3] = {0, 0, 0};
+      int v[3] = {0, 0, 0};
+      for (int k = 0; k < 4; ++k) {
+        if (k == 1) v[p0] = 1;
+        if (k == 2) v[p1] = 1;
+        if (k == 3) v[p2] = 1;
+        for (int a = 0; a < 3; ++a) c[a] += 0.25 * v[a];
+      }
+      const double s[3] = {0.5 * (((code >> 0) & 1) + c[0]), 0.5 * (((code >> 1) & 1) + c[1]),
+                           0.5 * (((code >> 2) & 1) + c[2])};
+      int sig[3] = {0, 1, 2};
+      std::sort(sig, sig + 3, [&](int a, int b) { return s[a] > s[b]; });
+      const int T = 2 * sig[0] + (sig[1] > sig[2] ? 1 : 0);
+      FE_REQUIRE(cnt[T] < 8, FE_ERR_CUDA, "refinement table construction failed");
+      ch[T * 8 + cnt[T]++] = code * 8 + t;
+    }
+  for (int T = 0; T < 6; ++T) FE_REQUIRE(cnt[T] == 8, FE_ERR_CUDA, "refinement table construction failed");
+  return ch;
+}
+
+// --------------------------------------------------- eigenvalue estimate
+// Largest eigenvalue of the symmetric tridiagonal (a, b) by Sturm bisection.
+static double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int k = (int)a.size();
+  double lo = 0.0, hi = 0.0;
+  for (int i = 0; i < k; ++i) {
+    const double r = std::fabs(i > 0 ? b[i - 1] : 0.0) + std::fabs(i + 1 < k ? b[i] : 0.0);
+    hi = std::max(hi, a[i] + r);
+    lo = std::min(lo, a[i] - r);
+  }
+  auto count_below = [&](double x) {
+    int c = 0;
+    double q = 1.0;
+    for (int i = 0; i < k; ++i) {
+      const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+      q = (a[i] - x) - (i > 0 ? bb / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= k)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return hi;
+}
+
+// lambda_max(D^-1 A_l) from `steps` Jacobi-PCG iterations on a seeded random
+// right-hand side: the CG coefficients define the Lanczos tridiagonal.
+static double estimate_lmax(fe_hierarchy* h, int l, int steps, cudaStream_t s) {
+  Level& L = h->L[l];
+  const int n = L.n;
+  ReduceCtx& R = h->red;
+  double *b = h->b, *x = h->x, *r = h->r, *z = h->z, *p = h->p, *q = h->q;
+  launch_random(n, 0x2104080120210416ull + (uint64_t)l, b, s);
+  launch_zero_boundary64(L, b, s);
+  CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  CUDA_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  launch_cheb_step<double>(n, r, nullptr, L.dinv64, p, z, 0.0, 1.0, true, s);  // z = p = D^-1 r
+  launch_dot<double>(R, n, r, z, S_RZ, s);
+  std::vector<double> al, be;
+  for (int it = 0; it < steps; ++it) {
+    launch_apply64(L, p, q, s);
+    launch_cg_alpha<double>(R, n, p, q, s);
+    launch_cg_update<double>(R, n, x, r, p, q, L.dinv64, z, s);
+    launch_cg_update_p<double>(R, n, p, z, s);
+    CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+    const double alpha = R.h_scal[S_ALPHA], beta = R.h_scal[S_BETA];
+    if (!(std::isfinite(alpha) && std::isfinite(beta)) || alpha <= 0) break;
+    al.push_back(alpha);
+    be.push_back(beta);
+    if (R.h_scal[S_RR] <= 0.0) break;
+  }
+  FE_REQUIRE(!al.empty(), FE_ERR_NAN, "eigenvalue estimate failed");
+  const int k = (int)al.size();
+  std::vector<double> a(k), off(k > 1 ? k - 1 : 0);
+  for (int i = 0; i < k; ++i) {
+    a[i] = 1.0 / al[i] + (i > 0 ? be[i - 1] / al[i - 1] : 0.0);
+    if (i + 1 < k) off[i] = std::sqrt(be[i]) / al[i];
+  }
+  return tridiag_max_eig(a, off);
+}
+
+// -------------------------------------------------------- V-cycle
+struct SmootherParams {
+  int steps = 2;
+  double lo = 0.1, hi = 1.1;
+};
+static thread_local SmootherParams g_sp;
+
+template <typename T> static T* lv_b(Level& L);
+template <typename T> static T* lv_x(Level& L);
+template <typename T> static T* lv_y(Level& L);
+template <typename T> static T* lv_d(Level& L);
+template <typename T> static const T* lv_dinv(const Level& L);
+template <> double* lv_b<double>(Level& L) { return L.b64; }
+template <> double* lv_x<double>(Level& L) { return L.x64; }
+template <> double* lv_y<double>(Level& L) { return L.y64; }
+template <> double* lv_d<double>(Level& L) { return L.d64; }
+template <> const double* lv_dinv<double>(const Level& L) { return L.dinv64; }
+template <> float* lv_b<float>(Level& L) { return L.b32; }
+template <> float* lv_x<float>(Level& L) { return L.x32; }
+template <> float* lv_y<float>(Level& L) { return L.y32; }
+template <> float* lv_d<float>(Level& L) { return L.d32; }
+template <> const float* lv_dinv<float>(const Level& L) { return L.dinv32; }
+
+void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s) {
+  const Level& L = h->L[level];
+  if (dtype == FE_F64)
+    launch_apply64(L, (const double*)x, (double*)y, s);
+  else if (dtype == FE_F32)
+    launch_apply32(L, (const float*)x, (float*)y, s);
+  else if (dtype == FE_BF16)
+    apply_bf16_enqueue(L, (const float*)x, (float*)y, s);
+  else
+    FE_FAIL(FE_ERR_ARG, "unknown dtype");
+}
+
+// Chebyshev iterations on level l (same recurrence as the oracle's).
+template <typename T>
+static void smooth_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d, int steps, double lo, double hi,
+                           bool x_zero, int dtype, cudaStream_t s) {
+  Level& L = h->L[l];
+  const double a = lo * L.lmax, bmax = hi * L.lmax;
+  const double theta = 0.5 * (bmax + a), delta = 0.5 * (bmax - a), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  for (int k = 0; k < steps; ++k) {
+    if (k == 0) {
+      if (x_zero) {
+        launch_cheb_step<T>(L.n, b, nullptr, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, true, s);
+      } else {
+        apply_enqueue(h, l, x, y, dtype, s);
+        launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, false, s);
+      }
+    } else {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      apply_enqueue(h, l, x, y, dtype, s);
+      launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, rn * rho, 2.0 * rn / delta, false, s);
+      rho = rn;
+    }
+  }
+}
+
+// One V-cycle on levels l..0: approximately solves A_l x_l = b_l.
+template <typename T>
+static void vcycle_level(fe_hierarchy* h, int l, int dtype, cudaStream_t s) {
+  Level& L = h->L[l];
+  T *b = lv_b<T>(L), *x = lv_x<T>(L), *y = lv_y<T>(L), *d = lv_d<T>(L);
+  if (l == 0) {
+    coarse_solve<T>(h, b, x, s);
+    return;
+  }
+  const int rdt = (dtype == FE_BF16) ? FE_F32 : dtype;  // residuals in FP32 when smoothing in bf16
+  smooth_enqueue<T>(h, l, b, x, y, d, g_sp.steps, g_sp.lo, g_sp.hi, true, dtype, s);
+  apply_enqueue(h, l, x, y, rdt, s);
+  Level& Lc = h->L[l - 1];
+  launch_restrict<T>(h, l, b, y, lv_b<T>(Lc), true, s);
+  vcycle_level<T>(h, l - 1, dtype, s);
+  launch_prolong<T>(h, l, lv_x<T>(Lc), x, true, s);
+  smooth_enqueue<T>(h, l, b, x, y, d, g_sp.steps, g_sp.lo, g_sp.hi, false, dtype, s);
+}
+
+// Enqueue one fine-level V-cycle (reads L.b of the finest level, writes
+// L.x); replays a captured CUDA graph when `use_graph` is set.
+static void run_vcycle(fe_hierarchy* h, int dtype, bool use_graph, cudaStream_t s) {
+  auto enqueue = [&](cudaStream_t st) {
+    if (dtype == FE_F64)
+      vcycle_level<double>(h, h->nlev - 1, dtype, st);
+    else
+      vcycle_level<float>(h, h->nlev - 1, dtype, st);
+  };
+  if (!use_graph) {
+    enqueue(s);
+    return;
+  }
+  GraphCache& gc = h->vgraph[dtype];
+  if (gc.exec && (gc.steps != g_sp.steps || gc.lo != g_sp.lo || gc.hi != g_sp.hi)) {
+    cudaGraphExecDestroy(gc.exec);
+    gc.exec = nullptr;
+  }
+  if (!gc.exec) {
+    if (!gc.stream) CUDA_CHECK(cudaStreamCreateWithFlags(&gc.stream, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    CUDA_CHECK(cudaStreamBeginCapture(gc.stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue(gc.stream);
+    } catch (...) {
+      cudaStreamEndCapture(gc.stream, &g);
+      throw;
+    }
+    CUDA_CHECK(cudaStreamEndCapture(gc.stream, &g));
+    CUDA_CHECK(cudaGraphInstantiate(&gc.exec, g, 0));
+    cudaGraphDestroy(g);
+    gc.steps = g_sp.steps;
+    gc.lo = g_sp.lo;
+    gc.hi = g_sp.hi;
+  }
+  CUDA_CHECK(cudaGraphLaunch(gc.exec, s));
+}
+
+static void invalidate_graphs(fe_hierarchy* h) {
+  for (auto& g : h->vgraph)
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+}
+
+// ------------------------------------------------------------ PCG
+struct PcgResult {
+  int it = 0;
+  double rr = 0, bb = 0;
+  int status = FE_OK;
+  int applies = 0;
+};
+
+// FP64 PCG on the finest level: b, x device vectors (x overwritten).
+static PcgResult pcg64(fe_hierarchy* h, const double* b, double* x, const fe_solver_opts& o, cudaStream_t s) {
+  Level& F = h->L[h->nlev - 1];
+  const int n = F.n;
+  ReduceCtx& R = h->red;
+  double *r = F.b64, *z = F.x64, *p = h->p, *q = h->q;
+  const bool gmg = o.precond == FE_PC_GMG && h->nlev > 1;
+  PcgResult res;
+  CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  CUDA_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  launch_dot<double>(R, n, b, b, S_BB, s);
+  if (gmg)
+    run_vcycle(h, FE_F64, o.use_graph != 0, s);
+  else
+    launch_cheb_step<double>(n, r, nullptr, F.dinv64, q, z, 0.0, 1.0, true, s);  // z = D^-1 r
+  launch_dot<double>(R, n, r, z, S_RZ, s);
+  CUDA_CHECK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  res.bb = R.h_scal[S_BB];
+  res.rr = res.bb;
+  const double tol2 = o.rtol * o.rtol * res.bb;
+  if (res.bb == 0.0) return res;
+  while (true) {
+    if (res.it >= o.max_it) {
+      res.status = FE_ERR_NO_CONVERGENCE;
+      break;
+    }
+    launch_apply64(F, p, q, s);
+    ++res.applies;
+    launch_cg_alpha<double>(R, n, p, q, s);
+    launch_cg_update<double>(R, n, x, r, p, q, gmg ? nullptr : F.dinv64.p, z, s);
+    CUDA_CHECK(cudaMemcpyAsync(R.h_scal + S_RR, R.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+    ++res.it;
+    res.rr = R.h_scal[S_RR];
+    if (!std::isfinite(res.rr)) {
+      res.status = FE_ERR_NAN;
+      break;
+    }
+    if (res.rr <= tol2) break;
+    if (gmg) {
+      run_vcycle(h, FE_F64, o.use_graph != 0, s);
+      launch_cg_beta<double>(R, n, r, z, s);
+    }
+    launch_cg_update_p<double>(R, n, p, z, s);
+  }
+  return res;
+}
+
+// Inner reduced-precision GMG-PCG for A e = r32 (||r32|| = 1), e in h->e32.
+static PcgResult pcg_low(fe_hierarchy* h, int dtype, const fe_solver_opts& o, cudaStream_t s) {
+  Level& F = h->L[h->nlev - 1];
+  const int n = F.n;
+  ReduceCtx& R = h->red;
+  float *r = F.b32, *z = F.x32, *p = h->p32, *q = h->q32, *e = h->e32;
+  PcgResult res;
+  CUDA_CHECK(cudaMemsetAsync(e, 0, sizeof(float) * n, s));
+  launch_dot<float>(R, n, r, r, S_BB, s);
+  run_vcycle(h, dtype, o.use_graph != 0, s);
+  launch_dot<float>(R, n, r, z, S_RZ, s);
+  CUDA_CHECK(cudaMemcpyAsync(p, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  res.bb = R.h_scal[S_BB];
+  const double tol2 = o.inner_rtol * o.inner_rtol * res.bb;
+  while (res.it < o.inner_max_it) {
+    launch_apply32(F, p, q, s);
+    ++res.applies;
+    launch_cg_alpha<float>(R, n, p, q, s);
+    launch_cg_update<float>(R, n, e, r, p, q, nullptr, z, s);
+    CUDA_CHECK(cudaMemcpyAsync(R.h_scal + S_RR, R.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+    ++res.it;
+    res.rr = R.h_scal[S_RR];
+    if (!std::isfinite(res.rr)) {
+      res.status = FE_ERR_NAN;
+      break;
+    }
+    if (res.rr <= tol2) break;
+    run_vcycle(h, dtype, o.use_graph != 0, s);
+    launch_cg_beta<float>(R, n, r, z, s);
+    launch_cg_update_p<float>(R, n, p, z, s);
+  }
+  return res;
+}
+
+// FP64 iterative refinement: r = b - A x in FP64, inner low-precision solve,
+// x += e, until ||r|| <= rtol ||b||.
+static PcgResult refine(fe_hierarchy* h, const double* b, double* x, const fe_solver_opts& o, int dtype,
+                        fe_solve_stats* st, cudaStream_t s) {
+  Level& F = h->L[h->nlev - 1];
+  const int n = F.n;
+  ReduceCtx& R = h->red;
+  double* r = h->r;
+  double* y = h->tmp;
+  PcgResult res;
+  CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  CUDA_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  launch_dot<double>(R, n, b, b, S_BB, s);
+  CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  res.bb = R.h_scal[S_BB];
+  double rr = res.bb;
+  const double bb = res.bb;
+  int outer = 0, inner_total = 0, low_applies = 0;
+  if (bb > 0.0) {
+    while (rr > o.rtol * o.rtol * bb) {
+      if (outer >= o.max_it) {
+        res.status = FE_ERR_NO_CONVERGENCE;
+        break;
+      }
+      // r32 = r / ||r||; ||r||^2 parked in S_TMP0 for the correction
+      CUDA_CHECK(cudaMemcpyAsync(R.scal + S_TMP0, R.scal + (outer == 0 ? S_BB : S_DOT), sizeof(double),
+                                 cudaMemcpyDeviceToDevice, s));
+      launch_scale_copy<float>(n, r, R.scal + S_TMP0, true, F.b32, s);
+      PcgResult in = pcg_low(h, dtype, o, s);
+      inner_total += in.it;
+      low_applies += in.applies;
+      if (in.status == FE_ERR_NAN) {
+        res.status = FE_ERR_NAN;
+        break;
+      }
+      launch_add_scaled<float>(n, h->e32, R.scal + S_TMP0, x, s);
+      launch_apply64(F, x, y, s);
+      ++res.applies;
+      launch_sub64(n, b, y, r, s);
+      launch_dot<double>(R, n, r, r, S_DOT, s);
+      CUDA_CHECK(cudaMemcpyAsync(R.h_scal + S_DOT, R.scal + S_DOT, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CUDA_CHECK(cudaStreamSynchronize(s));
+      rr = R.h_scal[S_DOT];
+      ++outer;
+      if (!std::isfinite(rr)) {
+        res.status = FE_ERR_NAN;
+        break;
+      }
+    }
+  }
+  res.rr = rr;
+  res.it = inner_total;
+  if (st) {
+    st->outer_iterations = outer;
+    st->fine_applies_low = low_applies;
+  }
+  return res;
+}
+
+// --------------------------------------------------------- setup
+static void set_coefficient_impl(fe_hierarchy* h, const double* kappa, cudaStream_t s) {
+  Level& F = h->L[h->nlev - 1];
+  if (kappa) {
+    const double* kd = stage_in<double>(h, 0, kappa, F.C, s);
+    FE_REQUIRE(launch_check_positive(kd, F.C, h->cs.flag, s) == 0, FE_ERR_ARG, "kappa must be positive and finite");
+    CUDA_CHECK(cudaMemcpyAsync(F.kappa, kd, sizeof(double) * F.C, cudaMemcpyDeviceToDevice, s));
+  } else {
+    launch_fill64(F.C, 1.0, F.kappa, s);
+  }
+  for (int l = h->nlev - 1; l >= 1; --l) launch_coarsen_kappa(h->L[l - 1], h->L[l], h->children, s);
+  for (int l = 0; l < h->nlev; ++l) {
+    launch_geometry(h->L[l], s);
+    launch_diag(h->L[l], h->tmp, s);
+  }
+  for (int l = 0; l < h->nlev; ++l) h->L[l].lmax = estimate_lmax(h, l, 20, s);
+  if (h->nlev > 1) coarse_setup(h, s);
+  invalidate_graphs(h);
+  CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+static const double* rhs_to_load(fe_hierarchy* h, const double* rhs, int kind, cudaStream_t s) {
+  Level& F = h->L[h->nlev - 1];
+  const double* rd = stage_in<double>(h, 1, rhs, F.n, s);
+  if (kind == FE_RHS_LOAD) {
+    if (rd != h->b.p) CUDA_CHECK(cudaMemcpyAsync(h->b, rd, sizeof(double) * F.n, cudaMemcpyDeviceToDevice, s));
+  } else if (kind == FE_RHS_NODAL_F) {
+    launch_mass(F, rd, h->b, s);
+    launch_zero_boundary64(F, h->b, s);
+  } else {
+    FE_FAIL(FE_ERR_ARG, "unknown rhs kind");
+  }
+  return h->b;
+}
+
+static void check_level(const fe_hierarchy* h, int level) {
+  FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
+  FE_REQUIRE(level >= 0 && level < h->nlev, FE_ERR_ARG, "level out of range");
+}
+
+static fe_solver_opts resolve_opts(const fe_solver_opts* o) {
+  fe_solver_opts d;
+  fe_default_opts(&d);
+  if (o) d = *o;
+  FE_REQUIRE(d.rtol >= 0 && d.max_it >= 0 && d.cheb_steps >= 1 && d.cheb_hi > d.cheb_lo && d.cheb_lo > 0,
+             FE_ERR_ARG, "invalid solver options");
+  return d;
+}
+
+// =================================================================== ABI
+extern "C" {
+
+void fe_default_opts(fe_solver_opts* o) {
+  if (!o) return;
+  o->rtol = 1e-8;
+  o->max_it = 500;
+  o->precond = FE_PC_GMG;
+  o->precision = FE_PREC_F64;
+  o->cheb_steps = 2;
+  o->cheb_lo = 0.1;
+  o->cheb_hi = 1.1;
+  o->inner_rtol = 1e-4;
+  o->inner_max_it = 60;
+  o->use_graph = 1;
+}
+
+const char* fe_last_error(void) { return g_err.c_str(); }
+
+int fe_device_count(void) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int fe_mesh_create(int nx, int ny, int nz, fe_mesh** out) {
+  API_BEGIN
+  FE_REQUIRE(out, FE_ERR_ARG, "null output handle");
+  *out = nullptr;
+  FE_REQUIRE(nx >= 1 && ny >= 1 && nz >= 1, FE_ERR_ARG, "mesh sizes must be >= 1");
+  FE_REQUIRE(nx == ny && ny == nz, FE_ERR_UNSUPPORTED, "only cubic UnitCubeMesh(N,N,N) is supported");
+  FE_REQUIRE(nx <= 1024, FE_ERR_ARG, "mesh too large");
+  *out = new fe_mesh{nx};
+  API_END
+}
+
+void fe_mesh_destroy(fe_mesh* m) { delete m; }
+
+int fe_hierarchy_refine(const fe_mesh* coarse, int nrefine, int degree, fe_hierarchy** out) {
+  API_BEGIN
+  FE_REQUIRE(out, FE_ERR_ARG, "null output handle");
+  *out = nullptr;
+  FE_REQUIRE(coarse, FE_ERR_ARG, "null mesh");
+  FE_REQUIRE(nrefine >= 0 && nrefine <= 8, FE_ERR_ARG, "nrefine must be in [0, 8]");
+  FE_REQUIRE(degree == 1 || degree == 2, FE_ERR_UNSUPPORTED, "degree must be 1 or 2");
+  const long long Nf = (long long)coarse->N << nrefine;
+  const long long nf = (long long)(degree * Nf + 1) * (degree * Nf + 1) * (degree * Nf + 1);
+  FE_REQUIRE(6 * Nf * Nf * Nf < (1ll << 31) && nf < (1ll << 31), FE_ERR_ARG, "finest level too large for 32-bit indices");
+  FE_REQUIRE(fe_device_count() > 0, FE_ERR_CUDA, "no CUDA device");
+  std::unique_ptr<fe_hierarchy> h(new fe_hierarchy());
+  int dev = 0;
+  CUDA_CHECK(cudaGetDevice(&dev));
+  CUDA_CHECK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+  static std::once_flag mass_once;
+  std::call_once(mass_once, upload_mass_tables);
+  h->N0 = coarse->N;
+  h->nlev = nrefine + 1;
+  h->deg = degree;
+  h->L.resize(h->nlev);
+  cudaStream_t s = 0;
+  for (int l = 0; l < h->nlev; ++l) {
+    Level& L = h->L[l];
+    L.N = coarse->N << l;
+    L.deg = degree;
+    L.nd = degree == 1 ? 4 : 10;
+    L.num = make_numbering(L.N, degree);
+    const int m = degree * L.N;
+    L.n = (m + 1) * (m + 1) * (m + 1);
+    L.C = 6 * L.N * L.N * L.N;
+    L.V = (L.N + 1) * (L.N + 1) * (L.N + 1);
+    L.map.alloc((size_t)L.nd * L.C);
+    L.vx.alloc(L.V);
+    L.vy.alloc(L.V);
+    L.vz.alloc(L.V);
+    L.detj.alloc(L.C);
+    L.kappa.alloc(L.C);
+    L.geo64.alloc((size_t)6 * L.C);
+    L.geo32.alloc((size_t)6 * L.C);
+    L.dinv64.alloc(L.n);
+    L.dinv32.alloc(L.n);
+    for (auto* v : {&L.b64, &L.x64, &L.y64, &L.d64}) v->alloc(L.n);
+    for (auto* v : {&L.b32, &L.x32, &L.y32, &L.d32}) v->alloc(L.n);
+    std::vector<int> bnd;
+    bnd.reserve((size_t)6 * (m + 1) * (m + 1));
+    for (int z = 0; z <= m; ++z)
+      for (int y = 0; y <= m; ++y)
+        for (int x = 0; x <= m; ++x)
+          if (x == 0 || y == 0 || z == 0 || x == m || y == m || z == m) {
+            bnd.push_back(lattice_to_dof(L.num, x, y, z));
+            if (!(z == 0 || z == m || y == 0 || y == m) && x == 0) x = m - 1;  // skip the interior of the row
+          }
+    std::sort(bnd.begin(), bnd.end());
+    L.nb = (int)bnd.size();
+    L.bnd.alloc(L.nb);
+    CUDA_CHECK(cudaMemcpy(L.bnd, bnd.data(), sizeof(int) * L.nb, cudaMemcpyHostToDevice));
+    launch_build_level(L, s);
+  }
+  build_transfer_tables(h->tt, degree);
+  std::vector<int> ch = build_children();
+  h->children.alloc(48);
+  CUDA_CHECK(cudaMemcpy(h->children, ch.data(), sizeof(int) * 48, cudaMemcpyHostToDevice));
+  red_init(h->red, h->sms);
+  const int nF = h->L.back().n;
+  for (auto* v : {&h->x, &h->r, &h->z, &h->p, &h->q, &h->b, &h->e, &h->tmp}) v->alloc(nF);
+  for (auto* v : {&h->r32, &h->z32, &h->p32, &h->q32, &h->e32}) v->alloc(nF);
+  h->cs.flag.alloc(1);
+  set_coefficient_impl(h.get(), nullptr, s);
+  *out = h.release();
+  API_END
+}
+
+void fe_hierarchy_destroy(fe_hierarchy* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  invalidate_graphs(h);
+  for (auto& g : h->vgraph)
+    if (g.stream) cudaStreamDestroy(g.stream);
+  red_free(h->red);
+  delete h;
+}
+
+int fe_num_levels(const fe_hierarchy* h) {
+  if (!h) {
+    fe_set_error("null hierarchy");
+    return FE_ERR_ARG;
+  }
+  return h->nlev;
+}
+
+int fe_level_sizes(const fe_hierarchy* h, int level, int* N, long long* n_dofs, long long* n_cells) {
+  API_BEGIN
+  check_level(h, level);
+  const Level& L = h->L[level];
+  if (N) *N = L.N;
+  if (n_dofs) *n_dofs = L.n;
+  if (n_cells) *n_cells = L.C;
+  API_END
+}
+
+int fe_dof_coordinates(const fe_hierarchy* hc, int level, double* xyz) {
+  API_BEGIN
+  check_level(hc, level);
+  FE_REQUIRE(xyz, FE_ERR_ARG, "null output");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  const Level& L = h->L[level];
+  cudaStream_t s = 0;
+  double* d = stage_out<double>(h, 2, xyz, (size_t)3 * L.n);
+  launch_dof_coords(L, d, s);
+  finish_out(xyz, d, (size_t)3 * L.n, s);
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  API_END
+}
+
+int fe_cell_centroids(const fe_hierarchy* hc, int level, double* xyz) {
+  API_BEGIN
+  check_level(hc, level);
+  FE_REQUIRE(xyz, FE_ERR_ARG, "null output");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  const Level& L = h->L[level];
+  cudaStream_t s = 0;
+  double* d = stage_out<double>(h, 2, xyz, (size_t)3 * L.C);
+  launch_centroids(L, d, s);
+  finish_out(xyz, d, (size_t)3 * L.C, s);
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  API_END
+}
+
+int fe_boundary_mask(const fe_hierarchy* hc, int level, unsigned char* mask) {
+  API_BEGIN
+  check_level(hc, level);
+  FE_REQUIRE(mask, FE_ERR_ARG, "null output");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  const Level& L = h->L[level];
+  cudaStream_t s = 0;
+  unsigned char* d = stage_out<unsigned char>(h, 2, mask, (size_t)L.n);
+  launch_bmask(L, d, s);
+  finish_out(mask, d, (size_t)L.n, s);
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  API_END
+}
+
+int fe_set_coefficient(fe_hierarchy* h, const double* kappa, void* stream) {
+  API_BEGIN
+  FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
+  set_coefficient_impl(h, kappa, as_stream(stream));
+  API_END
+}
+
+int fe_apply_operator(const fe_hierarchy* hc, int level, const void* x, void* y, int dtype, void* stream) {
+  API_BEGIN
+  check_level(hc, level);
+  FE_REQUIRE(x && y && x != y, FE_ERR_ARG, "x and y must be distinct non-null vectors");
+  FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32 || dtype == FE_BF16, FE_ERR_ARG, "unknown dtype");
+  if (dtype == FE_BF16) FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  const Level& L = h->L[level];
+  cudaStream_t s = as_stream(stream);
+  if (dtype == FE_F64) {
+    const double* xd = stage_in<double>(h, 0, (const double*)x, L.n, s);
+    double* yd = stage_out<double>(h, 1, (double*)y, L.n);
+    apply_enqueue(h, level, xd, yd, dtype, s);
+    finish_out((double*)y, yd, L.n, s);
+  } else {
+    const float* xd = stage_in<float>(h, 0, (const float*)x, L.n, s);
+    float* yd = stage_out<float>(h, 1, (float*)y, L.n);
+    apply_enqueue(h, level, xd, yd, dtype, s);
+    finish_out((float*)y, yd, L.n, s);
+  }
+  API_END
+}
+
+int fe_apply_mass(const fe_hierarchy* hc, int level, const double* x, double* y, void* stream) {
+  API_BEGIN
+  check_level(hc, level);
+  FE_REQUIRE(x && y && x != y, FE_ERR_ARG, "x and y must be distinct non-null vectors");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  const Level& L = h->L[level];
+  cudaStream_t s = as_stream(stream);
+  const double* xd = stage_in<double>(h, 0, x, L.n, s);
+  double* yd = stage_out<double>(h, 1, y, L.n);
+  launch_mass(L, xd, yd, s);
+  finish_out(y, yd, L.n, s);
+  API_END
+}
+
+int fe_diagonal(const fe_hierarchy* hc, int level, double* diag, void* stream) {
+  API_BEGIN
+  check_level(hc, level);
+  FE_REQUIRE(diag, FE_ERR_ARG, "null output");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  Level& L = h->L[level];
+  cudaStream_t s = as_stream(stream);
+  double* d = stage_out<double>(h, 1, diag, L.n);
+  launch_diag(L, d, s);
+  finish_out(diag, d, L.n, s);
+  API_END
+}
+
+int fe_lambda_max(const fe_hierarchy* h, int level, double* lmax) {
+  API_BEGIN
+  check_level(h, level);
+  FE_REQUIRE(lmax, FE_ERR_ARG, "null output");
+  *lmax = h->L[level].lmax;
+  API_END
+}
+
+int fe_prolong(const fe_hierarchy* hc, int lf, const double* xc, double* xf, int accumulate, void* stream) {
+  API_BEGIN
+  check_level(hc, lf);
+  FE_REQUIRE(lf >= 1, FE_ERR_ARG, "level_fine must be >= 1");
+  FE_REQUIRE(xc && xf, FE_ERR_ARG, "null vector");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  cudaStream_t s = as_stream(stream);
+  const Level &F = h->L[lf], &C = h->L[lf - 1];
+  const double* xcd = stage_in<double>(h, 0, xc, C.n, s);
+  double* xfd = stage_out<double>(h, 1, xf, F.n);
+  if (accumulate && xfd != xf) CUDA_CHECK(cudaMemcpyAsync(xfd, xf, sizeof(double) * F.n, cudaMemcpyHostToDevice, s));
+  launch_prolong<double>(h, lf, xcd, xfd, accumulate != 0, s);
+  finish_out(xf, xfd, F.n, s);
+  API_END
+}
+
+int fe_restrict(const fe_hierarchy* hc, int lf, const double* rf, double* rc, int zero_boundary, void* stream) {
+  API_BEGIN
+  check_level(hc, lf);
+  FE_REQUIRE(lf >= 1, FE_ERR_ARG, "level_fine must be >= 1");
+  FE_REQUIRE(rf && rc, FE_ERR_ARG, "null vector");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  cudaStream_t s = as_stream(stream);
+  const Level &F = h->L[lf], &C = h->L[lf - 1];
+  const double* rfd = stage_in<double>(h, 0, rf, F.n, s);
+  double* rcd = stage_out<double>(h, 1, rc, C.n);
+  launch_restrict<double>(h, lf, rfd, nullptr, rcd, zero_boundary != 0, s);
+  finish_out(rc, rcd, C.n, s);
+  API_END
+}
+
+int fe_smooth(const fe_hierarchy* hc, int level, const void* b, void* x, int steps, double lo, double hi, int dtype,
+              void* stream) {
+  API_BEGIN
+  check_level(hc, level);
+  FE_REQUIRE(b && x && steps >= 1 && hi > lo && lo > 0, FE_ERR_ARG, "invalid smoother arguments");
+  FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32 || dtype == FE_BF16, FE_ERR_ARG, "unknown dtype");
+  if (dtype == FE_BF16) FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  Level& L = h->L[level];
+  cudaStream_t s = as_stream(stream);
+  if (dtype == FE_F64) {
+    const double* bd = stage_in<double>(h, 0, (const double*)b, L.n, s);
+    double* xd = stage_out<double>(h, 1, (double*)x, L.n);
+    if (xd != x) CUDA_CHECK(cudaMemcpyAsync(xd, x, sizeof(double) * L.n, cudaMemcpyHostToDevice, s));
+    smooth_enqueue<double>(h, level, bd, xd, h->tmp, h->e, steps, lo, hi, false, dtype, s);
+    finish_out((double*)x, xd, L.n, s);
+  } else {
+    const float* bd = stage_in<float>(h, 0, (const float*)b, L.n, s);
+    float* xd = stage_out<float>(h, 1, (float*)x, L.n);
+    if (xd != x) CUDA_CHECK(cudaMemcpyAsync(xd, x, sizeof(float) * L.n, cudaMemcpyHostToDevice, s));
+    smooth_enqueue<float>(h, level, bd, xd, h->q32, h->p32, steps, lo, hi, false, dtype, s);
+    finish_out((float*)x, xd, L.n, s);
+  }
+  API_END
+}
+
+int fe_coarse_solve(const fe_hierarchy* hc, const double* b, double* x, void* stream) {
+  API_BEGIN
+  FE_REQUIRE(hc && hc->nlev > 1, FE_ERR_ARG, "coarse solve needs a hierarchy with at least 2 levels");
+  FE_REQUIRE(b && x, FE_ERR_ARG, "null vector");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  cudaStream_t s = as_stream(stream);
+  const Level& L0 = h->L[0];
+  const double* bd = stage_in<double>(h, 0, b, L0.n, s);
+  double* xd = stage_out<double>(h, 1, x, L0.n);
+  coarse_solve<double>(h, bd, xd, s);
+  finish_out(x, xd, L0.n, s);
+  API_END
+}
+
+int fe_vcycle(const fe_hierarchy* hc, const void* b, void* x, int dtype, void* stream) {
+  API_BEGIN
+  FE_REQUIRE(hc && hc->nlev > 1, FE_ERR_ARG, "V-cycle needs a hierarchy with at least 2 levels");
+  FE_REQUIRE(b && x, FE_ERR_ARG, "null vector");
+  FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32 || dtype == FE_BF16, FE_ERR_ARG, "unknown dtype");
+  if (dtype == FE_BF16) FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  Level& F = h->L[h->nlev - 1];
+  cudaStream_t s = as_stream(stream);
+  g_sp = SmootherParams{};
+  const size_t es = dtype == FE_F64 ? sizeof(double) : sizeof(float);
+  void* fb = dtype == FE_F64 ? (void*)F.b64.p : (void*)F.b32.p;
+  void* fx = dtype == FE_F64 ? (void*)F.x64.p : (void*)F.x32.p;
+  CUDA_CHECK(cudaMemcpyAsync(fb, b, es * F.n, cudaMemcpyDefault, s));
+  run_vcycle(h, dtype, false, s);
+  CUDA_CHECK(cudaMemcpyAsync(x, fx, es * F.n, cudaMemcpyDefault, s));
+  if (!is_device_ptr(x)) CUDA_CHECK(cudaStreamSynchronize(s));
+  API_END
+}
+
+int fe_load_vector(const fe_hierarchy* hc, const double* f, double* b, void* stream) {
+  API_BEGIN
+  FE_REQUIRE(hc && f && b, FE_ERR_ARG, "null argument");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  cudaStream_t s = as_stream(stream);
+  const Level& F = h->L[h->nlev - 1];
+  const double* bd = rhs_to_load(h, f, FE_RHS_NODAL_F, s);
+  CUDA_CHECK(cudaMemcpyAsync(b, bd, sizeof(double) * F.n, cudaMemcpyDefault, s));
+  if (!is_device_ptr(b)) CUDA_CHECK(cudaStreamSynchronize(s));
+  API_END
+}
+
+int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_solver_opts* opts, double* u,
+                     fe_solve_stats* stats, void* stream) {
+  API_BEGIN
+  FE_REQUIRE(h && rhs && u, FE_ERR_ARG, "null argument");
+  const fe_solver_opts o = resolve_opts(opts);
+  FE_REQUIRE(o.precision == FE_PREC_F64 || o.precond == FE_PC_GMG, FE_ERR_ARG, "mixed precision needs the GMG preconditioner");
+  if (o.precision == FE_PREC_MIXED_BF16)
+    FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
+  FE_REQUIRE(o.precision == FE_PREC_F64 || h->nlev > 1, FE_ERR_ARG, "mixed precision needs at least 2 levels");
+  cudaStream_t s = as_stream(stream);
+  const Level& F = h->L[h->nlev - 1];
+  const auto t0 = std::chrono::steady_clock::now();
+  g_sp = SmootherParams{o.cheb_steps, o.cheb_lo, o.cheb_hi};
+  const double* b = rhs_to_load(h, rhs, rhs_kind, s);
+  double* ud = is_device_ptr(u) ? u : h->x.p;
+  fe_solve_stats st{};
+  st.outer_iterations = 1;
+  PcgResult res;
+  if (o.precision == FE_PREC_F64) {
+    res = pcg64(h, b, ud, o, s);
+    st.fine_applies_f64 = res.applies;
+  } else {
+    res = refine(h, b, ud, o, o.precision == FE_PREC_MIXED_F32 ? FE_F32 : FE_BF16, &st, s);
+    st.fine_applies_f64 = res.applies;
+  }
+  finish_out(u, ud, F.n, s);
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  st.iterations = res.it;
+  st.bnorm = std::sqrt(res.bb);
+  st.rel_residual = res.bb > 0 ? std::sqrt(res.rr / res.bb) : 0.0;
+  st.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  if (res.status == FE_ERR_NO_CONVERGENCE) FE_FAIL(FE_ERR_NO_CONVERGENCE, "iteration limit reached before rtol");
+  if (res.status == FE_ERR_NAN) FE_FAIL(FE_ERR_NAN, "residual norm is not finite");
+  API_END
+}
+
+int fe_adjoint_gradient(fe_hierarchy* h, const double* rhs, int rhs_kind, const double* u_d, const double* u_ckpt,
+                        const fe_solver_opts* opts, double* dJ, double* J, double* u_out, void* stream) {
+  API_BEGIN
+  FE_REQUIRE(h && rhs && u_d && dJ, FE_ERR_ARG, "null argument");
+  fe_solver_opts o = resolve_opts(opts);
+  o.precision = FE_PREC_F64;
+  cudaStream_t s = as_stream(stream);
+  Level& F = h->L[h->nlev - 1];
+  const int n = F.n;
+  g_sp = SmootherParams{o.cheb_steps, o.cheb_lo, o.cheb_hi};
+  double *u = h->e, *Me = h->tmp, *lam = h->z;
+  if (u_ckpt) {
+    const double* uc = stage_in<double>(h, 0, u_ckpt, n, s);
+    CUDA_CHECK(cudaMemcpyAsync(u, uc, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    const double* b = rhs_to_load(h, rhs, rhs_kind, s);
+    PcgResult r1 = pcg64(h, b, u, o, s);
+    if (r1.status != FE_OK) FE_FAIL(r1.status, "forward solve failed");
+  }
+  const double* ud = stage_in<double>(h, 1, u_d, n, s);
+  // Me = M (u - u_d); J = (u - u_d)^T M (u - u_d)
+  launch_sub64(n, u, ud, h->b, s);
+  launch_mass(F, h->b, Me, s);
+  launch_dot<double>(h->red, n, h->b, Me, S_DOT, s);
+  double Jh = 0.0;
+  CUDA_CHECK(cudaMemcpyAsync(&Jh, h->red.scal + S_DOT, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  // adjoint right-hand side -2 M (u - u_d), zero on the Dirichlet dofs
+  CUDA_CHECK(cudaMemsetAsync(h->b, 0, sizeof(double) * n, s));
+  launch_axpy64(n, -2.0, Me, h->b, s);
+  launch_zero_boundary64(F, h->b, s);
+  PcgResult r2 = pcg64(h, h->b, lam, o, s);
+  if (r2.status != FE_OK) FE_FAIL(r2.status, "adjoint solve failed");
+  double* g = stage_out<double>(h, 3, dJ, F.C);
+  launch_gradient(F, u, lam, g, s);
+  finish_out(dJ, g, F.C, s);
+  if (u_out) {
+    CUDA_CHECK(cudaMemcpyAsync(u_out, u, sizeof(double) * n, cudaMemcpyDefault, s));
+  }
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  if (J) *J = Jh;
+  API_END
+}
+
+int fe_objective(const fe_hierarchy* hc, const double* u, const double* u_d, double* J, void* stream) {
+  API_BEGIN
+  FE_REQUIRE(hc && u && u_d && J, FE_ERR_ARG, "null argument");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  cudaStream_t s = as_stream(stream);
+  const Level& F = h->L[h->nlev - 1];
+  const double* ud = stage_in<double>(h, 0, u, F.n, s);
+  const double* udd = stage_in<double>(h, 1, u_d, F.n, s);
+  launch_sub64(F.n, ud, udd, h->tmp, s);
+  launch_mass(F, h->tmp, h->q, s);
+  launch_dot<double>(h->red, F.n, h->tmp.p, h->q.p, S_DOT, s);
+  CUDA_CHECK(cudaMemcpyAsync(J, h->red.scal + S_DOT, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,390 @@
+// Internal declarations of the GB300 finite element library: error handling,
+// device buffers, the dof numbering, the per-level device data and the
+// element kernels' arithmetic.  Not part of the public ABI (see include/fe.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "fe.h"
+
+// ----------------------------------------------------------------- errors ---
+struct FeError {
+  int code;
+  std::string msg;
+};
+
+#define FE_FAIL(code_, msg_) throw FeError{(code_), std::string(msg_)}
+#define FE_REQUIRE(cond_, code_, msg_) \
+  do {                                 \
+    if (!(cond_)) FE_FAIL(code_, msg_); \
+  } while (0)
+#define CUDA_CHECK(x)                                                                               \
+  do {                                                                                              \
+    cudaError_t e_ = (x);                                                                           \
+    if (e_ != cudaSuccess) {                                                                        \
+      throw FeError{e_ == cudaErrorMemoryAllocation ? FE_ERR_NOMEM : FE_ERR_CUDA,                   \
+                    std::string(#x) + " failed: " + cudaGetErrorString(e_) + " (" + __FILE__ + ":" + \
+                        std::to_string(__LINE__) + ")"};                                            \
+    }                                                                                               \
+  } while (0)
+#define LAUNCH_CHECK() CUDA_CHECK(cudaGetLastError())
+
+void fe_set_error(const std::string& msg);
+
+// ------------------------------------------------------- device buffers ---
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(size_t count) {
+    if (count == n && p) return;
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw FeError{FE_ERR_NOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                      " bytes failed: " + cudaGetErrorString(e)};
+    }
+    n = count;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  operator T*() const { return p; }
+};
+
+// ------------------------------------------------------------ numbering ---
+// Global dof numbering of the (deg*N)-lattice, see include/fe.h.  P1: one
+// class, lexicographic.  P2: 8 parity classes in the order
+// (000),(100),(010),(001),(110),(101),(011),(111).
+struct Numbering {
+  int N, deg, m;  // cubes per axis, degree, lattice extent m = deg*N
+  int off[9];     // first dof of each class, off[8] = n (P1: off[1] = n)
+  int sx[8], sy[8], sz[8];
+};
+
+Numbering make_numbering(int N, int deg);
+
+__host__ __device__ inline int class_parity_x(int c) { return (c == 1 || c == 4 || c == 5 || c == 7) ? 1 : 0; }
+__host__ __device__ inline int class_parity_y(int c) { return (c == 2 || c == 4 || c == 6 || c == 7) ? 1 : 0; }
+__host__ __device__ inline int class_parity_z(int c) { return (c == 3 || c == 5 || c == 6 || c == 7) ? 1 : 0; }
+
+__host__ __device__ inline int lattice_to_dof(const Numbering& nb, int x, int y, int z) {
+  if (nb.deg == 1) return x + (nb.N + 1) * (y + (nb.N + 1) * z);
+  const int code = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+  // code (px + 2py + 4pz) -> class index in the order above
+  const int c = (code == 3) ? 4 : (code == 4) ? 3 : code;
+  return nb.off[c] + (x >> 1) + nb.sx[c] * ((y >> 1) + nb.sy[c] * (z >> 1));
+}
+
+__host__ __device__ inline void dof_to_lattice(const Numbering& nb, int i, int& x, int& y, int& z) {
+  if (nb.deg == 1) {
+    const int n1 = nb.N + 1;
+    x = i % n1;
+    const int r = i / n1;
+    y = r % n1;
+    z = r / n1;
+    return;
+  }
+  int c = 0;
+#pragma unroll
+  for (int k = 1; k < 8; ++k)
+    if (i >= nb.off[k]) c = k;
+  int r = i - nb.off[c];
+  const int ax = r % nb.sx[c];
+  r /= nb.sx[c];
+  const int ay = r % nb.sy[c];
+  const int az = r / nb.sy[c];
+  x = 2 * ax + class_parity_x(c);
+  y = 2 * ay + class_parity_y(c);
+  z = 2 * az + class_parity_z(c);
+}
+
+// Kuhn simplex t of a cube: corners origin, +e[p0], +e[p0]+e[p1], +(1,1,1).
+__host__ __device__ inline void kuhn_perm(int t, int& p0, int& p1, int& p2) {
+  // (0,1,2),(0,2,1),(1,0,2),(1,2,0),(2,0,1),(2,1,0)
+  p0 = t >> 1;
+  const int lo = (p0 == 0) ? 1 : 0;
+  const int hi = (p0 == 2) ? 1 : 2;
+  p1 = (t & 1) ? hi : lo;
+  p2 = 3 - p0 - p1;
+}
+
+// ---------------------------------------------------------- level data ---
+struct Level {
+  int N = 0, deg = 0, nd = 0;
+  int n = 0, C = 0, V = 0, nb = 0;
+  Numbering num{};
+  DBuf<int> map;          // [nd][C]: dof j >= 0, or -1-j for a Dirichlet dof
+  DBuf<double> vx, vy, vz;  // vertex coordinates
+  DBuf<double> detj;      // |det J| per cell
+  DBuf<double> kappa;     // cell coefficient
+  DBuf<double> geo64;     // [6][C] kappa*|detJ| J^-1 J^-T / w  (w = 6 for P1, 120 for P2)
+  DBuf<float> geo32;
+  DBuf<double> dinv64;    // 1/diag(A)
+  DBuf<float> dinv32;
+  DBuf<int> bnd;          // Dirichlet dofs
+  double lmax = 2.0;
+  // V-cycle work vectors (level-owned so the cycle can be captured in a graph)
+  DBuf<double> b64, x64, y64, d64;
+  DBuf<float> b32, x32, y32, d32;
+};
+
+// Host-built transfer stencils (exact dyadic weights).
+struct TransferTables {
+  int deg = 0;
+  int n_pro_class = 0, n_res_class = 0;
+  DBuf<int> pro_start, res_start;  // class -> first entry, size n_class+1
+  DBuf<int4> pro_off, res_off;     // (dx,dy,dz,-) lattice offsets
+  DBuf<double> pro_w, res_w;
+  std::vector<int> h_pro_start, h_res_start;
+  std::vector<int4> h_pro_off, h_res_off;
+  std::vector<double> h_pro_w, h_res_w;
+};
+
+// Scalars of the device-side CG recurrences.
+enum ScalarSlot {
+  S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_RZNEW, S_DOT, S_BB, S_TMP0, S_TMP1, S_COUNT
+};
+
+struct ReduceCtx {
+  int grid = 0;                 // fixed number of blocks of every reduction (deterministic order)
+  DBuf<double> partials;        // grid * 2
+  DBuf<unsigned int> counter;   // last-block ticket
+  DBuf<double> scal;            // S_COUNT scalars
+  double* h_scal = nullptr;     // pinned mirror
+};
+
+struct CoarseSolver {
+  int nci = 0, band = 0;
+  DBuf<int> ci;        // interior unknown j -> coarse dof
+  DBuf<int> dof2int;   // coarse dof -> interior index or -1
+  DBuf<double> A;      // nci*nci dense, then L (lower)
+  DBuf<double> Linv, LinvT;
+  DBuf<double> t0, t1;  // nci
+  DBuf<int> flag;
+};
+
+struct fe_mesh {
+  int N;
+};
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+  int steps = 0;  // smoother parameters baked into the captured launches
+  double lo = 0, hi = 0;
+};
+
+struct fe_hierarchy {
+  int N0 = 0, nlev = 0, deg = 0;
+  int sms = 148;
+  std::vector<Level> L;
+  TransferTables tt;
+  CoarseSolver cs;
+  ReduceCtx red;
+  DBuf<int> children;  // [6][8] coarse Kuhn type -> (subcube code * 8 + fine type)
+  // fine-level Krylov vectors
+  DBuf<double> x, r, z, p, q, b, e, tmp;
+  DBuf<float> r32, z32, p32, q32, e32;
+  // staging for host pointers
+  DBuf<unsigned char> stage[4];
+  GraphCache vgraph[3];  // per dtype
+  bool lmax_valid = false;
+};
+
+// ------------------------------------------------------- launch wrappers ---
+// Operator kernels (fe_kernels.cu)
+void launch_build_level(Level& L, cudaStream_t s);
+void launch_geometry(Level& L, cudaStream_t s);
+void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s);
+void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s);
+void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);
+void launch_diag(Level& L, double* diag_out, cudaStream_t s);
+void launch_gradient(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s);
+void launch_dof_coords(const Level& L, double* xyz, cudaStream_t s);
+void launch_centroids(const Level& L, double* xyz, cudaStream_t s);
+void launch_bmask(const Level& L, unsigned char* m, cudaStream_t s);
+void launch_coarsen_kappa(const Level& Lc, const Level& Lf, const int* children, cudaStream_t s);
+int launch_check_positive(const double* v, int n, int* dflag, cudaStream_t s);
+// Transfers
+template <typename T>
+void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s);
+template <typename T>
+void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, bool zero_bd, cudaStream_t s);
+// Vector kernels
+template <typename T>
+void launch_cheb_step(int n, const T* b, const T* y, const T* dinv, T* x, T* d, double c1, double c2, bool first_from_zero,
+                      cudaStream_t s);
+template <typename Ti, typename To>
+void launch_convert(int n, const Ti* in, To* out, cudaStream_t s);
+void launch_set_boundary(const Level& L, const double* src, double* dst, cudaStream_t s);
+void launch_zero_boundary64(const Level& L, double* v, cudaStream_t s);
+void launch_random(int n, uint64_t seed, double* v, cudaStream_t s);
+// Reductions and CG updates (fe_blas.cu)
+void red_init(ReduceCtx& R, int sms);
+void red_free(ReduceCtx& R);
+template <typename T>
+void launch_dot(ReduceCtx& R, int n, const T* a, const T* b, int slot, cudaStream_t s);
+// q-dot: pq = p.q; alpha = rz/pq
+template <typename T>
+void launch_cg_alpha(ReduceCtx& R, int n, const T* p, const T* q, cudaStream_t s);
+// x += alpha p; r -= alpha q; rr = r.r; (jacobi: z = dinv r, rznew = r.z, beta = rznew/rz, rz = rznew)
+template <typename T>
+void launch_cg_update(ReduceCtx& R, int n, T* x, T* r, const T* p, const T* q, const T* dinv, T* z, cudaStream_t s);
+// rznew = r.z; beta = rznew/rz; rz = rznew
+template <typename T>
+void launch_cg_beta(ReduceCtx& R, int n, const T* r, const T* z, cudaStream_t s);
+template <typename T>
+void launch_cg_update_p(ReduceCtx& R, int n, T* p, const T* z, cudaStream_t s);
+void launch_axpy64(int n, double a, const double* x, double* y, cudaStream_t s);
+void launch_sub64(int n, const double* a, const double* b, double* out, cudaStream_t s);  // out = a - b
+template <typename T>
+void launch_scale_copy(int n, const double* in, const double* scale_slot, bool inverse, T* out, cudaStream_t s);
+template <typename T>
+void launch_add_scaled(int n, const T* e, const double* scale_slot, double* x, cudaStream_t s);
+// Coarse solver (fe_coarse.cu)
+void coarse_setup(fe_hierarchy* h, cudaStream_t s);
+template <typename T>
+void coarse_solve(const fe_hierarchy* h, const T* b, T* x, cudaStream_t s);
+
+// Orchestration helpers (fe_api.cu)
+template <typename T>
+void vcycle_enqueue(fe_hierarchy* h, int dtype, cudaStream_t s);  // reads L.b of the finest level, writes L.x
+void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s);
+void apply_bf16_enqueue(const Level& L, const float* x, float* y, cudaStream_t s);
+bool bf16_supported();
+
+// ------------------------------------------------------- element kernels ---
+// Geometry of one tet from its vertex coordinates: G = |det J| J^-1 J^-T
+// (symmetric, stored G00,G01,G02,G11,G12,G22) and |det J|.  With J = [a b c]
+// (columns p1-p0, p2-p0, p3-p0) the rows of det(J) J^-1 are b x c, c x a,
+// a x b, hence G_ij = r_i . r_j / |det J|.
+template <typename T>
+__host__ __device__ inline void tet_metric(const T p[4][3], T g[6], T& adet) {
+  T a[3], b[3], c[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    a[k] = p[1][k] - p[0][k];
+    b[k] = p[2][k] - p[0][k];
+    c[k] = p[3][k] - p[0][k];
+  }
+  T r0[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+  T r1[3] = {c[1] * a[2] - c[2] * a[1], c[2] * a[0] - c[0] * a[2], c[0] * a[1] - c[1] * a[0]};
+  T r2[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+  const T det = a[0] * r0[0] + a[1] * r0[1] + a[2] * r0[2];
+  adet = det < T(0) ? -det : det;
+  const T inv = T(1) / adet;
+  g[0] = (r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]) * inv;
+  g[1] = (r0[0] * r1[0] + r0[1] * r1[1] + r0[2] * r1[2]) * inv;
+  g[2] = (r0[0] * r2[0] + r0[1] * r2[1] + r0[2] * r2[2]) * inv;
+  g[3] = (r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]) * inv;
+  g[4] = (r1[0] * r2[0] + r1[1] * r2[1] + r1[2] * r2[2]) * inv;
+  g[5] = (r2[0] * r2[0] + r2[1] * r2[1] + r2[2] * r2[2]) * inv;
+}
+
+// P1 tet: grad u is constant; with reference gradient d = (u1-u0, u2-u0, u3-u0)
+// the element form is a(u,v) = (1/6) d^T G d', so y_{1..3} = G d / 6 and
+// y_0 = -(y_1 + y_2 + y_3).  `g` holds kappa * G / 6.
+template <typename T>
+__host__ __device__ inline void p1_element(const T u[4], const T g[6], T y[4]) {
+  const T d0 = u[1] - u[0], d1 = u[2] - u[0], d2 = u[3] - u[0];
+  const T h0 = g[0] * d0 + g[1] * d1 + g[2] * d2;
+  const T h1 = g[1] * d0 + g[3] * d1 + g[4] * d2;
+  const T h2 = g[2] * d0 + g[4] * d1 + g[5] * d2;
+  y[1] = h0;
+  y[2] = h1;
+  y[3] = h2;
+  y[0] = -(h0 + h1 + h2);
+}
+
+// Local P2 edge numbering: edge (w,v) of the tet -> local dof 4..9 for the
+// pairs (0,1),(0,2),(0,3),(1,2),(1,3),(2,3).
+__host__ __device__ constexpr int p2_edge(int w, int v) {
+  return (w > v) ? p2_edge(v, w) : (w == 0 ? 3 + v : (w == 1 ? 5 + v : 9));
+}
+
+// P2 tet.  grad u is affine, so it is fixed by its values at the 4 vertices:
+// in barycentric gradients, grad u(w) = sum_v c_wv grad(lambda_v) with
+// c_ww = 3 u_w and c_wv = 4 u_(wv) - u_v.  In reference coordinates
+// d_w = grad_ref u(w) = (c_w1 - c_w0, c_w2 - c_w0, c_w3 - c_w0).  With
+// int_ref lambda_w lambda_w' = (1 + delta_ww')/120 the element form is
+//   a(u,v) = (1/120) [ S^T G S' + sum_w d_w^T G d'_w ],  S = sum_w d_w,
+// so y = (d/du)^T h with h_w = G (S + d_w) / 120.  `g` holds kappa G / 120.
+// ~125 flops per tet instead of the 10x10 element matrix.
+template <typename T>
+__host__ __device__ inline void p2_element(const T u[10], const T g[6], T y[10]) {
+  T c[4][4];
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (v == w)
+        c[w][v] = T(3) * u[w];
+      else
+        c[w][v] = T(4) * u[p2_edge(w, v)] - u[v];
+    }
+  }
+  T d[4][3];
+  T S[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      d[w][a] = c[w][a + 1] - c[w][0];
+      S[a] += d[w][a];
+    }
+  }
+  T cb[4][4];
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const T t0 = S[0] + d[w][0], t1 = S[1] + d[w][1], t2 = S[2] + d[w][2];
+    const T h0 = g[0] * t0 + g[1] * t1 + g[2] * t2;
+    const T h1 = g[1] * t0 + g[3] * t1 + g[4] * t2;
+    const T h2 = g[2] * t0 + g[4] * t1 + g[5] * t2;
+    cb[w][1] = h0;
+    cb[w][2] = h1;
+    cb[w][3] = h2;
+    cb[w][0] = -(h0 + h1 + h2);
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    T s = T(3) * cb[v][v];
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+      if (w != v) s -= cb[w][v];
+    y[v] = s;
+  }
+#pragma unroll
+  for (int w = 0; w < 4; ++w)
+#pragma unroll
+    for (int v = w + 1; v < 4; ++v) y[p2_edge(w, v)] = T(4) * (cb[w][v] + cb[v][w]);
+}
+
+template <int DEG, typename T>
+__host__ __device__ inline void element_apply(const T* u, const T* g, T* y) {
+  if constexpr (DEG == 1)
+    p1_element<T>(u, g, y);
+  else
+    p2_element<T>(u, g, y);
+}
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

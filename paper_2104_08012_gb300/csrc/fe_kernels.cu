@@ -1,0 +1,613 @@
+// Cell-loop kernels of the matrix-free operator (paper Section 2, Eq. 4),
+// mass, diagonal, adjoint cell gradient, mesh construction, and the
+// multigrid transfer and smoother vector kernels (paper Section 3).
+#include "fe_internal.cuh"
+
+// Reference P1/P2 mass matrices int_ref phi_i phi_j, filled by fe_api.cu.
+__constant__ double c_mref1[16];
+__constant__ double c_mref2[100];
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ int decode(int m, bool& bd) {
+  bd = m < 0;
+  return bd ? -1 - m : m;
+}
+
+// ------------------------------------------------------ mesh construction
+template <int DEG>
+__global__ void k_build_map(Numbering num, int C, int* __restrict__ map) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int N = num.N;
+  const int q = c / 6, t = c - 6 * (c / 6);
+  const int ci = q % N, cj = (q / N) % N, ck = q / (N * N);
+  int p0, p1, p2;
+  kuhn_perm(t, p0, p1, p2);
+  int v[4][3];
+  v[0][0] = ci; v[0][1] = cj; v[0][2] = ck;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v[1][a] = v[0][a] + (a == p0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v[2][a] = v[1][a] + (a == p1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v[3][a] = v[0][a] + 1;
+  const int m = num.m;
+  auto put = [&](int j, int x, int y, int z) {
+    const int dof = lattice_to_dof(num, x, y, z);
+    const bool bd = x == 0 || y == 0 || z == 0 || x == m || y == m || z == m;
+    map[(size_t)j * C + c] = bd ? -1 - dof : dof;
+  };
+  if (DEG == 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) put(k, v[k][0], v[k][1], v[k][2]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) put(k, 2 * v[k][0], 2 * v[k][1], 2 * v[k][2]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a + 1; b < 4; ++b)
+        put(p2_edge(a, b), v[a][0] + v[b][0], v[a][1] + v[b][1], v[a][2] + v[b][2]);
+  }
+}
+
+__global__ void k_build_coords(int N, int V, double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const int n1 = N + 1;
+  const double h = 1.0 / N;
+  vx[v] = (v % n1) * h;
+  vy[v] = ((v / n1) % n1) * h;
+  vz[v] = (v / (n1 * n1)) * h;
+}
+
+// ----------------------------------------------------------- geometry
+template <int DEG>
+__global__ void k_geometry(int C, const int* __restrict__ map, const double* __restrict__ vx,
+                           const double* __restrict__ vy, const double* __restrict__ vz,
+                           const double* __restrict__ kappa, double* __restrict__ geo64, float* __restrict__ geo32,
+                           double* __restrict__ detj) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double p[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    bool bd;
+    const int v = decode(map[(size_t)k * C + c], bd);  // vertex dofs are numbered first
+    p[k][0] = vx[v];
+    p[k][1] = vy[v];
+    p[k][2] = vz[v];
+  }
+  double g[6], adet;
+  tet_metric<double>(p, g, adet);
+  const double s = kappa[c] / (DEG == 1 ? 6.0 : 120.0);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    geo64[(size_t)a * C + c] = g[a] * s;
+    geo32[(size_t)a * C + c] = (float)(g[a] * s);
+  }
+  detj[c] = adet;
+}
+
+// ------------------------------------------------------ operator apply
+// One thread per tet: gather the cell dofs through the cell->dof map
+// (coalesced: the map is stored [dof][cell]), contract with the cell's
+// geometric factors, scatter-add with atomics.  Extra threads past the last
+// cell copy x -> y on the Dirichlet dofs (identity rows).
+template <int DEG, typename T>
+__global__ void __launch_bounds__(kBlock) k_apply(int C, int Cpad, const int* __restrict__ map,
+                                                  const T* __restrict__ geo, const T* __restrict__ x,
+                                                  T* __restrict__ y, int nb, const int* __restrict__ bnd) {
+  constexpr int ND = DEG == 1 ? 4 : 10;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < C) {
+    int idx[ND];
+    T u[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      idx[j] = __ldg(map + (size_t)j * C + t);
+      u[j] = idx[j] >= 0 ? __ldg(x + idx[j]) : T(0);
+    }
+    T g[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) g[a] = __ldg(geo + (size_t)a * C + t);
+    T out[ND];
+    element_apply<DEG, T>(u, g, out);
+#pragma unroll
+    for (int j = 0; j < ND; ++j)
+      if (idx[j] >= 0) atomicAdd(y + idx[j], out[j]);
+  } else if (t >= Cpad && t - Cpad < nb) {
+    const int i = bnd[t - Cpad];
+    y[i] = x[i];
+  }
+}
+
+// ------------------------------------------------------------ mass
+template <int DEG>
+__global__ void k_mass(int C, const int* __restrict__ map, const double* __restrict__ detj,
+                       const double* __restrict__ x, double* __restrict__ y) {
+  constexpr int ND = DEG == 1 ? 4 : 10;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  int idx[ND];
+  double u[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    bool bd;
+    idx[j] = decode(map[(size_t)j * C + c], bd);
+    u[j] = x[idx[j]];
+  }
+  const double s = detj[c];
+  const double* M = DEG == 1 ? c_mref1 : c_mref2;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) acc += M[i * ND + j] * u[j];
+    atomicAdd(y + idx[i], s * acc);
+  }
+}
+
+// ------------------------------------------------------------ diagonal
+template <int DEG>
+__global__ void k_diag(int C, const int* __restrict__ map, const double* __restrict__ geo, double* __restrict__ diag) {
+  constexpr int ND = DEG == 1 ? 4 : 10;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double g[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) g[a] = geo[(size_t)a * C + c];
+  for (int i = 0; i < ND; ++i) {
+    const int m = map[(size_t)i * C + c];
+    if (m < 0) continue;
+    double u[ND], out[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) u[j] = (j == i) ? 1.0 : 0.0;
+    element_apply<DEG, double>(u, g, out);
+    atomicAdd(diag + m, out[i]);
+  }
+}
+
+__global__ void k_diag_finish(int n, int nb, const int* __restrict__ bnd, double* __restrict__ diag) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nb) diag[bnd[t]] = 1.0;
+}
+
+__global__ void k_invert(int n, const double* __restrict__ diag, double* __restrict__ d64, float* __restrict__ d32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = 1.0 / diag[i];
+  d64[i] = v;
+  d32[i] = (float)v;
+}
+
+// ---------------------------------------------------- adjoint gradient
+// g_K = int_K grad(lambda) . grad(u) = lambda_K^T A_K(kappa=1) u_K, with the
+// Dirichlet dofs of u and lambda taken as 0.
+template <int DEG>
+__global__ void k_gradient(int C, const int* __restrict__ map, const double* __restrict__ vx,
+                           const double* __restrict__ vy, const double* __restrict__ vz, const double* __restrict__ u,
+                           const double* __restrict__ lam, double* __restrict__ g) {
+  constexpr int ND = DEG == 1 ? 4 : 10;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double uu[ND], ll[ND];
+  double p[4][3];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    bool bd;
+    const int i = decode(map[(size_t)j * C + c], bd);
+    uu[j] = bd ? 0.0 : u[i];
+    ll[j] = bd ? 0.0 : lam[i];
+    if (j < 4) {
+      p[j][0] = vx[i];
+      p[j][1] = vy[i];
+      p[j][2] = vz[i];
+    }
+  }
+  double G[6], adet;
+  tet_metric<double>(p, G, adet);
+  const double s = 1.0 / (DEG == 1 ? 6.0 : 120.0);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) G[a] *= s;
+  double out[ND];
+  element_apply<DEG, double>(uu, G, out);
+  double acc = 0.0;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) acc += ll[j] * out[j];
+  g[c] = acc;
+}
+
+// ------------------------------------------------------ mesh queries
+__global__ void k_dof_coords(Numbering num, int n, double* __restrict__ xyz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x, y, z;
+  dof_to_lattice(num, i, x, y, z);
+  const double h = 1.0 / num.m;
+  xyz[3 * (size_t)i + 0] = x * h;
+  xyz[3 * (size_t)i + 1] = y * h;
+  xyz[3 * (size_t)i + 2] = z * h;
+}
+
+__global__ void k_centroids(int C, const int* __restrict__ map, const double* __restrict__ vx,
+                            const double* __restrict__ vy, const double* __restrict__ vz, double* __restrict__ xyz) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double s[3] = {0, 0, 0};
+  for (int k = 0; k < 4; ++k) {
+    bool bd;
+    const int v = decode(map[(size_t)k * C + c], bd);
+    s[0] += vx[v];
+    s[1] += vy[v];
+    s[2] += vz[v];
+  }
+  for (int a = 0; a < 3; ++a) xyz[3 * (size_t)c + a] = 0.25 * s[a];
+}
+
+__global__ void k_bmask(Numbering num, int n, unsigned char* __restrict__ m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x, y, z;
+  dof_to_lattice(num, i, x, y, z);
+  m[i] = (x == 0 || y == 0 || z == 0 || x == num.m || y == num.m || z == num.m) ? 1 : 0;
+}
+
+// coarse kappa = mean of the 8 child cells (fixed summation order)
+__global__ void k_coarsen_kappa(int Nc, int Cc, const int* __restrict__ children, const double* __restrict__ kf,
+                                double* __restrict__ kc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Cc) return;
+  const int q = c / 6, T = c - 6 * q;
+  const int ci = q % Nc, cj = (q / Nc) % Nc, ck = q / (Nc * Nc);
+  const int Nf = 2 * Nc;
+  double s = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    const int e = children[T * 8 + k];
+    const int code = e >> 3, tf = e & 7;
+    const int fi = 2 * ci + (code & 1), fj = 2 * cj + ((code >> 1) & 1), fk = 2 * ck + ((code >> 2) & 1);
+    s += kf[6 * (fi + Nf * (fj + Nf * fk)) + tf];
+  }
+  kc[c] = 0.125 * s;
+}
+
+__global__ void k_check_positive(const double* __restrict__ v, int n, int* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = v[i];
+  if (!(a > 0.0) || !isfinite(a)) atomicOr(flag, 1);
+}
+
+// ----------------------------------------------------------- transfers
+// Prolongation: fine lattice point L splits as L = 2k*c + o (c the coarse cube,
+// o in [0,2k)^3); the class o selects a stencil of (coarse lattice offset from
+// k*c, weight) pairs built on the host by evaluating the coarse basis.
+template <int DEG, typename T>
+__global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __restrict__ start,
+                          const int4* __restrict__ off, const double* __restrict__ w, const T* __restrict__ xc,
+                          T* __restrict__ xf, int accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_f) return;
+  int x, y, z;
+  dof_to_lattice(nf, i, x, y, z);
+  constexpr int K2 = 2 * DEG;
+  const int cx = x / K2, cy = y / K2, cz = z / K2;
+  const int cls = (x - K2 * cx) + K2 * ((y - K2 * cy) + K2 * (z - K2 * cz));
+  T s = T(0);
+  const int e1 = __ldg(start + cls + 1);
+  for (int e = __ldg(start + cls); e < e1; ++e) {
+    const int4 o = __ldg(off + e);
+    const int j = lattice_to_dof(nc, DEG * cx + o.x, DEG * cy + o.y, DEG * cz + o.z);
+    s += (T)__ldg(w + e) * __ldg(xc + j);
+  }
+  xf[i] = accumulate ? xf[i] + s : s;
+}
+
+// Restriction = exact transpose: coarse point Lc gathers fine points
+// 2 Lc + f_off for the stencil entries of its parity class.  With yf != null
+// the restricted vector is the residual bf - yf.
+template <int DEG, typename T>
+__global__ void k_restrict(Numbering nf, Numbering nc, int n_c, const int* __restrict__ start,
+                           const int4* __restrict__ off, const double* __restrict__ w, const T* __restrict__ bf,
+                           const T* __restrict__ yf, T* __restrict__ rc, int zero_bd) {
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= n_c) return;
+  int X, Y, Z;
+  dof_to_lattice(nc, J, X, Y, Z);
+  const bool bd = X == 0 || Y == 0 || Z == 0 || X == nc.m || Y == nc.m || Z == nc.m;
+  if (bd && zero_bd) {
+    rc[J] = T(0);
+    return;
+  }
+  const int cls = DEG == 2 ? ((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2)) : 0;
+  T s = T(0);
+  const int e1 = __ldg(start + cls + 1);
+  const int mf = nf.m;
+  for (int e = __ldg(start + cls); e < e1; ++e) {
+    const int4 o = __ldg(off + e);
+    const int fx = 2 * X + o.x, fy = 2 * Y + o.y, fz = 2 * Z + o.z;
+    if (fx < 0 || fy < 0 || fz < 0 || fx > mf || fy > mf || fz > mf) continue;
+    const int i = lattice_to_dof(nf, fx, fy, fz);
+    T v = __ldg(bf + i);
+    if (yf) v -= __ldg(yf + i);
+    s += (T)__ldg(w + e) * v;
+  }
+  rc[J] = s;
+}
+
+// --------------------------------------------------------- vector ops
+// Chebyshev step: d = c1 d + c2 D^-1 (b - y); x += d  (y = A x).  With
+// first_from_zero (x = 0, y unused): d = c2 D^-1 b; x = d.
+template <typename T>
+__global__ void k_cheb_step(int n, const T* __restrict__ b, const T* __restrict__ y, const T* __restrict__ dinv,
+                            T* __restrict__ x, T* __restrict__ d, T c1, T c2, int first_from_zero) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (first_from_zero) {
+    const T dn = c2 * dinv[i] * b[i];
+    d[i] = dn;
+    x[i] = dn;
+  } else {
+    const T r = b[i] - y[i];
+    const T dn = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * dinv[i] * r;
+    d[i] = dn;
+    x[i] += dn;
+  }
+}
+
+template <typename Ti, typename To>
+__global__ void k_convert(int n, const Ti* __restrict__ in, To* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (To)in[i];
+}
+
+__global__ void k_set_boundary(int nb, const int* __restrict__ bnd, const double* __restrict__ src,
+                               double* __restrict__ dst) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nb) dst[bnd[t]] = src ? src[bnd[t]] : 0.0;
+}
+
+__global__ void k_random(int n, uint64_t seed, double* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // splitmix64 of (seed, i) -> uniform(-1, 1)
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  v[i] = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+}  // namespace
+
+// ===================================================================== host
+void launch_build_level(Level& L, cudaStream_t s) {
+  if (L.deg == 1)
+    k_build_map<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.map);
+  else
+    k_build_map<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.map);
+  LAUNCH_CHECK();
+  k_build_coords<<<ceil_div(L.V, kBlock), kBlock, 0, s>>>(L.N, L.V, L.vx, L.vy, L.vz);
+  LAUNCH_CHECK();
+}
+
+void launch_geometry(Level& L, cudaStream_t s) {
+  if (L.deg == 1)
+    k_geometry<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64, L.geo32,
+                                                          L.detj);
+  else
+    k_geometry<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64, L.geo32,
+                                                          L.detj);
+  LAUNCH_CHECK();
+}
+
+template <typename T>
+static void apply_impl(const Level& L, const T* geo, const T* x, T* y, cudaStream_t s) {
+  CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)L.n, s));
+  const int Cpad = ceil_div(L.C, kBlock) * kBlock;
+  const int grid = ceil_div((long long)Cpad + L.nb, kBlock);
+  if (L.deg == 1)
+    k_apply<1, T><<<grid, kBlock, 0, s>>>(L.C, Cpad, L.map, geo, x, y, L.nb, L.bnd);
+  else
+    k_apply<2, T><<<grid, kBlock, 0, s>>>(L.C, Cpad, L.map, geo, x, y, L.nb, L.bnd);
+  LAUNCH_CHECK();
+}
+
+void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s) { apply_impl<double>(L, L.geo64, x, y, s); }
+void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) { apply_impl<float>(L, L.geo32, x, y, s); }
+
+void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s) {
+  CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
+  if (L.deg == 1)
+    k_mass<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.detj, x, y);
+  else
+    k_mass<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.detj, x, y);
+  LAUNCH_CHECK();
+}
+
+void launch_diag(Level& L, double* diag, cudaStream_t s) {
+  CUDA_CHECK(cudaMemsetAsync(diag, 0, sizeof(double) * (size_t)L.n, s));
+  if (L.deg == 1)
+    k_diag<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.geo64, diag);
+  else
+    k_diag<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.geo64, diag);
+  LAUNCH_CHECK();
+  if (L.nb > 0) {
+    k_diag_finish<<<ceil_div(L.nb, kBlock), kBlock, 0, s>>>(L.n, L.nb, L.bnd, diag);
+    LAUNCH_CHECK();
+  }
+  k_invert<<<ceil_div(L.n, kBlock), kBlock, 0, s>>>(L.n, diag, L.dinv64, L.dinv32);
+  LAUNCH_CHECK();
+}
+
+void launch_gradient(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s) {
+  if (L.deg == 1)
+    k_gradient<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, u, lam, g);
+  else
+    k_gradient<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, u, lam, g);
+  LAUNCH_CHECK();
+}
+
+void launch_dof_coords(const Level& L, double* xyz, cudaStream_t s) {
+  k_dof_coords<<<ceil_div(L.n, kBlock), kBlock, 0, s>>>(L.num, L.n, xyz);
+  LAUNCH_CHECK();
+}
+
+void launch_centroids(const Level& L, double* xyz, cudaStream_t s) {
+  k_centroids<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, xyz);
+  LAUNCH_CHECK();
+}
+
+void launch_bmask(const Level& L, unsigned char* m, cudaStream_t s) {
+  k_bmask<<<ceil_div(L.n, kBlock), kBlock, 0, s>>>(L.num, L.n, m);
+  LAUNCH_CHECK();
+}
+
+void launch_coarsen_kappa(const Level& Lc, const Level& Lf, const int* children, cudaStream_t s) {
+  k_coarsen_kappa<<<ceil_div(Lc.C, kBlock), kBlock, 0, s>>>(Lc.N, Lc.C, children, Lf.kappa, Lc.kappa);
+  LAUNCH_CHECK();
+}
+
+int launch_check_positive(const double* v, int n, int* dflag, cudaStream_t s) {
+  CUDA_CHECK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+  k_check_positive<<<ceil_div(n, kBlock), kBlock, 0, s>>>(v, n, dflag);
+  LAUNCH_CHECK();
+  int hflag = 0;
+  CUDA_CHECK(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  return hflag;
+}
+
+template <typename T>
+void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s) {
+  const Level& F = h->L[lf];
+  const Level& Cc = h->L[lf - 1];
+  const TransferTables& t = h->tt;
+  if (h->deg == 1)
+    k_prolong<1, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, F.n, t.pro_start, t.pro_off, t.pro_w, xc,
+                                                            xf, accumulate);
+  else
+    k_prolong<2, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, F.n, t.pro_start, t.pro_off, t.pro_w, xc,
+                                                            xf, accumulate);
+  LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, bool zero_bd, cudaStream_t s) {
+  const Level& F = h->L[lf];
+  const Level& Cc = h->L[lf - 1];
+  const TransferTables& t = h->tt;
+  if (h->deg == 1)
+    k_restrict<1, T><<<ceil_div(Cc.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off, t.res_w,
+                                                              bf, yf, rc, zero_bd);
+  else
+    k_restrict<2, T><<<ceil_div(Cc.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off, t.res_w,
+                                                              bf, yf, rc, zero_bd);
+  LAUNCH_CHECK();
+}
+
+template void launch_prolong<double>(const fe_hierarchy*, int, const double*, double*, bool, cudaStream_t);
+template void launch_prolong<float>(const fe_hierarchy*, int, const float*, float*, bool, cudaStream_t);
+template void launch_restrict<double>(const fe_hierarchy*, int, const double*, const double*, double*, bool,
+                                      cudaStream_t);
+template void launch_restrict<float>(const fe_hierarchy*, int, const float*, const float*, float*, bool, cudaStream_t);
+
+template <typename T>
+void launch_cheb_step(int n, const T* b, const T* y, const T* dinv, T* x, T* d, double c1, double c2,
+                      bool first_from_zero, cudaStream_t s) {
+  k_cheb_step<T><<<ceil_div(n, kBlock), kBlock, 0, s>>>(n, b, y, dinv, x, d, (T)c1, (T)c2, first_from_zero ? 1 : 0);
+  LAUNCH_CHECK();
+}
+template void launch_cheb_step<double>(int, const double*, const double*, const double*, double*, double*, double,
+                                       double, bool, cudaStream_t);
+template void launch_cheb_step<float>(int, const float*, const float*, const float*, float*, float*, double, double,
+                                      bool, cudaStream_t);
+
+template <typename Ti, typename To>
+void launch_convert(int n, const Ti* in, To* out, cudaStream_t s) {
+  k_convert<Ti, To><<<ceil_div(n, kBlock), kBlock, 0, s>>>(n, in, out);
+  LAUNCH_CHECK();
+}
+template void launch_convert<double, float>(int, const double*, float*, cudaStream_t);
+template void launch_convert<float, double>(int, const float*, double*, cudaStream_t);
+
+void launch_set_boundary(const Level& L, const double* src, double* dst, cudaStream_t s) {
+  if (L.nb == 0) return;
+  k_set_boundary<<<ceil_div(L.nb, kBlock), kBlock, 0, s>>>(L.nb, L.bnd, src, dst);
+  LAUNCH_CHECK();
+}
+
+void launch_zero_boundary64(const Level& L, double* v, cudaStream_t s) { launch_set_boundary(L, nullptr, v, s); }
+
+void launch_random(int n, uint64_t seed, double* v, cudaStream_t s) {
+  k_random<<<ceil_div(n, kBlock), kBlock, 0, s>>>(n, seed, v);
+  LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------- mass tables
+// int_ref phi_i phi_j on the reference tet.  Every P1/P2 basis function is a
+// homogeneous polynomial in the barycentrics (P1: lambda_i; P2: lambda_v^2 -
+// sum_{w!=v} lambda_v lambda_w and 4 lambda_a lambda_b), and
+// int_ref lambda^alpha = alpha! / (|alpha| + 3)!.
+static double fact(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return f;
+}
+
+void upload_mass_tables() {
+  double m1[16];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) m1[i * 4 + j] = (i == j ? 2.0 : 1.0) / 120.0;
+  // P2 basis as symmetric quadratic forms Q[i][a][b] in the barycentrics
+  double Q[10][4][4] = {};
+  for (int v = 0; v < 4; ++v) {
+    Q[v][v][v] = 1.0;
+    for (int w = 0; w < 4; ++w)
+      if (w != v) {
+        Q[v][v][w] -= 0.5;
+        Q[v][w][v] -= 0.5;
+      }
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = a + 1; b < 4; ++b) {
+      const int e = p2_edge(a, b);
+      Q[e][a][b] = 2.0;
+      Q[e][b][a] = 2.0;
+    }
+  double m2[100];
+  for (int i = 0; i < 10; ++i)
+    for (int j = 0; j < 10; ++j) {
+      double s = 0.0;
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b)
+          for (int c = 0; c < 4; ++c)
+            for (int d = 0; d < 4; ++d) {
+              const double q = Q[i][a][b] * Q[j][c][d];
+              if (q == 0.0) continue;
+              int al[4] = {0, 0, 0, 0};
+              al[a]++;
+              al[b]++;
+              al[c]++;
+              al[d]++;
+              s += q * fact(al[0]) * fact(al[1]) * fact(al[2]) * fact(al[3]) / fact(7);
+            }
+      m2[i * 10 + j] = s;
+    }
+  CUDA_CHECK(cudaMemcpyToSymbol(c_mref1, m1, sizeof(m1)));
+  CUDA_CHECK(cudaMemcpyToSymbol(c_mref2, m2, sizeof(m2)));
+}
+
+namespace {
+__global__ void k_fill64(size_t n, double v, double* __restrict__ p) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+}  // namespace
+
+void launch_fill64(size_t n, double v, double* p, cudaStream_t s) {
+  k_fill64<<<1024, 256, 0, s>>>(n, v, p);
+  LAUNCH_CHECK();
+}

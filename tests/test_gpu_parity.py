@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 operator/mass/diagonal/transfer/smoother applications are
+compared elementwise against |A||x| (the rounding-error scale of each row) with
+a factor 1e-13; FP32 applications at 1e-5 of that scale; FP64 solutions at a
+relative L2 error of 1e-10 with both sides solved to rtol 1e-13.
+"""
+import numpy as np
+import pytest
+
+import fe_inputs as I
+from oracle import fe_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_08012_gb300 import build
+    build.build()
+    import paper_2104_08012_gb300 as fe
+    fe.load()
+    return fe
+
+
+DEV = "cuda"
+
+
+def dt(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def assert_rowwise(got, ref, scale, tol, what):
+    err = np.abs(got - ref)
+    bound = tol * np.maximum(scale, 1e-300)
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, f"{what}: {bad.size} rows off, worst {np.max(err / bound):.3g}x tol at {bad[:5]}"
+
+
+# ------------------------------------------------------------------ mesh
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("N", [1, 3, 4])
+def test_mesh_queries_match_oracle(fe, k, N):
+    with fe.Hierarchy(N, 0, k) as h:
+        s = O.Space(O.Mesh(N), k)
+        assert h.n_dofs() == s.n and h.n_cells() == 6 * N ** 3
+        assert np.array_equal(h.dof_coordinates(), s.coords)
+        assert np.array_equal(h.boundary_mask(), s.boundary)
+        assert np.allclose(h.cell_centroids(), s.mesh.centroids(), atol=1e-15)
+
+
+# ------------------------------------------------------------ operator
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("coef", ["one", "grf"])
+def test_apply_f64(fe, k, N, coef):
+    with fe.Hierarchy(N, 0, k) as h:
+        kappa = None if coef == "one" else I.grf_kappa(h.cell_centroids(), seed=N)
+        h.set_coefficient(None if kappa is None else dt(kappa))
+        L = O.Level(N, k, kappa)
+        x = I.random_vector(L.n, 10 + N)
+        y = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        h.apply_operator(dt(x), y)
+        torch.cuda.synchronize()
+        scale = abs(L.A) @ np.abs(x)
+        assert_rowwise(host(y), L.A @ x, scale, 1e-13, "fp64 apply")
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_apply_f32(fe, k):
+    N = 6
+    with fe.Hierarchy(N, 0, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=3)
+        h.set_coefficient(dt(kappa))
+        L = O.Level(N, k, kappa)
+        x = I.random_vector(L.n, 4).astype(np.float32)
+        y = torch.empty(L.n, dtype=torch.float32, device=DEV)
+        h.apply_operator(dt(x, torch.float32), y, dtype=fe.FE_F32)
+        torch.cuda.synchronize()
+        xd = x.astype(np.float64)
+        assert_rowwise(host(y), L.A @ xd, abs(L.A) @ np.abs(xd), 1e-5, "fp32 apply")
+
+
+def test_apply_host_pointers_match_device(fe):
+    with fe.Hierarchy(4, 0, 2) as h:
+        x = I.random_vector(h.n_dofs(), 7)
+        y_host = np.empty_like(x)
+        h.apply_operator(x, y_host)  # numpy in, numpy out: staged through the library
+        y_dev = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+        h.apply_operator(dt(x), y_dev)
+        torch.cuda.synchronize()
+        L = O.Level(4, 2)
+        assert_rowwise(y_host, L.A @ x, abs(L.A) @ np.abs(x), 1e-13, "host-pointer apply")
+        assert_rowwise(host(y_dev), y_host, abs(L.A) @ np.abs(x), 1e-13, "host vs device")
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_mass_and_diagonal(fe, k):
+    N = 4
+    with fe.Hierarchy(N, 0, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=5)
+        h.set_coefficient(dt(kappa))
+        L = O.Level(N, k, kappa)
+        x = I.random_vector(L.n, 8)
+        y = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        h.apply_mass(dt(x), y)
+        d = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        h.diagonal(d)
+        torch.cuda.synchronize()
+        assert_rowwise(host(y), L.M @ x, abs(L.M) @ np.abs(x), 1e-13, "mass")
+        assert_rowwise(host(d), L.diag, np.abs(L.diag), 1e-13, "diagonal")
+
+
+# ------------------------------------------------------------ transfers
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("N0", [1, 2, 3])
+def test_prolong_restrict(fe, k, N0):
+    with fe.Hierarchy(N0, 1, k) as h:
+        c, f = O.Level(N0, k), O.Level(2 * N0, k)
+        P = O.prolongation(c, f)
+        xc = I.random_vector(c.n, 1)
+        xf = torch.empty(f.n, dtype=torch.float64, device=DEV)
+        h.prolong(dt(xc), xf, 1)
+        rf = I.random_vector(f.n, 2)
+        rc = torch.empty(c.n, dtype=torch.float64, device=DEV)
+        h.restrict(dt(rf), rc, 1)
+        rc0 = torch.empty(c.n, dtype=torch.float64, device=DEV)
+        h.restrict(dt(rf), rc0, 1, zero_boundary=True)
+        torch.cuda.synchronize()
+        assert_rowwise(host(xf), P @ xc, abs(P) @ np.abs(xc), 1e-15, "prolong")
+        ref = P.T @ rf
+        assert_rowwise(host(rc), ref, abs(P.T) @ np.abs(rf), 1e-14, "restrict")
+        ref[c.space.boundary] = 0
+        assert_rowwise(host(rc0), ref, abs(P.T) @ np.abs(rf), 1e-14, "restrict (zero bd)")
+
+
+# ------------------------------------------------------------ smoother
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("steps", [1, 2, 3])
+def test_chebyshev_smoother(fe, k, steps):
+    N = 4
+    with fe.Hierarchy(N, 0, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=11)
+        h.set_coefficient(dt(kappa))
+        L = O.Level(N, k, kappa)
+        lm = h.lambda_max()
+        b, x0 = I.random_vector(L.n, 3), I.random_vector(L.n, 4)
+        x = dt(x0)
+        h.smooth(dt(b), x, steps=steps, lo=0.1, hi=1.1)
+        torch.cuda.synchronize()
+        ref = O.chebyshev(lambda v: L.A @ v, L.diag, b, x0, 0.1 * lm, 1.1 * lm, steps)
+        assert np.linalg.norm(host(x) - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_lambda_max_p1_closed_form(fe):
+    """Lanczos estimate of lambda_max(D^-1 A) for P1 against 1 + cos(pi h) (Kuhn P1 = h x 7-point)."""
+    for N in (4, 8, 16):
+        with fe.Hierarchy(N, 0, 1) as h:
+            lm = h.lambda_max()
+            exact = 1 + np.cos(np.pi / N)
+            assert exact * (1 - 2e-2) <= lm <= exact * (1 + 1e-12), (N, lm, exact)
+
+
+# --------------------------------------------------------- coarse solve
+@pytest.mark.parametrize("k,N0", [(1, 4), (2, 2), (2, 4)])
+def test_coarse_cholesky(fe, k, N0):
+    with fe.Hierarchy(N0, 1, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=2)
+        h.set_coefficient(dt(kappa))
+        oh = O.Hierarchy(N0, 1, k, kappa)
+        c = oh.levels[0]
+        b = I.random_vector(c.n, 9)
+        x = torch.empty(c.n, dtype=torch.float64, device=DEV)
+        h.coarse_solve(dt(b), x)
+        torch.cuda.synchronize()
+        ref = np.linalg.solve(c.A.toarray(), b)
+        assert np.linalg.norm(host(x) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_vcycle_matches_oracle(fe, k):
+    with fe.Hierarchy(2, 2, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=4)
+        h.set_coefficient(dt(kappa))
+        oh = O.Hierarchy(2, 2, k, kappa)
+        oh.lmax = [h.lambda_max(l) for l in range(3)]  # same Chebyshev intervals
+        b = I.random_vector(oh.fine.n, 5)
+        b[oh.fine.space.boundary] = 0
+        x = torch.empty(oh.fine.n, dtype=torch.float64, device=DEV)
+        h.vcycle(dt(b), x)
+        torch.cuda.synchronize()
+        ref = oh.vcycle(b)
+        assert np.linalg.norm(host(x) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+# ---------------------------------------------------------------- solves
+def test_config0_jacobi_pcg(fe):
+    """P1 on UnitCubeMesh 8^3 (3072 cells, 729 vertices), Jacobi-PCG to rtol 1e-10."""
+    with fe.Hierarchy(8, 0, 1) as h:
+        assert h.n_cells() == 3072 and h.n_dofs() == 729
+        L = O.Level(8, 1)
+        f = I.sin_product_rhs(L.space.coords)
+        b = O.load_vector(L, f)
+        ue = O.direct_solve(L, b)
+        u = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        st = h.solve(dt(f), u, precond=fe.FE_PC_JACOBI, rtol=1e-10)
+        uh = host(u)
+        assert st.rel_residual <= 1e-10
+        assert np.linalg.norm(L.A @ uh - b) <= 1.01e-10 * np.linalg.norm(b)
+        _, it_orc, _ = O.solve(L, b, rtol=1e-10, precond="jacobi")
+        assert abs(st.iterations - it_orc) <= 1
+        st = h.solve(dt(f), u, precond=fe.FE_PC_JACOBI, rtol=1e-13)
+        assert np.linalg.norm(host(u) - ue) <= 1e-10 * np.linalg.norm(ue)
+        # the discrete solution converges to the sin product at O(h^2)
+        assert O.l2_error(L.space, host(u), I.sin_product) < 0.05
+
+
+@pytest.mark.parametrize("k,N0,nref", [(1, 2, 2), (2, 2, 2), (2, 3, 1)])
+def test_gmg_pcg_solution_parity(fe, k, N0, nref):
+    with fe.Hierarchy(N0, nref, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=6)
+        h.set_coefficient(dt(kappa))
+        L = O.Level(N0 * 2 ** nref, k, kappa)
+        f = I.sin_product_rhs(L.space.coords)
+        b = O.load_vector(L, f)
+        ue = O.direct_solve(L, b)
+        u = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        st = h.solve(dt(f), u, rtol=1e-13)
+        assert np.linalg.norm(host(u) - ue) <= 1e-10 * np.linalg.norm(ue)
+        assert st.iterations <= 30
+        st2 = h.solve(f, np.empty(L.n), rtol=1e-13)  # host pointers (end-to-end path)
+        assert st2.iterations == st.iterations
+
+
+def test_gmg_iterations_mesh_independent(fe):
+    its = []
+    for nref in (1, 2, 3):
+        with fe.Hierarchy(4, nref, 2) as h:
+            f = dt(I.sin_product_rhs(h.dof_coordinates()))
+            u = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+            its.append(h.solve(f, u, rtol=1e-8).iterations)
+    assert max(its) <= 15 and its[-1] - its[0] <= 3, its
+
+
+def test_solver_errors(fe):
+    with fe.Hierarchy(4, 1, 1) as h:
+        f = dt(I.sin_product_rhs(h.dof_coordinates()))
+        u = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+        with pytest.raises(fe.FeError) as e:
+            h.solve(f, u, rtol=1e-12, max_it=1)
+        assert e.value.code == fe.FE_ERR_NO_CONVERGENCE
+        with pytest.raises(fe.FeError) as e:
+            h.apply_operator(u, u)
+        assert e.value.code == fe.FE_ERR_ARG
+        with pytest.raises(fe.FeError) as e:
+            h.set_coefficient(dt(-np.ones(h.n_cells())))
+        assert e.value.code == fe.FE_ERR_ARG
+        nanf = f.clone()
+        nanf[5] = float("nan")
+        with pytest.raises(fe.FeError) as e:
+            h.solve(nanf, u, rtol=1e-8)
+        assert e.value.code == fe.FE_ERR_NAN
