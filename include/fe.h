@@ -89,6 +89,7 @@ typedef struct fe_solver_opts {
   double inner_rtol;  /* mixed precision: inner FP32 solve tolerance */
   int inner_max_it;   /* mixed precision: inner iteration limit per refinement step */
   int use_graph;      /* nonzero: replay each V-cycle from a captured CUDA graph */
+  int profile;        /* nonzero: time every CG operator application with CUDA events (stats.apply_ms) */
 } fe_solver_opts;
 
 typedef struct fe_solve_stats {
@@ -99,11 +100,13 @@ typedef struct fe_solve_stats {
   double solve_ms;       /* host wall time of the solve */
   int fine_applies_f64;  /* FP64 fine-level operator applications */
   int fine_applies_low;  /* FP32/bf16 fine-level operator applications */
+  double apply_ms;       /* profile: summed device time of the timed CG operator applications */
+  int apply_timed;       /* profile: number of operator applications in apply_ms */
 } fe_solve_stats;
 
 /* Fill `opts` with the defaults: rtol 1e-8, max_it 500, GMG, FP64,
  * 2 Chebyshev steps on [0.1, 1.1] lambda_max, inner_rtol 1e-4, inner_max_it 60,
- * graphs on. */
+ * graphs on, profiling off. */
 void fe_default_opts(fe_solver_opts* opts);
 
 /* Message of the last failure on this thread ("" if none).  The string is
@@ -112,6 +115,10 @@ const char* fe_last_error(void);
 
 /* Number of visible CUDA devices (0 without a GPU); never fails. */
 int fe_device_count(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (each replay of a captured graph counts every kernel node); never fails. */
+long long fe_kernel_launches(void);
 
 /* ---- mesh and hierarchy (paper Section 2: UnitCubeMesh, MeshHierarchy, FunctionSpace) ---- */
 

@@ -22,7 +22,7 @@ FE_RHS_LOAD, FE_RHS_NODAL_F = 0, 1
 
 # every symbol include/fe.h declares
 EXPORTED = (
-    "fe_default_opts", "fe_last_error", "fe_device_count", "fe_mesh_create", "fe_mesh_destroy",
+    "fe_default_opts", "fe_last_error", "fe_device_count", "fe_kernel_launches", "fe_mesh_create", "fe_mesh_destroy",
     "fe_hierarchy_refine", "fe_hierarchy_destroy", "fe_num_levels", "fe_level_sizes", "fe_dof_coordinates",
     "fe_cell_centroids", "fe_boundary_mask", "fe_set_coefficient", "fe_apply_operator", "fe_apply_mass",
     "fe_diagonal", "fe_lambda_max", "fe_prolong", "fe_restrict", "fe_smooth", "fe_coarse_solve", "fe_vcycle",
@@ -40,13 +40,13 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("precond", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cheb_steps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("inner_rtol", ctypes.c_double), ("inner_max_it", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("bnorm", ctypes.c_double), ("solve_ms", ctypes.c_double), ("fine_applies_f64", ctypes.c_int),
-                ("fine_applies_low", ctypes.c_int)]
+                ("fine_applies_low", ctypes.c_int), ("apply_ms", ctypes.c_double), ("apply_timed", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -73,6 +73,7 @@ def load():
         "fe_default_opts": (None, [ctypes.POINTER(SolverOpts)]),
         "fe_last_error": (ctypes.c_char_p, []),
         "fe_device_count": (i, []),
+        "fe_kernel_launches": (ll, []),
         "fe_mesh_create": (i, [i, i, i, ctypes.POINTER(vp)]),
         "fe_mesh_destroy": (None, [vp]),
         "fe_hierarchy_refine": (i, [vp, i, i, ctypes.POINTER(vp)]),
@@ -146,6 +147,10 @@ def default_opts(**kw):
 # ---- thin wrappers with the C names ----------------------------------------
 def fe_device_count():
     return load().fe_device_count()
+
+
+def fe_kernel_launches():
+    return load().fe_kernel_launches()
 
 
 def fe_mesh_create(nx, ny=None, nz=None):

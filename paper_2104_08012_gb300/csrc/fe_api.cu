@@ -5,6 +5,7 @@
 // fe_blas.cu, fe_coarse.cu and fe_tc.cu; the host only sequences launches and
 // tests convergence.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -18,6 +19,11 @@ void launch_fill64(size_t n, double v, double* p, cudaStream_t s);
 
 // ------------------------------------------------------------- errors
 static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+static thread_local bool g_capturing = false;
+void fe_count_launch() {
+  if (!g_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 void fe_set_error(const std::string& m) { g_err = m; }
 
 #define API_BEGIN try {
@@ -253,6 +259,9 @@ static double estimate_lmax(fe_hierarchy* h, int l, int steps, cudaStream_t s) {
   CUDA_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   launch_cheb_step<double>(n, r, nullptr, L.dinv64, p, z, 0.0, 1.0, true, s);  // z = p = D^-1 r
   launch_dot<double>(R, n, r, z, S_RZ, s);
+  CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  if (!(R.h_scal[S_RZ] > 0.0)) return 1.0;  // no interior dofs: D^-1 A is the identity
   std::vector<double> al, be;
   for (int it = 0; it < steps; ++it) {
     launch_apply64(L, p, q, s);
@@ -378,13 +387,26 @@ static void run_vcycle(fe_hierarchy* h, int dtype, bool use_graph, cudaStream_t 
     if (!gc.stream) CUDA_CHECK(cudaStreamCreateWithFlags(&gc.stream, cudaStreamNonBlocking));
     cudaGraph_t g;
     CUDA_CHECK(cudaStreamBeginCapture(gc.stream, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
     try {
       enqueue(gc.stream);
     } catch (...) {
+      g_capturing = false;
       cudaStreamEndCapture(gc.stream, &g);
       throw;
     }
+    g_capturing = false;
     CUDA_CHECK(cudaStreamEndCapture(gc.stream, &g));
+    size_t nn = 0;
+    CUDA_CHECK(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) CUDA_CHECK(cudaGraphGetNodes(g, nodes.data(), &nn));
+    gc.kernels = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      CUDA_CHECK(cudaGraphNodeGetType(nd, &ty));
+      if (ty == cudaGraphNodeTypeKernel) ++gc.kernels;
+    }
     CUDA_CHECK(cudaGraphInstantiate(&gc.exec, g, 0));
     cudaGraphDestroy(g);
     gc.steps = g_sp.steps;
@@ -392,6 +414,7 @@ static void run_vcycle(fe_hierarchy* h, int dtype, bool use_graph, cudaStream_t 
     gc.hi = g_sp.hi;
   }
   CUDA_CHECK(cudaGraphLaunch(gc.exec, s));
+  g_launches.fetch_add(gc.kernels, std::memory_order_relaxed);
 }
 
 static void invalidate_graphs(fe_hierarchy* h) {
@@ -408,6 +431,34 @@ struct PcgResult {
   double rr = 0, bb = 0;
   int status = FE_OK;
   int applies = 0;
+  double apply_ms = 0.0;
+  int apply_timed = 0;
+};
+
+// CUDA events around the CG operator application when profiling.
+struct ApplyTimer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool on = false;
+  explicit ApplyTimer(bool enable) : on(enable) {
+    if (on) {
+      CUDA_CHECK(cudaEventCreate(&e0));
+      CUDA_CHECK(cudaEventCreate(&e1));
+    }
+  }
+  ~ApplyTimer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+  void start(cudaStream_t s) { if (on) CUDA_CHECK(cudaEventRecord(e0, s)); }
+  void stop(cudaStream_t s) { if (on) CUDA_CHECK(cudaEventRecord(e1, s)); }
+  // after the stream has been synchronised
+  void collect(PcgResult& r) {
+    if (!on) return;
+    float ms = 0.f;
+    CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    r.apply_ms += ms;
+    ++r.apply_timed;
+  }
 };
 
 // FP64 PCG on the finest level: b, x device vectors (x overwritten).
@@ -433,17 +484,21 @@ static PcgResult pcg64(fe_hierarchy* h, const double* b, double* x, const fe_sol
   res.rr = res.bb;
   const double tol2 = o.rtol * o.rtol * res.bb;
   if (res.bb == 0.0) return res;
+  ApplyTimer timer(o.profile != 0);
   while (true) {
     if (res.it >= o.max_it) {
       res.status = FE_ERR_NO_CONVERGENCE;
       break;
     }
+    timer.start(s);
     launch_apply64(F, p, q, s);
+    timer.stop(s);
     ++res.applies;
     launch_cg_alpha<double>(R, n, p, q, s);
     launch_cg_update<double>(R, n, x, r, p, q, gmg ? nullptr : F.dinv64.p, z, s);
     CUDA_CHECK(cudaMemcpyAsync(R.h_scal + S_RR, R.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_CHECK(cudaStreamSynchronize(s));
+    timer.collect(res);
     ++res.it;
     res.rr = R.h_scal[S_RR];
     if (!std::isfinite(res.rr)) {
@@ -621,7 +676,10 @@ void fe_default_opts(fe_solver_opts* o) {
   o->inner_rtol = 1e-4;
   o->inner_max_it = 60;
   o->use_graph = 1;
+  o->profile = 0;
 }
+
+long long fe_kernel_launches(void) { return g_launches.load(); }
 
 const char* fe_last_error(void) { return g_err.c_str(); }
 
@@ -979,6 +1037,8 @@ int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_
   if (o.precision == FE_PREC_F64) {
     res = pcg64(h, b, ud, o, s);
     st.fine_applies_f64 = res.applies;
+    st.apply_ms = res.apply_ms;
+    st.apply_timed = res.apply_timed;
   } else {
     res = refine(h, b, ud, o, o.precision == FE_PREC_MIXED_F32 ? FE_F32 : FE_BF16, &st, s);
     st.fine_applies_f64 = res.applies;

@@ -33,7 +33,14 @@ struct FeError {
                         std::to_string(__LINE__) + ")"};                                            \
     }                                                                                               \
   } while (0)
-#define LAUNCH_CHECK() CUDA_CHECK(cudaGetLastError())
+// Every kernel launch is followed by LAUNCH_CHECK(), which also counts it
+// (launches recorded into a graph under capture are counted at replay).
+void fe_count_launch();
+#define LAUNCH_CHECK()                \
+  do {                                \
+    CUDA_CHECK(cudaGetLastError());   \
+    fe_count_launch();                \
+  } while (0)
 
 void fe_set_error(const std::string& msg);
 
@@ -189,6 +196,7 @@ struct fe_mesh {
 
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;  // kernel nodes of the captured graph
   cudaStream_t stream = nullptr;
   int steps = 0;  // smoother parameters baked into the captured launches
   double lo = 0, hi = 0;

@@ -58,10 +58,10 @@ __global__ void k_build_coords(int N, int V, double* __restrict__ vx, double* __
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
   const int n1 = N + 1;
-  const double h = 1.0 / N;
-  vx[v] = (v % n1) * h;
-  vy[v] = ((v / n1) % n1) * h;
-  vz[v] = (v / (n1 * n1)) * h;
+  const double dn = (double)N;
+  vx[v] = (v % n1) / dn;
+  vy[v] = ((v / n1) % n1) / dn;
+  vz[v] = (v / (n1 * n1)) / dn;
 }
 
 // ----------------------------------------------------------- geometry
@@ -227,10 +227,10 @@ __global__ void k_dof_coords(Numbering num, int n, double* __restrict__ xyz) {
   if (i >= n) return;
   int x, y, z;
   dof_to_lattice(num, i, x, y, z);
-  const double h = 1.0 / num.m;
-  xyz[3 * (size_t)i + 0] = x * h;
-  xyz[3 * (size_t)i + 1] = y * h;
-  xyz[3 * (size_t)i + 2] = z * h;
+  const double m = (double)num.m;
+  xyz[3 * (size_t)i + 0] = x / m;
+  xyz[3 * (size_t)i + 1] = y / m;
+  xyz[3 * (size_t)i + 2] = z / m;
 }
 
 __global__ void k_centroids(int C, const int* __restrict__ map, const double* __restrict__ vx,

@@ -134,7 +134,7 @@ def test_prolong_restrict(fe, k, N0):
         rc0 = torch.empty(c.n, dtype=torch.float64, device=DEV)
         h.restrict(dt(rf), rc0, 1, zero_boundary=True)
         torch.cuda.synchronize()
-        assert_rowwise(host(xf), P @ xc, abs(P) @ np.abs(xc), 1e-15, "prolong")
+        assert_rowwise(host(xf), P @ xc, abs(P) @ np.abs(xc), 1e-14, "prolong")
         ref = P.T @ rf
         assert_rowwise(host(rc), ref, abs(P.T) @ np.abs(rf), 1e-14, "restrict")
         ref[c.space.boundary] = 0
