@@ -1,0 +1,158 @@
+"""Parity of the extension forms: mixed-precision refinement and the adjoint gradient.
+
+Mixed precision (FP32 inner GMG-PCG inside FP64 iterative refinement) must
+reach the same 1e-8 FP64 residual and agree with the FP64 oracle solution to
+1e-6 relative L2.  The adjoint gradient dJ/dkappa must match the oracle's
+assembled adjoint to 1e-8 relative and central finite differences to 1e-6 of
+max |dJ/dkappa|; at the full adjoint size (P1 96^3) it must pass the Taylor
+test (second-order remainder).
+"""
+import numpy as np
+import pytest
+
+import fe_inputs as I
+from oracle import fe_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def fe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_08012_gb300 import build
+    build.build()
+    import paper_2104_08012_gb300 as fe
+    fe.load()
+    return fe
+
+
+def dt(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+# ------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("k,N0,nref", [(2, 4, 2), (1, 4, 3)])
+@pytest.mark.parametrize("coef", ["one", "grf"])
+def test_mixed_precision_refinement(fe, k, N0, nref, coef):
+    with fe.Hierarchy(N0, nref, k) as h:
+        kappa = None if coef == "one" else I.grf_kappa(h.cell_centroids(), seed=12)
+        h.set_coefficient(None if kappa is None else dt(kappa))
+        L = O.Level(N0 * 2 ** nref, k, kappa)
+        f = I.sin_product_rhs(L.space.coords)
+        b = O.load_vector(L, f)
+        ue = O.direct_solve(L, b)
+        u = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        st = h.solve(dt(f), u, rtol=1e-8, precision=fe.FE_PREC_MIXED_F32)
+        uh = host(u)
+        # the FP64 residual is recomputed by the oracle, not taken from the library
+        assert np.linalg.norm(L.A @ uh - b) <= 1.0001e-8 * np.linalg.norm(b)
+        assert st.rel_residual <= 1e-8 and st.outer_iterations >= 2
+        rel = np.linalg.norm(uh - ue) / np.linalg.norm(ue)
+        assert rel <= 1e-6, rel
+        u64 = torch.empty_like(u)
+        st64 = h.solve(dt(f), u64, rtol=1e-8)
+        assert np.linalg.norm(uh - host(u64)) <= 1e-6 * np.linalg.norm(ue)
+        # far fewer FP64 operator applications than the FP64 solve
+        assert st.fine_applies_f64 < st64.fine_applies_f64
+
+
+def test_mixed_precision_reaches_tight_tolerance(fe):
+    """Refinement converges past FP32 accuracy: rtol 1e-12 in FP64."""
+    with fe.Hierarchy(4, 2, 2) as h:
+        L = O.Level(16, 2)
+        f = I.sin_product_rhs(L.space.coords)
+        b = O.load_vector(L, f)
+        u = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        h.solve(dt(f), u, rtol=1e-12, precision=fe.FE_PREC_MIXED_F32)
+        assert np.linalg.norm(L.A @ host(u) - b) <= 1.001e-12 * np.linalg.norm(b)
+
+
+# ------------------------------------------------------------------- adjoint
+def _setup_adjoint(fe, N0, nref, k, seed=21):
+    h = fe.Hierarchy(N0, nref, k)
+    kappa = I.grf_kappa(h.cell_centroids(), seed=seed)
+    X = h.dof_coordinates()
+    f = np.ones(h.n_dofs())
+    ud = I.target_field(X)
+    return h, kappa, f, ud
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_adjoint_matches_oracle_assembled_adjoint(fe, k):
+    h, kappa, f, ud = _setup_adjoint(fe, 2, 2, k)
+    with h:
+        h.set_coefficient(dt(kappa))
+        g = torch.empty(h.n_cells(), dtype=torch.float64, device=DEV)
+        J = h.adjoint_gradient(dt(f), dt(ud), g, rtol=1e-13)
+        oh = O.Hierarchy(2, 2, k, kappa)
+        L = oh.fine
+        Jo, go, _, _ = O.adjoint_gradient(oh, O.load_vector(L, f), ud)
+        assert abs(J - Jo) <= 1e-10 * abs(Jo)
+        assert np.linalg.norm(host(g) - go) <= 1e-8 * np.linalg.norm(go)
+
+
+def test_adjoint_vs_central_differences_8cubed(fe):
+    """P1 on 8^3 (3072 cells): gradient against central FD of J computed by GPU solves."""
+    h, kappa, f, ud = _setup_adjoint(fe, 2, 2, 1)
+    with h:
+        fd_f, fd_ud = dt(f), dt(ud)
+        h.set_coefficient(dt(kappa))
+        g = torch.empty(h.n_cells(), dtype=torch.float64, device=DEV)
+        h.adjoint_gradient(fd_f, fd_ud, g, rtol=1e-13)
+        g = host(g)
+        u = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+
+        def J(kap):
+            h.set_coefficient(dt(kap))
+            h.solve(fd_f, u, rtol=1e-13)
+            return h.objective(u, fd_ud)
+
+        cells = np.random.default_rng(0).choice(h.n_cells(), 24, replace=False)
+        for c in cells:
+            eps = 1e-5 * kappa[c]
+            kp, km = kappa.copy(), kappa.copy()
+            kp[c] += eps
+            km[c] -= eps
+            fd = (J(kp) - J(km)) / (2 * eps)
+            assert abs(fd - g[c]) <= 1e-6 * np.abs(g).max(), (c, fd, g[c])
+
+
+def test_autograd_function(fe):
+    from paper_2104_08012_gb300.autograd import poisson_objective
+    h, kappa, f, ud = _setup_adjoint(fe, 2, 1, 2)
+    with h:
+        kap = dt(kappa).requires_grad_(True)
+        J = poisson_objective(kap, h, dt(f), dt(ud))
+        J.backward()
+        g = torch.empty(h.n_cells(), dtype=torch.float64, device=DEV)
+        h.set_coefficient(dt(kappa))
+        J2 = h.adjoint_gradient(dt(f), dt(ud), g, rtol=1e-12)
+        assert abs(J.item() - J2) <= 1e-10 * abs(J2)
+        assert torch.allclose(kap.grad, g, rtol=1e-8, atol=1e-12 * g.abs().max().item())
+
+
+def test_adjoint_full_size_taylor(fe):
+    """P1 UnitCubeMesh 96^3 (5,308,416 cells), 4 levels from 12^3: Taylor remainder is O(t^2)."""
+    h, kappa, f, ud = _setup_adjoint(fe, 12, 3, 1)
+    with h:
+        assert h.n_cells() == 5308416
+        fd_f, fd_ud = dt(f), dt(ud)
+        h.set_coefficient(dt(kappa))
+        g = torch.empty(h.n_cells(), dtype=torch.float64, device=DEV)
+        J0 = h.adjoint_gradient(fd_f, fd_ud, g, rtol=1e-12)
+        g = host(g)
+        dk = np.random.default_rng(5).normal(size=h.n_cells()) * kappa
+        u = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+        rem = []
+        for t in (1e-2, 5e-3):
+            h.set_coefficient(dt(kappa + t * dk))
+            h.solve(fd_f, u, rtol=1e-12)
+            rem.append(abs(h.objective(u, fd_ud) - J0 - t * (g @ dk)))
+        assert 3.0 < rem[0] / rem[1] < 5.0, rem
