@@ -62,11 +62,25 @@ def grf_features(seed=DEFAULT_SEED, n_features=2048, length=0.2):
     return omega, phase
 
 
-def grf_kappa(points, seed=DEFAULT_SEED, n_features=2048, length=0.2, sigma=1.0, chunk=1 << 16):
-    """kappa = exp(g) at ``points`` (n,3), g = sigma sqrt(2/M) sum_m cos(omega_m . x + phi_m)."""
+def grf_kappa(points, seed=DEFAULT_SEED, n_features=2048, length=0.2, sigma=1.0, chunk=1 << 16, device=None):
+    """kappa = exp(g) at ``points`` (n,3), g = sigma sqrt(2/M) sum_m cos(omega_m . x + phi_m).
+
+    ``device``: optionally a torch device on which to evaluate the same FP64
+    formula (for meshes of millions of cells; values agree with the numpy path
+    to rounding).  Returns a numpy array either way.
+    """
     omega, phase = grf_features(seed, n_features, length)
-    out = np.empty(points.shape[0])
     scale = sigma * np.sqrt(2.0 / n_features)
+    if device is not None:
+        import torch
+        om = torch.from_numpy(omega).to(device)
+        ph = torch.from_numpy(phase).to(device)
+        out = torch.empty(points.shape[0], dtype=torch.float64, device=device)
+        for s in range(0, points.shape[0], chunk):
+            p = torch.from_numpy(np.ascontiguousarray(points[s:s + chunk])).to(device)
+            out[s:s + chunk] = scale * torch.cos(p @ om.T + ph).sum(dim=1)
+        return torch.exp(out).cpu().numpy()
+    out = np.empty(points.shape[0])
     for s in range(0, points.shape[0], chunk):
         p = points[s:s + chunk]
         out[s:s + chunk] = scale * np.cos(p @ omega.T + phase).sum(axis=1)
@@ -90,8 +104,12 @@ def target_field(xyz, seed=DEFAULT_SEED, n_terms=8):
     return out
 
 
-def batched_problem_table(seed=DEFAULT_SEED, n_problems=64, sizes=tuple(range(16, 49, 4))):
-    """Mesh sizes N_i drawn uniformly from ``sizes``; half P1 and half P2, interleaved by the seed."""
+def batched_problem_table(seed=DEFAULT_SEED, n_problems=64, sizes=(16, 24, 32, 40, 48)):
+    """Mesh sizes N_i drawn uniformly from ``sizes``; half P1 and half P2, interleaved by the seed.
+
+    The default sizes are the multiples of 8 in [16, 48], so that every problem
+    has a 4-level hierarchy whose coarse mesh has N_i/8 <= 6 cubes per axis.
+    """
     r = rng(seed + 2)
     ns = r.choice(np.asarray(sizes), size=n_problems)
     degrees = np.array([1] * (n_problems // 2) + [2] * (n_problems - n_problems // 2))

@@ -77,6 +77,7 @@ extern "C" {
 
 typedef struct fe_mesh fe_mesh;
 typedef struct fe_hierarchy fe_hierarchy;
+typedef struct fe_batch fe_batch;
 
 typedef struct fe_solver_opts {
   double rtol;        /* stop when ||b - A u||_2 <= rtol ||b||_2 (unpreconditioned 2-norm) */
@@ -90,6 +91,7 @@ typedef struct fe_solver_opts {
   int inner_max_it;   /* mixed precision: inner iteration limit per refinement step */
   int use_graph;      /* nonzero: replay each V-cycle from a captured CUDA graph */
   int profile;        /* nonzero: time every CG operator application with CUDA events (stats.apply_ms) */
+  int wait_timeout_us; /* bound of every device-side wait of the persistent batched kernel (0 = 5 s) */
 } fe_solver_opts;
 
 typedef struct fe_solve_stats {
@@ -106,7 +108,7 @@ typedef struct fe_solve_stats {
 
 /* Fill `opts` with the defaults: rtol 1e-8, max_it 500, GMG, FP64,
  * 2 Chebyshev steps on [0.1, 1.1] lambda_max, inner_rtol 1e-4, inner_max_it 60,
- * graphs on, profiling off. */
+ * graphs on, profiling off, default wait bound. */
 void fe_default_opts(fe_solver_opts* opts);
 
 /* Message of the last failure on this thread ("" if none).  The string is
@@ -226,6 +228,37 @@ int fe_adjoint_gradient(fe_hierarchy* h, const double* rhs, int rhs_kind, const 
 /* J = (u - u_d)^T M (u - u_d) on the finest level (the objective whose
  * gradient fe_adjoint_gradient returns); J is one double in host memory. */
 int fe_objective(const fe_hierarchy* h, const double* u, const double* u_d, double* J, void* stream);
+
+/* ---- batched solves (extension form: many independent problems, one launch) ----
+ *
+ * A batch holds `nprob` independent Poisson problems, problem p on
+ * UnitCubeMesh(N0[p]) refined nrefine[p] times with Lagrange degree[p]
+ * (1 or 2); all problems need the same number of levels (2..6).  Host-only
+ * arguments; the hierarchies live on the current device. */
+int fe_batch_create(int nprob, const int* N0, const int* nrefine, const int* degree, fe_batch** out);
+void fe_batch_destroy(fe_batch* batch);
+
+/* The hierarchy of problem p (owned by the batch: do not destroy it).  Use it
+ * for fe_set_coefficient (per-problem kappa) and the mesh queries. */
+int fe_batch_hierarchy(fe_batch* batch, int p, fe_hierarchy** h);
+
+/* Solve all problems of the batch, FP64 GMG-PCG (2 Chebyshev-Jacobi steps per
+ * level, FP64 Cholesky coarse solve), right-hand sides given as nodal values
+ * f_nodal[p] (b = M f, Dirichlet rows 0), solutions written to u[p].  All of
+ * f_nodal[p] and u[p] must be DEVICE pointers.  One persistent cooperative
+ * kernel runs every phase of every iteration for all problems (grid-wide
+ * barriers between phases; converged problems drop out), replayed from a
+ * captured CUDA graph when opts->use_graph; the first graph solve runs the
+ * autotuner (cell-block size, CTAs per SM).  stats: nprob entries (may be
+ * NULL).  FE_ERR_TIMEOUT if a grid barrier exceeded opts->wait_timeout_us
+ * (the kernel then returns early; the batch stays usable);
+ * FE_ERR_NO_CONVERGENCE / FE_ERR_NAN if any problem failed.  Synchronises
+ * `stream`. */
+int fe_solve_batched(fe_batch* batch, const double* const* f_nodal, double* const* u, const fe_solver_opts* opts,
+                     fe_solve_stats* stats, void* stream);
+
+/* The schedule chosen by the autotuner (or the default before tuning). */
+int fe_batch_schedule(const fe_batch* batch, int* cell_block, int* dof_block, int* ctas_per_sm);
 
 #ifdef __cplusplus
 }

@@ -290,6 +290,21 @@ def apply_rows(space, kappa, x, rows):
     return y[rows]
 
 
+def apply_rows_mass(space, x, rows):
+    """Rows ``rows`` of y = M x (consistent mass, all dofs), computed cell by cell."""
+    rows = np.asarray(rows, dtype=np.int64)
+    want = np.zeros(space.n, dtype=bool)
+    want[rows] = True
+    cells = np.nonzero(want[space.cell_dofs].any(axis=1))[0]
+    y = np.zeros(space.n)
+    for s in range(0, cells.size, 1 << 15):
+        sel = cells[s:s + (1 << 15)]
+        Me = element_mass(space.mesh, space.degree, sel)
+        cd = space.cell_dofs[sel]
+        np.add.at(y, cd, np.einsum("cde,ce->cd", Me, x[cd]))
+    return y[rows]
+
+
 # ---------------------------------------------------------------- level -----
 class Level:
     """One level of the hierarchy: space, kappa, assembled A (with BCs), diagonal."""

@@ -27,6 +27,7 @@ EXPORTED = (
     "fe_cell_centroids", "fe_boundary_mask", "fe_set_coefficient", "fe_apply_operator", "fe_apply_mass",
     "fe_diagonal", "fe_lambda_max", "fe_prolong", "fe_restrict", "fe_smooth", "fe_coarse_solve", "fe_vcycle",
     "fe_load_vector", "fe_solve_poisson", "fe_adjoint_gradient", "fe_objective",
+    "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
 )
 
 
@@ -40,7 +41,7 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("precond", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cheb_steps", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("inner_rtol", ctypes.c_double), ("inner_max_it", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("profile", ctypes.c_int), ("wait_timeout_us", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -97,6 +98,11 @@ def load():
         "fe_solve_poisson": (i, [vp, vp, i, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(SolveStats), vp]),
         "fe_adjoint_gradient": (i, [vp, vp, i, vp, vp, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(d), vp, vp]),
         "fe_objective": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
+        "fe_batch_create": (i, [i, vp, vp, vp, ctypes.POINTER(vp)]),
+        "fe_batch_destroy": (None, [vp]),
+        "fe_batch_hierarchy": (i, [vp, i, ctypes.POINTER(vp)]),
+        "fe_solve_batched": (i, [vp, vp, vp, ctypes.POINTER(SolverOpts), vp, vp]),
+        "fe_batch_schedule": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -195,6 +201,61 @@ def fe_adjoint_gradient(h, rhs, rhs_kind, u_d, u_ckpt, opts, dJ, u_out=None, str
     return J.value
 
 
+class Batch:
+    """Owning wrapper of an ``fe_batch``: independent problems solved by one persistent launch."""
+
+    def __init__(self, sizes):
+        """sizes: list of (N0, nrefine, degree)."""
+        self._L = load()
+        P = len(sizes)
+        arr = lambda k: (ctypes.c_int * P)(*[int(s[k]) for s in sizes])
+        self.b = ctypes.c_void_p()
+        _check(self._L.fe_batch_create(P, arr(0), arr(1), arr(2), ctypes.byref(self.b)))
+        self.nprob = P
+        self.problems = []
+        for p in range(P):
+            hp = ctypes.c_void_p()
+            _check(self._L.fe_batch_hierarchy(self.b, p, ctypes.byref(hp)))
+            h = Hierarchy.__new__(Hierarchy)
+            h._L, h.h, h.mesh, h.degree = self._L, hp, None, int(sizes[p][2])
+            h.nlev = self._L.fe_num_levels(hp)
+            h._borrowed = True
+            self.problems.append(h)
+
+    def close(self):
+        if getattr(self, "b", None):
+            for h in self.problems:
+                h.h = None
+            self._L.fe_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, f_list, u_list, opts=None, stream=None, **kw):
+        o = opts if opts is not None else default_opts(**kw)
+        P = self.nprob
+        fp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in f_list])
+        up = (ctypes.c_void_p * P)(*[t.data_ptr() for t in u_list])
+        st = (SolveStats * P)()
+        _check(self._L.fe_solve_batched(self.b, fp, up, ctypes.byref(o), st, _stream(stream)))
+        return [st[p] for p in range(P)]
+
+    def schedule(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._L.fe_batch_schedule(self.b, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"cell_block": a.value, "dof_block": b.value, "ctas_per_sm": c.value}
+
+
 class Hierarchy:
     """Owning wrapper of an ``fe_hierarchy`` (UnitCubeMesh(N0) refined ``nrefine`` times, P``degree``)."""
 
@@ -212,6 +273,9 @@ class Hierarchy:
         self.nlev = self._L.fe_num_levels(self.h)
 
     def close(self):
+        if getattr(self, "_borrowed", False):
+            self.h = None
+            return
         if getattr(self, "h", None):
             fe_hierarchy_destroy(self.h)
             self.h = None

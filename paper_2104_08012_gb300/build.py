@@ -76,7 +76,7 @@ def build(force=False, verbose=False, extra_flags=()):
     lib = lib_path()
     objs = [os.path.join(OUTDIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
     if jobs or not os.path.exists(lib) or os.path.getmtime(lib) < _newest(objs):
-        cmd = [exe, *ARCH, "-shared", "-o", lib, *objs, "-lcudart", "-lcuda"]
+        cmd = [exe, *ARCH, "-shared", "-o", lib, *objs, "-lcudart"]
         if verbose:
             print(" ".join(cmd), flush=True)
         p = subprocess.run(cmd, capture_output=True, text=True)

@@ -661,6 +661,84 @@ static fe_solver_opts resolve_opts(const fe_solver_opts* o) {
   return d;
 }
 
+// Builds every level of UnitCubeMesh(N0 * 2^l), l = 0..nrefine, on the current
+// device and sets kappa = 1 (throws FeError).
+fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
+  FE_REQUIRE(N0 >= 1, FE_ERR_ARG, "mesh size must be >= 1");
+  FE_REQUIRE(nrefine >= 0 && nrefine <= 8, FE_ERR_ARG, "nrefine must be in [0, 8]");
+  FE_REQUIRE(degree == 1 || degree == 2, FE_ERR_UNSUPPORTED, "degree must be 1 or 2");
+  const long long Nf = (long long)N0 << nrefine;
+  const long long nf = (long long)(degree * Nf + 1) * (degree * Nf + 1) * (degree * Nf + 1);
+  FE_REQUIRE(6 * Nf * Nf * Nf < (1ll << 31) && nf < (1ll << 31), FE_ERR_ARG, "finest level too large for 32-bit indices");
+  FE_REQUIRE(fe_device_count() > 0, FE_ERR_CUDA, "no CUDA device");
+  std::unique_ptr<fe_hierarchy> h(new fe_hierarchy());
+  int dev = 0;
+  CUDA_CHECK(cudaGetDevice(&dev));
+  CUDA_CHECK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+  static std::once_flag mass_once;
+  std::call_once(mass_once, upload_mass_tables);
+  h->N0 = N0;
+  h->nlev = nrefine + 1;
+  h->deg = degree;
+  h->L.resize(h->nlev);
+  cudaStream_t s = 0;
+  for (int l = 0; l < h->nlev; ++l) {
+    Level& L = h->L[l];
+    L.N = N0 << l;
+    L.deg = degree;
+    L.nd = degree == 1 ? 4 : 10;
+    L.num = make_numbering(L.N, degree);
+    const int m = degree * L.N;
+    L.n = (m + 1) * (m + 1) * (m + 1);
+    L.C = 6 * L.N * L.N * L.N;
+    L.V = (L.N + 1) * (L.N + 1) * (L.N + 1);
+    L.Cs = (L.C + 127) / 128 * 128;
+    L.map.alloc((size_t)L.nd * L.Cs);
+    CUDA_CHECK(cudaMemset(L.map, 0, sizeof(int) * (size_t)L.nd * L.Cs));
+    L.vx.alloc(L.V);
+    L.vy.alloc(L.V);
+    L.vz.alloc(L.V);
+    L.detj.alloc(L.C);
+    L.kappa.alloc(L.C);
+    L.geo64.alloc((size_t)6 * L.Cs);
+    L.geo32.alloc((size_t)6 * L.Cs);
+    CUDA_CHECK(cudaMemset(L.geo32, 0, sizeof(float) * (size_t)6 * L.Cs));
+    L.dinv64.alloc(L.n);
+    L.dinv32.alloc(L.n);
+    for (auto* v : {&L.b64, &L.x64, &L.y64, &L.d64, &L.w64}) v->alloc(L.n);
+    for (auto* v : {&L.b32, &L.x32, &L.y32, &L.d32}) v->alloc(L.n);
+    std::vector<int> bnd;
+    bnd.reserve((size_t)6 * (m + 1) * (m + 1));
+    for (int z = 0; z <= m; ++z)
+      for (int y = 0; y <= m; ++y)
+        for (int x = 0; x <= m; ++x)
+          if (x == 0 || y == 0 || z == 0 || x == m || y == m || z == m) {
+            bnd.push_back(lattice_to_dof(L.num, x, y, z));
+            if (!(z == 0 || z == m || y == 0 || y == m) && x == 0) x = m - 1;  // skip the interior of the row
+          }
+    std::sort(bnd.begin(), bnd.end());
+    L.nb = (int)bnd.size();
+    L.bnd.alloc(L.nb);
+    CUDA_CHECK(cudaMemcpy(L.bnd, bnd.data(), sizeof(int) * L.nb, cudaMemcpyHostToDevice));
+    launch_build_level(L, s);
+  }
+  build_transfer_tables(h->tt, degree);
+  std::vector<int> ch = build_children();
+  h->children.alloc(48);
+  CUDA_CHECK(cudaMemcpy(h->children, ch.data(), sizeof(int) * 48, cudaMemcpyHostToDevice));
+  red_init(h->red, h->sms);
+  const int nF = h->L.back().n;
+  for (auto* v : {&h->x, &h->r, &h->z, &h->p, &h->q, &h->b, &h->e, &h->tmp}) v->alloc(nF);
+  for (auto* v : {&h->r32, &h->z32, &h->p32, &h->q32, &h->e32}) v->alloc(nF);
+  h->cs.flag.alloc(1);
+  set_coefficient_impl(h.get(), nullptr, s);
+  return h.release();
+}
+
+void hierarchy_set_coefficient(fe_hierarchy* h, const double* kappa, cudaStream_t s) { set_coefficient_impl(h, kappa, s); }
+
+void hierarchy_destroy(fe_hierarchy* h) { fe_hierarchy_destroy(h); }
+
 // =================================================================== ABI
 extern "C" {
 
@@ -677,6 +755,7 @@ void fe_default_opts(fe_solver_opts* o) {
   o->inner_max_it = 60;
   o->use_graph = 1;
   o->profile = 0;
+  o->wait_timeout_us = 0;
 }
 
 long long fe_kernel_launches(void) { return g_launches.load(); }
@@ -710,71 +789,7 @@ int fe_hierarchy_refine(const fe_mesh* coarse, int nrefine, int degree, fe_hiera
   FE_REQUIRE(out, FE_ERR_ARG, "null output handle");
   *out = nullptr;
   FE_REQUIRE(coarse, FE_ERR_ARG, "null mesh");
-  FE_REQUIRE(nrefine >= 0 && nrefine <= 8, FE_ERR_ARG, "nrefine must be in [0, 8]");
-  FE_REQUIRE(degree == 1 || degree == 2, FE_ERR_UNSUPPORTED, "degree must be 1 or 2");
-  const long long Nf = (long long)coarse->N << nrefine;
-  const long long nf = (long long)(degree * Nf + 1) * (degree * Nf + 1) * (degree * Nf + 1);
-  FE_REQUIRE(6 * Nf * Nf * Nf < (1ll << 31) && nf < (1ll << 31), FE_ERR_ARG, "finest level too large for 32-bit indices");
-  FE_REQUIRE(fe_device_count() > 0, FE_ERR_CUDA, "no CUDA device");
-  std::unique_ptr<fe_hierarchy> h(new fe_hierarchy());
-  int dev = 0;
-  CUDA_CHECK(cudaGetDevice(&dev));
-  CUDA_CHECK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
-  static std::once_flag mass_once;
-  std::call_once(mass_once, upload_mass_tables);
-  h->N0 = coarse->N;
-  h->nlev = nrefine + 1;
-  h->deg = degree;
-  h->L.resize(h->nlev);
-  cudaStream_t s = 0;
-  for (int l = 0; l < h->nlev; ++l) {
-    Level& L = h->L[l];
-    L.N = coarse->N << l;
-    L.deg = degree;
-    L.nd = degree == 1 ? 4 : 10;
-    L.num = make_numbering(L.N, degree);
-    const int m = degree * L.N;
-    L.n = (m + 1) * (m + 1) * (m + 1);
-    L.C = 6 * L.N * L.N * L.N;
-    L.V = (L.N + 1) * (L.N + 1) * (L.N + 1);
-    L.map.alloc((size_t)L.nd * L.C);
-    L.vx.alloc(L.V);
-    L.vy.alloc(L.V);
-    L.vz.alloc(L.V);
-    L.detj.alloc(L.C);
-    L.kappa.alloc(L.C);
-    L.geo64.alloc((size_t)6 * L.C);
-    L.geo32.alloc((size_t)6 * L.C);
-    L.dinv64.alloc(L.n);
-    L.dinv32.alloc(L.n);
-    for (auto* v : {&L.b64, &L.x64, &L.y64, &L.d64}) v->alloc(L.n);
-    for (auto* v : {&L.b32, &L.x32, &L.y32, &L.d32}) v->alloc(L.n);
-    std::vector<int> bnd;
-    bnd.reserve((size_t)6 * (m + 1) * (m + 1));
-    for (int z = 0; z <= m; ++z)
-      for (int y = 0; y <= m; ++y)
-        for (int x = 0; x <= m; ++x)
-          if (x == 0 || y == 0 || z == 0 || x == m || y == m || z == m) {
-            bnd.push_back(lattice_to_dof(L.num, x, y, z));
-            if (!(z == 0 || z == m || y == 0 || y == m) && x == 0) x = m - 1;  // skip the interior of the row
-          }
-    std::sort(bnd.begin(), bnd.end());
-    L.nb = (int)bnd.size();
-    L.bnd.alloc(L.nb);
-    CUDA_CHECK(cudaMemcpy(L.bnd, bnd.data(), sizeof(int) * L.nb, cudaMemcpyHostToDevice));
-    launch_build_level(L, s);
-  }
-  build_transfer_tables(h->tt, degree);
-  std::vector<int> ch = build_children();
-  h->children.alloc(48);
-  CUDA_CHECK(cudaMemcpy(h->children, ch.data(), sizeof(int) * 48, cudaMemcpyHostToDevice));
-  red_init(h->red, h->sms);
-  const int nF = h->L.back().n;
-  for (auto* v : {&h->x, &h->r, &h->z, &h->p, &h->q, &h->b, &h->e, &h->tmp}) v->alloc(nF);
-  for (auto* v : {&h->r32, &h->z32, &h->p32, &h->q32, &h->e32}) v->alloc(nF);
-  h->cs.flag.alloc(1);
-  set_coefficient_impl(h.get(), nullptr, s);
-  *out = h.release();
+  *out = hierarchy_create(coarse->N, nrefine, degree);
   API_END
 }
 
@@ -784,6 +799,7 @@ void fe_hierarchy_destroy(fe_hierarchy* h) {
   invalidate_graphs(h);
   for (auto& g : h->vgraph)
     if (g.stream) cudaStreamDestroy(g.stream);
+  for (auto& L : h->L) bf16_forget_level(&L);
   red_free(h->red);
   delete h;
 }
@@ -874,6 +890,7 @@ int fe_apply_operator(const fe_hierarchy* hc, int level, const void* x, void* y,
     float* yd = stage_out<float>(h, 1, (float*)y, L.n);
     apply_enqueue(h, level, xd, yd, dtype, s);
     finish_out((float*)y, yd, L.n, s);
+    if (dtype == FE_BF16) FE_REQUIRE(bf16_take_error(s) == 0, FE_ERR_TIMEOUT, "tensor-core apply gave up a bounded wait");
   }
   API_END
 }
@@ -1001,6 +1018,7 @@ int fe_vcycle(const fe_hierarchy* hc, const void* b, void* x, int dtype, void* s
   run_vcycle(h, dtype, false, s);
   CUDA_CHECK(cudaMemcpyAsync(x, fx, es * F.n, cudaMemcpyDefault, s));
   if (!is_device_ptr(x)) CUDA_CHECK(cudaStreamSynchronize(s));
+  if (dtype == FE_BF16) FE_REQUIRE(bf16_take_error(s) == 0, FE_ERR_TIMEOUT, "tensor-core apply gave up a bounded wait");
   API_END
 }
 
@@ -1045,6 +1063,8 @@ int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_
   }
   finish_out(u, ud, F.n, s);
   CUDA_CHECK(cudaStreamSynchronize(s));
+  if (o.precision == FE_PREC_MIXED_BF16)
+    FE_REQUIRE(bf16_take_error(s) == 0, FE_ERR_TIMEOUT, "tensor-core apply gave up a bounded wait");
   st.iterations = res.it;
   st.bnorm = std::sqrt(res.bb);
   st.rel_residual = res.bb > 0 ? std::sqrt(res.rr / res.bb) : 0.0;

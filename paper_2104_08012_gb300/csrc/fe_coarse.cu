@@ -17,7 +17,7 @@ namespace {
 constexpr int kBlock = 256;
 
 template <int DEG>
-__global__ void k_coarse_assemble(int C, const int* __restrict__ map, const double* __restrict__ geo,
+__global__ void k_coarse_assemble(int C, int Cs, const int* __restrict__ map, const double* __restrict__ geo,
                                   const int* __restrict__ dof2int, int nci, double* __restrict__ A) {
   constexpr int ND = DEG == 1 ? 4 : 10;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -26,11 +26,11 @@ __global__ void k_coarse_assemble(int C, const int* __restrict__ map, const doub
   double g[6];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    const int m = map[(size_t)j * C + c];
+    const int m = map[(size_t)j * Cs + c];
     ii[j] = m >= 0 ? dof2int[m] : -1;
   }
 #pragma unroll
-  for (int a = 0; a < 6; ++a) g[a] = geo[(size_t)a * C + c];
+  for (int a = 0; a < 6; ++a) g[a] = geo[(size_t)a * Cs + c];
   for (int j = 0; j < ND; ++j) {
     if (ii[j] < 0) continue;
     double u[ND], out[ND];
@@ -180,9 +180,9 @@ void coarse_setup(fe_hierarchy* h, cudaStream_t s) {
   const size_t nn = (size_t)nci * nci;
   CUDA_CHECK(cudaMemsetAsync(cs.A, 0, sizeof(double) * nn, s));
   if (L0.deg == 1)
-    k_coarse_assemble<1><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.map, L0.geo64, cs.dof2int, nci, cs.A);
+    k_coarse_assemble<1><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci, cs.A);
   else
-    k_coarse_assemble<2><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.map, L0.geo64, cs.dof2int, nci, cs.A);
+    k_coarse_assemble<2><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci, cs.A);
   LAUNCH_CHECK();
   const int w = cs.band;
   for (int j = 0; j + 1 < nci; ++j) {

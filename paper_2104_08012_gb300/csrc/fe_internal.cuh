@@ -139,19 +139,20 @@ __host__ __device__ inline void kuhn_perm(int t, int& p0, int& p1, int& p2) {
 struct Level {
   int N = 0, deg = 0, nd = 0;
   int n = 0, C = 0, V = 0, nb = 0;
+  int Cs = 0;  // row stride of the [row][cell] arrays (map, geo): C rounded up to 128 (TMA rows)
   Numbering num{};
-  DBuf<int> map;          // [nd][C]: dof j >= 0, or -1-j for a Dirichlet dof
+  DBuf<int> map;          // [nd][Cs]: dof j >= 0, or -1-j for a Dirichlet dof
   DBuf<double> vx, vy, vz;  // vertex coordinates
   DBuf<double> detj;      // |det J| per cell
   DBuf<double> kappa;     // cell coefficient
-  DBuf<double> geo64;     // [6][C] kappa*|detJ| J^-1 J^-T / w  (w = 6 for P1, 120 for P2)
+  DBuf<double> geo64;     // [6][Cs] kappa*|detJ| J^-1 J^-T / w  (w = 6 for P1, 120 for P2)
   DBuf<float> geo32;
   DBuf<double> dinv64;    // 1/diag(A)
   DBuf<float> dinv32;
   DBuf<int> bnd;          // Dirichlet dofs
   double lmax = 2.0;
   // V-cycle work vectors (level-owned so the cycle can be captured in a graph)
-  DBuf<double> b64, x64, y64, d64;
+  DBuf<double> b64, x64, y64, d64, w64;
   DBuf<float> b32, x32, y32, d32;
 };
 
@@ -275,11 +276,16 @@ template <typename T>
 void coarse_solve(const fe_hierarchy* h, const T* b, T* x, cudaStream_t s);
 
 // Orchestration helpers (fe_api.cu)
+fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree);  // throws FeError
+void hierarchy_set_coefficient(fe_hierarchy* h, const double* kappa, cudaStream_t s);
+void hierarchy_destroy(fe_hierarchy* h);
 template <typename T>
 void vcycle_enqueue(fe_hierarchy* h, int dtype, cudaStream_t s);  // reads L.b of the finest level, writes L.x
 void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s);
 void apply_bf16_enqueue(const Level& L, const float* x, float* y, cudaStream_t s);
 bool bf16_supported();
+int bf16_take_error(cudaStream_t s);      // nonzero if a tensor-core launch gave up a bounded wait
+void bf16_forget_level(const Level* L);  // drop the cached tensor maps of a level being destroyed
 
 // ------------------------------------------------------- element kernels ---
 // Geometry of one tet from its vertex coordinates: G = |det J| J^-1 J^-T

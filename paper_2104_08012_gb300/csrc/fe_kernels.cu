@@ -18,7 +18,7 @@ __device__ __forceinline__ int decode(int m, bool& bd) {
 
 // ------------------------------------------------------ mesh construction
 template <int DEG>
-__global__ void k_build_map(Numbering num, int C, int* __restrict__ map) {
+__global__ void k_build_map(Numbering num, int C, int Cs, int* __restrict__ map) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const int N = num.N;
@@ -38,7 +38,7 @@ __global__ void k_build_map(Numbering num, int C, int* __restrict__ map) {
   auto put = [&](int j, int x, int y, int z) {
     const int dof = lattice_to_dof(num, x, y, z);
     const bool bd = x == 0 || y == 0 || z == 0 || x == m || y == m || z == m;
-    map[(size_t)j * C + c] = bd ? -1 - dof : dof;
+    map[(size_t)j * Cs + c] = bd ? -1 - dof : dof;
   };
   if (DEG == 1) {
 #pragma unroll
@@ -66,7 +66,7 @@ __global__ void k_build_coords(int N, int V, double* __restrict__ vx, double* __
 
 // ----------------------------------------------------------- geometry
 template <int DEG>
-__global__ void k_geometry(int C, const int* __restrict__ map, const double* __restrict__ vx,
+__global__ void k_geometry(int C, int Cs, const int* __restrict__ map, const double* __restrict__ vx,
                            const double* __restrict__ vy, const double* __restrict__ vz,
                            const double* __restrict__ kappa, double* __restrict__ geo64, float* __restrict__ geo32,
                            double* __restrict__ detj) {
@@ -76,7 +76,7 @@ __global__ void k_geometry(int C, const int* __restrict__ map, const double* __r
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     bool bd;
-    const int v = decode(map[(size_t)k * C + c], bd);  // vertex dofs are numbered first
+    const int v = decode(map[(size_t)k * Cs + c], bd);  // vertex dofs are numbered first
     p[k][0] = vx[v];
     p[k][1] = vy[v];
     p[k][2] = vz[v];
@@ -86,8 +86,8 @@ __global__ void k_geometry(int C, const int* __restrict__ map, const double* __r
   const double s = kappa[c] / (DEG == 1 ? 6.0 : 120.0);
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    geo64[(size_t)a * C + c] = g[a] * s;
-    geo32[(size_t)a * C + c] = (float)(g[a] * s);
+    geo64[(size_t)a * Cs + c] = g[a] * s;
+    geo32[(size_t)a * Cs + c] = (float)(g[a] * s);
   }
   detj[c] = adet;
 }
@@ -98,7 +98,7 @@ __global__ void k_geometry(int C, const int* __restrict__ map, const double* __r
 // geometric factors, scatter-add with atomics.  Extra threads past the last
 // cell copy x -> y on the Dirichlet dofs (identity rows).
 template <int DEG, typename T>
-__global__ void __launch_bounds__(kBlock) k_apply(int C, int Cpad, const int* __restrict__ map,
+__global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const int* __restrict__ map,
                                                   const T* __restrict__ geo, const T* __restrict__ x,
                                                   T* __restrict__ y, int nb, const int* __restrict__ bnd) {
   constexpr int ND = DEG == 1 ? 4 : 10;
@@ -108,12 +108,12 @@ __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cpad, const int* __
     T u[ND];
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
-      idx[j] = __ldg(map + (size_t)j * C + t);
+      idx[j] = __ldg(map + (size_t)j * Cs + t);
       u[j] = idx[j] >= 0 ? __ldg(x + idx[j]) : T(0);
     }
     T g[6];
 #pragma unroll
-    for (int a = 0; a < 6; ++a) g[a] = __ldg(geo + (size_t)a * C + t);
+    for (int a = 0; a < 6; ++a) g[a] = __ldg(geo + (size_t)a * Cs + t);
     T out[ND];
     element_apply<DEG, T>(u, g, out);
 #pragma unroll
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cpad, const int* __
 
 // ------------------------------------------------------------ mass
 template <int DEG>
-__global__ void k_mass(int C, const int* __restrict__ map, const double* __restrict__ detj,
+__global__ void k_mass(int C, int Cs, const int* __restrict__ map, const double* __restrict__ detj,
                        const double* __restrict__ x, double* __restrict__ y) {
   constexpr int ND = DEG == 1 ? 4 : 10;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,7 +137,7 @@ __global__ void k_mass(int C, const int* __restrict__ map, const double* __restr
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     bool bd;
-    idx[j] = decode(map[(size_t)j * C + c], bd);
+    idx[j] = decode(map[(size_t)j * Cs + c], bd);
     u[j] = x[idx[j]];
   }
   const double s = detj[c];
@@ -153,15 +153,15 @@ __global__ void k_mass(int C, const int* __restrict__ map, const double* __restr
 
 // ------------------------------------------------------------ diagonal
 template <int DEG>
-__global__ void k_diag(int C, const int* __restrict__ map, const double* __restrict__ geo, double* __restrict__ diag) {
+__global__ void k_diag(int C, int Cs, const int* __restrict__ map, const double* __restrict__ geo, double* __restrict__ diag) {
   constexpr int ND = DEG == 1 ? 4 : 10;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   double g[6];
 #pragma unroll
-  for (int a = 0; a < 6; ++a) g[a] = geo[(size_t)a * C + c];
+  for (int a = 0; a < 6; ++a) g[a] = geo[(size_t)a * Cs + c];
   for (int i = 0; i < ND; ++i) {
-    const int m = map[(size_t)i * C + c];
+    const int m = map[(size_t)i * Cs + c];
     if (m < 0) continue;
     double u[ND], out[ND];
 #pragma unroll
@@ -188,7 +188,7 @@ __global__ void k_invert(int n, const double* __restrict__ diag, double* __restr
 // g_K = int_K grad(lambda) . grad(u) = lambda_K^T A_K(kappa=1) u_K, with the
 // Dirichlet dofs of u and lambda taken as 0.
 template <int DEG>
-__global__ void k_gradient(int C, const int* __restrict__ map, const double* __restrict__ vx,
+__global__ void k_gradient(int C, int Cs, const int* __restrict__ map, const double* __restrict__ vx,
                            const double* __restrict__ vy, const double* __restrict__ vz, const double* __restrict__ u,
                            const double* __restrict__ lam, double* __restrict__ g) {
   constexpr int ND = DEG == 1 ? 4 : 10;
@@ -199,7 +199,7 @@ __global__ void k_gradient(int C, const int* __restrict__ map, const double* __r
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     bool bd;
-    const int i = decode(map[(size_t)j * C + c], bd);
+    const int i = decode(map[(size_t)j * Cs + c], bd);
     uu[j] = bd ? 0.0 : u[i];
     ll[j] = bd ? 0.0 : lam[i];
     if (j < 4) {
@@ -233,14 +233,14 @@ __global__ void k_dof_coords(Numbering num, int n, double* __restrict__ xyz) {
   xyz[3 * (size_t)i + 2] = z / m;
 }
 
-__global__ void k_centroids(int C, const int* __restrict__ map, const double* __restrict__ vx,
+__global__ void k_centroids(int C, int Cs, const int* __restrict__ map, const double* __restrict__ vx,
                             const double* __restrict__ vy, const double* __restrict__ vz, double* __restrict__ xyz) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   double s[3] = {0, 0, 0};
   for (int k = 0; k < 4; ++k) {
     bool bd;
-    const int v = decode(map[(size_t)k * C + c], bd);
+    const int v = decode(map[(size_t)k * Cs + c], bd);
     s[0] += vx[v];
     s[1] += vy[v];
     s[2] += vz[v];
@@ -386,9 +386,9 @@ __global__ void k_random(int n, uint64_t seed, double* __restrict__ v) {
 // ===================================================================== host
 void launch_build_level(Level& L, cudaStream_t s) {
   if (L.deg == 1)
-    k_build_map<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.map);
+    k_build_map<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.Cs, L.map);
   else
-    k_build_map<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.map);
+    k_build_map<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.Cs, L.map);
   LAUNCH_CHECK();
   k_build_coords<<<ceil_div(L.V, kBlock), kBlock, 0, s>>>(L.N, L.V, L.vx, L.vy, L.vz);
   LAUNCH_CHECK();
@@ -396,10 +396,10 @@ void launch_build_level(Level& L, cudaStream_t s) {
 
 void launch_geometry(Level& L, cudaStream_t s) {
   if (L.deg == 1)
-    k_geometry<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64, L.geo32,
+    k_geometry<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64, L.geo32,
                                                           L.detj);
   else
-    k_geometry<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64, L.geo32,
+    k_geometry<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64, L.geo32,
                                                           L.detj);
   LAUNCH_CHECK();
 }
@@ -410,9 +410,9 @@ static void apply_impl(const Level& L, const T* geo, const T* x, T* y, cudaStrea
   const int Cpad = ceil_div(L.C, kBlock) * kBlock;
   const int grid = ceil_div((long long)Cpad + L.nb, kBlock);
   if (L.deg == 1)
-    k_apply<1, T><<<grid, kBlock, 0, s>>>(L.C, Cpad, L.map, geo, x, y, L.nb, L.bnd);
+    k_apply<1, T><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, geo, x, y, L.nb, L.bnd);
   else
-    k_apply<2, T><<<grid, kBlock, 0, s>>>(L.C, Cpad, L.map, geo, x, y, L.nb, L.bnd);
+    k_apply<2, T><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, geo, x, y, L.nb, L.bnd);
   LAUNCH_CHECK();
 }
 
@@ -422,18 +422,18 @@ void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) { 
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
   if (L.deg == 1)
-    k_mass<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.detj, x, y);
+    k_mass<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, x, y);
   else
-    k_mass<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.detj, x, y);
+    k_mass<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, x, y);
   LAUNCH_CHECK();
 }
 
 void launch_diag(Level& L, double* diag, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(diag, 0, sizeof(double) * (size_t)L.n, s));
   if (L.deg == 1)
-    k_diag<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.geo64, diag);
+    k_diag<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geo64, diag);
   else
-    k_diag<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.geo64, diag);
+    k_diag<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geo64, diag);
   LAUNCH_CHECK();
   if (L.nb > 0) {
     k_diag_finish<<<ceil_div(L.nb, kBlock), kBlock, 0, s>>>(L.n, L.nb, L.bnd, diag);
@@ -445,9 +445,9 @@ void launch_diag(Level& L, double* diag, cudaStream_t s) {
 
 void launch_gradient(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s) {
   if (L.deg == 1)
-    k_gradient<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, u, lam, g);
+    k_gradient<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, u, lam, g);
   else
-    k_gradient<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, u, lam, g);
+    k_gradient<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, u, lam, g);
   LAUNCH_CHECK();
 }
 
@@ -457,7 +457,7 @@ void launch_dof_coords(const Level& L, double* xyz, cudaStream_t s) {
 }
 
 void launch_centroids(const Level& L, double* xyz, cudaStream_t s) {
-  k_centroids<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.map, L.vx, L.vy, L.vz, xyz);
+  k_centroids<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, xyz);
   LAUNCH_CHECK();
 }
 
@@ -558,8 +558,16 @@ static double fact(int k) {
   return f;
 }
 
+void mass_tables_host(double m1[16], double m2[100]);
+
 void upload_mass_tables() {
-  double m1[16];
+  double m1[16], m2[100];
+  mass_tables_host(m1, m2);
+  CUDA_CHECK(cudaMemcpyToSymbol(c_mref1, m1, sizeof(m1)));
+  CUDA_CHECK(cudaMemcpyToSymbol(c_mref2, m2, sizeof(m2)));
+}
+
+void mass_tables_host(double m1[16], double m2[100]) {
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) m1[i * 4 + j] = (i == j ? 2.0 : 1.0) / 120.0;
   // P2 basis as symmetric quadratic forms Q[i][a][b] in the barycentrics
@@ -578,7 +586,6 @@ void upload_mass_tables() {
       Q[e][a][b] = 2.0;
       Q[e][b][a] = 2.0;
     }
-  double m2[100];
   for (int i = 0; i < 10; ++i)
     for (int j = 0; j < 10; ++j) {
       double s = 0.0;
@@ -597,8 +604,6 @@ void upload_mass_tables() {
             }
       m2[i * 10 + j] = s;
     }
-  CUDA_CHECK(cudaMemcpyToSymbol(c_mref1, m1, sizeof(m1)));
-  CUDA_CHECK(cudaMemcpyToSymbol(c_mref2, m2, sizeof(m2)));
 }
 
 namespace {

@@ -77,7 +77,8 @@ def test_mixed_precision_reaches_tight_tolerance(fe):
 # ------------------------------------------------------------------- adjoint
 def _setup_adjoint(fe, N0, nref, k, seed=21):
     h = fe.Hierarchy(N0, nref, k)
-    kappa = I.grf_kappa(h.cell_centroids(), seed=seed)
+    big = h.n_cells() > 100000
+    kappa = I.grf_kappa(h.cell_centroids(), seed=seed, device=DEV if big else None)
     X = h.dof_coordinates()
     f = np.ones(h.n_dofs())
     ud = I.target_field(X)
@@ -156,3 +157,53 @@ def test_adjoint_full_size_taylor(fe):
             h.solve(fd_f, u, rtol=1e-12)
             rem.append(abs(h.objective(u, fd_ud) - J0 - t * (g @ dk)))
         assert 3.0 < rem[0] / rem[1] < 5.0, rem
+
+
+# ------------------------------------------------------- bf16 tensor cores
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("N", [3, 8, 16])
+def test_apply_bf16_tensor_core(fe, k, N):
+    """tcgen05 GEMM-form apply: dofs rounded to bf16, tables exact, FP32 accumulation.
+
+    Rowwise bound 4e-3 |A||x| (bf16 unit roundoff 2^-9 plus FP32 sums); N=3
+    gives 162 cells, i.e. one partial 128-cell tile.
+    """
+    with fe.Hierarchy(N, 0, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=N + 40)
+        h.set_coefficient(dt(kappa))
+        L = O.Level(N, k, kappa)
+        x = I.random_vector(L.n, 50 + N).astype(np.float32)
+        y = torch.empty(L.n, dtype=torch.float32, device=DEV)
+        h.apply_operator(dt(x, torch.float32), y, dtype=fe.FE_BF16)
+        y32 = torch.empty(L.n, dtype=torch.float32, device=DEV)
+        h.apply_operator(dt(x, torch.float32), y32, dtype=fe.FE_F32)
+        torch.cuda.synchronize()
+        xd = x.astype(np.float64)
+        scale = abs(L.A) @ np.abs(xd)
+        got = host(y)
+        err = np.abs(got - L.A @ xd)
+        assert np.all(err <= 4e-3 * scale), np.max(err / scale)
+        # interior rows are exactly the GEMM of the bf16-rounded dofs (up to FP32
+        # accumulation); Dirichlet rows copy the FP32 x (identity rows)
+        xb = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+        inter = ~L.space.boundary
+        err_b = np.abs(got - L.A @ xb)[inter]
+        sb = (abs(L.A) @ np.abs(xb))[inter]
+        assert np.all(err_b <= 2e-5 * sb), np.max(err_b / sb)
+        assert np.array_equal(got[~inter], x[~inter].astype(np.float64))
+
+
+def test_mixed_bf16_refinement(fe):
+    with fe.Hierarchy(4, 2, 2) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=13)
+        h.set_coefficient(dt(kappa))
+        L = O.Level(16, 2, kappa)
+        f = I.sin_product_rhs(L.space.coords)
+        b = O.load_vector(L, f)
+        ue = O.direct_solve(L, b)
+        u = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        st = h.solve(dt(f), u, rtol=1e-8, precision=fe.FE_PREC_MIXED_BF16)
+        uh = host(u)
+        assert np.linalg.norm(L.A @ uh - b) <= 1.0001e-8 * np.linalg.norm(b)
+        assert np.linalg.norm(uh - ue) <= 1e-6 * np.linalg.norm(ue)
+        assert st.outer_iterations >= 2

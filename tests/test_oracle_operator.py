@@ -114,6 +114,14 @@ def test_apply_rows_matches_assembled(k):
 
 
 @pytest.mark.parametrize("k", [1, 2])
+def test_apply_rows_mass_matches_assembled(k):
+    L = O.Level(4, k)
+    x = I.random_vector(L.n, 6)
+    rows = np.random.default_rng(2).choice(L.n, 40, replace=False)
+    assert np.allclose(O.apply_rows_mass(L.space, x, rows), (L.M @ x)[rows], atol=1e-15)
+
+
+@pytest.mark.parametrize("k", [1, 2])
 def test_prolongation_reproduces_polynomials(k):
     c, f = O.Level(2, k), O.Level(4, k)
     P = O.prolongation(c, f)
