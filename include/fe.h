@@ -260,6 +260,29 @@ int fe_solve_batched(fe_batch* batch, const double* const* f_nodal, double* cons
 /* The schedule chosen by the autotuner (or the default before tuning). */
 int fe_batch_schedule(const fe_batch* batch, int* cell_block, int* dof_block, int* ctas_per_sm);
 
+/* ---- allocation-free entry point (no counterpart in the paper) ----
+ *
+ * Deterministic FP64 dot product *out = sum_i x[i] y[i] for callers that may
+ * not allocate device memory: a host application that owns the whole device
+ * memory budget through its own pool, or a latency-critical loop in which
+ * cudaMalloc/cudaFree (which can synchronise the device) are not allowed.
+ * The call allocates nothing: its partial sums live in a static device array
+ * of the library (16384 partials + 2 slots, 128.5 KiB, held by every GPU that
+ * loads the library until the process exits).
+ *   x, y: DEVICE pointers to n doubles (host pointers are rejected with
+ *         FE_ERR_ARG, since staging them would need device memory).
+ *   n:    0 <= n <= 67,108,864 (4096 elements per partial sum); larger n is
+ *         rejected with FE_ERR_ARG.
+ *   out:  one double, device or host pointer; a host `out` makes the call
+ *         synchronise `stream`.
+ * The result does not depend on scheduling (fixed summation order).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call shares the one array and overwrites it: calls that overlap on the
+ * GPU (several streams, or several host threads) race and must be serialised
+ * by the caller. */
+int fe_dot_noalloc(const double* x, const double* y, long long n, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTED = (
     "fe_hierarchy_refine", "fe_hierarchy_destroy", "fe_num_levels", "fe_level_sizes", "fe_dof_coordinates",
     "fe_cell_centroids", "fe_boundary_mask", "fe_set_coefficient", "fe_apply_operator", "fe_apply_mass",
     "fe_diagonal", "fe_lambda_max", "fe_prolong", "fe_restrict", "fe_smooth", "fe_coarse_solve", "fe_vcycle",
-    "fe_load_vector", "fe_solve_poisson", "fe_adjoint_gradient", "fe_objective",
+    "fe_load_vector", "fe_solve_poisson", "fe_adjoint_gradient", "fe_objective", "fe_dot_noalloc",
     "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
 )
 
@@ -98,6 +98,7 @@ def load():
         "fe_solve_poisson": (i, [vp, vp, i, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(SolveStats), vp]),
         "fe_adjoint_gradient": (i, [vp, vp, i, vp, vp, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(d), vp, vp]),
         "fe_objective": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
+        "fe_dot_noalloc": (i, [vp, vp, ll, vp, vp]),
         "fe_batch_create": (i, [i, vp, vp, vp, ctypes.POINTER(vp)]),
         "fe_batch_destroy": (None, [vp]),
         "fe_batch_hierarchy": (i, [vp, i, ctypes.POINTER(vp)]),
@@ -199,6 +200,22 @@ def fe_adjoint_gradient(h, rhs, rhs_kind, u_d, u_ckpt, opts, dJ, u_out=None, str
     _check(load().fe_adjoint_gradient(h, _ptr(rhs), rhs_kind, _ptr(u_d), _ptr(u_ckpt), ctypes.byref(opts), _ptr(dJ),
                                       ctypes.byref(J), _ptr(u_out), _stream(stream)))
     return J.value
+
+
+def fe_dot_noalloc(x, y, n=None, out=None, stream=None):
+    """sum_i x[i] y[i] of two device vectors without any device allocation (see include/fe.h).
+
+    ``out``: optional device tensor / host array of one double; returns the value when ``out`` is None.
+    """
+    if n is None:
+        n = x.numel() if hasattr(x, "numel") else x.size
+    n = int(n)
+    if out is None:
+        res = np.zeros(1)
+        _check(load().fe_dot_noalloc(_ptr(x), _ptr(y), n, _ptr(res), _stream(stream)))
+        return float(res[0])
+    _check(load().fe_dot_noalloc(_ptr(x), _ptr(y), n, _ptr(out), _stream(stream)))
+    return out
 
 
 class Batch:
