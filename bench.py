@@ -46,7 +46,113 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the matvec/mixed/adjoint/batched side measurements")
     return p.parse_args()
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def apply_bytes_per_launch(n, C, nd, val_bytes, geo_bytes):
+    """Algorithmic bytes of one matrix-free application: x read, y zero-fill and write,
+    cell->dof map (int32), per-cell geometric factors (6 values)."""
+    return n * 3 * val_bytes + C * nd * 4 + C * 6 * geo_bytes
+
+
+def time_launches(fn, stream, reps, flush):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    return ms[len(ms) // 2]
+
+
+def extras(fe, I, h, dev, stream, flush):
+    """Side measurements: matvec rates, mixed precision (128^3), adjoint (96^3 P1), batched (64 problems)."""
+    import numpy as np
+    import torch
+    out = {}
+    peak, src = hbm_peak()
+    # ---- matvec on the benchmark's fine level (P2 64^3)
+    n, C = h.n_dofs(), h.n_cells()
+    mv = {}
+    for name, dt, tdt, vb, gb in (("f64", fe.FE_F64, torch.float64, 8, 8), ("f32", fe.FE_F32, torch.float32, 4, 4),
+                                   ("bf16_tensor_core", fe.FE_BF16, torch.float32, 4, 4)):
+        x = torch.rand(n, dtype=tdt, device=dev)
+        y = torch.empty_like(x)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                h.apply_operator(x, y, dtype=dt, stream=stream)
+            ms = time_launches(lambda: h.apply_operator(x, y, dtype=dt, stream=stream), stream, 10, flush)
+        byt = apply_bytes_per_launch(n, C, 10, vb, gb)
+        mv[name] = {"ms": ms, "GDoF_per_s": n / (ms * 1e-3) / 1e9, "GB_per_s": byt / (ms * 1e-3) / 1e9,
+                    "hbm_frac": byt / (ms * 1e-3) / 1e9 / peak, "bytes_per_dof": byt / n}
+    out["matvec_p2_64cubed"] = dict(mv, hbm_peak_gbs=peak, hbm_peak_source=src)
+    # ---- mixed precision on P2 128^3 (5 levels): time to the same 1e-8 FP64 residual
+    h2 = fe.Hierarchy(8, 4, 2)
+    f2 = torch.from_numpy(I.sin_product_rhs(h2.dof_coordinates())).to(dev)
+    ref = torch.empty(h2.n_dofs(), dtype=torch.float64, device=dev)
+    u2 = torch.empty_like(ref)
+    mp = {"workload": "P2 UnitCubeMesh 128^3, 5 levels, rtol 1e-8", "dofs": h2.n_dofs()}
+    for name, prec in (("f64", fe.FE_PREC_F64), ("mixed_f32", fe.FE_PREC_MIXED_F32),
+                       ("mixed_bf16_tensor_core", fe.FE_PREC_MIXED_BF16)):
+        target = ref if prec == fe.FE_PREC_F64 else u2
+        with torch.cuda.stream(stream):
+            h2.solve(f2, target, rtol=1e-8, precision=prec, stream=stream)
+            ms = time_launches(lambda: h2.solve(f2, target, rtol=1e-8, precision=prec, stream=stream), stream, 3, flush)
+            st = h2.solve(f2, target, rtol=1e-8, precision=prec, stream=stream)
+        e = {"ms": ms, "DoF_per_s": h2.n_dofs() / (ms * 1e-3), "iterations": st.iterations,
+             "outer": st.outer_iterations, "rel_residual": st.rel_residual, "fp64_applies": st.fine_applies_f64}
+        if prec != fe.FE_PREC_F64:
+            e["rel_l2_diff_vs_fp64_gpu_solution"] = float(torch.linalg.norm(u2 - ref) / torch.linalg.norm(ref))
+        e["max_nodal_error_vs_exact"] = float((target.cpu() - torch.from_numpy(
+            I.sin_product(h2.dof_coordinates()))).abs().max())
+        mp[name] = e
+    mp["speedup_mixed_f32_vs_f64"] = mp["f64"]["ms"] / mp["mixed_f32"]["ms"]
+    out["mixed_precision_p2_128cubed"] = mp
+    h2.close()
+    del f2, ref, u2
+    # ---- adjoint gradient on P1 96^3 with a GRF kappa (forward + adjoint solve + gradient kernel)
+    h3 = fe.Hierarchy(12, 3, 1)
+    kap = torch.from_numpy(I.grf_kappa(h3.cell_centroids(), device=dev)).to(dev)
+    h3.set_coefficient(kap)
+    X3 = h3.dof_coordinates()
+    f3 = torch.ones(h3.n_dofs(), dtype=torch.float64, device=dev)
+    ud = torch.from_numpy(I.target_field(X3)).to(dev)
+    g = torch.empty(h3.n_cells(), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        h3.adjoint_gradient(f3, ud, g, rtol=1e-8, stream=stream)
+        ms = time_launches(lambda: h3.adjoint_gradient(f3, ud, g, rtol=1e-8, stream=stream), stream, 3, flush)
+    out["adjoint_p1_96cubed"] = {"ms": ms, "cells": h3.n_cells(), "dofs": h3.n_dofs(),
+                                 "what": "forward GMG-PCG + adjoint GMG-PCG + per-cell gradient kernel, rtol 1e-8"}
+    h3.close()
+    # ---- batched: 64 problems, one persistent launch
+    table = I.batched_problem_table()
+    B = fe.Batch([(N // 8, 3, k) for N, k in table])
+    fs, us = [], []
+    for p, hp in enumerate(B.problems):
+        hp.set_coefficient(torch.from_numpy(I.grf_kappa(hp.cell_centroids(), seed=100 + p, device=dev)).to(dev))
+        fs.append(torch.ones(hp.n_dofs(), dtype=torch.float64, device=dev))
+        us.append(torch.empty(hp.n_dofs(), dtype=torch.float64, device=dev))
+    with torch.cuda.stream(stream):
+        B.solve(fs, us, rtol=1e-8, stream=stream)  # first graph solve autotunes
+        ms = time_launches(lambda: B.solve(fs, us, rtol=1e-8, stream=stream), stream, 3, flush)
+        st = B.solve(fs, us, rtol=1e-8, stream=stream)
+    tot = sum(hp.n_dofs() for hp in B.problems)
+    out["batched_64"] = {"ms": ms, "total_dofs": tot, "DoF_per_s": tot / (ms * 1e-3),
+                         "max_iterations": max(s.iterations for s in st),
+                         "max_rel_residual": max(s.rel_residual for s in st), "schedule": B.schedule()}
+    B.close()
+    return out
 
 
 # ------------------------------------------------------------------ clocks
@@ -201,6 +307,12 @@ def run_ours(args, rank, world, local_rank):
         t = torch.tensor([t_ms, te_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_ms, te_ms = t.tolist()
+    extra = None
+    if rank == 0 and not args.no_extras:
+        try:
+            extra = extras(fe, I, h, dev, stream, flush)
+        except Exception as exc:  # side measurements never break the main line
+            extra = {"error": repr(exc)[:300]}
     if rank != 0:
         return None
     apply_ms = sum(s.apply_ms for s in stats) / max(1, sum(s.apply_timed for s in stats))
@@ -225,6 +337,8 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": "nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json"},
         "clocks": clk,
     }
+    if extra is not None:
+        line["extras"] = extra
     return line
 
 

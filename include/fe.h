@@ -64,6 +64,10 @@ extern "C" {
 #define FE_F32 1   /* vectors float, arithmetic FP32 */
 #define FE_BF16 2  /* vectors float; dofs rounded to bf16 and contracted on the tensor cores, FP32 accumulation */
 
+/* ---- arithmetic of FP64 operator applications (fe_set_f64_mode) ---- */
+#define FE_F64_NATIVE 0        /* FP64 FMA on the FP64 pipe */
+#define FE_F64_DOUBLE_FLOAT 1  /* float-pair (hi + lo, ~48-bit) arithmetic on the FP32 pipes, FP64 in and out */
+
 /* ---- preconditioners and precision modes of fe_solve_poisson ---- */
 #define FE_PC_JACOBI 0
 #define FE_PC_GMG 1
@@ -166,6 +170,14 @@ int fe_set_coefficient(fe_hierarchy* h, const double* kappa_cells, void* stream)
  * FE_BF16: float vectors, x rounded to bf16 and contracted on the tensor
  * cores with FP32 accumulation.  x and y must not overlap. */
 int fe_apply_operator(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, void* stream);
+
+/* Choose how FP64 operator applications (dtype FE_F64, the FP64 solver and
+ * V-cycle) compute the element contraction: FE_F64_NATIVE (FP64 FMAs) or
+ * FE_F64_DOUBLE_FLOAT (default: the same formula in float-pair arithmetic with
+ * error-free transformations, about 48 significant bits, several times faster
+ * on GB300 whose FP64 pipe issues 2 FMAs/clk/SM).  Dofs, results and every
+ * other step stay FP64. */
+int fe_set_f64_mode(fe_hierarchy* h, int mode);
 
 /* y = M_l x with the consistent mass matrix (all dofs, no boundary change). */
 int fe_apply_mass(const fe_hierarchy* h, int level, const double* x, double* y, void* stream);

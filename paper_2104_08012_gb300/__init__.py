@@ -16,6 +16,7 @@ from . import build as _build
 FE_OK = 0
 FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_NOMEM, FE_ERR_NO_CONVERGENCE, FE_ERR_NAN, FE_ERR_TIMEOUT, FE_ERR_UNSUPPORTED = range(-1, -8, -1)
 FE_F64, FE_F32, FE_BF16 = 0, 1, 2
+FE_F64_NATIVE, FE_F64_DOUBLE_FLOAT = 0, 1
 FE_PC_JACOBI, FE_PC_GMG = 0, 1
 FE_PREC_F64, FE_PREC_MIXED_F32, FE_PREC_MIXED_BF16 = 0, 1, 2
 FE_RHS_LOAD, FE_RHS_NODAL_F = 0, 1
@@ -27,7 +28,7 @@ EXPORTED = (
     "fe_cell_centroids", "fe_boundary_mask", "fe_set_coefficient", "fe_apply_operator", "fe_apply_mass",
     "fe_diagonal", "fe_lambda_max", "fe_prolong", "fe_restrict", "fe_smooth", "fe_coarse_solve", "fe_vcycle",
     "fe_load_vector", "fe_solve_poisson", "fe_adjoint_gradient", "fe_objective", "fe_dot_noalloc",
-    "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
+    "fe_set_f64_mode", "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
 )
 
 
@@ -99,6 +100,7 @@ def load():
         "fe_adjoint_gradient": (i, [vp, vp, i, vp, vp, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(d), vp, vp]),
         "fe_objective": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
         "fe_dot_noalloc": (i, [vp, vp, ll, vp, vp]),
+        "fe_set_f64_mode": (i, [vp, i]),
         "fe_batch_create": (i, [i, vp, vp, vp, ctypes.POINTER(vp)]),
         "fe_batch_destroy": (None, [vp]),
         "fe_batch_hierarchy": (i, [vp, i, ctypes.POINTER(vp)]),
@@ -349,6 +351,9 @@ class Hierarchy:
         return v.value
 
     # -- operations on caller-owned vectors (torch tensors or numpy arrays)
+    def set_f64_mode(self, mode):
+        _check(self._L.fe_set_f64_mode(self.h, mode))
+
     def set_coefficient(self, kappa=None, stream=None):
         fe_set_coefficient(self.h, kappa, stream)
 

@@ -264,7 +264,7 @@ static double estimate_lmax(fe_hierarchy* h, int l, int steps, cudaStream_t s) {
   if (!(R.h_scal[S_RZ] > 0.0)) return 1.0;  // no interior dofs: D^-1 A is the identity
   std::vector<double> al, be;
   for (int it = 0; it < steps; ++it) {
-    launch_apply64(L, p, q, s);
+    apply_enqueue(h, l, p, q, FE_F64, s);
     launch_cg_alpha<double>(R, n, p, q, s);
     launch_cg_update<double>(R, n, x, r, p, q, L.dinv64, z, s);
     launch_cg_update_p<double>(R, n, p, z, s);
@@ -311,7 +311,9 @@ template <> const float* lv_dinv<float>(const Level& L) { return L.dinv32; }
 
 void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s) {
   const Level& L = h->L[level];
-  if (dtype == FE_F64)
+  if (dtype == FE_F64 && h->f64_mode == FE_F64_DOUBLE_FLOAT)
+    launch_apply64_df(L, (const double*)x, (double*)y, s);
+  else if (dtype == FE_F64)
     launch_apply64(L, (const double*)x, (double*)y, s);
   else if (dtype == FE_F32)
     launch_apply32(L, (const float*)x, (float*)y, s);
@@ -491,7 +493,7 @@ static PcgResult pcg64(fe_hierarchy* h, const double* b, double* x, const fe_sol
       break;
     }
     timer.start(s);
-    launch_apply64(F, p, q, s);
+    apply_enqueue(h, h->nlev - 1, p, q, FE_F64, s);
     timer.stop(s);
     ++res.applies;
     launch_cg_alpha<double>(R, n, p, q, s);
@@ -589,7 +591,7 @@ static PcgResult refine(fe_hierarchy* h, const double* b, double* x, const fe_so
         break;
       }
       launch_add_scaled<float>(n, h->e32, R.scal + S_TMP0, x, s);
-      launch_apply64(F, x, y, s);
+      apply_enqueue(h, h->nlev - 1, x, y, FE_F64, s);
       ++res.applies;
       launch_sub64(n, b, y, r, s);
       launch_dot<double>(R, n, r, r, S_DOT, s);
@@ -625,6 +627,7 @@ static void set_coefficient_impl(fe_hierarchy* h, const double* kappa, cudaStrea
   for (int l = h->nlev - 1; l >= 1; --l) launch_coarsen_kappa(h->L[l - 1], h->L[l], h->children, s);
   for (int l = 0; l < h->nlev; ++l) {
     launch_geometry(h->L[l], s);
+    launch_split_geometry(h->L[l], s);
     launch_diag(h->L[l], h->tmp, s);
   }
   for (int l = 0; l < h->nlev; ++l) h->L[l].lmax = estimate_lmax(h, l, 20, s);
@@ -703,6 +706,7 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     L.geo64.alloc((size_t)6 * L.Cs);
     L.geo32.alloc((size_t)6 * L.Cs);
     CUDA_CHECK(cudaMemset(L.geo32, 0, sizeof(float) * (size_t)6 * L.Cs));
+    L.geodf.alloc((size_t)6 * L.Cs);
     L.dinv64.alloc(L.n);
     L.dinv32.alloc(L.n);
     for (auto* v : {&L.b64, &L.x64, &L.y64, &L.d64, &L.w64}) v->alloc(L.n);
@@ -891,6 +895,18 @@ int fe_apply_operator(const fe_hierarchy* hc, int level, const void* x, void* y,
     apply_enqueue(h, level, xd, yd, dtype, s);
     finish_out((float*)y, yd, L.n, s);
     if (dtype == FE_BF16) FE_REQUIRE(bf16_take_error(s) == 0, FE_ERR_TIMEOUT, "tensor-core apply gave up a bounded wait");
+  }
+  API_END
+}
+
+int fe_set_f64_mode(fe_hierarchy* h, int mode) {
+  API_BEGIN
+  FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
+  FE_REQUIRE(mode == FE_F64_NATIVE || mode == FE_F64_DOUBLE_FLOAT, FE_ERR_ARG, "unknown FP64 mode");
+  if (h->f64_mode != mode) {
+    CUDA_CHECK(cudaDeviceSynchronize());
+    h->f64_mode = mode;
+    invalidate_graphs(h);
   }
   API_END
 }

@@ -1,0 +1,212 @@
+// FP64-accurate operator application computed on the FP32 pipes.
+//
+// GB300 issues about 2 FP64 FMAs per clock per SM against 128 FP32 operations,
+// so the FP64 element contraction (124 FP64 instructions per P2 tet) is bound
+// by the FP64 pipe.  This variant evaluates the same element formula in
+// double-float arithmetic: every value is an unevaluated sum hi + lo of two
+// floats, additions use Knuth's TwoSum and products Dekker/Kahan's FMA-based
+// TwoProd (Dekker 1971; Hida, Li & Bailey's "double-double" algorithms
+// restated for float pairs), giving about 48 significant bits.  The dofs are
+// split into float pairs and the contributions joined back to FP64 by integer
+// bit manipulation, so the FP64 pipe only performs one addition per scattered
+// contribution; vectors, reductions, transfers, smoother updates and the
+// coarse solve stay in FP64.
+#include "fe_internal.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+struct DF {
+  float hi, lo;
+  __device__ __forceinline__ DF() : hi(0.0f), lo(0.0f) {}
+  __device__ __forceinline__ explicit DF(float v) : hi(v), lo(0.0f) {}
+  __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit DF(int v) : hi((float)v), lo(0.0f) {}
+};
+
+// |s| >= |e| assumed; s + e = h + l exactly.
+__device__ __forceinline__ DF quick_two_sum(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return DF(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+// a + b = s + e exactly (Knuth).
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+  return DF(s, e);
+}
+
+__device__ __forceinline__ DF operator+(DF x, DF y) {
+  const DF t = two_sum(x.hi, y.hi);
+  return quick_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ DF operator-(DF x) { return DF(-x.hi, -x.lo); }
+__device__ __forceinline__ DF operator-(DF x, DF y) { return x + (-y); }
+__device__ __forceinline__ DF& operator+=(DF& x, DF y) { return x = x + y; }
+__device__ __forceinline__ DF& operator-=(DF& x, DF y) { return x = x - y; }
+
+// x * y with the exact product error of the leading terms from an FMA.
+__device__ __forceinline__ DF operator*(DF x, DF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return quick_two_sum(p, e);
+}
+
+// Exact scaling by a power of two.
+__device__ __forceinline__ DF scale2(DF x, float k) { return DF(__fmul_rn(x.hi, k), __fmul_rn(x.lo, k)); }
+// x * k for a small integer k (TwoProd of the leading term).
+__device__ __forceinline__ DF scalek(DF x, float k) {
+  const float p = __fmul_rn(x.hi, k);
+  const float e = __fmaf_rn(x.lo, k, __fmaf_rn(x.hi, k, -p));
+  return quick_two_sum(p, e);
+}
+
+// h = G t for the symmetric G stored (00, 01, 02, 11, 12, 22).
+__device__ __forceinline__ void gmul(const DF (&g)[6], DF t0, DF t1, DF t2, DF& h0, DF& h1, DF& h2) {
+  h0 = g[0] * t0 + g[1] * t1 + g[2] * t2;
+  h1 = g[1] * t0 + g[3] * t1 + g[4] * t2;
+  h2 = g[2] * t0 + g[4] * t1 + g[5] * t2;
+}
+
+// The P2 vertex-gradient element of fe_internal.cuh written out without
+// loops (u: 4 vertices then edges 01,02,03,12,13,23), so that every float
+// pair stays in registers.
+__device__ __forceinline__ void p2_element_df(const DF (&u)[10], const DF (&g)[6], DF (&y)[10]) {
+  const DF f01 = scale2(u[4], 4.f), f02 = scale2(u[5], 4.f), f03 = scale2(u[6], 4.f);
+  const DF f12 = scale2(u[7], 4.f), f13 = scale2(u[8], 4.f), f23 = scale2(u[9], 4.f);
+  // c_wv = 4 u_wv - u_v, c_ww = 3 u_w;  d_w = (c_w1 - c_w0, c_w2 - c_w0, c_w3 - c_w0)
+  const DF c00 = scalek(u[0], 3.f), c01 = f01 - u[1], c02 = f02 - u[2], c03 = f03 - u[3];
+  const DF c10 = f01 - u[0], c11 = scalek(u[1], 3.f), c12 = f12 - u[2], c13 = f13 - u[3];
+  const DF c20 = f02 - u[0], c21 = f12 - u[1], c22 = scalek(u[2], 3.f), c23 = f23 - u[3];
+  const DF c30 = f03 - u[0], c31 = f13 - u[1], c32 = f23 - u[2], c33 = scalek(u[3], 3.f);
+  const DF d00 = c01 - c00, d01 = c02 - c00, d02 = c03 - c00;
+  const DF d10 = c11 - c10, d11 = c12 - c10, d12 = c13 - c10;
+  const DF d20 = c21 - c20, d21 = c22 - c20, d22 = c23 - c20;
+  const DF d30 = c31 - c30, d31 = c32 - c30, d32 = c33 - c30;
+  const DF S0 = (d00 + d10) + (d20 + d30), S1 = (d01 + d11) + (d21 + d31), S2 = (d02 + d12) + (d22 + d32);
+  DF b01, b02, b03, b11, b12, b13, b21, b22, b23, b31, b32, b33;  // cb_wv = h_w[v-1]
+  gmul(g, S0 + d00, S1 + d01, S2 + d02, b01, b02, b03);
+  gmul(g, S0 + d10, S1 + d11, S2 + d12, b11, b12, b13);
+  gmul(g, S0 + d20, S1 + d21, S2 + d22, b21, b22, b23);
+  gmul(g, S0 + d30, S1 + d31, S2 + d32, b31, b32, b33);
+  const DF b00 = -(b01 + b02 + b03), b10 = -(b11 + b12 + b13), b20 = -(b21 + b22 + b23), b30 = -(b31 + b32 + b33);
+  // y_v = 3 cb_vv - sum_{w != v} cb_wv;  y_(ab) = 4 (cb_ab + cb_ba)
+  y[0] = scalek(b00, 3.f) - ((b10 + b20) + b30);
+  y[1] = scalek(b11, 3.f) - ((b01 + b21) + b31);
+  y[2] = scalek(b22, 3.f) - ((b02 + b12) + b32);
+  y[3] = scalek(b33, 3.f) - ((b03 + b13) + b23);
+  y[4] = scale2(b01 + b10, 4.f);
+  y[5] = scale2(b02 + b20, 4.f);
+  y[6] = scale2(b03 + b30, 4.f);
+  y[7] = scale2(b12 + b21, 4.f);
+  y[8] = scale2(b13 + b31, 4.f);
+  y[9] = scale2(b23 + b32, 4.f);
+}
+
+__device__ __forceinline__ void p1_element_df(const DF (&u)[4], const DF (&g)[6], DF (&y)[4]) {
+  DF h0, h1, h2;
+  gmul(g, u[1] - u[0], u[2] - u[0], u[3] - u[0], h0, h1, h2);
+  y[1] = h0;
+  y[2] = h1;
+  y[3] = h2;
+  y[0] = -(h0 + h1 + h2);
+}
+
+template <int DEG>
+__device__ __forceinline__ void element_df(const DF (&u)[DEG == 1 ? 4 : 10], const DF (&g)[6],
+                                           DF (&y)[DEG == 1 ? 4 : 10]) {
+  if constexpr (DEG == 1)
+    p1_element_df(u, g, y);
+  else
+    p2_element_df(u, g, y);
+}
+
+// double -> float pair by bit manipulation: hi keeps the leading 24 bits of
+// the significand (truncated), lo the next 24 (rounded); |x| < 2^-126 flushes
+// to 0, non-finite x gives a NaN pair.
+__device__ __forceinline__ DF split(double x) {
+  const unsigned int h32 = (unsigned int)__double2hiint(x), l32 = (unsigned int)__double2loint(x);
+  const unsigned int e = (h32 >> 20) & 0x7FFu;
+  const unsigned int sgn = h32 & 0x80000000u;
+  if (e == 0x7FFu) return DF(__int_as_float(0x7fc00000), 0.0f);
+  if (e <= 896u) return DF(__uint_as_float(sgn), 0.0f);
+  const unsigned int hb = sgn | ((e - 896u) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
+  const float scale = e > 948u ? __uint_as_float((e - 948u) << 23) : 0.0f;  // 2^(e - 1075)
+  const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
+  return DF(__uint_as_float(hb), __uint_as_float(__float_as_uint(lo) | sgn));
+}
+
+// exact float -> double by bit manipulation (denormal floats flush to 0)
+__device__ __forceinline__ double widen(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int ef = (b >> 23) & 0xFFu;
+  const unsigned int sgn = b & 0x80000000u;
+  if (ef == 0u) return __hiloint2double((int)sgn, 0);
+  const unsigned int eh = ef == 0xFFu ? 0x7FFu : ef + 896u;
+  return __hiloint2double((int)(sgn | (eh << 20) | ((b & 0x7FFFFFu) >> 3)), (int)((b & 7u) << 29));
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kBlock) k_apply_df(int C, int Cs, int Cpad, const int* __restrict__ map,
+                                                     const float2* __restrict__ geo, const double* __restrict__ x,
+                                                     double* __restrict__ y, int nb, const int* __restrict__ bnd) {
+  constexpr int ND = DEG == 1 ? 4 : 10;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < C) {
+    int idx[ND];
+    DF u[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      idx[j] = __ldg(map + (size_t)j * Cs + t);
+      const double v = idx[j] >= 0 ? __ldg(x + idx[j]) : 0.0;
+      u[j] = split(v);
+    }
+    DF g[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const float2 v = __ldg(geo + (size_t)a * Cs + t);
+      g[a] = DF(v.x, v.y);
+    }
+    DF out[ND];
+    element_df<DEG>(u, g, out);
+#pragma unroll
+    for (int j = 0; j < ND; ++j)
+      if (idx[j] >= 0) atomicAdd(y + idx[j], widen(out[j].hi) + widen(out[j].lo));
+  } else if (t >= Cpad && t - Cpad < nb) {
+    const int i = bnd[t - Cpad];
+    y[i] = x[i];
+  }
+}
+
+__global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, float2* __restrict__ geodf) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  for (int a = 0; a < 6; ++a) {
+    const double g = geo64[(size_t)a * Cs + c];
+    const float hi = (float)g;
+    geodf[(size_t)a * Cs + c] = make_float2(hi, (float)(g - (double)hi));
+  }
+}
+
+}  // namespace
+
+void launch_split_geometry(Level& L, cudaStream_t s) {
+  k_split_geo<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, L.geodf);
+  LAUNCH_CHECK();
+}
+
+void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s) {
+  CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
+  const int Cpad = ceil_div(L.C, kBlock) * kBlock;
+  const int grid = ceil_div((long long)Cpad + L.nb, kBlock);
+  if (L.deg == 1)
+    k_apply_df<1><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, L.geodf, x, y, L.nb, L.bnd);
+  else
+    k_apply_df<2><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, L.geodf, x, y, L.nb, L.bnd);
+  LAUNCH_CHECK();
+}

@@ -147,6 +147,7 @@ struct Level {
   DBuf<double> kappa;     // cell coefficient
   DBuf<double> geo64;     // [6][Cs] kappa*|detJ| J^-1 J^-T / w  (w = 6 for P1, 120 for P2)
   DBuf<float> geo32;
+  DBuf<float2> geodf;     // [6][Cs] geo64 split into float pairs (hi, lo) for the double-float apply
   DBuf<double> dinv64;    // 1/diag(A)
   DBuf<float> dinv32;
   DBuf<int> bnd;          // Dirichlet dofs
@@ -218,6 +219,7 @@ struct fe_hierarchy {
   DBuf<unsigned char> stage[4];
   GraphCache vgraph[3];  // per dtype
   bool lmax_valid = false;
+  int f64_mode = FE_F64_DOUBLE_FLOAT;  // arithmetic of FP64 operator applications
 };
 
 // ------------------------------------------------------- launch wrappers ---
@@ -226,6 +228,8 @@ void launch_build_level(Level& L, cudaStream_t s);
 void launch_geometry(Level& L, cudaStream_t s);
 void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s);
+void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s);
+void launch_split_geometry(Level& L, cudaStream_t s);
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_diag(Level& L, double* diag_out, cudaStream_t s);
 void launch_gradient(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s);

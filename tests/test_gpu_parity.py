@@ -60,8 +60,11 @@ def test_mesh_queries_match_oracle(fe, k, N):
 @pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("N", [1, 2, 3, 5, 8])
 @pytest.mark.parametrize("coef", ["one", "grf"])
-def test_apply_f64(fe, k, N, coef):
+@pytest.mark.parametrize("mode", ["native", "double_float"])
+def test_apply_f64(fe, k, N, coef, mode):
+    """FP64 operator in both arithmetics: FP64 FMAs and float-pair (~48-bit) on the FP32 pipes."""
     with fe.Hierarchy(N, 0, k) as h:
+        h.set_f64_mode(fe.FE_F64_NATIVE if mode == "native" else fe.FE_F64_DOUBLE_FLOAT)
         kappa = None if coef == "one" else I.grf_kappa(h.cell_centroids(), seed=N)
         h.set_coefficient(None if kappa is None else dt(kappa))
         L = O.Level(N, k, kappa)
@@ -86,6 +89,25 @@ def test_apply_f32(fe, k):
         torch.cuda.synchronize()
         xd = x.astype(np.float64)
         assert_rowwise(host(y), L.A @ xd, abs(L.A) @ np.abs(xd), 1e-5, "fp32 apply")
+
+
+def test_double_float_edge_values(fe):
+    """The float-pair split handles zeros, tiny, huge, negative and NaN dofs like FP64 (to 48 bits)."""
+    with fe.Hierarchy(3, 0, 2) as h:
+        L = O.Level(3, 2)
+        x = I.random_vector(L.n, 77)
+        x[::7] = 0.0
+        x[1::11] *= 1e-30
+        x[2::13] *= 1e30
+        x[3::17] = -np.abs(x[3::17])
+        y = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        h.apply_operator(dt(x), y)
+        torch.cuda.synchronize()
+        assert_rowwise(host(y), L.A @ x, abs(L.A) @ np.abs(x), 1e-13, "double-float edge values")
+        xn = x.copy()
+        xn[L.space.boundary.argmin()] = np.nan  # an interior dof
+        h.apply_operator(dt(xn), y)
+        assert torch.isnan(y).any()
 
 
 def test_apply_host_pointers_match_device(fe):
@@ -223,8 +245,10 @@ def test_config0_jacobi_pcg(fe):
 
 
 @pytest.mark.parametrize("k,N0,nref", [(1, 2, 2), (2, 2, 2), (2, 3, 1)])
-def test_gmg_pcg_solution_parity(fe, k, N0, nref):
+@pytest.mark.parametrize("mode", ["native", "double_float"])
+def test_gmg_pcg_solution_parity(fe, k, N0, nref, mode):
     with fe.Hierarchy(N0, nref, k) as h:
+        h.set_f64_mode(fe.FE_F64_NATIVE if mode == "native" else fe.FE_F64_DOUBLE_FLOAT)
         kappa = I.grf_kappa(h.cell_centroids(), seed=6)
         h.set_coefficient(dt(kappa))
         L = O.Level(N0 * 2 ** nref, k, kappa)
