@@ -33,10 +33,18 @@ WORKLOAD = {"workload": "poisson_p2_unitcube64_gmg4_fp64", "mesh": "UnitCubeMesh
             "degree": 2, "levels": 4, "coarse_mesh": 8, "cells": 1572864, "dofs": 2146689, "rtol": 1e-8,
             "preconditioner": "GMG V(2,2) Chebyshev-Jacobi + FP64 Cholesky coarse", "l2_between_steps": "flushed"}
 SAMPLE = {"N0": 8, "nrefine": 2, "degree": 2}  # oracle bounded sample: P2 32^3, 3 levels
-# FP64 flops of one P2 element application in the matrix-free kernel (c, d, S,
-# four G-products, transpose: see the element routine), per tet.
-FLOPS_PER_CELL_P2 = 160
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2)
+F64_MODE = 1  # FE_F64_DOUBLE_FLOAT: the library default for FP64 operator applications
+# DRAM bytes per launch of the dominant kernel on this workload from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by FP64 mode; None until captured
+TRAFFIC = {0: 188.2e6}
+# Flops of one P2 element application (c, d, S, four G-products, transpose;
+# an FMA counts 2), per tet: 151 in the FP64 formula; the double-float form of
+# the same formula costs 1493 FP32 flops (95 float-pair additions x 11, 36
+# float-pair products x 10, scalings 88).
+FLOPS_PER_CELL_P2_F64 = 151
+FLOPS_PER_CELL_P2_DF = 1493
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64: 152 SMs x 2 FMA/clk/SM x 2 flops x 2.07 GHz (recipe table)
+FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (recipe unit counts and clock)
 
 
 def parse():
@@ -97,6 +105,17 @@ def extras(fe, I, h, dev, stream, flush):
         mv[name] = {"ms": ms, "GDoF_per_s": n / (ms * 1e-3) / 1e9, "GB_per_s": byt / (ms * 1e-3) / 1e9,
                     "hbm_frac": byt / (ms * 1e-3) / 1e9 / peak, "bytes_per_dof": byt / n}
     out["matvec_p2_64cubed"] = dict(mv, hbm_peak_gbs=peak, hbm_peak_source=src)
+    # ---- the benchmark solve with the native FP64 operator, for comparison
+    u_n = torch.empty(n, dtype=torch.float64, device=dev)
+    f_n = torch.from_numpy(I.sin_product_rhs(h.dof_coordinates())).to(dev)
+    h.set_f64_mode(fe.FE_F64_NATIVE)
+    with torch.cuda.stream(stream):
+        h.solve(f_n, u_n, rtol=1e-8, stream=stream)
+        ms = time_launches(lambda: h.solve(f_n, u_n, rtol=1e-8, stream=stream), stream, 3, flush)
+        st = h.solve(f_n, u_n, rtol=1e-8, stream=stream)
+    h.set_f64_mode(F64_MODE)
+    out["native_fp64_operator_solve"] = {"ms": ms, "DoF_per_s": n / (ms * 1e-3), "iterations": st.iterations,
+                                         "rel_residual": st.rel_residual}
     # ---- mixed precision on P2 128^3 (5 levels): time to the same 1e-8 FP64 residual
     h2 = fe.Hierarchy(8, 4, 2)
     f2 = torch.from_numpy(I.sin_product_rhs(h2.dof_coordinates())).to(dev)
@@ -106,10 +125,15 @@ def extras(fe, I, h, dev, stream, flush):
     for name, prec in (("f64", fe.FE_PREC_F64), ("mixed_f32", fe.FE_PREC_MIXED_F32),
                        ("mixed_bf16_tensor_core", fe.FE_PREC_MIXED_BF16)):
         target = ref if prec == fe.FE_PREC_F64 else u2
-        with torch.cuda.stream(stream):
-            h2.solve(f2, target, rtol=1e-8, precision=prec, stream=stream)
-            ms = time_launches(lambda: h2.solve(f2, target, rtol=1e-8, precision=prec, stream=stream), stream, 3, flush)
-            st = h2.solve(f2, target, rtol=1e-8, precision=prec, stream=stream)
+        try:
+            with torch.cuda.stream(stream):
+                h2.solve(f2, target, rtol=1e-8, precision=prec, max_it=30, stream=stream)
+                ms = time_launches(lambda: h2.solve(f2, target, rtol=1e-8, precision=prec, max_it=30, stream=stream),
+                                   stream, 3, flush)
+                st = h2.solve(f2, target, rtol=1e-8, precision=prec, max_it=30, stream=stream)
+        except fe.FeError as exc:
+            mp[name] = {"error": str(exc)}
+            continue
         e = {"ms": ms, "DoF_per_s": h2.n_dofs() / (ms * 1e-3), "iterations": st.iterations,
              "outer": st.outer_iterations, "rel_residual": st.rel_residual, "fp64_applies": st.fine_applies_f64}
         if prec != fe.FE_PREC_F64:
@@ -117,7 +141,8 @@ def extras(fe, I, h, dev, stream, flush):
         e["max_nodal_error_vs_exact"] = float((target.cpu() - torch.from_numpy(
             I.sin_product(h2.dof_coordinates()))).abs().max())
         mp[name] = e
-    mp["speedup_mixed_f32_vs_f64"] = mp["f64"]["ms"] / mp["mixed_f32"]["ms"]
+    if "ms" in mp.get("f64", {}) and "ms" in mp.get("mixed_f32", {}):
+        mp["speedup_mixed_f32_vs_f64"] = mp["f64"]["ms"] / mp["mixed_f32"]["ms"]
     out["mixed_precision_p2_128cubed"] = mp
     h2.close()
     del f2, ref, u2
@@ -248,6 +273,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     t_setup = time.time()
     h = fe.Hierarchy(WORKLOAD["coarse_mesh"], WORKLOAD["levels"] - 1, WORKLOAD["degree"])
+    h.set_f64_mode(F64_MODE)
     n, C = h.n_dofs(), h.n_cells()
     assert n == WORKLOAD["dofs"] and C == WORKLOAD["cells"]
     f_host = I.sin_product_rhs(h.dof_coordinates())
@@ -316,7 +342,12 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return None
     apply_ms = sum(s.apply_ms for s in stats) / max(1, sum(s.apply_timed for s in stats))
-    flops = FLOPS_PER_CELL_P2 * C
+    if F64_MODE == fe.FE_F64_DOUBLE_FLOAT:
+        kname, flops, peak = "k_apply_df<2> (FP64 operator in double-float on the FP32 pipes)", FLOPS_PER_CELL_P2_DF * C, FP32_PEAK_TFLOPS
+        psrc = "nominal FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (recipe unit counts and clock); no measured FP32 peak"
+    else:
+        kname, flops, peak = "k_apply<2,double> (native FP64 operator)", FLOPS_PER_CELL_P2_F64 * C, FP64_PEAK_TFLOPS
+        psrc = "nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json"
     achieved = flops / (apply_ms * 1e-3) / 1e12
     value = world * n * args.steps / (t_ms * 1e-3)
     line = {
@@ -324,17 +355,18 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (manufactured sin-product right-hand side, kappa = 1)",
-        "config": dict(WORKLOAD, parallelism=f"replicas{world}"),
+        "config": dict(WORKLOAD, parallelism=f"replicas{world}",
+                       f64_operator="double-float element arithmetic (~48 bits) on FP32 pipes; FP64 vectors, "
+                                    "reductions, transfers, smoother, coarse Cholesky" if F64_MODE == 1 else "native FP64"),
         "iterations": stats[-1].iterations, "rel_residual": stats[-1].rel_residual,
         "max_nodal_error_vs_exact": nodal_err, "setup_s": setup_s,
         "e2e": {"value": world * n * args.steps / (te_ms * 1e-3), "unit": "DoF/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_apply<2,double> (FP64 P2 matrix-free operator)", "bound": "alu",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "apply_ms": apply_ms, "flops_per_launch": flops,
-                     "peak_source": "nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json"},
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": TRAFFIC.get(F64_MODE), "apply_ms": apply_ms,
+                     "flops_per_launch": flops, "fp64_formula_flops_per_launch": FLOPS_PER_CELL_P2_F64 * C,
+                     "peak_source": psrc},
         "clocks": clk,
     }
     if extra is not None:

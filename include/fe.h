@@ -85,7 +85,8 @@ typedef struct fe_batch fe_batch;
 
 typedef struct fe_solver_opts {
   double rtol;        /* stop when ||b - A u||_2 <= rtol ||b||_2 (unpreconditioned 2-norm) */
-  int max_it;         /* CG iteration limit (outer refinement steps for mixed precision) */
+  int max_it;         /* CG iteration limit (mixed precision: outer refinement steps, at most 100; refinement
+                         also stops with FE_ERR_NO_CONVERGENCE after 3 steps in a row that reduce ||r|| < 2x) */
   int precond;        /* FE_PC_JACOBI or FE_PC_GMG */
   int precision;      /* FE_PREC_* */
   int cheb_steps;     /* Chebyshev iterations per smoothing (2 in the paper's options) */

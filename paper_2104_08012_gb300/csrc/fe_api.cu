@@ -572,13 +572,17 @@ static PcgResult refine(fe_hierarchy* h, const double* b, double* x, const fe_so
   res.bb = R.h_scal[S_BB];
   double rr = res.bb;
   const double bb = res.bb;
-  int outer = 0, inner_total = 0, low_applies = 0;
+  int outer = 0, inner_total = 0, low_applies = 0, stalled = 0;
+  const int max_outer = std::min(o.max_it, 100);
   if (bb > 0.0) {
     while (rr > o.rtol * o.rtol * bb) {
-      if (outer >= o.max_it) {
+      // stop when the limit is reached or refinement stagnates (3 steps in a row
+      // reducing ||r|| by less than 2x: the low-precision solve no longer helps)
+      if (outer >= max_outer || stalled >= 3) {
         res.status = FE_ERR_NO_CONVERGENCE;
         break;
       }
+      const double rr_prev = rr;
       // r32 = r / ||r||; ||r||^2 parked in S_TMP0 for the correction
       CUDA_CHECK(cudaMemcpyAsync(R.scal + S_TMP0, R.scal + (outer == 0 ? S_BB : S_DOT), sizeof(double),
                                  cudaMemcpyDeviceToDevice, s));
@@ -603,6 +607,7 @@ static PcgResult refine(fe_hierarchy* h, const double* b, double* x, const fe_so
         res.status = FE_ERR_NAN;
         break;
       }
+      stalled = (rr > 0.25 * rr_prev) ? stalled + 1 : 0;
     }
   }
   res.rr = rr;
@@ -696,6 +701,9 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     L.C = 6 * L.N * L.N * L.N;
     L.V = (L.N + 1) * (L.N + 1) * (L.N + 1);
     L.Cs = (L.C + 127) / 128 * 128;
+    L.Q = L.N * L.N * L.N;
+    L.Qs = (L.Q + 127) / 128 * 128;
+    L.cmap.alloc((size_t)(degree + 1) * (degree + 1) * (degree + 1) * L.Qs);
     L.map.alloc((size_t)L.nd * L.Cs);
     CUDA_CHECK(cudaMemset(L.map, 0, sizeof(int) * (size_t)L.nd * L.Cs));
     L.vx.alloc(L.V);

@@ -45,8 +45,6 @@ __device__ __forceinline__ DF operator+(DF x, DF y) {
 }
 __device__ __forceinline__ DF operator-(DF x) { return DF(-x.hi, -x.lo); }
 __device__ __forceinline__ DF operator-(DF x, DF y) { return x + (-y); }
-__device__ __forceinline__ DF& operator+=(DF& x, DF y) { return x = x + y; }
-__device__ __forceinline__ DF& operator-=(DF& x, DF y) { return x = x - y; }
 
 // x * y with the exact product error of the leading terms from an FMA.
 __device__ __forceinline__ DF operator*(DF x, DF y) {

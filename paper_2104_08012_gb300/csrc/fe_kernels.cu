@@ -125,6 +125,60 @@ __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const
   }
 }
 
+// Cube-aggregated apply: one thread per cube gathers the cube's (k+1)^3 dofs
+// once, applies its six Kuhn tets into register accumulators and scatters
+// (k+1)^3 atomics instead of 6 * nd (27 instead of 60 for P2).
+template <int DEG, typename T>
+__global__ void __launch_bounds__(kBlock) k_apply_cube(int Q, int Qs, int Cs, int Qpad, const int* __restrict__ cmap,
+                                                       const T* __restrict__ geo, const T* __restrict__ x,
+                                                       T* __restrict__ y, int nb, const int* __restrict__ bnd) {
+  constexpr int NL = DEG == 1 ? 8 : 27, ND = DEG == 1 ? 4 : 10;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < Q) {
+    T xv[NL], acc[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const int i = __ldg(cmap + (size_t)l * Qs + q);
+      xv[l] = i >= 0 ? __ldg(x + i) : T(0);
+      acc[l] = T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      T u[ND], g[6], o[ND];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) u[j] = xv[cube_local(DEG, t, j)];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) g[a] = __ldg(geo + (size_t)a * Cs + 6 * q + t);
+      element_apply<DEG, T>(u, g, o);
+#pragma unroll
+      for (int j = 0; j < ND; ++j) acc[cube_local(DEG, t, j)] += o[j];
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const int i = __ldg(cmap + (size_t)l * Qs + q);
+      if (i >= 0) atomicAdd(y + i, acc[l]);
+    }
+  } else if (q >= Qpad && q - Qpad < nb) {
+    const int i = bnd[q - Qpad];
+    y[i] = x[i];
+  }
+}
+
+template <int DEG>
+__global__ void k_build_cube_map(Numbering num, int Q, int Qs, int* __restrict__ cmap) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const int N = num.N, m = num.m;
+  const int ci = q % N, cj = (q / N) % N, ck = q / (N * N);
+  constexpr int K = DEG + 1;
+  for (int l = 0; l < K * K * K; ++l) {
+    const int x = DEG * ci + l % K, y = DEG * cj + (l / K) % K, z = DEG * ck + l / (K * K);
+    const int dof = lattice_to_dof(num, x, y, z);
+    const bool bd = x == 0 || y == 0 || z == 0 || x == m || y == m || z == m;
+    cmap[(size_t)l * Qs + q] = bd ? -1 - dof : dof;
+  }
+}
+
 // ------------------------------------------------------------ mass
 template <int DEG>
 __global__ void k_mass(int C, int Cs, const int* __restrict__ map, const double* __restrict__ detj,
@@ -390,6 +444,11 @@ void launch_build_level(Level& L, cudaStream_t s) {
   else
     k_build_map<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.Cs, L.map);
   LAUNCH_CHECK();
+  if (L.deg == 1)
+    k_build_cube_map<1><<<ceil_div(L.Q, kBlock), kBlock, 0, s>>>(L.num, L.Q, L.Qs, L.cmap);
+  else
+    k_build_cube_map<2><<<ceil_div(L.Q, kBlock), kBlock, 0, s>>>(L.num, L.Q, L.Qs, L.cmap);
+  LAUNCH_CHECK();
   k_build_coords<<<ceil_div(L.V, kBlock), kBlock, 0, s>>>(L.N, L.V, L.vx, L.vy, L.vz);
   LAUNCH_CHECK();
 }
@@ -416,8 +475,23 @@ static void apply_impl(const Level& L, const T* geo, const T* x, T* y, cudaStrea
   LAUNCH_CHECK();
 }
 
+template <typename T>
+static void apply_cube_impl(const Level& L, const T* geo, const T* x, T* y, cudaStream_t s) {
+  CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)L.n, s));
+  const int Qpad = ceil_div(L.Q, kBlock) * kBlock;
+  const int grid = ceil_div((long long)Qpad + L.nb, kBlock);
+  if (L.deg == 1)
+    k_apply_cube<1, T><<<grid, kBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, geo, x, y, L.nb, L.bnd);
+  else
+    k_apply_cube<2, T><<<grid, kBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, geo, x, y, L.nb, L.bnd);
+  LAUNCH_CHECK();
+}
+
 void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s) { apply_impl<double>(L, L.geo64, x, y, s); }
-void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) { apply_impl<float>(L, L.geo32, x, y, s); }
+void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) { apply_cube_impl<float>(L, L.geo32, x, y, s); }
+void launch_apply32_cells(const Level& L, const float* x, float* y, cudaStream_t s) {
+  apply_impl<float>(L, L.geo32, x, y, s);
+}
 
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
