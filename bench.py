@@ -58,6 +58,22 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(values, device=None):
+    """Element-wise max of a list of floats over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(units_per_rank, steps, world, total_ms):
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (total_ms * 1e-3)
+
+
 def hbm_peak():
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
@@ -329,10 +345,7 @@ def run_ours(args, rank, world, local_rank):
     # independent check of the error against the analytic solution at the nodes
     u_host = u.cpu().numpy()
     nodal_err = float(np.abs(u_host - I.sin_product(h.dof_coordinates())).max())
-    if world > 1:
-        t = torch.tensor([t_ms, te_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms, te_ms = t.tolist()
+    t_ms, te_ms = max_over_ranks([t_ms, te_ms], device=dev)
     extra = None
     if rank == 0 and not args.no_extras:
         try:
@@ -349,7 +362,7 @@ def run_ours(args, rank, world, local_rank):
         kname, flops, peak = "k_apply<2,double> (native FP64 operator)", FLOPS_PER_CELL_P2_F64 * C, FP64_PEAK_TFLOPS
         psrc = "nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json"
     achieved = flops / (apply_ms * 1e-3) / 1e12
-    value = world * n * args.steps / (t_ms * 1e-3)
+    value = job_throughput(n, args.steps, world, t_ms)
     line = {
         "metric": "Poisson GMG-CG solve DoF/s at 1e-8 residual",
         "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -360,7 +373,7 @@ def run_ours(args, rank, world, local_rank):
                                     "reductions, transfers, smoother, coarse Cholesky" if F64_MODE == 1 else "native FP64"),
         "iterations": stats[-1].iterations, "rel_residual": stats[-1].rel_residual,
         "max_nodal_error_vs_exact": nodal_err, "setup_s": setup_s,
-        "e2e": {"value": world * n * args.steps / (te_ms * 1e-3), "unit": "DoF/s",
+        "e2e": {"value": job_throughput(n, args.steps, world, te_ms), "unit": "DoF/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(launches),
         "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -112,19 +112,36 @@ __global__ void k_coarse_gather(int nci, const int* __restrict__ ci, const T* __
   if (j < nci) t[j] = (double)b[ci[j]];
 }
 
-// out_i = sum_{j<=i} M[i][j] in_j (lower) or out_i = sum_{j>=i} M[i][j] in_j (upper); one warp per row.
-__global__ void k_trimv(int n, const double* __restrict__ M, const double* __restrict__ in, double* __restrict__ out,
-                        int upper) {
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
+// out_i = sum_{j<=i} M[i][j] in_j (lower) or out_i = sum_{j>=i} M[i][j] in_j (upper).
+// One 256-thread block per row with two independent accumulators per thread:
+// the per-row dot products are long (up to n) and FP64-FMA latency bound when
+// a single warp walks them.
+constexpr int kRowThreads = 256;
+__global__ void __launch_bounds__(kRowThreads) k_trimv(int n, const double* __restrict__ M,
+                                                       const double* __restrict__ in, double* __restrict__ out,
+                                                       int upper) {
+  __shared__ double sh[kRowThreads / 32];
+  const int row = blockIdx.x;
   const double* Mr = M + (size_t)row * n;
   const int j0 = upper ? row : 0, j1 = upper ? n : row + 1;
-  double s = 0.0;
-  for (int jj = j0 + lane; jj < j1; jj += 32) s += __ldg(Mr + jj) * __ldg(in + jj);
+  double s0 = 0.0, s1 = 0.0;
+  int jj = j0 + threadIdx.x;
+  for (; jj + kRowThreads < j1; jj += 2 * kRowThreads) {
+    s0 += __ldg(Mr + jj) * __ldg(in + jj);
+    s1 += __ldg(Mr + jj + kRowThreads) * __ldg(in + jj + kRowThreads);
+  }
+  if (jj < j1) s0 += __ldg(Mr + jj) * __ldg(in + jj);
+  double s = s0 + s1;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[row] = s;
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRowThreads / 32; ++w) t += sh[w];
+    out[row] = t;
+  }
 }
 
 template <typename T>
@@ -223,10 +240,9 @@ void coarse_solve(const fe_hierarchy* h, const T* b, T* x, cudaStream_t s) {
   }
   k_coarse_gather<T><<<ceil_div(nci, kBlock), kBlock, 0, s>>>(nci, cs.ci, b, cs.t0);
   LAUNCH_CHECK();
-  const int grid = ceil_div((long long)nci * 32, kBlock);
-  k_trimv<<<grid, kBlock, 0, s>>>(nci, cs.Linv, cs.t0, cs.t1, 0);
+  k_trimv<<<nci, kRowThreads, 0, s>>>(nci, cs.Linv, cs.t0, cs.t1, 0);
   LAUNCH_CHECK();
-  k_trimv<<<grid, kBlock, 0, s>>>(nci, cs.LinvT, cs.t1, cs.t0, 1);
+  k_trimv<<<nci, kRowThreads, 0, s>>>(nci, cs.LinvT, cs.t1, cs.t0, 1);
   LAUNCH_CHECK();
   k_coarse_scatter<T><<<ceil_div(L0.n, kBlock), kBlock, 0, s>>>(L0.n, cs.dof2int, cs.t0, b, x);
   LAUNCH_CHECK();

@@ -103,7 +103,16 @@ def test_double_float_edge_values(fe):
         y = torch.empty(L.n, dtype=torch.float64, device=DEV)
         h.apply_operator(dt(x), y)
         torch.cuda.synchronize()
-        assert_rowwise(host(y), L.A @ x, abs(L.A) @ np.abs(x), 1e-13, "double-float edge values")
+        # Element contributions that cancel in assembly leave errors of order
+        # eps * sum_K |A_K||x_K| in any matrix-free evaluation (and in the
+        # oracle's own assembly), so the bound is the element-wise scale.
+        xb = np.where(L.space.boundary, 0.0, x)
+        Ae = np.abs(O.element_stiffness(L.mesh, 2, None))
+        cd = L.space.cell_dofs
+        scale = np.zeros(L.n)
+        np.add.at(scale, cd, np.einsum("cde,ce->cd", Ae, np.abs(xb[cd])))
+        scale = np.where(L.space.boundary, np.abs(x), scale)
+        assert_rowwise(host(y), L.A @ x, scale, 1e-13, "double-float edge values")
         xn = x.copy()
         xn[L.space.boundary.argmin()] = np.nan  # an interior dof
         h.apply_operator(dt(xn), y)
