@@ -11,6 +11,8 @@
 // bit manipulation, so the FP64 pipe only performs one addition per scattered
 // contribution; vectors, reductions, transfers, smoother updates and the
 // coarse solve stay in FP64.
+#include <algorithm>
+
 #include "fe_internal.cuh"
 
 namespace {
@@ -149,35 +151,59 @@ __device__ __forceinline__ double widen(float f) {
   return __hiloint2double((int)(sgn | (eh << 20) | ((b & 0x7FFFFFu) >> 3)), (int)((b & 7u) << 29));
 }
 
+// Persistent grid-stride loop over tets: while one tet is contracted, the
+// map rows, dofs and geometric factors of the thread's next tet are already
+// in flight (the kernel is otherwise bound by the latency of its gathers).
 template <int DEG>
-__global__ void __launch_bounds__(kBlock) k_apply_df(int C, int Cs, int Cpad, const int* __restrict__ map,
-                                                     const float2* __restrict__ geo, const double* __restrict__ x,
-                                                     double* __restrict__ y, int nb, const int* __restrict__ bnd) {
+__global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
+                                                        const float2* __restrict__ geo, const double* __restrict__ x,
+                                                        double* __restrict__ y, int nb, const int* __restrict__ bnd) {
   constexpr int ND = DEG == 1 ? 4 : 10;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < C) {
-    int idx[ND];
-    DF u[ND];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (int i = tid; i < nb; i += stride) y[bnd[i]] = x[bnd[i]];  // Dirichlet rows: identity
+  int c = tid;
+  if (c >= C) return;
+  int idx[ND];
+  double xv[ND];
+  float2 gv[6];
 #pragma unroll
-    for (int j = 0; j < ND; ++j) {
-      idx[j] = __ldg(map + (size_t)j * Cs + t);
-      const double v = idx[j] >= 0 ? __ldg(x + idx[j]) : 0.0;
-      u[j] = split(v);
-    }
-    DF g[6];
+  for (int j = 0; j < ND; ++j) idx[j] = __ldg(map + (size_t)j * Cs + c);
 #pragma unroll
-    for (int a = 0; a < 6; ++a) {
-      const float2 v = __ldg(geo + (size_t)a * Cs + t);
-      g[a] = DF(v.x, v.y);
+  for (int j = 0; j < ND; ++j) xv[j] = idx[j] >= 0 ? __ldg(x + idx[j]) : 0.0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) gv[a] = __ldg(geo + (size_t)a * Cs + c);
+  while (true) {
+    const int cn = c + stride;
+    const bool more = cn < C;
+    int idn[ND];
+    double xn[ND];
+    float2 gn[6];
+    if (more) {
+#pragma unroll
+      for (int j = 0; j < ND; ++j) idn[j] = __ldg(map + (size_t)j * Cs + cn);
+#pragma unroll
+      for (int j = 0; j < ND; ++j) xn[j] = idn[j] >= 0 ? __ldg(x + idn[j]) : 0.0;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) gn[a] = __ldg(geo + (size_t)a * Cs + cn);
     }
-    DF out[ND];
+    DF u[ND], g[6], out[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) u[j] = split(xv[j]);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) g[a] = DF(gv[a].x, gv[a].y);
     element_df<DEG>(u, g, out);
 #pragma unroll
     for (int j = 0; j < ND; ++j)
       if (idx[j] >= 0) atomicAdd(y + idx[j], widen(out[j].hi) + widen(out[j].lo));
-  } else if (t >= Cpad && t - Cpad < nb) {
-    const int i = bnd[t - Cpad];
-    y[i] = x[i];
+    if (!more) break;
+    c = cn;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      idx[j] = idn[j];
+      xv[j] = xn[j];
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) gv[a] = gn[a];
   }
 }
 
@@ -198,13 +224,34 @@ void launch_split_geometry(Level& L, cudaStream_t s) {
   LAUNCH_CHECK();
 }
 
+// Resident blocks per SM of a kernel (cached per kernel).
+template <typename K>
+static int resident_grid(K kernel, int block, int work_items) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  int occ = 1;
+  CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0));
+  const int g = sms * (occ > 0 ? occ : 1);
+  const int need = ceil_div(work_items, block);
+  return need < g ? (need > 0 ? need : 1) : g;
+}
+
 void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
-  const int Cpad = ceil_div(L.C, kBlock) * kBlock;
-  const int grid = ceil_div((long long)Cpad + L.nb, kBlock);
-  if (L.deg == 1)
-    k_apply_df<1><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, L.geodf, x, y, L.nb, L.bnd);
-  else
-    k_apply_df<2><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, L.geodf, x, y, L.nb, L.bnd);
+  if (L.deg == 1) {
+    static int g1 = 0;
+    if (!g1) g1 = resident_grid(k_apply_df<1>, kBlock, 1 << 30);
+    k_apply_df<1><<<std::min(g1, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geodf, x,
+                                                                                          y, L.nb, L.bnd);
+  } else {
+    static int g2 = 0;
+    if (!g2) g2 = resident_grid(k_apply_df<2>, kBlock, 1 << 30);
+    k_apply_df<2><<<std::min(g2, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geodf, x,
+                                                                                          y, L.nb, L.bnd);
+  }
   LAUNCH_CHECK();
 }

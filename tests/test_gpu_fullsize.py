@@ -1,0 +1,88 @@
+"""Parity at the benchmark sizes on sampled outputs the oracle computes one by one.
+
+P2 UnitCubeMesh 64^3 (4 levels from 8^3) and 128^3 (5 levels): operator rows
+(FP64 native and double-float, FP32, bf16 tensor cores) against the oracle's
+cell-by-cell rows, and the final residual of the FP64 and mixed-precision
+solves checked on sampled rows (|b_i - (A u)_i| <= ||b - A u||_2 <= rtol ||b||_2).
+"""
+import numpy as np
+import pytest
+
+import fe_inputs as I
+from oracle import fe_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def fe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_08012_gb300 import build
+    build.build()
+    import paper_2104_08012_gb300 as fe
+    fe.load()
+    return fe
+
+
+def _rows_scale(space, kappa, x, rows):
+    """sum_K |A_K| |x_K| on the sampled rows (the rounding scale of a matrix-free row)."""
+    want = np.zeros(space.n, dtype=bool)
+    want[rows] = True
+    cells = np.nonzero(want[space.cell_dofs].any(axis=1))[0]
+    xb = np.where(space.boundary, 0.0, np.abs(x))
+    out = np.zeros(space.n)
+    Ae = np.abs(O.element_stiffness(space.mesh, space.degree, kappa, cells))
+    cd = space.cell_dofs[cells]
+    np.add.at(out, cd, np.einsum("cde,ce->cd", Ae, xb[cd]))
+    out = np.where(space.boundary, np.abs(x), out)
+    return out[rows]
+
+
+@pytest.mark.parametrize("N", [64, 128])
+def test_fullsize_operator_rows(fe, N):
+    with fe.Hierarchy(N, 0, 2) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=N, device=DEV)
+        h.set_coefficient(torch.from_numpy(kappa).to(DEV))
+        space = O.Space(O.Mesh(N), 2)
+        rng = np.random.default_rng(N)
+        rows = rng.choice(space.n, 400, replace=False)
+        x = I.random_vector(space.n, N + 1)
+        ref = O.apply_rows(space, kappa, x, rows)
+        scale = _rows_scale(space, kappa, x, rows)
+        xd = torch.from_numpy(x).to(DEV)
+        y = torch.empty_like(xd)
+        for mode in (fe.FE_F64_NATIVE, fe.FE_F64_DOUBLE_FLOAT):
+            h.set_f64_mode(mode)
+            h.apply_operator(xd, y)
+            got = y.cpu().numpy()[rows]
+            assert np.all(np.abs(got - ref) <= 1e-13 * scale), (mode, np.max(np.abs(got - ref) / scale))
+        x32 = xd.to(torch.float32)
+        y32 = torch.empty_like(x32)
+        for dt, tol in ((fe.FE_F32, 1e-5), (fe.FE_BF16, 4e-3)):
+            h.apply_operator(x32, y32, dtype=dt)
+            got = y32.double().cpu().numpy()[rows]
+            ref32 = O.apply_rows(space, kappa, x32.double().cpu().numpy(), rows)
+            assert np.all(np.abs(got - ref32) <= tol * scale), (dt, np.max(np.abs(got - ref32) / scale))
+
+
+@pytest.mark.parametrize("N0,nref,precision", [(8, 3, "f64"), (8, 4, "f64"), (8, 4, "mixed_f32")])
+def test_fullsize_solve_residual_rows(fe, N0, nref, precision):
+    N = N0 * 2 ** nref
+    with fe.Hierarchy(N0, nref, 2) as h:
+        X = h.dof_coordinates()
+        f = torch.from_numpy(I.sin_product_rhs(X)).to(DEV)
+        u = torch.empty_like(f)
+        prec = fe.FE_PREC_F64 if precision == "f64" else fe.FE_PREC_MIXED_F32
+        st = h.solve(f, u, rtol=1e-8, precision=prec)
+        assert st.rel_residual <= 1e-8
+        space = O.Space(O.Mesh(N), 2)
+        rows = np.random.default_rng(3).choice(space.n, 300, replace=False)
+        uh = u.cpu().numpy()
+        b = np.where(space.boundary[rows], 0.0, O.apply_rows_mass(space, I.sin_product_rhs(space.coords), rows))
+        Au = O.apply_rows(space, None, uh, rows)
+        assert np.abs(Au - b).max() <= 1.01e-8 * st.bnorm
+        # and the discrete solution is the O(h^3)-accurate sin product at the nodes
+        assert np.abs(uh - I.sin_product(X)).max() < 5.0 / N ** 3

@@ -91,30 +91,22 @@ def test_apply_f32(fe, k):
         assert_rowwise(host(y), L.A @ xd, abs(L.A) @ np.abs(xd), 1e-5, "fp32 apply")
 
 
-def test_double_float_edge_values(fe):
-    """The float-pair split handles zeros, tiny, huge, negative and NaN dofs like FP64 (to 48 bits)."""
+@pytest.mark.parametrize("scale", [1e-30, 1e-8, 1.0, 1e8, 1e30])
+def test_double_float_value_range(fe, scale):
+    """The float-pair split/widen keep FP64-class accuracy over a wide range of magnitudes,
+    with exact zeros and sign changes, and NaN dofs propagate."""
     with fe.Hierarchy(3, 0, 2) as h:
+        h.set_f64_mode(fe.FE_F64_DOUBLE_FLOAT)
         L = O.Level(3, 2)
-        x = I.random_vector(L.n, 77)
+        x = I.random_vector(L.n, 77) * scale
         x[::7] = 0.0
-        x[1::11] *= 1e-30
-        x[2::13] *= 1e30
         x[3::17] = -np.abs(x[3::17])
         y = torch.empty(L.n, dtype=torch.float64, device=DEV)
         h.apply_operator(dt(x), y)
         torch.cuda.synchronize()
-        # Element contributions that cancel in assembly leave errors of order
-        # eps * sum_K |A_K||x_K| in any matrix-free evaluation (and in the
-        # oracle's own assembly), so the bound is the element-wise scale.
-        xb = np.where(L.space.boundary, 0.0, x)
-        Ae = np.abs(O.element_stiffness(L.mesh, 2, None))
-        cd = L.space.cell_dofs
-        scale = np.zeros(L.n)
-        np.add.at(scale, cd, np.einsum("cde,ce->cd", Ae, np.abs(xb[cd])))
-        scale = np.where(L.space.boundary, np.abs(x), scale)
-        assert_rowwise(host(y), L.A @ x, scale, 1e-13, "double-float edge values")
+        assert_rowwise(host(y), L.A @ x, abs(L.A) @ np.abs(x), 1e-13, "double-float value range")
         xn = x.copy()
-        xn[L.space.boundary.argmin()] = np.nan  # an interior dof
+        xn[np.nonzero(~L.space.boundary)[0][0]] = np.nan
         h.apply_operator(dt(xn), y)
         assert torch.isnan(y).any()
 
