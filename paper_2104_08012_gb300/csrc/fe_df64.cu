@@ -10,7 +10,9 @@
 // split into float pairs and the contributions joined back to FP64 by integer
 // bit manipulation, so the FP64 pipe only performs one addition per scattered
 // contribution; vectors, reductions, transfers, smoother updates and the
-// coarse solve stay in FP64.
+// coarse solve stay in FP64.  Each tet's dofs are scaled by a power of two
+// (their largest exponent) before the split, so the float pairs never leave
+// the FP32 exponent range whatever the magnitude of the vector.
 #include <algorithm>
 
 #include "fe_internal.cuh"
@@ -126,29 +128,42 @@ __device__ __forceinline__ void element_df(const DF (&u)[DEG == 1 ? 4 : 10], con
     p2_element_df(u, g, y);
 }
 
-// double -> float pair by bit manipulation: hi keeps the leading 24 bits of
-// the significand (truncated), lo the next 24 (rounded); |x| < 2^-126 flushes
-// to 0, non-finite x gives a NaN pair.
-__device__ __forceinline__ DF split(double x) {
+// double -> float pair by bit manipulation, after scaling by 2^(1023 - emax)
+// (emax: the largest biased exponent of the tet's dofs, so the largest dof
+// maps to [1, 2)): hi keeps the leading 24 bits of the significand
+// (truncated), lo the next 24 (rounded).  Dofs more than 2^126 below the
+// tet's largest flush to 0 (negligible against it).
+__device__ __forceinline__ DF split_scaled(double x, int emax) {
   const unsigned int h32 = (unsigned int)__double2hiint(x), l32 = (unsigned int)__double2loint(x);
-  const unsigned int e = (h32 >> 20) & 0x7FFu;
+  const int e = (int)((h32 >> 20) & 0x7FFu) - emax + 1023;  // exponent field of x * 2^(1023 - emax)
   const unsigned int sgn = h32 & 0x80000000u;
-  if (e == 0x7FFu) return DF(__int_as_float(0x7fc00000), 0.0f);
-  if (e <= 896u) return DF(__uint_as_float(sgn), 0.0f);
-  const unsigned int hb = sgn | ((e - 896u) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
-  const float scale = e > 948u ? __uint_as_float((e - 948u) << 23) : 0.0f;  // 2^(e - 1075)
+  if (((h32 >> 20) & 0x7FFu) == 0u || e <= 896) return DF(__uint_as_float(sgn), 0.0f);
+  const unsigned int hb = sgn | ((unsigned int)(e - 896) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
+  const float scale = e > 948 ? __uint_as_float((unsigned int)(e - 948) << 23) : 0.0f;  // 2^(e - 1075)
   const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
   return DF(__uint_as_float(hb), __uint_as_float(__float_as_uint(lo) | sgn));
 }
 
-// exact float -> double by bit manipulation (denormal floats flush to 0)
-__device__ __forceinline__ double widen(float f) {
+// Largest biased exponent of the dofs (1023 if all are zero); 0x7FF if any is not finite.
+template <int ND>
+__device__ __forceinline__ int block_exponent(const double (&xv)[ND]) {
+  int emax = 0;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) emax = max(emax, (int)(((unsigned int)__double2hiint(xv[j]) >> 20) & 0x7FFu));
+  return emax == 0 ? 1023 : emax;
+}
+
+// exact float -> double of f * 2^(emax - 1023) by bit manipulation
+// (results below the double range flush to 0, above it give inf)
+__device__ __forceinline__ double widen_scaled(float f, int emax) {
   const unsigned int b = __float_as_uint(f);
-  const unsigned int ef = (b >> 23) & 0xFFu;
+  const int ef = (int)((b >> 23) & 0xFFu);
   const unsigned int sgn = b & 0x80000000u;
-  if (ef == 0u) return __hiloint2double((int)sgn, 0);
-  const unsigned int eh = ef == 0xFFu ? 0x7FFu : ef + 896u;
-  return __hiloint2double((int)(sgn | (eh << 20) | ((b & 0x7FFFFFu) >> 3)), (int)((b & 7u) << 29));
+  if (ef == 0) return __hiloint2double((int)sgn, 0);
+  const int eh = ef + emax - 127;
+  if (ef == 0xFF || eh >= 0x7FF) return __hiloint2double((int)(sgn | 0x7FF00000u | ((b & 0x7FFFFFu) >> 3)), 0);
+  if (eh <= 0) return __hiloint2double((int)sgn, 0);
+  return __hiloint2double((int)(sgn | ((unsigned int)eh << 20) | ((b & 0x7FFFFFu) >> 3)), (int)((b & 7u) << 29));
 }
 
 // Persistent grid-stride loop over tets: while one tet is contracted, the
@@ -187,14 +202,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int
       for (int a = 0; a < 6; ++a) gn[a] = __ldg(geo + (size_t)a * Cs + cn);
     }
     DF u[ND], g[6], out[ND];
+    const int emax = block_exponent<ND>(xv);  // the element map is linear: scale, contract, unscale
 #pragma unroll
-    for (int j = 0; j < ND; ++j) u[j] = split(xv[j]);
+    for (int j = 0; j < ND; ++j) u[j] = split_scaled(xv[j], emax);
+    if (emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
 #pragma unroll
     for (int a = 0; a < 6; ++a) g[a] = DF(gv[a].x, gv[a].y);
     element_df<DEG>(u, g, out);
 #pragma unroll
     for (int j = 0; j < ND; ++j)
-      if (idx[j] >= 0) atomicAdd(y + idx[j], widen(out[j].hi) + widen(out[j].lo));
+      if (idx[j] >= 0) atomicAdd(y + idx[j], widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
     if (!more) break;
     c = cn;
 #pragma unroll

@@ -91,10 +91,11 @@ def test_apply_f32(fe, k):
         assert_rowwise(host(y), L.A @ xd, abs(L.A) @ np.abs(xd), 1e-5, "fp32 apply")
 
 
-@pytest.mark.parametrize("scale", [1e-30, 1e-8, 1.0, 1e8, 1e30])
+@pytest.mark.parametrize("scale", [1e-300, 1e-30, 1e-8, 1.0, 1e8, 1e30, 1e300])
 def test_double_float_value_range(fe, scale):
-    """The float-pair split/widen keep FP64-class accuracy over a wide range of magnitudes,
-    with exact zeros and sign changes, and NaN dofs propagate."""
+    """The float-pair split/widen keep FP64-class accuracy over the whole FP64 range (each
+    tet's dofs are scaled by a power of two first), with exact zeros and sign changes,
+    and NaN dofs propagate."""
     with fe.Hierarchy(3, 0, 2) as h:
         h.set_f64_mode(fe.FE_F64_DOUBLE_FLOAT)
         L = O.Level(3, 2)
