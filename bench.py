@@ -36,7 +36,7 @@ SAMPLE = {"N0": 8, "nrefine": 2, "degree": 2}  # oracle bounded sample: P2 32^3,
 F64_MODE = 1  # FE_F64_DOUBLE_FLOAT: the library default for FP64 operator applications
 # DRAM bytes per launch of the dominant kernel on this workload from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by FP64 mode; None until captured
-TRAFFIC = {0: 188.2e6}
+TRAFFIC = {0: 188.2e6, 1: 183.6e6}
 # Flops of one P2 element application (c, d, S, four G-products, transpose;
 # an FMA counts 2), per tet: 151 in the FP64 formula; the double-float form of
 # the same formula costs 1493 FP32 flops (95 float-pair additions x 11, 36
@@ -81,10 +81,12 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def apply_bytes_per_launch(n, C, nd, val_bytes, geo_bytes):
+def apply_bytes_per_launch(n, C, nd, val_bytes, geo_bytes, cube_map=False):
     """Algorithmic bytes of one matrix-free application: x read, y zero-fill and write,
-    cell->dof map (int32), per-cell geometric factors (6 values)."""
-    return n * 3 * val_bytes + C * nd * 4 + C * 6 * geo_bytes
+    the dof map (int32: nd per tet, or (k+1)^3 per cube for the cube-aggregated kernel),
+    per-tet geometric factors (6 values)."""
+    map_bytes = (C // 6) * (27 if nd == 10 else 8) * 4 if cube_map else C * nd * 4
+    return n * 3 * val_bytes + map_bytes + C * 6 * geo_bytes
 
 
 def time_launches(fn, stream, reps, flush):
@@ -109,15 +111,16 @@ def extras(fe, I, h, dev, stream, flush):
     # ---- matvec on the benchmark's fine level (P2 64^3)
     n, C = h.n_dofs(), h.n_cells()
     mv = {}
-    for name, dt, tdt, vb, gb in (("f64", fe.FE_F64, torch.float64, 8, 8), ("f32", fe.FE_F32, torch.float32, 4, 4),
-                                   ("bf16_tensor_core", fe.FE_BF16, torch.float32, 4, 4)):
+    for name, dt, tdt, vb, gb, cube in (("f64", fe.FE_F64, torch.float64, 8, 8, False),
+                                         ("f32", fe.FE_F32, torch.float32, 4, 4, True),
+                                         ("bf16_tensor_core", fe.FE_BF16, torch.float32, 4, 4, False)):
         x = torch.rand(n, dtype=tdt, device=dev)
         y = torch.empty_like(x)
         with torch.cuda.stream(stream):
             for _ in range(3):
                 h.apply_operator(x, y, dtype=dt, stream=stream)
             ms = time_launches(lambda: h.apply_operator(x, y, dtype=dt, stream=stream), stream, 10, flush)
-        byt = apply_bytes_per_launch(n, C, 10, vb, gb)
+        byt = apply_bytes_per_launch(n, C, 10, vb, gb, cube)
         mv[name] = {"ms": ms, "GDoF_per_s": n / (ms * 1e-3) / 1e9, "GB_per_s": byt / (ms * 1e-3) / 1e9,
                     "hbm_frac": byt / (ms * 1e-3) / 1e9 / peak, "bytes_per_dof": byt / n}
     out["matvec_p2_64cubed"] = dict(mv, hbm_peak_gbs=peak, hbm_peak_source=src)

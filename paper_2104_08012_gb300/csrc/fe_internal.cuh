@@ -264,6 +264,11 @@ template <typename T>
 void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s);
 template <typename T>
 void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, bool zero_bd, cudaStream_t s);
+// V-cycle restriction rc = P^T (bf - yf) on interior coarse dofs, 0 on Dirichlet dofs (cube-based)
+template <typename T>
+void launch_restrict_residual(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, cudaStream_t s);
+void upload_restriction_stencils(int deg, const std::vector<int>& start, const std::vector<int>& node,
+                                 const std::vector<double>& w);
 // Vector kernels
 template <typename T>
 void launch_cheb_step(int n, const T* b, const T* y, const T* dinv, T* x, T* d, double c1, double c2, bool first_from_zero,
