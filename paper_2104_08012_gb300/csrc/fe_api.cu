@@ -174,23 +174,6 @@ static void build_transfer_tables(TransferTables& t, int deg) {
     }
     t.h_res_start.push_back((int)t.h_res_off.size());
   }
-  {  // the same stencils by prolongation class with coarse-cube-local nodes, for the cube restriction
-    const int K = deg + 1, ncls = K2 * K2 * K2;
-    std::vector<int> st(ncls + 1, 0), node;
-    std::vector<double> w;
-    int prev = 0;
-    for (const Ent& e : all) {
-      const int cls = e.o[0] + K2 * (e.o[1] + K2 * e.o[2]);
-      FE_REQUIRE(cls >= prev, FE_ERR_CUDA, "prolongation stencils out of class order");
-      prev = cls;
-      ++st[cls + 1];
-      node.push_back(e.d[0] + K * (e.d[1] + K * e.d[2]));
-      w.push_back(e.w);
-    }
-    for (int c = 0; c < ncls; ++c) st[c + 1] += st[c];
-    static std::once_flag once[2];
-    std::call_once(once[deg - 1], [&] { upload_restriction_stencils(deg, st, node, w); });
-  }
   auto up = [](auto& dbuf, const auto& vec) {
     using T = typename std::decay_t<decltype(vec)>::value_type;
     dbuf.alloc(vec.size());
@@ -378,7 +361,7 @@ static void vcycle_level(fe_hierarchy* h, int l, int dtype, cudaStream_t s) {
   smooth_enqueue<T>(h, l, b, x, y, d, g_sp.steps, g_sp.lo, g_sp.hi, true, dtype, s);
   apply_enqueue(h, l, x, y, rdt, s);
   Level& Lc = h->L[l - 1];
-  launch_restrict_residual<T>(h, l, b, y, lv_b<T>(Lc), s);
+  launch_restrict<T>(h, l, b, y, lv_b<T>(Lc), true, s);
   vcycle_level<T>(h, l - 1, dtype, s);
   launch_prolong<T>(h, l, lv_x<T>(Lc), x, true, s);
   smooth_enqueue<T>(h, l, b, x, y, d, g_sp.steps, g_sp.lo, g_sp.hi, false, dtype, s);
@@ -403,6 +386,9 @@ static void run_vcycle(fe_hierarchy* h, int dtype, bool use_graph, cudaStream_t 
     gc.exec = nullptr;
   }
   if (!gc.exec) {
+    // everything a captured launch needs must exist before the capture starts
+    if (dtype == FE_BF16)
+      for (int l = 1; l < h->nlev; ++l) bf16_prepare(h->L[l]);
     if (!gc.stream) CUDA_CHECK(cudaStreamCreateWithFlags(&gc.stream, cudaStreamNonBlocking));
     cudaGraph_t g;
     CUDA_CHECK(cudaStreamBeginCapture(gc.stream, cudaStreamCaptureModeThreadLocal));

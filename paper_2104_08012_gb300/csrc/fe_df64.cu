@@ -50,15 +50,6 @@ __device__ __forceinline__ DF operator+(DF x, DF y) {
 __device__ __forceinline__ DF operator-(DF x) { return DF(-x.hi, -x.lo); }
 __device__ __forceinline__ DF operator-(DF x, DF y) { return x + (-y); }
 
-// x * y with the exact product error of the leading terms from an FMA.
-__device__ __forceinline__ DF operator*(DF x, DF y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);
-  e = __fmaf_rn(x.hi, y.lo, e);
-  e = __fmaf_rn(x.lo, y.hi, e);
-  return quick_two_sum(p, e);
-}
-
 // Exact scaling by a power of two.
 __device__ __forceinline__ DF scale2(DF x, float k) { return DF(__fmul_rn(x.hi, k), __fmul_rn(x.lo, k)); }
 // x * k for a small integer k (TwoProd of the leading term).
@@ -68,11 +59,25 @@ __device__ __forceinline__ DF scalek(DF x, float k) {
   return quick_two_sum(p, e);
 }
 
+// a0 b0 + a1 b1 + a2 b2 with one renormalisation: the three leading products
+// are summed exactly (TwoSum), every error term (product errors, cross terms,
+// summation errors) is gathered in one float.
+__device__ __forceinline__ DF dot3(DF a0, DF b0, DF a1, DF b1, DF a2, DF b2) {
+  const float p0 = __fmul_rn(a0.hi, b0.hi), p1 = __fmul_rn(a1.hi, b1.hi), p2 = __fmul_rn(a2.hi, b2.hi);
+  float e0 = __fmaf_rn(a0.hi, b0.hi, -p0), e1 = __fmaf_rn(a1.hi, b1.hi, -p1), e2 = __fmaf_rn(a2.hi, b2.hi, -p2);
+  e0 = __fmaf_rn(a0.lo, b0.hi, __fmaf_rn(a0.hi, b0.lo, e0));
+  e1 = __fmaf_rn(a1.lo, b1.hi, __fmaf_rn(a1.hi, b1.lo, e1));
+  e2 = __fmaf_rn(a2.lo, b2.hi, __fmaf_rn(a2.hi, b2.lo, e2));
+  const DF s1 = two_sum(p0, p1);
+  const DF s2 = two_sum(s1.hi, p2);
+  return quick_two_sum(s2.hi, __fadd_rn(__fadd_rn(e0, e1), __fadd_rn(__fadd_rn(e2, s1.lo), s2.lo)));
+}
+
 // h = G t for the symmetric G stored (00, 01, 02, 11, 12, 22).
 __device__ __forceinline__ void gmul(const DF (&g)[6], DF t0, DF t1, DF t2, DF& h0, DF& h1, DF& h2) {
-  h0 = g[0] * t0 + g[1] * t1 + g[2] * t2;
-  h1 = g[1] * t0 + g[3] * t1 + g[4] * t2;
-  h2 = g[2] * t0 + g[4] * t1 + g[5] * t2;
+  h0 = dot3(g[0], t0, g[1], t1, g[2], t2);
+  h1 = dot3(g[1], t0, g[3], t1, g[4], t2);
+  h2 = dot3(g[2], t0, g[4], t1, g[5], t2);
 }
 
 // The P2 vertex-gradient element of fe_internal.cuh written out without

@@ -264,11 +264,7 @@ template <typename T>
 void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s);
 template <typename T>
 void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, bool zero_bd, cudaStream_t s);
-// V-cycle restriction rc = P^T (bf - yf) on interior coarse dofs, 0 on Dirichlet dofs (cube-based)
-template <typename T>
-void launch_restrict_residual(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, cudaStream_t s);
-void upload_restriction_stencils(int deg, const std::vector<int>& start, const std::vector<int>& node,
-                                 const std::vector<double>& w);
+
 // Vector kernels
 template <typename T>
 void launch_cheb_step(int n, const T* b, const T* y, const T* dinv, T* x, T* d, double c1, double c2, bool first_from_zero,
@@ -315,6 +311,7 @@ void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int
 void apply_bf16_enqueue(const Level& L, const float* x, float* y, cudaStream_t s);
 bool bf16_supported();
 int bf16_take_error(cudaStream_t s);      // nonzero if a tensor-core launch gave up a bounded wait
+void bf16_prepare(const Level& L);        // build the level's tensor maps and tables (never inside a capture)
 void bf16_forget_level(const Level* L);  // drop the cached tensor maps of a level being destroyed
 
 // ------------------------------------------------------- element kernels ---

@@ -3,12 +3,6 @@
 // multigrid transfer and smoother vector kernels (paper Section 3).
 #include "fe_internal.cuh"
 
-// Prolongation stencils for the cube-based restriction, per degree: class
-// o in [0,2k)^3 -> entries (coarse-cube-local node (k+1)^3 index, weight).
-__constant__ int c_rs_start[2][65];
-__constant__ int c_rs_node[2][320];
-__constant__ double c_rs_w[2][320];
-
 // Reference P1/P2 mass matrices int_ref phi_i phi_j, filled by fe_api.cu.
 __constant__ double c_mref1[16];
 __constant__ double c_mref2[100];
@@ -398,42 +392,6 @@ __global__ void k_restrict(Numbering nf, Numbering nc, int n_c, const int* __res
   rc[J] = s;
 }
 
-// Residual restriction for the V-cycle, one thread per coarse cube: the fine
-// lattice points 2k c + o, o in [0,2k)^3, are exactly the points whose
-// prolongation row is taken from coarse cube c, so walking them applies P^T
-// once per fine point.  Partial sums for the cube's (k+1)^3 coarse nodes live
-// in shared memory; they are scattered with atomics to interior coarse dofs
-// only (rc must be zero on entry; Dirichlet entries stay 0).
-template <int DEG, typename T>
-__global__ void __launch_bounds__(128) k_restrict_cube(Numbering nf, int Qc, int Nc, int Qcs,
-                                                       const int* __restrict__ cmap_c, const T* __restrict__ bf,
-                                                       const T* __restrict__ yf, T* __restrict__ rc) {
-  constexpr int K = DEG + 1, NL = K * K * K, K2 = 2 * DEG;
-  __shared__ T acc[NL][128];
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = q < Qc;
-#pragma unroll
-  for (int l = 0; l < NL; ++l) acc[l][threadIdx.x] = T(0);
-  const int ci = live ? q % Nc : 0, cj = live ? (q / Nc) % Nc : 0, ck = live ? q / (Nc * Nc) : 0;
-  for (int o = 0; o < K2 * K2 * K2; ++o) {
-    const int ox = o % K2, oy = (o / K2) % K2, oz = o / (K2 * K2);
-    T r = T(0);
-    if (live) {
-      const int i = lattice_to_dof(nf, K2 * ci + ox, K2 * cj + oy, K2 * ck + oz);
-      r = bf[i] - yf[i];
-    }
-    const int e1 = c_rs_start[DEG - 1][o + 1];
-    for (int e = c_rs_start[DEG - 1][o]; e < e1; ++e)
-      acc[c_rs_node[DEG - 1][e]][threadIdx.x] += (T)c_rs_w[DEG - 1][e] * r;
-  }
-  if (!live) return;
-#pragma unroll
-  for (int l = 0; l < NL; ++l) {
-    const int j = __ldg(cmap_c + (size_t)l * Qcs + q);
-    if (j >= 0) atomicAdd(rc + j, acc[l][threadIdx.x]);
-  }
-}
-
 // --------------------------------------------------------- vector ops
 // Chebyshev step: d = c1 d + c2 D^-1 (b - y); x += d  (y = A x).  With
 // first_from_zero (x = 0, y unused): d = c2 D^-1 b; x = d.
@@ -624,30 +582,6 @@ void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T*
                                                               bf, yf, rc, zero_bd);
   LAUNCH_CHECK();
 }
-
-void upload_restriction_stencils(int deg, const std::vector<int>& start, const std::vector<int>& node,
-                                 const std::vector<double>& w) {
-  FE_REQUIRE((int)start.size() <= 65 && (int)node.size() <= 320, FE_ERR_CUDA, "restriction stencil too large");
-  CUDA_CHECK(cudaMemcpyToSymbol(c_rs_start, start.data(), sizeof(int) * start.size(), sizeof(int) * 65 * (deg - 1)));
-  CUDA_CHECK(cudaMemcpyToSymbol(c_rs_node, node.data(), sizeof(int) * node.size(), sizeof(int) * 320 * (deg - 1)));
-  CUDA_CHECK(cudaMemcpyToSymbol(c_rs_w, w.data(), sizeof(double) * w.size(), sizeof(double) * 320 * (deg - 1)));
-}
-
-template <typename T>
-void launch_restrict_residual(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, cudaStream_t s) {
-  const Level& F = h->L[lf];
-  const Level& Cc = h->L[lf - 1];
-  CUDA_CHECK(cudaMemsetAsync(rc, 0, sizeof(T) * (size_t)Cc.n, s));
-  if (h->deg == 1)
-    k_restrict_cube<1, T><<<ceil_div(Cc.Q, 128), 128, 0, s>>>(F.num, Cc.Q, Cc.N, Cc.Qs, Cc.cmap, bf, yf, rc);
-  else
-    k_restrict_cube<2, T><<<ceil_div(Cc.Q, 128), 128, 0, s>>>(F.num, Cc.Q, Cc.N, Cc.Qs, Cc.cmap, bf, yf, rc);
-  LAUNCH_CHECK();
-}
-template void launch_restrict_residual<double>(const fe_hierarchy*, int, const double*, const double*, double*,
-                                               cudaStream_t);
-template void launch_restrict_residual<float>(const fe_hierarchy*, int, const float*, const float*, float*,
-                                              cudaStream_t);
 
 template void launch_prolong<double>(const fe_hierarchy*, int, const double*, double*, bool, cudaStream_t);
 template void launch_prolong<float>(const fe_hierarchy*, int, const float*, float*, bool, cudaStream_t);

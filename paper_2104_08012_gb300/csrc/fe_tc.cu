@@ -426,6 +426,8 @@ const TcLevelData& level_data(const Level& L) {
   if (!g_err.p) {
     g_err.alloc(1);
     CUDA_CHECK(cudaMemset(g_err.p, 0, sizeof(int)));
+    CUDA_CHECK(cudaFuncSetAttribute(k_apply_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<1>::REQUEST));
+    CUDA_CHECK(cudaFuncSetAttribute(k_apply_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<2>::REQUEST));
   }
   g_levels.push_back(d);
   return g_levels.back();
@@ -434,11 +436,6 @@ const TcLevelData& level_data(const Level& L) {
 template <int DEG>
 void launch_tc(const Level& L, const TcLevelData& d, const float* x, float* y, cudaStream_t s, int sms) {
   using S = Smem<DEG>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    CUDA_CHECK(cudaFuncSetAttribute(k_apply_tc<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::REQUEST));
-    attr_set = true;
-  }
   const int ntiles = L.Cs / kTile;
   int grid = 4 * sms;
   if (grid > ntiles) grid = ntiles;
@@ -460,9 +457,12 @@ bool bf16_supported() {
 void apply_bf16_enqueue(const Level& L, const float* x, float* y, cudaStream_t s) {
   FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply needs an sm_103 device");
   const TcLevelData& d = level_data(L);
-  int dev = 0, sms = 148;
-  CUDA_CHECK(cudaGetDevice(&dev));
-  CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)L.n, s));
   if (L.deg == 1)
     launch_tc<1>(L, d, x, y, s, sms);
@@ -472,6 +472,11 @@ void apply_bf16_enqueue(const Level& L, const float* x, float* y, cudaStream_t s
     k_bnd_copy32<<<ceil_div(L.nb, 256), 256, 0, s>>>(L.nb, L.bnd, x, y);
     LAUNCH_CHECK();
   }
+}
+
+void bf16_prepare(const Level& L) {
+  FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply needs an sm_103 device");
+  level_data(L);
 }
 
 // Raised by k_apply_tc when a bounded wait expired; read and cleared by the host.
