@@ -250,6 +250,7 @@ void launch_geometry(Level& L, cudaStream_t s);
 void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s);
 void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s);
+void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_split_geometry(Level& L, cudaStream_t s);
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_diag(Level& L, double* diag_out, cudaStream_t s);

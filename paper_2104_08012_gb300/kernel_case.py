@@ -21,6 +21,7 @@ def main():
     ap.add_argument("--nrefine", type=int, default=0)
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--f64-mode", type=int, default=None, help="0 native, 1 double-float per cube, 2 per tet")
     a = ap.parse_args()
     import numpy as np
     import torch
@@ -32,6 +33,8 @@ def main():
     tdt = torch.float64 if a.dtype == "f64" else torch.float32
     N0 = a.N >> a.nrefine
     h = fe.Hierarchy(N0, a.nrefine, a.degree)
+    if a.f64_mode is not None:
+        h.set_f64_mode(a.f64_mode)
     n = h.n_dofs()
     x = torch.from_numpy(np.random.default_rng(0).uniform(-1, 1, n)).to("cuda", tdt)
     y = torch.empty_like(x)
