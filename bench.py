@@ -36,7 +36,7 @@ SAMPLE = {"N0": 8, "nrefine": 2, "degree": 2}  # oracle bounded sample: P2 32^3,
 F64_MODE = 1  # FE_F64_DOUBLE_FLOAT: the library default for FP64 operator applications
 # DRAM bytes per launch of the dominant kernel on this workload from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by FP64 mode; None until captured
-TRAFFIC = {0: 188.2e6, 1: 183.6e6}
+TRAFFIC = {0: 188.2e6, 1: 183.6e6, 2: 183.6e6}
 # Flops of one P2 element application (c, d, S, four G-products, transpose;
 # an FMA counts 2), per tet: 151 in the FP64 formula; the double-float form of
 # the same formula costs 1493 FP32 flops (95 float-pair additions x 11, 36
@@ -359,7 +359,8 @@ def run_ours(args, rank, world, local_rank):
         return None
     apply_ms = sum(s.apply_ms for s in stats) / max(1, sum(s.apply_timed for s in stats))
     if F64_MODE == fe.FE_F64_DOUBLE_FLOAT:
-        kname, flops, peak = "k_apply_df<2> (FP64 operator in double-float on the FP32 pipes)", FLOPS_PER_CELL_P2_DF * C, FP32_PEAK_TFLOPS
+        kname, flops, peak = ("k_apply_df<2> (FP64 operator in double-float on the FP32 pipes, persistent, one tet "
+                              "per thread)", FLOPS_PER_CELL_P2_DF * C, FP32_PEAK_TFLOPS)
         psrc = "nominal FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (recipe unit counts and clock); no measured FP32 peak"
     else:
         kname, flops, peak = "k_apply<2,double> (native FP64 operator)", FLOPS_PER_CELL_P2_F64 * C, FP64_PEAK_TFLOPS

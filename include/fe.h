@@ -66,9 +66,10 @@ extern "C" {
 
 /* ---- arithmetic of FP64 operator applications (fe_set_f64_mode) ---- */
 #define FE_F64_NATIVE 0        /* FP64 FMA on the FP64 pipe */
-#define FE_F64_DOUBLE_FLOAT 1  /* float-pair (hi + lo, ~48-bit) arithmetic on the FP32 pipes, FP64 in and out;
-                                  one thread per cube (six tets) */
-#define FE_F64_DOUBLE_FLOAT_TET 2  /* the same arithmetic, one thread per tet (persistent, prefetching) */
+#define FE_F64_DOUBLE_FLOAT 1       /* float-pair (hi + lo, ~48-bit) arithmetic on the FP32 pipes, FP64 in and
+                                       out, with the faster layout per degree (P1: per cube, P2: per tet) */
+#define FE_F64_DOUBLE_FLOAT_TET 2   /* the same arithmetic, one thread per tet (persistent, prefetching) */
+#define FE_F64_DOUBLE_FLOAT_CUBE 3  /* the same arithmetic, one thread per cube (27/8 dofs split and scattered once) */
 
 /* ---- preconditioners and precision modes of fe_solve_poisson ---- */
 #define FE_PC_JACOBI 0

@@ -21,7 +21,7 @@ def main():
     ap.add_argument("--nrefine", type=int, default=0)
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--f64-mode", type=int, default=None, help="0 native, 1 double-float per cube, 2 per tet")
+    ap.add_argument("--f64-mode", type=int, default=None, help="0 native, 1 double-float (best layout), 2 per tet, 3 per cube")
     a = ap.parse_args()
     import numpy as np
     import torch

@@ -54,7 +54,7 @@ def test_fullsize_operator_rows(fe, N):
         scale = _rows_scale(space, kappa, x, rows)
         xd = torch.from_numpy(x).to(DEV)
         y = torch.empty_like(xd)
-        for mode in (fe.FE_F64_NATIVE, fe.FE_F64_DOUBLE_FLOAT, fe.FE_F64_DOUBLE_FLOAT_TET):
+        for mode in (fe.FE_F64_NATIVE, fe.FE_F64_DOUBLE_FLOAT_TET, fe.FE_F64_DOUBLE_FLOAT_CUBE):
             h.set_f64_mode(mode)
             h.apply_operator(xd, y)
             got = y.cpu().numpy()[rows]

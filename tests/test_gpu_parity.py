@@ -60,12 +60,12 @@ def test_mesh_queries_match_oracle(fe, k, N):
 @pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("N", [1, 2, 3, 5, 8])
 @pytest.mark.parametrize("coef", ["one", "grf"])
-@pytest.mark.parametrize("mode", ["native", "double_float", "double_float_tet"])
+@pytest.mark.parametrize("mode", ["native", "double_float_tet", "double_float_cube"])
 def test_apply_f64(fe, k, N, coef, mode):
     """FP64 operator in both arithmetics: FP64 FMAs and float-pair (~48-bit) on the FP32 pipes
     (per cube and per tet)."""
     with fe.Hierarchy(N, 0, k) as h:
-        h.set_f64_mode({"native": fe.FE_F64_NATIVE, "double_float": fe.FE_F64_DOUBLE_FLOAT,
+        h.set_f64_mode({"native": fe.FE_F64_NATIVE, "double_float_cube": fe.FE_F64_DOUBLE_FLOAT_CUBE,
                         "double_float_tet": fe.FE_F64_DOUBLE_FLOAT_TET}[mode])
         kappa = None if coef == "one" else I.grf_kappa(h.cell_centroids(), seed=N)
         h.set_coefficient(None if kappa is None else dt(kappa))
@@ -94,13 +94,13 @@ def test_apply_f32(fe, k):
 
 
 @pytest.mark.parametrize("scale", [1e-250, 1e-30, 1e-8, 1.0, 1e8, 1e30, 1e250])
-@pytest.mark.parametrize("mode", ["double_float", "double_float_tet"])
+@pytest.mark.parametrize("mode", ["double_float_cube", "double_float_tet"])
 def test_double_float_value_range(fe, scale, mode):
     """The float-pair split/widen keep FP64-class accuracy over the whole FP64 range (each
     tet's dofs are scaled by a power of two first), with exact zeros and sign changes,
     and NaN dofs propagate."""
     with fe.Hierarchy(3, 0, 2) as h:
-        h.set_f64_mode(fe.FE_F64_DOUBLE_FLOAT if mode == "double_float" else fe.FE_F64_DOUBLE_FLOAT_TET)
+        h.set_f64_mode(fe.FE_F64_DOUBLE_FLOAT_CUBE if mode == "double_float_cube" else fe.FE_F64_DOUBLE_FLOAT_TET)
         L = O.Level(3, 2)
         x = I.random_vector(L.n, 77) * scale
         x[::7] = 0.0
