@@ -22,7 +22,7 @@
 #include <chrono>
 #include <memory>
 
-#include "fe_internal.cuh"
+#include "fe_df.cuh"
 
 void mass_tables_host(double m1[16], double m2[100]);
 
@@ -36,6 +36,7 @@ struct BLevel {
   Numbering num;
   const int* map;
   const double* geo;
+  const float2* geodf;  // geo as float pairs (double-float operator)
   const double* dinv;
   const double* detj;
   const int* bnd;
@@ -86,6 +87,7 @@ struct Params {
   const double* mref1;
   const double* mref2;
   int nprob, nlev, max_it;
+  int df;  // FP64 operator in double-float arithmetic (the library default) or native FP64
   double rtol;
   unsigned long long timeout_ns;
   Work W;
@@ -312,6 +314,24 @@ __device__ void apply_cells(const Params& A, const BProb& P, const BLevel& L, in
         for (int j = 0; j < ND; ++j) a += mref[i * ND + j] * u[j];
         atomicAdd(out + idx[i], s * a);
       }
+    } else if (A.df) {
+#pragma unroll
+      for (int j = 0; j < ND; ++j) u[j] = idx[j] >= 0 ? in[idx[j]] : 0.0;
+      const int emax = fe_df::block_exponent<ND>(u);
+      fe_df::DF ud[ND], gd[6], od[ND];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) ud[j] = fe_df::split_scaled(u[j], emax);
+      if (emax == 0x7FF) ud[0] = fe_df::DF(__int_as_float(0x7fc00000), 0.0f);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const float2 v = L.geodf[(size_t)a * L.Cs + c];
+        gd[a] = fe_df::DF(v.x, v.y);
+      }
+      fe_df::element_df<DEG>(ud, gd, od);
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+        if (idx[j] >= 0)
+          atomicAdd(out + idx[j], fe_df::widen_scaled(od[j].hi, emax) + fe_df::widen_scaled(od[j].lo, emax));
     } else {
 #pragma unroll
       for (int j = 0; j < ND; ++j) u[j] = idx[j] >= 0 ? in[idx[j]] : 0.0;
@@ -582,6 +602,7 @@ void fill_problems(fe_batch* B, double cheb_lo, double cheb_hi) {
       D.num = L.num;
       D.map = L.map;
       D.geo = L.geo64;
+      D.geodf = L.geodf;
       D.dinv = L.dinv64;
       D.detj = L.detj;
       D.bnd = L.bnd;
@@ -651,6 +672,7 @@ Params make_params(fe_batch* B, const fe_solver_opts& o) {
   A.mref2 = B->mref2;
   A.nprob = (int)B->hs.size();
   A.nlev = B->nlev;
+  A.df = B->hs[0]->f64_mode != FE_F64_NATIVE;
   A.max_it = o.max_it;
   A.rtol = o.rtol;
   A.timeout_ns = o.wait_timeout_us > 0 ? (unsigned long long)o.wait_timeout_us * 1000ull : 5000000000ull;

@@ -15,170 +15,12 @@
 // the FP32 exponent range whatever the magnitude of the vector.
 #include <algorithm>
 
-#include "fe_internal.cuh"
+#include "fe_df.cuh"
 
 namespace {
 
+using namespace fe_df;
 constexpr int kBlock = 256;
-
-struct DF {
-  float hi, lo;
-  __device__ __forceinline__ DF() : hi(0.0f), lo(0.0f) {}
-  __device__ __forceinline__ explicit DF(float v) : hi(v), lo(0.0f) {}
-  __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
-  __device__ __forceinline__ explicit DF(int v) : hi((float)v), lo(0.0f) {}
-};
-
-// |s| >= |e| assumed; s + e = h + l exactly.
-__device__ __forceinline__ DF quick_two_sum(float s, float e) {
-  const float h = __fadd_rn(s, e);
-  return DF(h, __fsub_rn(e, __fsub_rn(h, s)));
-}
-
-// a + b = s + e exactly (Knuth).
-__device__ __forceinline__ DF two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float v = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
-  return DF(s, e);
-}
-
-__device__ __forceinline__ DF operator+(DF x, DF y) {
-  const DF t = two_sum(x.hi, y.hi);
-  return quick_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(x.lo, y.lo)));
-}
-__device__ __forceinline__ DF operator-(DF x) { return DF(-x.hi, -x.lo); }
-__device__ __forceinline__ DF operator-(DF x, DF y) { return x + (-y); }
-
-// Exact scaling by a power of two.
-__device__ __forceinline__ DF scale2(DF x, float k) { return DF(__fmul_rn(x.hi, k), __fmul_rn(x.lo, k)); }
-// x * k for a small integer k (TwoProd of the leading term).
-__device__ __forceinline__ DF scalek(DF x, float k) {
-  const float p = __fmul_rn(x.hi, k);
-  const float e = __fmaf_rn(x.lo, k, __fmaf_rn(x.hi, k, -p));
-  return quick_two_sum(p, e);
-}
-
-// a0 b0 + a1 b1 + a2 b2 with one renormalisation: the three leading products
-// are summed exactly (TwoSum), every error term (product errors, cross terms,
-// summation errors) is gathered in one float.
-__device__ __forceinline__ DF dot3(DF a0, DF b0, DF a1, DF b1, DF a2, DF b2) {
-  const float p0 = __fmul_rn(a0.hi, b0.hi), p1 = __fmul_rn(a1.hi, b1.hi), p2 = __fmul_rn(a2.hi, b2.hi);
-  float e0 = __fmaf_rn(a0.hi, b0.hi, -p0), e1 = __fmaf_rn(a1.hi, b1.hi, -p1), e2 = __fmaf_rn(a2.hi, b2.hi, -p2);
-  e0 = __fmaf_rn(a0.lo, b0.hi, __fmaf_rn(a0.hi, b0.lo, e0));
-  e1 = __fmaf_rn(a1.lo, b1.hi, __fmaf_rn(a1.hi, b1.lo, e1));
-  e2 = __fmaf_rn(a2.lo, b2.hi, __fmaf_rn(a2.hi, b2.lo, e2));
-  const DF s1 = two_sum(p0, p1);
-  const DF s2 = two_sum(s1.hi, p2);
-  return quick_two_sum(s2.hi, __fadd_rn(__fadd_rn(e0, e1), __fadd_rn(__fadd_rn(e2, s1.lo), s2.lo)));
-}
-
-// h = G t for the symmetric G stored (00, 01, 02, 11, 12, 22).
-__device__ __forceinline__ void gmul(const DF (&g)[6], DF t0, DF t1, DF t2, DF& h0, DF& h1, DF& h2) {
-  h0 = dot3(g[0], t0, g[1], t1, g[2], t2);
-  h1 = dot3(g[1], t0, g[3], t1, g[4], t2);
-  h2 = dot3(g[2], t0, g[4], t1, g[5], t2);
-}
-
-// The P2 vertex-gradient element of fe_internal.cuh written out without
-// loops (u: 4 vertices then edges 01,02,03,12,13,23), so that every float
-// pair stays in registers.
-__device__ __forceinline__ void p2_element_df(const DF (&u)[10], const DF (&g)[6], DF (&y)[10]) {
-  const DF f01 = scale2(u[4], 4.f), f02 = scale2(u[5], 4.f), f03 = scale2(u[6], 4.f);
-  const DF f12 = scale2(u[7], 4.f), f13 = scale2(u[8], 4.f), f23 = scale2(u[9], 4.f);
-  // c_wv = 4 u_wv - u_v, c_ww = 3 u_w;  d_w = (c_w1 - c_w0, c_w2 - c_w0, c_w3 - c_w0)
-  const DF c00 = scalek(u[0], 3.f), c01 = f01 - u[1], c02 = f02 - u[2], c03 = f03 - u[3];
-  const DF c10 = f01 - u[0], c11 = scalek(u[1], 3.f), c12 = f12 - u[2], c13 = f13 - u[3];
-  const DF c20 = f02 - u[0], c21 = f12 - u[1], c22 = scalek(u[2], 3.f), c23 = f23 - u[3];
-  const DF c30 = f03 - u[0], c31 = f13 - u[1], c32 = f23 - u[2], c33 = scalek(u[3], 3.f);
-  const DF d00 = c01 - c00, d01 = c02 - c00, d02 = c03 - c00;
-  const DF d10 = c11 - c10, d11 = c12 - c10, d12 = c13 - c10;
-  const DF d20 = c21 - c20, d21 = c22 - c20, d22 = c23 - c20;
-  const DF d30 = c31 - c30, d31 = c32 - c30, d32 = c33 - c30;
-  const DF S0 = (d00 + d10) + (d20 + d30), S1 = (d01 + d11) + (d21 + d31), S2 = (d02 + d12) + (d22 + d32);
-  DF b01, b02, b03, b11, b12, b13, b21, b22, b23, b31, b32, b33;  // cb_wv = h_w[v-1]
-  gmul(g, S0 + d00, S1 + d01, S2 + d02, b01, b02, b03);
-  gmul(g, S0 + d10, S1 + d11, S2 + d12, b11, b12, b13);
-  gmul(g, S0 + d20, S1 + d21, S2 + d22, b21, b22, b23);
-  gmul(g, S0 + d30, S1 + d31, S2 + d32, b31, b32, b33);
-  const DF b00 = -(b01 + b02 + b03), b10 = -(b11 + b12 + b13), b20 = -(b21 + b22 + b23), b30 = -(b31 + b32 + b33);
-  // y_v = 3 cb_vv - sum_{w != v} cb_wv;  y_(ab) = 4 (cb_ab + cb_ba)
-  y[0] = scalek(b00, 3.f) - ((b10 + b20) + b30);
-  y[1] = scalek(b11, 3.f) - ((b01 + b21) + b31);
-  y[2] = scalek(b22, 3.f) - ((b02 + b12) + b32);
-  y[3] = scalek(b33, 3.f) - ((b03 + b13) + b23);
-  y[4] = scale2(b01 + b10, 4.f);
-  y[5] = scale2(b02 + b20, 4.f);
-  y[6] = scale2(b03 + b30, 4.f);
-  y[7] = scale2(b12 + b21, 4.f);
-  y[8] = scale2(b13 + b31, 4.f);
-  y[9] = scale2(b23 + b32, 4.f);
-}
-
-__device__ __forceinline__ void p1_element_df(const DF (&u)[4], const DF (&g)[6], DF (&y)[4]) {
-  DF h0, h1, h2;
-  gmul(g, u[1] - u[0], u[2] - u[0], u[3] - u[0], h0, h1, h2);
-  y[1] = h0;
-  y[2] = h1;
-  y[3] = h2;
-  y[0] = -(h0 + h1 + h2);
-}
-
-template <int DEG>
-__device__ __forceinline__ void element_df(const DF (&u)[DEG == 1 ? 4 : 10], const DF (&g)[6],
-                                           DF (&y)[DEG == 1 ? 4 : 10]) {
-  if constexpr (DEG == 1)
-    p1_element_df(u, g, y);
-  else
-    p2_element_df(u, g, y);
-}
-
-// Whether cube-local node l already received a contribution from one of the
-// tets 0..t-1 (decides at compile time between initialising and adding).
-__host__ __device__ constexpr bool touched_before(int deg, int t, int l) {
-  bool hit = false;
-  for (int s = 0; s < t; ++s)
-    for (int j = 0; j < (deg == 1 ? 4 : 10); ++j) hit = hit || cube_local(deg, s, j) == l;
-  return hit;
-}
-
-// double -> float pair by bit manipulation, after scaling by 2^(1023 - emax)
-// (emax: the largest biased exponent of the tet's dofs, so the largest dof
-// maps to [1, 2)): hi keeps the leading 24 bits of the significand
-// (truncated), lo the next 24 (rounded).  Dofs more than 2^126 below the
-// tet's largest flush to 0 (negligible against it).
-__device__ __forceinline__ DF split_scaled(double x, int emax) {
-  const unsigned int h32 = (unsigned int)__double2hiint(x), l32 = (unsigned int)__double2loint(x);
-  const int e = (int)((h32 >> 20) & 0x7FFu) - emax + 1023;  // exponent field of x * 2^(1023 - emax)
-  const unsigned int sgn = h32 & 0x80000000u;
-  if (((h32 >> 20) & 0x7FFu) == 0u || e <= 896) return DF(__uint_as_float(sgn), 0.0f);
-  const unsigned int hb = sgn | ((unsigned int)(e - 896) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
-  const float scale = e > 948 ? __uint_as_float((unsigned int)(e - 948) << 23) : 0.0f;  // 2^(e - 1075)
-  const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
-  return DF(__uint_as_float(hb), __uint_as_float(__float_as_uint(lo) | sgn));
-}
-
-// Largest biased exponent of the dofs (1023 if all are zero); 0x7FF if any is not finite.
-template <int ND>
-__device__ __forceinline__ int block_exponent(const double (&xv)[ND]) {
-  int emax = 0;
-#pragma unroll
-  for (int j = 0; j < ND; ++j) emax = max(emax, (int)(((unsigned int)__double2hiint(xv[j]) >> 20) & 0x7FFu));
-  return emax == 0 ? 1023 : emax;
-}
-
-// exact float -> double of f * 2^(emax - 1023) by bit manipulation
-// (results below the double range flush to 0, above it give inf)
-__device__ __forceinline__ double widen_scaled(float f, int emax) {
-  const unsigned int b = __float_as_uint(f);
-  const int ef = (int)((b >> 23) & 0xFFu);
-  const unsigned int sgn = b & 0x80000000u;
-  if (ef == 0) return __hiloint2double((int)sgn, 0);
-  const int eh = ef + emax - 127;
-  if (ef == 0xFF || eh >= 0x7FF) return __hiloint2double((int)(sgn | 0x7FF00000u | ((b & 0x7FFFFFu) >> 3)), 0);
-  if (eh <= 0) return __hiloint2double((int)sgn, 0);
-  return __hiloint2double((int)(sgn | ((unsigned int)eh << 20) | ((b & 0x7FFFFFu) >> 3)), (int)((b & 7u) << 29));
-}
 
 // Persistent grid-stride loop over tets: while one tet is contracted, the
 // map rows, dofs and geometric factors of the thread's next tet are already
