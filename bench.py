@@ -141,6 +141,19 @@ def extras(fe, I, h, dev, stream, flush):
     ref = torch.empty(h2.n_dofs(), dtype=torch.float64, device=dev)
     u2 = torch.empty_like(ref)
     mp = {"workload": "P2 UnitCubeMesh 128^3, 5 levels, rtol 1e-8", "dofs": h2.n_dofs()}
+    # FP32 matvec on the 128^3 level (inputs 8x larger than L2)
+    n2 = h2.n_dofs()
+    x32 = torch.rand(n2, dtype=torch.float32, device=dev)
+    y32 = torch.empty_like(x32)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            h2.apply_operator(x32, y32, dtype=fe.FE_F32, stream=stream)
+        ms = time_launches(lambda: h2.apply_operator(x32, y32, dtype=fe.FE_F32, stream=stream), stream, 10, flush)
+    byt = apply_bytes_per_launch(n2, h2.n_cells(), 10, 4, 4, cube_map=True)
+    out["matvec_p2_128cubed_f32"] = {"ms": ms, "GDoF_per_s": n2 / (ms * 1e-3) / 1e9, "GB_per_s": byt / (ms * 1e-3) / 1e9,
+                                     "hbm_frac": byt / (ms * 1e-3) / 1e9 / peak, "bytes_per_dof": byt / n2,
+                                     "hbm_peak_gbs": peak, "hbm_peak_source": src}
+    del x32, y32
     for name, prec in (("f64", fe.FE_PREC_F64), ("mixed_f32", fe.FE_PREC_MIXED_F32),
                        ("mixed_bf16_tensor_core", fe.FE_PREC_MIXED_BF16)):
         target = ref if prec == fe.FE_PREC_F64 else u2

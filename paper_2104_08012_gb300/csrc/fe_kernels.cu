@@ -128,28 +128,35 @@ __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const
 // Cube-aggregated apply: one thread per cube gathers the cube's (k+1)^3 dofs
 // once, applies its six Kuhn tets into register accumulators and scatters
 // (k+1)^3 atomics instead of 6 * nd (27 instead of 60 for P2).
-template <int DEG, typename T>
+template <int DEG>
 __global__ void __launch_bounds__(kBlock) k_apply_cube(int Q, int Qs, int Cs, int Qpad, const int* __restrict__ cmap,
-                                                       const T* __restrict__ geo, const T* __restrict__ x,
-                                                       T* __restrict__ y, int nb, const int* __restrict__ bnd) {
+                                                       const float* __restrict__ geo, const float* __restrict__ x,
+                                                       float* __restrict__ y, int nb, const int* __restrict__ bnd) {
   constexpr int NL = DEG == 1 ? 8 : 27, ND = DEG == 1 ? 4 : 10;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < Q) {
-    T xv[NL], acc[NL];
+    float xv[NL], acc[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       const int i = __ldg(cmap + (size_t)l * Qs + q);
-      xv[l] = i >= 0 ? __ldg(x + i) : T(0);
-      acc[l] = T(0);
+      xv[l] = i >= 0 ? __ldg(x + i) : 0.0f;
+      acc[l] = 0.0f;
     }
+    // The cube's six tets are cells 6q .. 6q+5, contiguous in every row of
+    // geo: one 8-byte load fetches G_a of two tets.
+    float2 gp[6][3];
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int h = 0; h < 3; ++h) gp[a][h] = __ldg(reinterpret_cast<const float2*>(geo + (size_t)a * Cs + 6 * q) + h);
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
-      T u[ND], g[6], o[ND];
+      float u[ND], g[6], o[ND];
 #pragma unroll
       for (int j = 0; j < ND; ++j) u[j] = xv[cube_local(DEG, t, j)];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) g[a] = __ldg(geo + (size_t)a * Cs + 6 * q + t);
-      element_apply<DEG, T>(u, g, o);
+      for (int a = 0; a < 6; ++a) g[a] = (t & 1) ? gp[a][t >> 1].y : gp[a][t >> 1].x;
+      element_apply<DEG, float>(u, g, o);
 #pragma unroll
       for (int j = 0; j < ND; ++j) acc[cube_local(DEG, t, j)] += o[j];
     }
@@ -475,23 +482,19 @@ static void apply_impl(const Level& L, const T* geo, const T* x, T* y, cudaStrea
   LAUNCH_CHECK();
 }
 
-template <typename T>
-static void apply_cube_impl(const Level& L, const T* geo, const T* x, T* y, cudaStream_t s) {
-  CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)L.n, s));
+static void apply_cube32(const Level& L, const float* x, float* y, cudaStream_t s) {
+  CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)L.n, s));
   const int Qpad = ceil_div(L.Q, kBlock) * kBlock;
   const int grid = ceil_div((long long)Qpad + L.nb, kBlock);
   if (L.deg == 1)
-    k_apply_cube<1, T><<<grid, kBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, geo, x, y, L.nb, L.bnd);
+    k_apply_cube<1><<<grid, kBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd);
   else
-    k_apply_cube<2, T><<<grid, kBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, geo, x, y, L.nb, L.bnd);
+    k_apply_cube<2><<<grid, kBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd);
   LAUNCH_CHECK();
 }
 
 void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s) { apply_impl<double>(L, L.geo64, x, y, s); }
-void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) { apply_cube_impl<float>(L, L.geo32, x, y, s); }
-void launch_apply32_cells(const Level& L, const float* x, float* y, cudaStream_t s) {
-  apply_impl<float>(L, L.geo32, x, y, s);
-}
+void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) { apply_cube32(L, x, y, s); }
 
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));

@@ -79,11 +79,14 @@ def test_apply_f64(fe, k, N, coef, mode):
 
 
 @pytest.mark.parametrize("k", [1, 2])
-def test_apply_f32(fe, k):
-    N = 6
+@pytest.mark.parametrize("N,variable_kappa", [(6, True), (17, True), (12, False)])
+def test_apply_f32(fe, k, N, variable_kappa):
+    """FP32 apply (one thread per cube, 256 per block): meshes whose cube counts leave a
+    ragged last block (N=6, N=17) and a constant coefficient (N=12)."""
     with fe.Hierarchy(N, 0, k) as h:
-        kappa = I.grf_kappa(h.cell_centroids(), seed=3)
-        h.set_coefficient(dt(kappa))
+        kappa = I.grf_kappa(h.cell_centroids(), seed=3) if variable_kappa else np.ones(6 * N ** 3)
+        if variable_kappa:
+            h.set_coefficient(dt(kappa))
         L = O.Level(N, k, kappa)
         x = I.random_vector(L.n, 4).astype(np.float32)
         y = torch.empty(L.n, dtype=torch.float32, device=DEV)
