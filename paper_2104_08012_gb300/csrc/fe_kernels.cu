@@ -369,34 +369,41 @@ __global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __rest
 
 // Restriction = exact transpose: coarse point Lc gathers fine points
 // 2 Lc + f_off for the stencil entries of its parity class.  With yf != null
-// the restricted vector is the residual bf - yf.
-template <int DEG, typename T>
+// the restricted vector is the residual bf - yf.  TPC consecutive threads share
+// one coarse point (a P2 vertex gathers 125 fine points): each takes every
+// TPC-th stencil entry and the partial sums meet in a butterfly of shuffles,
+// so the gather runs with TPC times more loads in flight than one thread per
+// coarse point would have.
+template <int DEG, typename T, int TPC>
 __global__ void k_restrict(Numbering nf, Numbering nc, int n_c, const int* __restrict__ start,
                            const int4* __restrict__ off, const double* __restrict__ w, const T* __restrict__ bf,
                            const T* __restrict__ yf, T* __restrict__ rc, int zero_bd) {
-  const int J = blockIdx.x * blockDim.x + threadIdx.x;
-  if (J >= n_c) return;
-  int X, Y, Z;
-  dof_to_lattice(nc, J, X, Y, Z);
-  const bool bd = X == 0 || Y == 0 || Z == 0 || X == nc.m || Y == nc.m || Z == nc.m;
-  if (bd && zero_bd) {
-    rc[J] = T(0);
-    return;
-  }
-  const int cls = DEG == 2 ? ((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2)) : 0;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = gt / TPC, sub = gt % TPC;
   T s = T(0);
-  const int e1 = __ldg(start + cls + 1);
-  const int mf = nf.m;
-  for (int e = __ldg(start + cls); e < e1; ++e) {
-    const int4 o = __ldg(off + e);
-    const int fx = 2 * X + o.x, fy = 2 * Y + o.y, fz = 2 * Z + o.z;
-    if (fx < 0 || fy < 0 || fz < 0 || fx > mf || fy > mf || fz > mf) continue;
-    const int i = lattice_to_dof(nf, fx, fy, fz);
-    T v = __ldg(bf + i);
-    if (yf) v -= __ldg(yf + i);
-    s += (T)__ldg(w + e) * v;
+  if (J < n_c) {
+    int X, Y, Z;
+    dof_to_lattice(nc, J, X, Y, Z);
+    const bool bd = X == 0 || Y == 0 || Z == 0 || X == nc.m || Y == nc.m || Z == nc.m;
+    if (!(bd && zero_bd)) {
+      const int cls = DEG == 2 ? ((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2)) : 0;
+      const int e1 = __ldg(start + cls + 1);
+      const int mf = nf.m;
+#pragma unroll 2
+      for (int e = __ldg(start + cls) + sub; e < e1; e += TPC) {
+        const int4 o = __ldg(off + e);
+        const int fx = 2 * X + o.x, fy = 2 * Y + o.y, fz = 2 * Z + o.z;
+        if (fx < 0 || fy < 0 || fz < 0 || fx > mf || fy > mf || fz > mf) continue;
+        const int i = lattice_to_dof(nf, fx, fy, fz);
+        T v = __ldg(bf + i);
+        if (yf) v -= __ldg(yf + i);
+        s += (T)__ldg(w + e) * v;
+      }
+    }
   }
-  rc[J] = s;
+#pragma unroll
+  for (int o = TPC / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (J < n_c && sub == 0) rc[J] = s;
 }
 
 // --------------------------------------------------------- vector ops
@@ -578,11 +585,11 @@ void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T*
   const Level& Cc = h->L[lf - 1];
   const TransferTables& t = h->tt;
   if (h->deg == 1)
-    k_restrict<1, T><<<ceil_div(Cc.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off, t.res_w,
-                                                              bf, yf, rc, zero_bd);
+    k_restrict<1, T, 4><<<ceil_div(4LL * Cc.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off,
+                                                                       t.res_w, bf, yf, rc, zero_bd);
   else
-    k_restrict<2, T><<<ceil_div(Cc.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off, t.res_w,
-                                                              bf, yf, rc, zero_bd);
+    k_restrict<2, T, 8><<<ceil_div(8LL * Cc.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off,
+                                                                       t.res_w, bf, yf, rc, zero_bd);
   LAUNCH_CHECK();
 }
 
