@@ -309,6 +309,15 @@ template <> float* lv_y<float>(Level& L) { return L.y32; }
 template <> float* lv_d<float>(Level& L) { return L.d32; }
 template <> const float* lv_dinv<float>(const Level& L) { return L.dinv32; }
 
+// Consistent mass y = M x in FP64: float-pair arithmetic unless the hierarchy
+// is in native-FP64 mode (the operator's mode decides both).
+static void mass_enqueue(const fe_hierarchy* h, const Level& L, const double* x, double* y, cudaStream_t s) {
+  if (h->f64_mode == FE_F64_NATIVE)
+    launch_mass(L, x, y, s);
+  else
+    launch_mass_df(L, x, y, s);
+}
+
 void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s) {
   const Level& L = h->L[level];
   // measured on GB300 (P*64^3): P1 per cube 0.025 ms vs per tet 0.041 ms; P2 per tet 0.139 ms vs per cube
@@ -655,7 +664,7 @@ static const double* rhs_to_load(fe_hierarchy* h, const double* rhs, int kind, c
   if (kind == FE_RHS_LOAD) {
     if (rd != h->b.p) CUDA_CHECK(cudaMemcpyAsync(h->b, rd, sizeof(double) * F.n, cudaMemcpyDeviceToDevice, s));
   } else if (kind == FE_RHS_NODAL_F) {
-    launch_mass(F, rd, h->b, s);
+    mass_enqueue(h, F, rd, h->b, s);
     launch_zero_boundary64(F, h->b, s);
   } else {
     FE_FAIL(FE_ERR_ARG, "unknown rhs kind");
@@ -723,6 +732,7 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     L.geo32.alloc((size_t)6 * L.Cs);
     CUDA_CHECK(cudaMemset(L.geo32, 0, sizeof(float) * (size_t)6 * L.Cs));
     L.geodf.alloc((size_t)6 * L.Cs);
+    L.massdf.alloc(L.C);
     L.dinv64.alloc(L.n);
     L.dinv32.alloc(L.n);
     for (auto* v : {&L.b64, &L.x64, &L.y64, &L.d64, &L.w64}) v->alloc(L.n);
@@ -936,7 +946,7 @@ int fe_apply_mass(const fe_hierarchy* hc, int level, const double* x, double* y,
   cudaStream_t s = as_stream(stream);
   const double* xd = stage_in<double>(h, 0, x, L.n, s);
   double* yd = stage_out<double>(h, 1, y, L.n);
-  launch_mass(L, xd, yd, s);
+  mass_enqueue(h, L, xd, yd, s);
   finish_out(y, yd, L.n, s);
   API_END
 }
@@ -1129,7 +1139,7 @@ int fe_adjoint_gradient(fe_hierarchy* h, const double* rhs, int rhs_kind, const 
   const double* ud = stage_in<double>(h, 1, u_d, n, s);
   // Me = M (u - u_d); J = (u - u_d)^T M (u - u_d)
   launch_sub64(n, u, ud, h->b, s);
-  launch_mass(F, h->b, Me, s);
+  mass_enqueue(h, F, h->b, Me, s);
   launch_dot<double>(h->red, n, h->b, Me, S_DOT, s);
   double Jh = 0.0;
   CUDA_CHECK(cudaMemcpyAsync(&Jh, h->red.scal + S_DOT, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1160,7 +1170,7 @@ int fe_objective(const fe_hierarchy* hc, const double* u, const double* u_d, dou
   const double* ud = stage_in<double>(h, 0, u, F.n, s);
   const double* udd = stage_in<double>(h, 1, u_d, F.n, s);
   launch_sub64(F.n, ud, udd, h->tmp, s);
-  launch_mass(F, h->tmp, h->q, s);
+  mass_enqueue(h, F, h->tmp, h->q, s);
   launch_dot<double>(h->red, F.n, h->tmp.p, h->q.p, S_DOT, s);
   CUDA_CHECK(cudaMemcpyAsync(J, h->red.scal + S_DOT, sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_CHECK(cudaStreamSynchronize(s));

@@ -66,6 +66,12 @@ __device__ __forceinline__ DF dot3(DF a0, DF b0, DF a1, DF b1, DF a2, DF b2) {
   return DF(s2.hi, __fadd_rn(__fadd_rn(e0, e1), __fadd_rn(__fadd_rn(e2, s1.lo), s2.lo)));  // unnormalised, as +
 }
 
+// a * b with the leading product exact (TwoProd), unnormalised like +.
+__device__ __forceinline__ DF mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  return DF(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p))));
+}
+
 // h = G t for the symmetric G stored (00, 01, 02, 11, 12, 22).
 __device__ __forceinline__ void gmul(const DF (&g)[6], DF t0, DF t1, DF t2, DF& h0, DF& h1, DF& h2) {
   h0 = dot3(g[0], t0, g[1], t1, g[2], t2);
@@ -115,6 +121,38 @@ __device__ __forceinline__ void p1_element_df(const DF (&u)[4], const DF (&g)[6]
   y[2] = h1;
   y[3] = h2;
   y[0] = -(h0 + h1 + h2);
+}
+
+// Consistent mass of a tet, y = s K u with s = |det J| / 2520 and the integer
+// P2 matrix K of 2520 int_ref phi_i phi_j (vertices 6 on the diagonal, 1 off it;
+// vertex-edge -4 if the edge holds the vertex, else -6; edge-edge 32 on the
+// diagonal, 8 for the opposite edge, 16 otherwise), applied through sums:
+// (K u)_v = 5 u_v + U - 6 E + 2 E_v,  (K u)_ab = 16 E + 16 u_ab - 8 u_opp - 6 U + 2 (u_a + u_b)
+// with U the vertex sum, E the edge sum and E_v the sum over the edges at v.
+__device__ __forceinline__ void p2_mass_df(const DF (&u)[10], DF s, DF (&y)[10]) {
+  const DF U = (u[0] + u[1]) + (u[2] + u[3]);
+  const DF E0 = (u[4] + u[5]) + u[6], E1 = (u[4] + u[7]) + u[8], E2 = (u[5] + u[7]) + u[9], E3 = (u[6] + u[8]) + u[9];
+  const DF E = (E0 + u[7]) + (u[8] + u[9]);
+  const DF W = U - (scale2(E, 4.f) + scale2(E, 2.f));                // U - 6E
+  const DF Z = scale2(E, 16.f) - (scale2(U, 4.f) + scale2(U, 2.f));  // 16E - 6U
+  y[0] = mul(s, ((scale2(u[0], 4.f) + u[0]) + W) + scale2(E0, 2.f));
+  y[1] = mul(s, ((scale2(u[1], 4.f) + u[1]) + W) + scale2(E1, 2.f));
+  y[2] = mul(s, ((scale2(u[2], 4.f) + u[2]) + W) + scale2(E2, 2.f));
+  y[3] = mul(s, ((scale2(u[3], 4.f) + u[3]) + W) + scale2(E3, 2.f));
+  // edges 01, 02, 03, 12, 13, 23; opposite pairs (01, 23), (02, 13), (03, 12)
+  y[4] = mul(s, (Z + (scale2(u[4], 16.f) - scale2(u[9], 8.f))) + scale2(u[0] + u[1], 2.f));
+  y[5] = mul(s, (Z + (scale2(u[5], 16.f) - scale2(u[8], 8.f))) + scale2(u[0] + u[2], 2.f));
+  y[6] = mul(s, (Z + (scale2(u[6], 16.f) - scale2(u[7], 8.f))) + scale2(u[0] + u[3], 2.f));
+  y[7] = mul(s, (Z + (scale2(u[7], 16.f) - scale2(u[6], 8.f))) + scale2(u[1] + u[2], 2.f));
+  y[8] = mul(s, (Z + (scale2(u[8], 16.f) - scale2(u[5], 8.f))) + scale2(u[1] + u[3], 2.f));
+  y[9] = mul(s, (Z + (scale2(u[9], 16.f) - scale2(u[4], 8.f))) + scale2(u[2] + u[3], 2.f));
+}
+
+// P1: 120 int_ref phi_i phi_j = 1 + delta_ij, so y_i = s (u_i + U) with s = |det J| / 120.
+__device__ __forceinline__ void p1_mass_df(const DF (&u)[4], DF s, DF (&y)[4]) {
+  const DF U = (u[0] + u[1]) + (u[2] + u[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) y[i] = mul(s, u[i] + U);
 }
 
 template <int DEG>

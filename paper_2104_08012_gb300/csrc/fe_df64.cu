@@ -129,7 +129,39 @@ __global__ void __launch_bounds__(kBlock, 1) k_apply_cube_df(int Q, int Qs, int 
   }
 }
 
-__global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, float2* __restrict__ geodf) {
+// Consistent mass, one tet per thread: y += s K u in float pairs (see
+// p2_mass_df), dofs scaled by the tet's largest power of two like the operator.
+template <int DEG>
+__global__ void __launch_bounds__(kBlock) k_mass_df(int C, int Cs, const int* __restrict__ map,
+                                                    const float2* __restrict__ mdf, const double* __restrict__ x,
+                                                    double* __restrict__ y) {
+  constexpr int ND = DEG == 1 ? 4 : 10;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  int idx[ND];
+  double xv[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const int m = __ldg(map + (size_t)j * Cs + c);
+    idx[j] = m < 0 ? -1 - m : m;  // the full mass matrix: Dirichlet dofs take part
+    xv[j] = __ldg(x + idx[j]);
+  }
+  const int emax = block_exponent<ND>(xv);
+  DF u[ND], out[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) u[j] = split_scaled(xv[j], emax);
+  if (emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
+  const float2 sv = __ldg(mdf + c);
+  if constexpr (DEG == 1)
+    p1_mass_df(u, DF(sv.x, sv.y), out);
+  else
+    p2_mass_df(u, DF(sv.x, sv.y), out);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) atomicAdd(y + idx[j], widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
+}
+
+__global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, float2* __restrict__ geodf,
+                            const double* __restrict__ detj, double wmass, float2* __restrict__ mdf) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   for (int a = 0; a < 6; ++a) {
@@ -137,12 +169,25 @@ __global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, flo
     const float hi = (float)g;
     geodf[(size_t)a * Cs + c] = make_float2(hi, (float)(g - (double)hi));
   }
+  const double m = detj[c] * wmass;
+  const float mh = (float)m;
+  mdf[c] = make_float2(mh, (float)(m - (double)mh));
 }
 
 }  // namespace
 
 void launch_split_geometry(Level& L, cudaStream_t s) {
-  k_split_geo<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, L.geodf);
+  k_split_geo<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, L.geodf, L.detj,
+                                                       L.deg == 1 ? 1.0 / 120.0 : 1.0 / 2520.0, L.massdf);
+  LAUNCH_CHECK();
+}
+
+void launch_mass_df(const Level& L, const double* x, double* y, cudaStream_t s) {
+  CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
+  if (L.deg == 1)
+    k_mass_df<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.massdf, x, y);
+  else
+    k_mass_df<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.massdf, x, y);
   LAUNCH_CHECK();
 }
 

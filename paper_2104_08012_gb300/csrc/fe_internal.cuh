@@ -167,6 +167,7 @@ struct Level {
   DBuf<double> geo64;     // [6][Cs] kappa*|detJ| J^-1 J^-T / w  (w = 6 for P1, 120 for P2)
   DBuf<float> geo32;
   DBuf<float2> geodf;     // [6][Cs] geo64 split into float pairs (hi, lo) for the double-float apply
+  DBuf<float2> massdf;    // |det J| / 120 (P1) or / 2520 (P2) per cell as a float pair (double-float mass)
   DBuf<double> dinv64;    // 1/diag(A)
   DBuf<float> dinv32;
   DBuf<int> bnd;          // Dirichlet dofs
@@ -253,6 +254,7 @@ void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t 
 void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_split_geometry(Level& L, cudaStream_t s);
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);
+void launch_mass_df(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_diag(Level& L, double* diag_out, cudaStream_t s);
 void launch_gradient(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s);
 void launch_dof_coords(const Level& L, double* xyz, cudaStream_t s);
