@@ -174,6 +174,10 @@ static void build_transfer_tables(TransferTables& t, int deg) {
     }
     t.h_res_start.push_back((int)t.h_res_off.size());
   }
+  // the prolongation kernel unrolls at most 2 (P1) or 10 (P2) entries per fine point
+  for (int c = 0; c < t.n_pro_class; ++c)
+    FE_REQUIRE(t.h_pro_start[c + 1] - t.h_pro_start[c] <= (deg == 1 ? 2 : 10), FE_ERR_UNSUPPORTED,
+               "prolongation stencil longer than the kernel's bound");
   auto up = [](auto& dbuf, const auto& vec) {
     using T = typename std::decay_t<decltype(vec)>::value_type;
     dbuf.alloc(vec.size());

@@ -358,11 +358,17 @@ __global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __rest
   const int cx = x / K2, cy = y / K2, cz = z / K2;
   const int cls = (x - K2 * cx) + K2 * ((y - K2 * cy) + K2 * (z - K2 * cz));
   T s = T(0);
-  const int e1 = __ldg(start + cls + 1);
-  for (int e = __ldg(start + cls); e < e1; ++e) {
-    const int4 o = __ldg(off + e);
-    const int j = lattice_to_dof(nc, DEG * cx + o.x, DEG * cy + o.y, DEG * cz + o.z);
-    s += (T)__ldg(w + e) * __ldg(xc + j);
+  const int e0 = __ldg(start + cls), ne = __ldg(start + cls + 1) - e0;
+  // at most 10 coarse P2 dofs (2 for P1) per fine dof: unrolled and predicated,
+  // so all the gathers of a fine dof are in flight together
+  constexpr int MAXE = DEG == 1 ? 2 : 10;
+#pragma unroll
+  for (int k = 0; k < MAXE; ++k) {
+    if (k < ne) {
+      const int4 o = __ldg(off + e0 + k);
+      const int j = lattice_to_dof(nc, DEG * cx + o.x, DEG * cy + o.y, DEG * cz + o.z);
+      s += (T)__ldg(w + e0 + k) * __ldg(xc + j);
+    }
   }
   xf[i] = accumulate ? xf[i] + s : s;
 }
