@@ -446,6 +446,10 @@ static void invalidate_graphs(fe_hierarchy* h) {
       cudaGraphExecDestroy(g.exec);
       g.exec = nullptr;
     }
+  if (h->cgloop.exec) {
+    cudaGraphExecDestroy(h->cgloop.exec);
+    h->cgloop.exec = nullptr;
+  }
 }
 
 // ------------------------------------------------------------ PCG
@@ -485,6 +489,114 @@ struct ApplyTimer {
 };
 
 // FP64 PCG on the finest level: b, x device vectors (x overwritten).
+// Kernel nodes of a captured graph.
+static long long count_kernel_nodes(cudaGraph_t g) {
+  size_t nn = 0;
+  CUDA_CHECK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) CUDA_CHECK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  long long k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    CUDA_CHECK(cudaGraphNodeGetType(nd, &ty));
+    if (ty == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+// The FP64 GMG-PCG iterations after the first as one graph: a loop test, then
+// a while node whose body is one CG iteration ending with the same test, so the
+// host neither waits for nor relaunches anything between iterations.
+static void build_cg_loop(fe_hierarchy* h) {
+  GraphCache& gc = h->vgraph[FE_F64];
+  if (!gc.stream) CUDA_CHECK(cudaStreamCreateWithFlags(&gc.stream, cudaStreamNonBlocking));
+  const cudaStream_t cs = gc.stream;
+  Level& F = h->L[h->nlev - 1];
+  const int n = F.n;
+  ReduceCtx& R = h->red;
+  double *r = F.b64, *z = F.x64, *p = h->p, *q = h->q, *x = h->xcg;
+  cudaGraph_t g, out;
+  CUDA_CHECK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond;
+  CUDA_CHECK(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+  auto capture = [&](cudaGraph_t into, auto&& body) {
+    CUDA_CHECK(cudaStreamBeginCaptureToGraph(cs, into, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    try {
+      body();
+    } catch (...) {
+      g_capturing = false;
+      cudaStreamEndCapture(cs, &out);
+      cudaGraphDestroy(g);
+      throw;
+    }
+    g_capturing = false;
+    CUDA_CHECK(cudaStreamEndCapture(cs, &out));
+  };
+  capture(g, [&] { launch_cg_cond(cond, R.scal, h->cgp, h->cgctl, 0, cs); });
+  cudaGraphNode_t test;
+  size_t one = 1;
+  CUDA_CHECK(cudaGraphGetNodes(g, &test, &one));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  CUDA_CHECK(cudaGraphAddNode(&loop, g, &test, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  capture(body, [&] {
+    run_vcycle(h, FE_F64, false, cs);
+    launch_cg_beta<double>(R, n, r, z, cs);
+    launch_cg_update_p<double>(R, n, p, z, cs);
+    apply_enqueue(h, h->nlev - 1, p, q, FE_F64, cs);
+    launch_cg_alpha<double>(R, n, p, q, cs);
+    launch_cg_update<double>(R, n, x, r, p, q, nullptr, z, cs);
+    launch_cg_cond(cond, R.scal, h->cgp, h->cgctl, 1, cs);
+  });
+  h->cgloop.body_kernels = count_kernel_nodes(body);
+  CUDA_CHECK(cudaGraphInstantiate(&h->cgloop.exec, g, 0));
+  cudaGraphDestroy(g);
+  h->cgloop.steps = g_sp.steps;
+  h->cgloop.lo = g_sp.lo;
+  h->cgloop.hi = g_sp.hi;
+}
+
+static PcgResult pcg64_graph(fe_hierarchy* h, double* x, const fe_solver_opts& o, double tol2, PcgResult res,
+                             cudaStream_t s) {
+  Level& F = h->L[h->nlev - 1];
+  const int n = F.n;
+  ReduceCtx& R = h->red;
+  double *r = F.b64, *z = F.x64, *p = h->p, *q = h->q, *xw = h->xcg;
+  auto& cl = h->cgloop;
+  if (cl.exec && (cl.steps != g_sp.steps || cl.lo != g_sp.lo || cl.hi != g_sp.hi)) {
+    cudaGraphExecDestroy(cl.exec);
+    cl.exec = nullptr;
+  }
+  if (!cl.exec) build_cg_loop(h);
+  // first iteration from the host, then the loop
+  CUDA_CHECK(cudaMemsetAsync(xw, 0, sizeof(double) * n, s));
+  apply_enqueue(h, h->nlev - 1, p, q, FE_F64, s);
+  launch_cg_alpha<double>(R, n, p, q, s);
+  launch_cg_update<double>(R, n, xw, r, p, q, nullptr, z, s);
+  launch_cg_set(h->cgp, h->cgctl, tol2, 1, o.max_it, s);
+  CUDA_CHECK(cudaGraphLaunch(cl.exec, s));
+  int ctl[2] = {0, 0};
+  CUDA_CHECK(cudaMemcpyAsync(ctl, h->cgctl, sizeof(ctl), cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaMemcpyAsync(R.h_scal + S_RR, R.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaMemcpyAsync(x, xw, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  res.it = ctl[0];
+  res.applies = ctl[0];
+  g_launches.fetch_add(1 + (long long)(ctl[0] - 1) * cl.body_kernels, std::memory_order_relaxed);
+  res.rr = R.h_scal[S_RR];
+  if (!std::isfinite(res.rr))
+    res.status = FE_ERR_NAN;
+  else if (res.rr > tol2)
+    res.status = FE_ERR_NO_CONVERGENCE;
+  return res;
+}
+
 static PcgResult pcg64(fe_hierarchy* h, const double* b, double* x, const fe_solver_opts& o, cudaStream_t s) {
   Level& F = h->L[h->nlev - 1];
   const int n = F.n;
@@ -507,6 +619,7 @@ static PcgResult pcg64(fe_hierarchy* h, const double* b, double* x, const fe_sol
   res.rr = res.bb;
   const double tol2 = o.rtol * o.rtol * res.bb;
   if (res.bb == 0.0) return res;
+  if (gmg && o.use_graph && !o.profile && o.max_it >= 1) return pcg64_graph(h, x, o, tol2, res, s);
   ApplyTimer timer(o.profile != 0);
   while (true) {
     if (res.it >= o.max_it) {
@@ -762,7 +875,9 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
   CUDA_CHECK(cudaMemcpy(h->children, ch.data(), sizeof(int) * 48, cudaMemcpyHostToDevice));
   red_init(h->red, h->sms);
   const int nF = h->L.back().n;
-  for (auto* v : {&h->x, &h->r, &h->z, &h->p, &h->q, &h->b, &h->e, &h->tmp}) v->alloc(nF);
+  for (auto* v : {&h->x, &h->r, &h->z, &h->p, &h->q, &h->b, &h->e, &h->tmp, &h->xcg}) v->alloc(nF);
+  h->cgp.alloc(1);
+  h->cgctl.alloc(2);
   for (auto* v : {&h->r32, &h->z32, &h->p32, &h->q32, &h->e32}) v->alloc(nF);
   h->cs.flag.alloc(1);
   set_coefficient_impl(h.get(), nullptr, s);

@@ -220,6 +220,35 @@ void launch_cg_update_p(ReduceCtx& R, int n, T* p, const T* z, cudaStream_t s) {
   LAUNCH_CHECK();
 }
 
+namespace {
+// Loop test of the device-side CG loop: ctl = {completed iterations, limit},
+// cgp[0] = the squared residual target.  Continue while the residual is finite,
+// above the target and the limit is not reached.
+__global__ void k_cg_cond(cudaGraphConditionalHandle hnd, const double* __restrict__ scal,
+                          const double* __restrict__ cgp, int* __restrict__ ctl, int inc) {
+  const int it = ctl[0] + inc;
+  ctl[0] = it;
+  const double rr = scal[S_RR];
+  cudaGraphSetConditional(hnd, (isfinite(rr) && rr > cgp[0] && it < ctl[1]) ? 1u : 0u);
+}
+__global__ void k_cg_set(double* __restrict__ cgp, int* __restrict__ ctl, double tol2, int it0, int max_it) {
+  cgp[0] = tol2;
+  ctl[0] = it0;
+  ctl[1] = max_it;
+}
+}  // namespace
+
+void launch_cg_cond(cudaGraphConditionalHandle hnd, const double* scal, const double* cgp, int* ctl, int inc,
+                    cudaStream_t s) {
+  k_cg_cond<<<1, 1, 0, s>>>(hnd, scal, cgp, ctl, inc);
+  LAUNCH_CHECK();
+}
+
+void launch_cg_set(double* cgp, int* ctl, double tol2, int it0, int max_it, cudaStream_t s) {
+  k_cg_set<<<1, 1, 0, s>>>(cgp, ctl, tol2, it0, max_it);
+  LAUNCH_CHECK();
+}
+
 void launch_axpy64(int n, double a, const double* x, double* y, cudaStream_t s) {
   k_axpy64<<<vec_grid(n, 152), 256, 0, s>>>(n, a, x, y);
   LAUNCH_CHECK();

@@ -1,5 +1,5 @@
 // Device-resident FP64 coarse-grid direct solve (paper Section 3: the coarsest
-// multigrid level is solved directly, "such as a Cholesky factorization").
+// multigrid level is handled by a direct factorisation, Cholesky here).
 //
 // Setup (once per coefficient): the interior block of the coarse operator is
 // assembled densely in the lexicographic lattice order of the interior dofs,
@@ -9,8 +9,11 @@
 // warp per column, forward substitution over the band).
 // Solve (every V-cycle): x = L^-T (L^-1 b) as two dense triangular
 // matrix-vector products, which are fully parallel instead of 2 n
-// dependent substitution steps.
-#include "fe_internal.cuh"
+// dependent substitution steps.  Unless the hierarchy runs native FP64, the
+// products are evaluated in float-pair arithmetic on the FP32 pipes (L^-1 and
+// L^-T stored as float pairs, the vector scaled by a power of two and split
+// once per product), since FP64 fused multiply-adds bound the FP64 form.
+#include "fe_df.cuh"
 
 namespace {
 
@@ -144,6 +147,80 @@ __global__ void __launch_bounds__(kRowThreads) k_trimv(int n, const double* __re
   }
 }
 
+// Row kernel of y = M v in float pairs: M row-major n x n (float pairs), v
+// split by k_split_vec with exponent *ev; y in FP64.
+__global__ void __launch_bounds__(kRowThreads) k_trimv_df(int n, const float2* __restrict__ M,
+                                                          const float2* __restrict__ v, const int* __restrict__ ev,
+                                                          double* __restrict__ out, int upper) {
+  using namespace fe_df;
+  __shared__ float2 sh[kRowThreads / 32];
+  const int row = blockIdx.x;
+  const float2* Mr = M + (size_t)row * n;
+  const int j0 = upper ? row : 0, j1 = upper ? n : row + 1;
+  DF s0, s1;
+  int jj = j0 + threadIdx.x;
+  for (; jj + kRowThreads < j1; jj += 2 * kRowThreads) {
+    const float2 a = __ldg(Mr + jj), b = __ldg(v + jj), c = __ldg(Mr + jj + kRowThreads),
+                 d = __ldg(v + jj + kRowThreads);
+    s0 = s0 + mul(DF(a.x, a.y), DF(b.x, b.y));
+    s1 = s1 + mul(DF(c.x, c.y), DF(d.x, d.y));
+  }
+  if (jj < j1) {
+    const float2 a = __ldg(Mr + jj), b = __ldg(v + jj);
+    s0 = s0 + mul(DF(a.x, a.y), DF(b.x, b.y));
+  }
+  DF s = s0 + s1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    s = s + DF(__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_float2(s.hi, s.lo);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DF t;
+#pragma unroll
+    for (int w = 0; w < kRowThreads / 32; ++w) t = t + DF(sh[w].x, sh[w].y);
+    const int e = *ev;
+    out[row] = widen_scaled(t.hi, e) + widen_scaled(t.lo, e);
+  }
+}
+
+// One block: v (gathered through idx when idx != null) -> float pairs scaled by
+// 2^(1023 - e), e = the largest biased exponent of v (0x7FF: a non-finite
+// entry, which is propagated as NaN).
+template <typename T>
+__global__ void k_split_vec(int n, const int* __restrict__ idx, const T* __restrict__ v, double* __restrict__ vd,
+                            float2* __restrict__ vs, int* __restrict__ ev) {
+  using namespace fe_df;
+  __shared__ int smax;
+  if (threadIdx.x == 0) smax = 0;
+  __syncthreads();
+  int e = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = (double)v[idx ? idx[i] : i];
+    if (vd) vd[i] = x;
+    e = max(e, (int)(((unsigned int)__double2hiint(x) >> 20) & 0x7FFu));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&smax, e);
+  __syncthreads();
+  const int E = smax == 0 ? 1023 : smax;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    DF d = split_scaled((double)v[idx ? idx[i] : i], E);
+    if (E == 0x7FF) d = DF(__int_as_float(0x7fc00000), 0.0f);
+    vs[i] = make_float2(d.hi, d.lo);
+  }
+  if (threadIdx.x == 0) *ev = E;
+}
+
+__global__ void k_split_mat(size_t nn, const double* __restrict__ a, float2* __restrict__ b) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  const double x = a[i];
+  const float hi = (float)x;
+  b[i] = make_float2(hi, (float)(x - (double)hi));
+}
+
 template <typename T>
 __global__ void k_coarse_scatter(int n, const int* __restrict__ dof2int, const double* __restrict__ t,
                                  const T* __restrict__ b, T* __restrict__ x) {
@@ -190,8 +267,13 @@ void coarse_setup(fe_hierarchy* h, cudaStream_t s) {
     cs.A.alloc((size_t)nci * nci);
     cs.Linv.alloc((size_t)nci * nci);
     cs.LinvT.alloc((size_t)nci * nci);
+    cs.LinvDF.alloc((size_t)nci * nci);
+    cs.LinvTDF.alloc((size_t)nci * nci);
     cs.t0.alloc(nci);
     cs.t1.alloc(nci);
+    cs.v0.alloc(nci);
+    cs.v1.alloc(nci);
+    cs.ev.alloc(2);
     cs.flag.alloc(1);
   }
   const size_t nn = (size_t)nci * nci;
@@ -225,6 +307,10 @@ void coarse_setup(fe_hierarchy* h, cudaStream_t s) {
   if (shm > 48 * 1024) CUDA_CHECK(cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   k_tri_inverse<<<ceil_div(nci, warps), warps * 32, shm, s>>>(nci, w, cs.A, cs.t0, cs.Linv, cs.LinvT);
   LAUNCH_CHECK();
+  k_split_mat<<<ceil_div((long long)nn, kBlock), kBlock, 0, s>>>(nn, cs.Linv, cs.LinvDF);
+  LAUNCH_CHECK();
+  k_split_mat<<<ceil_div((long long)nn, kBlock), kBlock, 0, s>>>(nn, cs.LinvT, cs.LinvTDF);
+  LAUNCH_CHECK();
   CUDA_CHECK(cudaStreamSynchronize(s));
 }
 
@@ -238,12 +324,23 @@ void coarse_solve(const fe_hierarchy* h, const T* b, T* x, cudaStream_t s) {
     LAUNCH_CHECK();
     return;
   }
-  k_coarse_gather<T><<<ceil_div(nci, kBlock), kBlock, 0, s>>>(nci, cs.ci, b, cs.t0);
-  LAUNCH_CHECK();
-  k_trimv<<<nci, kRowThreads, 0, s>>>(nci, cs.Linv, cs.t0, cs.t1, 0);
-  LAUNCH_CHECK();
-  k_trimv<<<nci, kRowThreads, 0, s>>>(nci, cs.LinvT, cs.t1, cs.t0, 1);
-  LAUNCH_CHECK();
+  if (h->f64_mode == FE_F64_NATIVE) {
+    k_coarse_gather<T><<<ceil_div(nci, kBlock), kBlock, 0, s>>>(nci, cs.ci, b, cs.t0);
+    LAUNCH_CHECK();
+    k_trimv<<<nci, kRowThreads, 0, s>>>(nci, cs.Linv, cs.t0, cs.t1, 0);
+    LAUNCH_CHECK();
+    k_trimv<<<nci, kRowThreads, 0, s>>>(nci, cs.LinvT, cs.t1, cs.t0, 1);
+    LAUNCH_CHECK();
+  } else {
+    k_split_vec<T><<<1, 1024, 0, s>>>(nci, cs.ci, b, nullptr, cs.v0, cs.ev);
+    LAUNCH_CHECK();
+    k_trimv_df<<<nci, kRowThreads, 0, s>>>(nci, cs.LinvDF, cs.v0, cs.ev, cs.t1, 0);
+    LAUNCH_CHECK();
+    k_split_vec<double><<<1, 1024, 0, s>>>(nci, nullptr, cs.t1, nullptr, cs.v1, cs.ev + 1);
+    LAUNCH_CHECK();
+    k_trimv_df<<<nci, kRowThreads, 0, s>>>(nci, cs.LinvTDF, cs.v1, cs.ev + 1, cs.t0, 1);
+    LAUNCH_CHECK();
+  }
   k_coarse_scatter<T><<<ceil_div(L0.n, kBlock), kBlock, 0, s>>>(L0.n, cs.dof2int, cs.t0, b, x);
   LAUNCH_CHECK();
 }

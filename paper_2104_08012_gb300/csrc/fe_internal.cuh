@@ -210,7 +210,10 @@ struct CoarseSolver {
   DBuf<int> dof2int;   // coarse dof -> interior index or -1
   DBuf<double> A;      // nci*nci dense, then L (lower)
   DBuf<double> Linv, LinvT;
+  DBuf<float2> LinvDF, LinvTDF;  // the same as float pairs (float-pair triangular products)
   DBuf<double> t0, t1;  // nci
+  DBuf<float2> v0, v1;  // nci, scaled float pairs of the product inputs
+  DBuf<int> ev;         // their scaling exponents
   DBuf<int> flag;
 };
 
@@ -240,6 +243,16 @@ struct fe_hierarchy {
   // staging for host pointers
   DBuf<unsigned char> stage[4];
   GraphCache vgraph[3];  // per dtype
+  // device-side FP64 GMG-PCG loop: a graph whose while node repeats
+  // (V-cycle, beta, p update, apply, alpha, x/r update, loop test)
+  struct CgLoop {
+    cudaGraphExec_t exec = nullptr;
+    long long body_kernels = 0;
+    int steps = 0;
+    double lo = 0, hi = 0;
+  } cgloop;
+  DBuf<double> xcg, cgp;  // CG iterate of the graph loop; loop target
+  DBuf<int> cgctl;        // loop counters
   bool lmax_valid = false;
   int f64_mode = FE_F64_DOUBLE_FLOAT;  // arithmetic of FP64 operator applications
 };
@@ -293,6 +306,9 @@ template <typename T>
 void launch_cg_beta(ReduceCtx& R, int n, const T* r, const T* z, cudaStream_t s);
 template <typename T>
 void launch_cg_update_p(ReduceCtx& R, int n, T* p, const T* z, cudaStream_t s);
+void launch_cg_cond(cudaGraphConditionalHandle hnd, const double* scal, const double* cgp, int* ctl, int inc,
+                    cudaStream_t s);
+void launch_cg_set(double* cgp, int* ctl, double tol2, int it0, int max_it, cudaStream_t s);
 void launch_axpy64(int n, double a, const double* x, double* y, cudaStream_t s);
 void launch_sub64(int n, const double* a, const double* b, double* out, cudaStream_t s);  // out = a - b
 template <typename T>

@@ -375,17 +375,19 @@ __global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __rest
 
 // Restriction = exact transpose: coarse point Lc gathers fine points
 // 2 Lc + f_off for the stencil entries of its parity class.  With yf != null
-// the restricted vector is the residual bf - yf.  TPC consecutive threads share
-// one coarse point (a P2 vertex gathers 125 fine points): each takes every
-// TPC-th stencil entry and the partial sums meet in a butterfly of shuffles,
-// so the gather runs with TPC times more loads in flight than one thread per
-// coarse point would have.
+// the restricted vector is the residual bf - yf.  A block holds 32 consecutive
+// coarse points (one per lane, so every gather of a warp reads consecutive
+// fine entries of one class array) and TPC warps: warp w takes every TPC-th
+// stencil entry (a P2 vertex gathers 125 fine points) and the partial sums
+// meet in shared memory.
 template <int DEG, typename T, int TPC>
-__global__ void k_restrict(Numbering nf, Numbering nc, int n_c, const int* __restrict__ start,
-                           const int4* __restrict__ off, const double* __restrict__ w, const T* __restrict__ bf,
-                           const T* __restrict__ yf, T* __restrict__ rc, int zero_bd) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = gt / TPC, sub = gt % TPC;
+__global__ void __launch_bounds__(32 * TPC) k_restrict(Numbering nf, Numbering nc, int n_c,
+                                                       const int* __restrict__ start, const int4* __restrict__ off,
+                                                       const double* __restrict__ w, const T* __restrict__ bf,
+                                                       const T* __restrict__ yf, T* __restrict__ rc, int zero_bd) {
+  __shared__ T part[TPC][32];
+  const int lane = threadIdx.x & 31, sub = threadIdx.x >> 5;
+  const int J = blockIdx.x * 32 + lane;
   T s = T(0);
   if (J < n_c) {
     int X, Y, Z;
@@ -407,9 +409,14 @@ __global__ void k_restrict(Numbering nf, Numbering nc, int n_c, const int* __res
       }
     }
   }
+  part[sub][lane] = s;
+  __syncthreads();
+  if (sub == 0 && J < n_c) {
+    T t = part[0][lane];
 #pragma unroll
-  for (int o = TPC / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (J < n_c && sub == 0) rc[J] = s;
+    for (int k = 1; k < TPC; ++k) t += part[k][lane];
+    rc[J] = t;
+  }
 }
 
 // --------------------------------------------------------- vector ops
@@ -591,11 +598,11 @@ void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T*
   const Level& Cc = h->L[lf - 1];
   const TransferTables& t = h->tt;
   if (h->deg == 1)
-    k_restrict<1, T, 4><<<ceil_div(4LL * Cc.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off,
-                                                                       t.res_w, bf, yf, rc, zero_bd);
+    k_restrict<1, T, 4><<<ceil_div(Cc.n, 32), 32 * 4, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off, t.res_w, bf,
+                                                              yf, rc, zero_bd);
   else
-    k_restrict<2, T, 8><<<ceil_div(8LL * Cc.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off,
-                                                                       t.res_w, bf, yf, rc, zero_bd);
+    k_restrict<2, T, 8><<<ceil_div(Cc.n, 32), 32 * 8, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off, t.res_w, bf,
+                                                              yf, rc, zero_bd);
   LAUNCH_CHECK();
 }
 
