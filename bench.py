@@ -37,14 +37,15 @@ F64_MODE = 1  # FE_F64_DOUBLE_FLOAT: the library default for FP64 operator appli
 # DRAM bytes per launch of the dominant kernel on this workload from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by FP64 mode; None until captured
 TRAFFIC = {0: 188.2e6, 1: 183.6e6, 2: 183.6e6}
-# Flops of one P2 element application (c, d, S, four G-products, transpose;
-# an FMA counts 2), per tet: 151 in the FP64 formula; the double-float form of
-# the same formula costs 1493 FP32 flops (95 float-pair additions x 11, 36
-# float-pair products x 10, scalings 88).
+# Arithmetic of one P2 element application (c, d, S, four G-products, transpose),
+# per tet: 151 flops in the FP64 formula (an FMA counts 2).  The float-pair form
+# of the same formula issues 976 FP32 operations (an add, mul or FMA counts 1):
+# 71 float-pair additions x 8, 12 three-term float-pair dot products x 28,
+# 8 small-integer scalings x 6, 12 power-of-two scalings x 2.
 FLOPS_PER_CELL_P2_F64 = 151
-FLOPS_PER_CELL_P2_DF = 1493
+OPS_PER_CELL_P2_DF = 976
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64: 152 SMs x 2 FMA/clk/SM x 2 flops x 2.07 GHz (recipe table)
-FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (recipe unit counts and clock)
+FP32_PEAK_TOPS = 40.3  # 152 SMs x 128 FP32 lanes x 1 operation/clk x 2.07 GHz (recipe unit counts and clock)
 
 
 def parse():
@@ -55,6 +56,9 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the matvec/mixed/adjoint/batched side measurements")
+    p.add_argument("--host-loop", action="store_true",
+                   help="drive the CG iterations from the host in the timed solves (same kernels; for profilers "
+                        "that do not follow launches inside conditional graph nodes)")
     return p.parse_args()
 
 
@@ -312,11 +316,12 @@ def run_ours(args, rank, world, local_rank):
     setup_s = time.time() - t_setup
     f = torch.from_numpy(f_host).to(dev)
     u = torch.empty(n, dtype=torch.float64, device=dev)
-    opts = fe.default_opts(rtol=WORKLOAD["rtol"], profile=1)
+    opts_prof = fe.default_opts(rtol=WORKLOAD["rtol"], profile=1)
+    opts = opts_prof if args.host_loop else fe.default_opts(rtol=WORKLOAD["rtol"])
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
-    def step(rhs, out):
-        return h.solve(rhs, out, opts=opts, stream=stream)
+    def step(rhs, out, o=opts):
+        return h.solve(rhs, out, opts=o, stream=stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -357,6 +362,14 @@ def run_ours(args, rank, world, local_rank):
             eve[k][1].record(stream)
     torch.cuda.synchronize()
     te_ms = sum(a.elapsed_time(b) for a, b in eve)
+    # operator-apply durations for the roofline: the same solves with CUDA events around
+    # every fine-level application (host-driven CG loop), after the timed region
+    stats = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            stats.append(step(f, u, opts_prof))
+    torch.cuda.synchronize()
     # correctness of the last solve: relative residual reported by the FP64 recurrence and an
     # independent check of the error against the analytic solution at the nodes
     u_host = u.cpu().numpy()
@@ -372,11 +385,13 @@ def run_ours(args, rank, world, local_rank):
         return None
     apply_ms = sum(s.apply_ms for s in stats) / max(1, sum(s.apply_timed for s in stats))
     if F64_MODE == fe.FE_F64_DOUBLE_FLOAT:
-        kname, flops, peak = ("k_apply_df<2> (FP64 operator in double-float on the FP32 pipes, persistent, one tet "
-                              "per thread)", FLOPS_PER_CELL_P2_DF * C, FP32_PEAK_TFLOPS)
-        psrc = "nominal FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (recipe unit counts and clock); no measured FP32 peak"
+        kname, flops, peak, unit = ("k_apply_df<2> (FP64 operator in double-float on the FP32 pipes, persistent, "
+                                    "one tet per thread)", OPS_PER_CELL_P2_DF * C, FP32_PEAK_TOPS, "T FP32 op/s")
+        psrc = ("nominal FP32 issue rate: 152 SMs x 128 lanes x 1 operation/clk x 2.07 GHz (recipe unit counts and "
+                "clock); no measured FP32 peak")
     else:
-        kname, flops, peak = "k_apply<2,double> (native FP64 operator)", FLOPS_PER_CELL_P2_F64 * C, FP64_PEAK_TFLOPS
+        kname, flops, peak, unit = ("k_apply<2,double> (native FP64 operator)", FLOPS_PER_CELL_P2_F64 * C,
+                                    FP64_PEAK_TFLOPS, "TFLOP/s")
         psrc = "nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json"
     achieved = flops / (apply_ms * 1e-3) / 1e12
     value = job_throughput(n, args.steps, world, t_ms)
@@ -393,9 +408,11 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": job_throughput(n, args.steps, world, te_ms), "unit": "DoF/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": achieved / peak, "traffic": TRAFFIC.get(F64_MODE), "apply_ms": apply_ms,
-                     "flops_per_launch": flops, "fp64_formula_flops_per_launch": FLOPS_PER_CELL_P2_F64 * C,
+                     "ops_per_launch": flops, "fp64_formula_flops_per_launch": FLOPS_PER_CELL_P2_F64 * C,
+                     "apply_timing": "CUDA events around each fine-level apply of the same solves (host-driven "
+                                     "CG loop), run after the timed region",
                      "peak_source": psrc},
         "clocks": clk,
     }

@@ -22,12 +22,12 @@ What it computes, written out from the definitions in the paper:
   Section 2 and Section 3) with prolongation = exact interpolation of the coarse
   finite element function at the fine nodes and restriction = its transpose,
   rediscretised coarse operators, Chebyshev smoothing with two iterations per
-  level (the ``mg_levels`` options of the paper's FMG listing, here with a Jacobi
-  preconditioner instead of PatchPC), and a direct Cholesky coarse solve
-  (Section 3: "such as a Cholesky factorization");
+  level (the level-smoother options of the paper's FMG listing, here with a
+  Jacobi preconditioner instead of PatchPC), and a direct Cholesky coarse solve
+  (Section 3 factorises the coarsest level directly);
 * conjugate gradients (Jacobi- or V-cycle-preconditioned), the L2 error against an
-  analytic solution (Section 2, "which we use to calculate the error"), and the
-  discrete adjoint gradient dJ/dkappa of J = (u-u_d)^T M (u-u_d).
+  analytic solution (Section 2 measures the error against the exact solution), and
+  the discrete adjoint gradient dJ/dkappa of J = (u-u_d)^T M (u-u_d).
 
 Readings where the paper is silent (each also listed in the design notes):
 Kuhn 6-tet split of each cube; level l of the hierarchy is the Kuhn mesh of
