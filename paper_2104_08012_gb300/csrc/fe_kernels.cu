@@ -128,10 +128,14 @@ __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const
 // Cube-aggregated apply: one thread per cube gathers the cube's (k+1)^3 dofs
 // once, applies its six Kuhn tets into register accumulators and scatters
 // (k+1)^3 atomics instead of 6 * nd (27 instead of 60 for P2).
+constexpr int kCubeBlock = 128;  // 4 blocks of 128 per SM at 128 registers: 5% faster than 2 of 256
+
 template <int DEG>
-__global__ void __launch_bounds__(kBlock) k_apply_cube(int Q, int Qs, int Cs, int Qpad, const int* __restrict__ cmap,
-                                                       const float* __restrict__ geo, const float* __restrict__ x,
-                                                       float* __restrict__ y, int nb, const int* __restrict__ bnd) {
+__global__ void __launch_bounds__(kCubeBlock, 4) k_apply_cube(int Q, int Qs, int Cs, int Qpad,
+                                                            const int* __restrict__ cmap,
+                                                            const float* __restrict__ geo,
+                                                            const float* __restrict__ x, float* __restrict__ y,
+                                                            int nb, const int* __restrict__ bnd) {
   constexpr int NL = DEG == 1 ? 8 : 27, ND = DEG == 1 ? 4 : 10;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < Q) {
@@ -504,12 +508,12 @@ static void apply_impl(const Level& L, const T* geo, const T* x, T* y, cudaStrea
 
 static void apply_cube32(const Level& L, const float* x, float* y, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)L.n, s));
-  const int Qpad = ceil_div(L.Q, kBlock) * kBlock;
-  const int grid = ceil_div((long long)Qpad + L.nb, kBlock);
+  const int Qpad = ceil_div(L.Q, kCubeBlock) * kCubeBlock;
+  const int grid = ceil_div((long long)Qpad + L.nb, kCubeBlock);
   if (L.deg == 1)
-    k_apply_cube<1><<<grid, kBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd);
+    k_apply_cube<1><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd);
   else
-    k_apply_cube<2><<<grid, kBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd);
+    k_apply_cube<2><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd);
   LAUNCH_CHECK();
 }
 
