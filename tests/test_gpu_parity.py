@@ -281,6 +281,50 @@ def test_gmg_iterations_mesh_independent(fe):
     assert max(its) <= 15 and its[-1] - its[0] <= 3, its
 
 
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("cheb_steps", [2, 3])
+def test_graph_cg_loop_matches_host_loop(fe, k, cheb_steps):
+    """The device-side CG loop (conditional graph node) runs the same kernels as the host-driven loop: the same
+    iteration count and the same solution up to the order of the operator's atomic additions; the launch counter
+    sees the loop's kernels (the graph path adds one parameter kernel, one loop test before the loop and one per
+    further iteration)."""
+    with fe.Hierarchy(4, 2, k) as h:
+        f = dt(I.sin_product_rhs(h.dof_coordinates()))
+        u1 = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+        u2 = torch.empty_like(u1)
+        h.solve(f, u1, rtol=1e-10, cheb_steps=cheb_steps)  # builds the loop graph
+        n0 = fe.fe_kernel_launches()
+        s1 = h.solve(f, u1, rtol=1e-10, cheb_steps=cheb_steps)
+        n1 = fe.fe_kernel_launches()
+        s2 = h.solve(f, u2, rtol=1e-10, cheb_steps=cheb_steps, profile=1)  # host-driven loop
+        n2 = fe.fe_kernel_launches()
+        torch.cuda.synchronize()
+        assert s1.iterations == s2.iterations > 1
+        assert s1.rel_residual <= 1e-10 and s2.rel_residual <= 1e-10
+        assert abs(s1.rel_residual - s2.rel_residual) <= 1e-6 * s2.rel_residual
+        assert float(torch.linalg.norm(u1 - u2)) <= 1e-12 * float(torch.linalg.norm(u2))
+        assert (n1 - n0) == (n2 - n1) + s1.iterations + 1
+
+
+def test_graph_cg_loop_limits(fe):
+    """Iteration limit and non-finite residuals end the device-side loop with the host loop's status codes."""
+    with fe.Hierarchy(4, 1, 2) as h:
+        f = dt(I.sin_product_rhs(h.dof_coordinates()))
+        u = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+        for it in (1, 2, 3):
+            for prof in (0, 1):
+                with pytest.raises(fe.FeError) as e:
+                    h.solve(f, u, rtol=1e-14, max_it=it, profile=prof)
+                assert e.value.code == fe.FE_ERR_NO_CONVERGENCE
+        st = h.solve(f, u, rtol=1e-8, max_it=50)
+        assert st.iterations < 50 and st.rel_residual <= 1e-8
+        nanf = f.clone()
+        nanf[7] = float("inf")
+        with pytest.raises(fe.FeError) as e:
+            h.solve(nanf, u, rtol=1e-8)
+        assert e.value.code == fe.FE_ERR_NAN
+
+
 def test_solver_errors(fe):
     with fe.Hierarchy(4, 1, 1) as h:
         f = dt(I.sin_product_rhs(h.dof_coordinates()))
