@@ -350,17 +350,18 @@ static void smooth_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d,
   const double theta = 0.5 * (bmax + a), delta = 0.5 * (bmax - a), sigma = theta / delta;
   double rho = 1.0 / sigma;
   for (int k = 0; k < steps; ++k) {
+    const bool last = k + 1 == steps;  // its direction d is not used again
     if (k == 0) {
       if (x_zero) {
-        launch_cheb_step<T>(L.n, b, nullptr, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, true, s);
+        launch_cheb_step<T>(L.n, b, nullptr, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, true, s, !last);
       } else {
         apply_enqueue(h, l, x, y, dtype, s);
-        launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, false, s);
+        launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, false, s, !last);
       }
     } else {
       const double rn = 1.0 / (2.0 * sigma - rho);
       apply_enqueue(h, l, x, y, dtype, s);
-      launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, rn * rho, 2.0 * rn / delta, false, s);
+      launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, rn * rho, 2.0 * rn / delta, false, s, !last);
       rho = rn;
     }
   }

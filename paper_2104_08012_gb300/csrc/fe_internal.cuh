@@ -284,7 +284,7 @@ void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T*
 // Vector kernels
 template <typename T>
 void launch_cheb_step(int n, const T* b, const T* y, const T* dinv, T* x, T* d, double c1, double c2, bool first_from_zero,
-                      cudaStream_t s);
+                      cudaStream_t s, bool store_d = true);
 template <typename Ti, typename To>
 void launch_convert(int n, const Ti* in, To* out, cudaStream_t s);
 void launch_set_boundary(const Level& L, const double* src, double* dst, cudaStream_t s);

@@ -428,17 +428,17 @@ __global__ void __launch_bounds__(32 * TPC) k_restrict(Numbering nf, Numbering n
 // first_from_zero (x = 0, y unused): d = c2 D^-1 b; x = d.
 template <typename T>
 __global__ void k_cheb_step(int n, const T* __restrict__ b, const T* __restrict__ y, const T* __restrict__ dinv,
-                            T* __restrict__ x, T* __restrict__ d, T c1, T c2, int first_from_zero) {
+                            T* __restrict__ x, T* __restrict__ d, T c1, T c2, int first_from_zero, int store_d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (first_from_zero) {
     const T dn = c2 * dinv[i] * b[i];
-    d[i] = dn;
+    if (store_d) d[i] = dn;
     x[i] = dn;
   } else {
     const T r = b[i] - y[i];
     const T dn = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * dinv[i] * r;
-    d[i] = dn;
+    if (store_d) d[i] = dn;  // the last step of a sweep does not need d again
     x[i] += dn;
   }
 }
@@ -618,14 +618,15 @@ template void launch_restrict<float>(const fe_hierarchy*, int, const float*, con
 
 template <typename T>
 void launch_cheb_step(int n, const T* b, const T* y, const T* dinv, T* x, T* d, double c1, double c2,
-                      bool first_from_zero, cudaStream_t s) {
-  k_cheb_step<T><<<ceil_div(n, kBlock), kBlock, 0, s>>>(n, b, y, dinv, x, d, (T)c1, (T)c2, first_from_zero ? 1 : 0);
+                      bool first_from_zero, cudaStream_t s, bool store_d) {
+  k_cheb_step<T><<<ceil_div(n, kBlock), kBlock, 0, s>>>(n, b, y, dinv, x, d, (T)c1, (T)c2, first_from_zero ? 1 : 0,
+                                                        store_d ? 1 : 0);
   LAUNCH_CHECK();
 }
 template void launch_cheb_step<double>(int, const double*, const double*, const double*, double*, double*, double,
-                                       double, bool, cudaStream_t);
+                                       double, bool, cudaStream_t, bool);
 template void launch_cheb_step<float>(int, const float*, const float*, const float*, float*, float*, double, double,
-                                      bool, cudaStream_t);
+                                      bool, cudaStream_t, bool);
 
 template <typename Ti, typename To>
 void launch_convert(int n, const Ti* in, To* out, cudaStream_t s) {
