@@ -7,16 +7,22 @@
 // followed by the G-weighted reduction y_K[i] = sum_p G_p W[p*nd + i] and an
 // atomic scatter.  With the scaled tables (120 S for P2, 6 S for P1, whose
 // 1/120 and 1/6 are folded into the per-cell geometric factors) every table
-// entry is a small integer, exact in bf16; only the dofs are rounded to bf16.
+// entry is a small integer, exact in bf16.  Each FP32 dof is split into two
+// bf16 terms, x = x_hi + x_lo + O(2^-17 |x|) (x_hi = bf16(x), x_lo =
+// bf16(x - x_hi)), and W = X_hi S + X_lo S accumulates both products in the
+// same TMEM tile (two MMAs), so the apply carries 16 significant bits of the
+// dofs instead of bf16's 8 at no cost in tensor time (the tensor pipe is idle
+// most of the kernel).
 //
 // Per CTA (persistent, 128 threads = one cell per thread, up to 4 CTAs/SM):
 //   * TMA (cp.async.bulk.tensor.2d) stages the tile's rows of the cell->dof
 //     map and of the FP32 geometric factors into shared memory (double
 //     buffered, mbarrier completion);
-//   * each thread gathers its cell's dofs from x (FP32), rounds them to bf16
-//     and writes its row of the A tile (canonical K-major layout, no swizzle);
-//   * one thread issues tcgen05.mma (M=128, N=64 or 32, K=16) into a TMEM
-//     accumulator and commits to an mbarrier;
+//   * each thread gathers its cell's dofs from x (FP32), splits them into two
+//     bf16 terms and writes its rows of the two A tiles (canonical K-major
+//     layout, no swizzle);
+//   * one thread issues two tcgen05.mma (M=128, N=64 or 32, K=16; the second
+//     accumulates) into a TMEM accumulator and commits to an mbarrier;
 //   * each warp reads its 32 TMEM lanes with tcgen05.ld, applies G and scatters.
 // Every mbarrier wait is bounded in time; on expiry the kernel raises an error
 // flag, waits (bounded) for its own copies/MMA in flight, frees its TMEM and
@@ -50,9 +56,10 @@ struct TcShape<2> {
 template <int DEG>
 struct Smem {
   static constexpr int ND = TcShape<DEG>::ND, N = TcShape<DEG>::N;
-  static constexpr int A = 0;                         // 128 x 16 bf16
+  static constexpr int A = 0;                         // 128 x 16 bf16 (leading terms)
   static constexpr int B = A + kTile * 16 * 2;        // N x 16 bf16
-  static constexpr int MAP = B + N * 16 * 2;          // 2 stages x ND x 128 int32
+  static constexpr int A2 = B + N * 16 * 2;           // 128 x 16 bf16 (trailing terms), 1024-aligned
+  static constexpr int MAP = A2 + kTile * 16 * 2;     // 2 stages x ND x 128 int32
   static constexpr int MAP_STAGE = ND * kTile * 4;
   static constexpr int GEO = MAP + 2 * MAP_STAGE;     // 2 stages x 6 x 128 float
   static constexpr int GEO_STAGE = 6 * kTile * 4;
@@ -138,11 +145,13 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(NCOL) : "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
+// D = A B (accumulate == 0) or D += A B.
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, 0, 0;\n"
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -174,6 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_tc(const __grid_constant__ C
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   unsigned char* sA = smem + S::A;
+  unsigned char* sA2 = smem + S::A2;
   const uint32_t bar_tma0 = smem_u32(smem + S::BAR), bar_mma = smem_u32(smem + S::BAR + 16);
   uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(smem + S::TADDR);
   constexpr uint32_t tx_bytes = S::MAP_STAGE + S::GEO_STAGE;
@@ -192,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_tc(const __grid_constant__ C
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *taddr_slot;
-  const uint64_t adesc = smem_desc(smem_u32(sA));
+  const uint64_t adesc = smem_desc(smem_u32(sA)), adesc2 = smem_desc(smem_u32(sA2));
   const uint64_t bdesc = smem_desc(smem_u32(smem + S::B));
   const uint32_t idesc = instr_desc<N>();
 
@@ -226,15 +236,16 @@ __global__ void __launch_bounds__(kThreads) k_apply_tc(const __grid_constant__ C
     const float* gs = reinterpret_cast<const float*>(smem + S::GEO + stage * S::GEO_STAGE);
     int idx[ND];
     float g[6];
-    __nv_bfloat16 a[16];
+    __nv_bfloat16 a[16], a2[16];
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
       idx[j] = ms[j * kTile + tid];
       const float v = (c < C && idx[j] >= 0) ? __ldg(x + idx[j]) : 0.0f;
       a[j] = __float2bfloat16_rn(v);
+      a2[j] = __float2bfloat16_rn(v - __bfloat162float(a[j]));
     }
 #pragma unroll
-    for (int j = ND; j < 16; ++j) a[j] = __float2bfloat16_rn(0.0f);
+    for (int j = ND; j < 16; ++j) a[j] = a2[j] = __float2bfloat16_rn(0.0f);
 #pragma unroll
     for (int p = 0; p < 6; ++p) g[p] = gs[p * kTile + tid];
     {
@@ -244,13 +255,18 @@ __global__ void __launch_bounds__(kThreads) k_apply_tc(const __grid_constant__ C
       memcpy(&hi, &a[8], 16);
       *reinterpret_cast<uint4*>(sA + row_off) = lo;
       *reinterpret_cast<uint4*>(sA + row_off + kLBO) = hi;
+      memcpy(&lo, &a2[0], 16);
+      memcpy(&hi, &a2[8], 16);
+      *reinterpret_cast<uint4*>(sA2 + row_off) = lo;
+      *reinterpret_cast<uint4*>(sA2 + row_off + kLBO) = hi;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (tid == 0) {
-      mma_bf16(tbase, adesc, bdesc, idesc);
+      mma_bf16(tbase, adesc, bdesc, idesc, 0u);
+      mma_bf16(tbase, adesc2, bdesc, idesc, 1u);
       mma_commit(bar_mma);
     }
     const bool ok_mma = mbar_wait(bar_mma, it & 1);

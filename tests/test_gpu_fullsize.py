@@ -61,7 +61,7 @@ def test_fullsize_operator_rows(fe, N):
             assert np.all(np.abs(got - ref) <= 1e-13 * scale), (mode, np.max(np.abs(got - ref) / scale))
         x32 = xd.to(torch.float32)
         y32 = torch.empty_like(x32)
-        for dt, tol in ((fe.FE_F32, 1e-5), (fe.FE_BF16, 4e-3)):
+        for dt, tol in ((fe.FE_F32, 1e-5), (fe.FE_BF16, 5e-5)):
             h.apply_operator(x32, y32, dtype=dt)
             got = y32.double().cpu().numpy()[rows]
             ref32 = O.apply_rows(space, kappa, x32.double().cpu().numpy(), rows)
