@@ -505,6 +505,27 @@ class Hierarchy:
         x = x + self.P[l] @ self.vcycle(rc, l - 1)
         return self.smooth(l, b, x)
 
+    def fmg(self, b, cycles=1):
+        """Full multigrid as the whole solve (the paper's outer solver, Section 3: full
+        multigrid with a direct coarse solve): the right-hand side restricted to every
+        level (boundary entries zero), the coarsest level solved directly, then on each
+        finer level the interpolated coarser solution corrected by ``cycles`` V-cycles
+        (x += V(b_l - A_l x), i.e. a V-cycle started from x)."""
+        nl = len(self.levels)
+        bs = [None] * nl
+        bs[-1] = np.asarray(b, dtype=np.float64)
+        for l in range(nl - 1, 0, -1):
+            rc = self.P[l].T @ bs[l]
+            rc[self.levels[l - 1].space.boundary] = 0.0
+            bs[l - 1] = rc
+        x = self.coarse_solve(bs[0])
+        for l in range(1, nl):
+            x = self.P[l] @ x
+            A = self.levels[l].A
+            for _ in range(cycles):
+                x = x + self.vcycle(bs[l] - A @ x, l)
+        return x
+
 
 def load_vector(level, f_nodal, bc_values=None):
     """b = M I_h f on interior rows, minus A_ib g_b; b_bd = g_bd (symmetric elimination)."""

@@ -148,3 +148,40 @@ def test_adjoint_taylor_remainder_is_second_order():
     for t in (1e-2, 5e-3):
         rem.append(abs(_J_direct(N, 1, kappa + t * dk, f_fn, I.target_field) - J - t * (g @ dk)))
     assert 3.0 < rem[0] / rem[1] < 5.0  # O(t^2): halving t divides the remainder by ~4
+
+
+# ------------------------------------------------------------ full multigrid
+def test_fmg_single_level_is_the_direct_solve():
+    """With one level FMG is the coarse Cholesky solve: the exact discrete solution."""
+    H = O.Hierarchy(3, 0, 2)
+    L = H.fine
+    b = O.load_vector(L, I.sin_product_rhs(L.space.coords))
+    assert np.allclose(H.fmg(b), O.direct_solve(L, b), rtol=0, atol=1e-13)
+
+
+def test_fmg_cycles_converge_to_discrete_solution():
+    """Many V-cycles per level make FMG a converged multigrid iteration: the discrete solution."""
+    H = O.Hierarchy(2, 2, 2)
+    L = H.fine
+    b = O.load_vector(L, I.sin_product_rhs(L.space.coords))
+    uh = O.direct_solve(L, b)
+    assert np.linalg.norm(H.fmg(b, cycles=25) - uh) <= 1e-11 * np.linalg.norm(uh)
+
+
+def test_fmg_reaches_discretisation_accuracy():
+    """One FMG cycle already solves to the order of the discretisation error (the property
+    that makes a single F-cycle a complete solve): its L2 error against the exact solution is
+    within 2x that of the exact discrete solution (within 10% with two V-cycles per level)
+    and converges at the discretisation's O(h^3) rate for P2."""
+    errs = []
+    for N0 in (2, 4):
+        H = O.Hierarchy(N0, 2, 2)
+        L = H.fine
+        X = L.space.coords
+        b = O.load_vector(L, I.sin_product_rhs(X))
+        eh = O.l2_error(L.space, O.direct_solve(L, b), I.sin_product)
+        e1 = O.l2_error(L.space, H.fmg(b), I.sin_product)
+        e2 = O.l2_error(L.space, H.fmg(b, cycles=2), I.sin_product)
+        assert eh < e1 <= 2.0 * eh and e2 <= 1.1 * eh, (e1, e2, eh)
+        errs.append(e1)
+    assert 2.6 <= np.log2(errs[0] / errs[1]) <= 3.4, errs
