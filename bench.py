@@ -139,6 +139,20 @@ def extras(fe, I, h, dev, stream, flush):
     h.set_f64_mode(F64_MODE)
     out["native_fp64_operator_solve"] = {"ms": ms, "DoF_per_s": n / (ms * 1e-3), "iterations": st.iterations,
                                          "rel_residual": st.rel_residual}
+    # ---- full multigrid as the whole solve (the paper's outer solver) on the same problem
+    ue = torch.from_numpy(I.sin_product(h.dof_coordinates()))
+    fm = {"what": "one full-multigrid cycle (restrict b to all levels, coarse Cholesky, per finer level: "
+                  "interpolate, V-cycles), P2 64^3, 4 levels",
+          "cg_max_nodal_error_vs_exact": float((u_n.cpu() - ue).abs().max())}
+    for cyc in (1, 2):
+        with torch.cuda.stream(stream):
+            h.solve(f_n, u_n, precond=fe.FE_PC_FMG, max_it=cyc, stream=stream)
+            ms = time_launches(lambda: h.solve(f_n, u_n, precond=fe.FE_PC_FMG, max_it=cyc, stream=stream), stream, 5,
+                               flush)
+            st = h.solve(f_n, u_n, precond=fe.FE_PC_FMG, max_it=cyc, stream=stream)
+        fm[f"vcycles_per_level_{cyc}"] = {"ms": ms, "DoF_per_s": n / (ms * 1e-3), "rel_residual": st.rel_residual,
+                                          "max_nodal_error_vs_exact": float((u_n.cpu() - ue).abs().max())}
+    out["fmg_p2_64cubed"] = fm
     # ---- mixed precision on P2 128^3 (5 levels): time to the same 1e-8 FP64 residual
     h2 = fe.Hierarchy(8, 4, 2)
     f2 = torch.from_numpy(I.sin_product_rhs(h2.dof_coordinates())).to(dev)

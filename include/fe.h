@@ -74,6 +74,10 @@ extern "C" {
 /* ---- preconditioners and precision modes of fe_solve_poisson ---- */
 #define FE_PC_JACOBI 0
 #define FE_PC_GMG 1
+#define FE_PC_FMG 2   /* no Krylov method: full multigrid is the whole solve (paper Section 3): b restricted to every
+                         level, a direct solve on the coarsest, then on each finer level the interpolated coarser
+                         solution corrected by max_it V-cycles; rtol is not a stopping test (stats report the
+                         final residual); FP64 only */
 #define FE_PREC_F64 0         /* everything FP64 */
 #define FE_PREC_MIXED_F32 1   /* FP64 iterative refinement around an FP32 GMG-PCG */
 #define FE_PREC_MIXED_BF16 2  /* as FE_PREC_MIXED_F32 with bf16 tensor-core smoother applications */
@@ -90,7 +94,7 @@ typedef struct fe_solver_opts {
   double rtol;        /* stop when ||b - A u||_2 <= rtol ||b||_2 (unpreconditioned 2-norm) */
   int max_it;         /* CG iteration limit (mixed precision: outer refinement steps, at most 100; refinement
                          also stops with FE_ERR_NO_CONVERGENCE after 3 steps in a row that reduce ||r|| < 2x) */
-  int precond;        /* FE_PC_JACOBI or FE_PC_GMG */
+  int precond;        /* FE_PC_JACOBI, FE_PC_GMG (CG preconditioned by one V-cycle) or FE_PC_FMG */
   int precision;      /* FE_PREC_* */
   int cheb_steps;     /* Chebyshev iterations per smoothing (2 in the paper's options) */
   double cheb_lo;     /* Chebyshev interval [cheb_lo, cheb_hi] * lambda_max(D^-1 A) */

@@ -451,6 +451,74 @@ static void invalidate_graphs(fe_hierarchy* h) {
     cudaGraphExecDestroy(h->cgloop.exec);
     h->cgloop.exec = nullptr;
   }
+  if (h->fmggraph.exec) {
+    cudaGraphExecDestroy(h->fmggraph.exec);
+    h->fmggraph.exec = nullptr;
+  }
+}
+
+static long long count_kernel_nodes(cudaGraph_t g);
+
+// Full multigrid as the whole solve (paper Section 3): b restricted to every
+// level (boundary entries zero), the coarsest level solved directly, then on
+// each finer level x_l = P x_{l-1} corrected by `cycles` V-cycles in defect
+// form x_l += V(b_l - A_l x_l) (a V-cycle started from x_l; the smoother is
+// linear).  The solution is left in the fine level's fx64.
+static void fmg_enqueue(fe_hierarchy* h, const double* b, int cycles, cudaStream_t s) {
+  const int top = h->nlev - 1;
+  CUDA_CHECK(cudaMemcpyAsync(h->L[top].fb64, b, sizeof(double) * h->L[top].n, cudaMemcpyDeviceToDevice, s));
+  for (int l = top; l >= 1; --l) launch_restrict<double>(h, l, h->L[l].fb64, nullptr, h->L[l - 1].fb64, true, s);
+  coarse_solve<double>(h, h->L[0].fb64, h->L[0].fx64, s);
+  for (int l = 1; l <= top; ++l) {
+    Level& L = h->L[l];
+    launch_prolong<double>(h, l, h->L[l - 1].fx64, L.fx64, false, s);
+    for (int c = 0; c < cycles; ++c) {
+      apply_enqueue(h, l, L.fx64, L.y64, FE_F64, s);
+      launch_sub64(L.n, L.fb64, L.y64, L.b64, s);
+      vcycle_level<double>(h, l, FE_F64, s);
+      launch_axpy64(L.n, 1.0, L.x64, L.fx64, s);
+    }
+  }
+}
+
+static void run_fmg(fe_hierarchy* h, const double* b, int cycles, bool use_graph, cudaStream_t s) {
+  GraphCache& gc = h->fmggraph;
+  const int top = h->nlev - 1;
+  if (!use_graph) {
+    fmg_enqueue(h, b, cycles, s);
+    return;
+  }
+  // the graph reads the fine right-hand side from fb64 (copied in outside the graph)
+  if (b != h->L[top].fb64.p)
+    CUDA_CHECK(cudaMemcpyAsync(h->L[top].fb64, b, sizeof(double) * h->L[top].n, cudaMemcpyDeviceToDevice, s));
+  if (gc.exec && (gc.steps != g_sp.steps || gc.lo != g_sp.lo || gc.hi != g_sp.hi || gc.extra != cycles)) {
+    cudaGraphExecDestroy(gc.exec);
+    gc.exec = nullptr;
+  }
+  if (!gc.exec) {
+    if (!gc.stream) CUDA_CHECK(cudaStreamCreateWithFlags(&gc.stream, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    CUDA_CHECK(cudaStreamBeginCapture(gc.stream, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    try {
+      fmg_enqueue(h, h->L[top].fb64, cycles, gc.stream);
+    } catch (...) {
+      g_capturing = false;
+      cudaStreamEndCapture(gc.stream, &g);
+      throw;
+    }
+    g_capturing = false;
+    CUDA_CHECK(cudaStreamEndCapture(gc.stream, &g));
+    gc.kernels = count_kernel_nodes(g);
+    CUDA_CHECK(cudaGraphInstantiate(&gc.exec, g, 0));
+    cudaGraphDestroy(g);
+    gc.steps = g_sp.steps;
+    gc.lo = g_sp.lo;
+    gc.hi = g_sp.hi;
+    gc.extra = cycles;
+  }
+  CUDA_CHECK(cudaGraphLaunch(gc.exec, s));
+  g_launches.fetch_add(gc.kernels, std::memory_order_relaxed);
 }
 
 // ------------------------------------------------------------ PCG
@@ -801,6 +869,10 @@ static fe_solver_opts resolve_opts(const fe_solver_opts* o) {
   if (o) d = *o;
   FE_REQUIRE(d.rtol >= 0 && d.max_it >= 0 && d.cheb_steps >= 1 && d.cheb_hi > d.cheb_lo && d.cheb_lo > 0,
              FE_ERR_ARG, "invalid solver options");
+  FE_REQUIRE(d.precond == FE_PC_JACOBI || d.precond == FE_PC_GMG || d.precond == FE_PC_FMG, FE_ERR_ARG,
+             "unknown preconditioner");
+  FE_REQUIRE(d.precond != FE_PC_FMG || (d.precision == FE_PREC_F64 && d.max_it >= 1 && d.max_it <= 100), FE_ERR_ARG,
+             "full multigrid runs in FP64 with 1..100 V-cycles per level (max_it)");
   return d;
 }
 
@@ -853,7 +925,7 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     L.massdf.alloc(L.C);
     L.dinv64.alloc(L.n);
     L.dinv32.alloc(L.n);
-    for (auto* v : {&L.b64, &L.x64, &L.y64, &L.d64, &L.w64}) v->alloc(L.n);
+    for (auto* v : {&L.b64, &L.x64, &L.y64, &L.d64, &L.w64, &L.fb64, &L.fx64}) v->alloc(L.n);
     for (auto* v : {&L.b32, &L.x32, &L.y32, &L.d32}) v->alloc(L.n);
     std::vector<int> bnd;
     bnd.reserve((size_t)6 * (m + 1) * (m + 1));
@@ -1214,7 +1286,23 @@ int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_
   fe_solve_stats st{};
   st.outer_iterations = 1;
   PcgResult res;
-  if (o.precision == FE_PREC_F64) {
+  if (o.precond == FE_PC_FMG) {
+    // one full-multigrid cycle, then the residual of its solution for the stats
+    run_fmg(h, b, o.max_it, o.use_graph != 0, s);
+    Level& Ft = h->L[h->nlev - 1];
+    CUDA_CHECK(cudaMemcpyAsync(ud, Ft.fx64, sizeof(double) * Ft.n, cudaMemcpyDeviceToDevice, s));
+    apply_enqueue(h, h->nlev - 1, Ft.fx64, Ft.y64, FE_F64, s);
+    launch_sub64(Ft.n, b, Ft.y64, Ft.w64, s);
+    ReduceCtx& R = h->red;
+    launch_dot<double>(R, Ft.n, b, b, S_BB, s);
+    launch_dot<double>(R, Ft.n, Ft.w64.p, Ft.w64.p, S_RR, s);
+    CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+    res.bb = R.h_scal[S_BB];
+    res.rr = R.h_scal[S_RR];
+    res.it = o.max_it;
+    if (!std::isfinite(res.rr)) res.status = FE_ERR_NAN;
+  } else if (o.precision == FE_PREC_F64) {
     res = pcg64(h, b, ud, o, s);
     st.fine_applies_f64 = res.applies;
     st.apply_ms = res.apply_ms;

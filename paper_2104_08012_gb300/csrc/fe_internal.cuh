@@ -176,6 +176,7 @@ struct Level {
   double lmax = 2.0;
   // V-cycle work vectors (level-owned so the cycle can be captured in a graph)
   DBuf<double> b64, x64, y64, d64, w64;
+  DBuf<double> fb64, fx64;  // full multigrid: this level's right-hand side and solution
   DBuf<float> b32, x32, y32, d32;
 };
 
@@ -227,6 +228,7 @@ struct GraphCache {
   cudaStream_t stream = nullptr;
   int steps = 0;  // smoother parameters baked into the captured launches
   double lo = 0, hi = 0;
+  int extra = 0;  // another baked parameter (V-cycles per level of the full-multigrid graph)
 };
 
 struct fe_hierarchy {
@@ -243,6 +245,7 @@ struct fe_hierarchy {
   // staging for host pointers
   DBuf<unsigned char> stage[4];
   GraphCache vgraph[3];  // per dtype
+  GraphCache fmggraph;   // the full-multigrid sequence (steps = V-cycles per level in `lo`)
   // device-side FP64 GMG-PCG loop: a graph whose while node repeats
   // (V-cycle, beta, p update, apply, alpha, x/r update, loop test)
   struct CgLoop {
