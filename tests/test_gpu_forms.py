@@ -210,3 +210,30 @@ def test_mixed_bf16_refinement(fe):
         assert np.linalg.norm(L.A @ uh - b) <= 1.0001e-8 * np.linalg.norm(b)
         assert np.linalg.norm(uh - ue) <= 1e-6 * np.linalg.norm(ue)
         assert st.outer_iterations >= 2
+
+
+# --------------------------------------------- the paper's manufactured problem
+def test_paper_manufactured_problem_converges():
+    """The paper's own problem (Section 2, Eqs. 2-3: u = sin(pi x) tan(pi x/4) sin(pi y) sin(2 pi z),
+    f as printed) solved by GPU GMG-PCG on P2 hierarchies: the L2 error (oracle's conical-product
+    rule) converges at the P2 rate O(h^3) and FMG with two V-cycles per level stays within 2x of it."""
+    import paper_2104_08012_gb300 as fe
+    from paper_2104_08012_gb300 import build
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    errs = []
+    for N0 in (2, 4, 8):
+        with fe.Hierarchy(N0, 2, 2) as h:
+            X = h.dof_coordinates()
+            f = torch.from_numpy(I.paper_rhs(X)).to(DEV)
+            u = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+            h.solve(f, u, rtol=1e-11)
+            space = O.Space(O.Mesh(4 * N0), 2)
+            e = O.l2_error(space, host(u), I.paper_solution)
+            h.solve(f, u, precond=fe.FE_PC_FMG, max_it=2)
+            e_fmg = O.l2_error(space, host(u), I.paper_solution)
+            assert e_fmg <= 2.0 * e, (N0, e_fmg, e)
+            errs.append(e)
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((rates > 2.6) & (rates < 3.4)), (errs, rates)
