@@ -527,6 +527,30 @@ class Hierarchy:
         return x
 
 
+QUAD_N = 3  # Gauss points per direction of the quadrature load vector: 27 per tet, exact to degree 3
+
+
+def quadrature_points(mesh, n=QUAD_N):
+    """Physical points x = p0 + J xi of the conical-product rule on every cell: (C, n^3, 3)."""
+    xi, _ = tet_quadrature(n)
+    J = mesh.jacobians()
+    p0 = mesh.coords[mesh.cells[:, 0]]
+    return p0[:, None, :] + np.einsum("cab,qb->cqa", J, xi)
+
+
+def load_vector_quadrature(level, f_qp, n=QUAD_N):
+    """b_i = sum_K sum_q w_q |det J_K| f(x_Kq) phi_i(xi_q): the linear form of f v dx (Section 2)
+    by quadrature with f given at the points of ``quadrature_points``; b = 0 on the boundary."""
+    xi, w = tet_quadrature(n)
+    phi, _ = ref_basis(level.space.degree, xi)
+    det = np.abs(np.linalg.det(level.space.mesh.jacobians()))
+    be = np.einsum("q,c,cq,qd->cd", w, det, np.asarray(f_qp, dtype=np.float64), phi)
+    b = np.zeros(level.n)
+    np.add.at(b, level.space.cell_dofs, be)
+    b[level.space.boundary] = 0.0
+    return b
+
+
 def load_vector(level, f_nodal, bc_values=None):
     """b = M I_h f on interior rows, minus A_ib g_b; b_bd = g_bd (symmetric elimination)."""
     b = level.M @ f_nodal

@@ -160,3 +160,31 @@ def test_coarsen_kappa_has_eight_children():
     kf = I.grf_kappa(f.centroids())
     kc = O.coarsen_kappa(c, f, kf)
     assert np.allclose(kc, np.bincount(parent, kf) / 8)
+
+
+# ---------------------------------------------------- quadrature load vector
+@pytest.mark.parametrize("k", [1, 2])
+def test_quadrature_load_vector_exact_cases(k):
+    """The 27-point rule is exact to degree 3: for f = 1 and for f linear (P_k x f of degree <= 3)
+    the quadrature load vector equals M I_h f on the interior rows (I_h f = f); the points lie
+    inside their cells (barycentric coordinates in [0, 1])."""
+    L = O.Level(3, k)
+    P = O.quadrature_points(L.space.mesh)
+    assert P.shape == (L.space.mesh.n_cells, 27, 3)
+    inside = L.space.mesh.coords[L.space.mesh.cells].min(axis=1)[:, None, :] <= P + 1e-15
+    assert inside.all()
+    X = L.space.coords
+    for f, fx in ((lambda p: np.ones(p.shape[:-1]), np.ones(len(X))),
+                  (lambda p: 0.3 + 2 * p[..., 0] - p[..., 1] + 0.5 * p[..., 2], 0.3 + 2 * X[:, 0] - X[:, 1] + 0.5 * X[:, 2])):
+        b = O.load_vector_quadrature(L, f(P))
+        assert np.allclose(b, O.load_vector(L, fx), rtol=0, atol=1e-15)
+
+
+def test_quadrature_load_vector_converges():
+    """Solving with the quadrature load vector of the sin-product f converges at the P2 rate."""
+    errs = []
+    for N in (4, 8):
+        L = O.Level(N, 2)
+        b = O.load_vector_quadrature(L, I.sin_product_rhs(O.quadrature_points(L.space.mesh).reshape(-1, 3)).reshape(-1, 27))
+        errs.append(O.l2_error(L.space, O.direct_solve(L, b), I.sin_product))
+    assert 2.6 <= np.log2(errs[0] / errs[1]) <= 3.4, errs
