@@ -85,6 +85,14 @@ extern "C" {
 /* ---- right-hand side kinds ---- */
 #define FE_RHS_LOAD 0     /* rhs is the assembled load vector b (boundary entries = Dirichlet values) */
 #define FE_RHS_NODAL_F 1  /* rhs holds nodal values of f; b = M f on interior rows, 0 on the boundary */
+#define FE_RHS_QUAD_F 2   /* rhs holds f at the quadrature points of fe_quadrature_points ([n_cells][FE_QUAD_POINTS]);
+                             b_i = sum_K sum_q w_q |det J_K| f(x_Kq) phi_i(xi_q) on interior rows, 0 on the boundary */
+
+/* Quadrature rule of FE_RHS_QUAD_F: the conical-product Gauss rule with 3
+ * points per direction on the reference tet (27 points, exact for polynomials
+ * of degree 3): xi = (u, (1-u) v, (1-u)(1-v) w) for u, v, w in the 3 Gauss-
+ * Legendre nodes of [0, 1], u slowest and w fastest. */
+#define FE_QUAD_POINTS 27
 
 typedef struct fe_mesh fe_mesh;
 typedef struct fe_hierarchy fe_hierarchy;
@@ -226,6 +234,18 @@ int fe_vcycle(const fe_hierarchy* h, const void* b, void* x, int dtype, void* st
 
 /* b = M f on interior rows and b_bd = 0, from nodal values f (n_dofs). */
 int fe_load_vector(const fe_hierarchy* h, const double* f_nodal, double* b, void* stream);
+
+/* Physical coordinates of the FE_QUAD_POINTS quadrature points of every cell of
+ * the finest level (paper Section 2: the linear form of f v dx evaluated by
+ * quadrature): xyz[(cell * FE_QUAD_POINTS + q) * 3 + axis], host or device
+ * pointer of 3 * FE_QUAD_POINTS * n_cells doubles (caller-owned).  Synchronous. */
+int fe_quadrature_points(const fe_hierarchy* h, double* xyz);
+
+/* b = the load vector of f by quadrature (FE_RHS_QUAD_F): f_qp holds f at the
+ * points of fe_quadrature_points ([n_cells][FE_QUAD_POINTS]); b (n_dofs) gets
+ * b_i = sum_K sum_q w_q |det J_K| f(x_Kq) phi_i(xi_q) on interior rows and 0 on
+ * the boundary.  FP64 accumulation; host or device pointers. */
+int fe_load_vector_quadrature(const fe_hierarchy* h, const double* f_qp, double* b, void* stream);
 
 /* Solve A u = b on the finest level by PCG (Jacobi or GMG V-cycle), or by
  * FP64 iterative refinement around a reduced-precision GMG-PCG.  rhs:

@@ -18,8 +18,9 @@ FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_NOMEM, FE_ERR_NO_CONVERGENCE, FE_ERR_NAN, FE_ERR
 FE_F64, FE_F32, FE_BF16 = 0, 1, 2
 FE_F64_NATIVE, FE_F64_DOUBLE_FLOAT, FE_F64_DOUBLE_FLOAT_TET, FE_F64_DOUBLE_FLOAT_CUBE = 0, 1, 2, 3
 FE_PC_JACOBI, FE_PC_GMG, FE_PC_FMG = 0, 1, 2
+FE_QUAD_POINTS = 27
 FE_PREC_F64, FE_PREC_MIXED_F32, FE_PREC_MIXED_BF16 = 0, 1, 2
-FE_RHS_LOAD, FE_RHS_NODAL_F = 0, 1
+FE_RHS_LOAD, FE_RHS_NODAL_F, FE_RHS_QUAD_F = 0, 1, 2
 
 # every symbol include/fe.h declares
 EXPORTED = (
@@ -27,7 +28,8 @@ EXPORTED = (
     "fe_hierarchy_refine", "fe_hierarchy_destroy", "fe_num_levels", "fe_level_sizes", "fe_dof_coordinates",
     "fe_cell_centroids", "fe_boundary_mask", "fe_set_coefficient", "fe_apply_operator", "fe_apply_mass",
     "fe_diagonal", "fe_lambda_max", "fe_prolong", "fe_restrict", "fe_smooth", "fe_coarse_solve", "fe_vcycle",
-    "fe_load_vector", "fe_solve_poisson", "fe_adjoint_gradient", "fe_objective", "fe_dot_noalloc",
+    "fe_load_vector", "fe_quadrature_points", "fe_load_vector_quadrature", "fe_solve_poisson", "fe_adjoint_gradient",
+    "fe_objective", "fe_dot_noalloc",
     "fe_set_f64_mode", "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
 )
 
@@ -96,6 +98,8 @@ def load():
         "fe_coarse_solve": (i, [vp, vp, vp, vp]),
         "fe_vcycle": (i, [vp, vp, vp, i, vp]),
         "fe_load_vector": (i, [vp, vp, vp, vp]),
+        "fe_quadrature_points": (i, [vp, vp]),
+        "fe_load_vector_quadrature": (i, [vp, vp, vp, vp]),
         "fe_solve_poisson": (i, [vp, vp, i, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(SolveStats), vp]),
         "fe_adjoint_gradient": (i, [vp, vp, i, vp, vp, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(d), vp, vp]),
         "fe_objective": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
@@ -391,6 +395,16 @@ class Hierarchy:
 
     def load_vector(self, f, b, stream=None):
         _check(self._L.fe_load_vector(self.h, _ptr(f), _ptr(b), _stream(stream)))
+        return b
+
+    def quadrature_points(self):
+        """Physical quadrature points of the finest level's cells, shape (n_cells, FE_QUAD_POINTS, 3)."""
+        out = np.empty((self.n_cells(), FE_QUAD_POINTS, 3))
+        _check(self._L.fe_quadrature_points(self.h, _ptr(out)))
+        return out
+
+    def load_vector_quadrature(self, f_qp, b, stream=None):
+        _check(self._L.fe_load_vector_quadrature(self.h, _ptr(f_qp), _ptr(b), _stream(stream)))
         return b
 
     def objective(self, u, u_d, stream=None):

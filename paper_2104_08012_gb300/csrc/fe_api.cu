@@ -846,8 +846,11 @@ static void set_coefficient_impl(fe_hierarchy* h, const double* kappa, cudaStrea
 
 static const double* rhs_to_load(fe_hierarchy* h, const double* rhs, int kind, cudaStream_t s) {
   Level& F = h->L[h->nlev - 1];
-  const double* rd = stage_in<double>(h, 1, rhs, F.n, s);
-  if (kind == FE_RHS_LOAD) {
+  const double* rd = stage_in<double>(h, 1, rhs, kind == FE_RHS_QUAD_F ? (size_t)F.C * FE_QUAD_POINTS : F.n, s);
+  if (kind == FE_RHS_QUAD_F) {
+    launch_load_quadrature(F, rd, h->b, s);
+    launch_zero_boundary64(F, h->b, s);
+  } else if (kind == FE_RHS_LOAD) {
     if (rd != h->b.p) CUDA_CHECK(cudaMemcpyAsync(h->b, rd, sizeof(double) * F.n, cudaMemcpyDeviceToDevice, s));
   } else if (kind == FE_RHS_NODAL_F) {
     mass_enqueue(h, F, rd, h->b, s);
@@ -1263,6 +1266,32 @@ int fe_load_vector(const fe_hierarchy* hc, const double* f, double* b, void* str
   cudaStream_t s = as_stream(stream);
   const Level& F = h->L[h->nlev - 1];
   const double* bd = rhs_to_load(h, f, FE_RHS_NODAL_F, s);
+  CUDA_CHECK(cudaMemcpyAsync(b, bd, sizeof(double) * F.n, cudaMemcpyDefault, s));
+  if (!is_device_ptr(b)) CUDA_CHECK(cudaStreamSynchronize(s));
+  API_END
+}
+
+int fe_quadrature_points(const fe_hierarchy* hc, double* xyz) {
+  API_BEGIN
+  FE_REQUIRE(hc && xyz, FE_ERR_ARG, "null argument");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  const Level& F = h->L[h->nlev - 1];
+  const size_t n = (size_t)3 * FE_QUAD_POINTS * F.C;
+  cudaStream_t s = 0;
+  double* d = stage_out<double>(h, 2, xyz, n);
+  launch_quad_points(F, d, s);
+  finish_out(xyz, d, n, s);
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  API_END
+}
+
+int fe_load_vector_quadrature(const fe_hierarchy* hc, const double* f_qp, double* b, void* stream) {
+  API_BEGIN
+  FE_REQUIRE(hc && f_qp && b, FE_ERR_ARG, "null argument");
+  fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
+  cudaStream_t s = as_stream(stream);
+  const Level& F = h->L[h->nlev - 1];
+  const double* bd = rhs_to_load(h, f_qp, FE_RHS_QUAD_F, s);
   CUDA_CHECK(cudaMemcpyAsync(b, bd, sizeof(double) * F.n, cudaMemcpyDefault, s));
   if (!is_device_ptr(b)) CUDA_CHECK(cudaStreamSynchronize(s));
   API_END

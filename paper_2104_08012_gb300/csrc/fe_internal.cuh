@@ -271,6 +271,8 @@ void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStre
 void launch_split_geometry(Level& L, cudaStream_t s);
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_mass_df(const Level& L, const double* x, double* y, cudaStream_t s);
+void launch_quad_points(const Level& L, double* xyz, cudaStream_t s);
+void launch_load_quadrature(const Level& L, const double* fq, double* b, cudaStream_t s);
 void launch_diag(Level& L, double* diag_out, cudaStream_t s);
 void launch_gradient(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s);
 void launch_dof_coords(const Level& L, double* xyz, cudaStream_t s);

@@ -1,11 +1,19 @@
 // Cell-loop kernels of the matrix-free operator (paper Section 2, Eq. 4),
 // mass, diagonal, adjoint cell gradient, mesh construction, and the
 // multigrid transfer and smoother vector kernels (paper Section 3).
+#include <cmath>
+
 #include "fe_internal.cuh"
 
 // Reference P1/P2 mass matrices int_ref phi_i phi_j, filled by fe_api.cu.
 __constant__ double c_mref1[16];
 __constant__ double c_mref2[100];
+// Quadrature rule of the load vector (conical-product Gauss, 3 points per
+// direction, FE_QUAD_POINTS = 27 per tet): reference points, weights, basis values.
+__constant__ double c_qxi[FE_QUAD_POINTS][3];
+__constant__ double c_qw[FE_QUAD_POINTS];
+__constant__ double c_qphi1[FE_QUAD_POINTS][4];
+__constant__ double c_qphi2[FE_QUAD_POINTS][10];
 
 namespace {
 
@@ -213,6 +221,52 @@ __global__ void k_mass(int C, int Cs, const int* __restrict__ map, const double*
 #pragma unroll
     for (int j = 0; j < ND; ++j) acc += M[i * ND + j] * u[j];
     atomicAdd(y + idx[i], s * acc);
+  }
+}
+
+// ------------------------------------------------------ quadrature load
+// Physical quadrature points x = p0 + J xi of every cell: xyz [C][27][3].
+__global__ void k_quad_points(int C, int Cs, const int* __restrict__ map, const double* __restrict__ vx,
+                              const double* __restrict__ vy, const double* __restrict__ vz, double* __restrict__ xyz) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double p[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    bool bd;
+    const int v = decode(map[(size_t)k * Cs + c], bd);  // vertex dofs index the vertices
+    p[k][0] = vx[v];
+    p[k][1] = vy[v];
+    p[k][2] = vz[v];
+  }
+  for (int q = 0; q < FE_QUAD_POINTS; ++q)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      xyz[((size_t)c * FE_QUAD_POINTS + q) * 3 + a] = p[0][a] + (p[1][a] - p[0][a]) * c_qxi[q][0] +
+                                                       (p[2][a] - p[0][a]) * c_qxi[q][1] +
+                                                       (p[3][a] - p[0][a]) * c_qxi[q][2];
+}
+
+// b_i += sum_q w_q |det J| f(x_q) phi_i(xi_q) for the cell's dofs (boundary rows are zeroed afterwards).
+template <int DEG>
+__global__ void k_load_quad(int C, int Cs, const int* __restrict__ map, const double* __restrict__ detj,
+                            const double* __restrict__ fq, double* __restrict__ b) {
+  constexpr int ND = DEG == 1 ? 4 : 10;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double acc[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) acc[i] = 0.0;
+  const double dj = detj[c];
+  for (int q = 0; q < FE_QUAD_POINTS; ++q) {
+    const double sq = c_qw[q] * dj * __ldg(fq + (size_t)c * FE_QUAD_POINTS + q);
+#pragma unroll
+    for (int i = 0; i < ND; ++i) acc[i] += sq * (DEG == 1 ? c_qphi1[q][i] : c_qphi2[q][i]);
+  }
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    bool bd;
+    atomicAdd(b + decode(map[(size_t)i * Cs + c], bd), acc[i]);
   }
 }
 
@@ -662,11 +716,59 @@ static double fact(int k) {
 
 void mass_tables_host(double m1[16], double m2[100]);
 
+// The load vector's rule: Gauss-Legendre with 3 nodes on [0, 1] per direction,
+// collapsed to the reference tet (xi = u, eta = (1-u) v, zeta = (1-u)(1-v) w,
+// weight w_u w_v w_w (1-u)^2 (1-v)), points ordered u slowest, w fastest.
+void quad_tables_host(double xi[FE_QUAD_POINTS][3], double w[FE_QUAD_POINTS], double phi1[FE_QUAD_POINTS][4],
+                      double phi2[FE_QUAD_POINTS][10]) {
+  const double r = std::sqrt(0.6);
+  const double t[3] = {0.5 * (1.0 - r), 0.5, 0.5 * (1.0 + r)};
+  const double wt[3] = {0.5 * 5.0 / 9.0, 0.5 * 8.0 / 9.0, 0.5 * 5.0 / 9.0};
+  int q = 0;
+  for (int iu = 0; iu < 3; ++iu)
+    for (int iv = 0; iv < 3; ++iv)
+      for (int iw = 0; iw < 3; ++iw, ++q) {
+        const double u = t[iu], v = t[iv], ww = t[iw];
+        xi[q][0] = u;
+        xi[q][1] = (1.0 - u) * v;
+        xi[q][2] = (1.0 - u) * (1.0 - v) * ww;
+        w[q] = wt[iu] * wt[iv] * wt[iw] * (1.0 - u) * (1.0 - u) * (1.0 - v);
+        const double lam[4] = {1.0 - xi[q][0] - xi[q][1] - xi[q][2], xi[q][0], xi[q][1], xi[q][2]};
+        for (int k = 0; k < 4; ++k) {
+          phi1[q][k] = lam[k];
+          phi2[q][k] = lam[k] * (2.0 * lam[k] - 1.0);
+        }
+        int e = 4;
+        for (int a = 0; a < 4; ++a)
+          for (int b2 = a + 1; b2 < 4; ++b2) phi2[q][e++] = 4.0 * lam[a] * lam[b2];
+      }
+}
+
 void upload_mass_tables() {
   double m1[16], m2[100];
   mass_tables_host(m1, m2);
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref1, m1, sizeof(m1)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref2, m2, sizeof(m2)));
+  double xi[FE_QUAD_POINTS][3], w[FE_QUAD_POINTS], p1[FE_QUAD_POINTS][4], p2[FE_QUAD_POINTS][10];
+  quad_tables_host(xi, w, p1, p2);
+  CUDA_CHECK(cudaMemcpyToSymbol(c_qxi, xi, sizeof(xi)));
+  CUDA_CHECK(cudaMemcpyToSymbol(c_qw, w, sizeof(w)));
+  CUDA_CHECK(cudaMemcpyToSymbol(c_qphi1, p1, sizeof(p1)));
+  CUDA_CHECK(cudaMemcpyToSymbol(c_qphi2, p2, sizeof(p2)));
+}
+
+void launch_quad_points(const Level& L, double* xyz, cudaStream_t s) {
+  k_quad_points<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, xyz);
+  LAUNCH_CHECK();
+}
+
+void launch_load_quadrature(const Level& L, const double* fq, double* b, cudaStream_t s) {
+  CUDA_CHECK(cudaMemsetAsync(b, 0, sizeof(double) * (size_t)L.n, s));
+  if (L.deg == 1)
+    k_load_quad<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, fq, b);
+  else
+    k_load_quad<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, fq, b);
+  LAUNCH_CHECK();
 }
 
 void mass_tables_host(double m1[16], double m2[100]) {

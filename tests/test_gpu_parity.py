@@ -230,6 +230,40 @@ def test_vcycle_matches_oracle(fe, k):
         assert np.linalg.norm(host(x) - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
+# ---------------------------------------------------- quadrature load vector
+@pytest.mark.parametrize("k", [1, 2])
+def test_quadrature_load_vector(fe, k):
+    """fe_quadrature_points and fe_load_vector_quadrature against the oracle (points to 1e-15,
+    load vector rowwise 1e-13), and a solve with FE_RHS_QUAD_F equals a solve with the assembled
+    load vector passed as FE_RHS_LOAD."""
+    with fe.Hierarchy(2, 1, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=8)
+        h.set_coefficient(dt(kappa))
+        L = O.Level(4, k, kappa)
+        P = h.quadrature_points()
+        Pref = O.quadrature_points(L.space.mesh)
+        assert np.abs(P - Pref).max() <= 1e-15
+        fq = I.sin_product_rhs(P.reshape(-1, 3)).reshape(P.shape[:2])
+        ref = O.load_vector_quadrature(L, fq)
+        b = torch.empty(L.n, dtype=torch.float64, device=DEV)
+        h.load_vector_quadrature(dt(fq), b)
+        torch.cuda.synchronize()
+        # rowwise scale sum_K sum_q w_q |det J| |f| |phi_i| (P2 vertex functions change sign)
+        xi, w = O.tet_quadrature(O.QUAD_N)
+        phi, _ = O.ref_basis(k, xi)
+        det = np.abs(np.linalg.det(L.space.mesh.jacobians()))
+        scale = np.zeros(L.n)
+        np.add.at(scale, L.space.cell_dofs, np.einsum("q,c,cq,qd->cd", w, det, np.abs(fq), np.abs(phi)))
+        scale[L.space.boundary] = 1.0
+        assert np.all(np.abs(host(b) - ref) <= 1e-13 * scale), np.max(np.abs(host(b) - ref) / scale)
+        u1 = torch.empty_like(b)
+        u2 = torch.empty_like(b)
+        h.solve(dt(fq), u1, rhs_kind=fe.FE_RHS_QUAD_F, rtol=1e-12)
+        h.solve(b, u2, rhs_kind=fe.FE_RHS_LOAD, rtol=1e-12)
+        torch.cuda.synchronize()
+        assert float(torch.linalg.norm(u1 - u2)) <= 1e-11 * float(torch.linalg.norm(u2))
+
+
 # ---------------------------------------------------------- full multigrid
 @pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("cycles", [1, 2])
