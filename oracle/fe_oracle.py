@@ -9,8 +9,8 @@ It shares no code with the CUDA library (the only module both use is
 What it computes, written out from the definitions in the paper:
 
 * the Poisson problem -div(kappa grad u) = f on the unit cube with homogeneous
-  (or given) Dirichlet data on all six faces (Section 2, Eq. 1, and the
-  ``DirichletBC`` on boundary ids 1-6 in the paper's Poisson script);
+  (or given) Dirichlet data on all six faces (Section 2, Eq. 1, and the boundary
+  conditions of the paper's Poisson script);
 * its Galerkin discretisation in continuous Lagrange P1/P2 on a tetrahedral
   ``UnitCubeMesh`` (Section 2, the weak form Eq. 4): the global stiffness
   A_ij = int kappa grad(phi_j) . grad(phi_i) dx and mass M_ij = int phi_j phi_i dx
