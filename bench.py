@@ -226,6 +226,13 @@ def extras(fe, I, h, dev, stream, flush):
     out["batched_64"] = {"ms": ms, "total_dofs": tot, "DoF_per_s": tot / (ms * 1e-3),
                          "max_iterations": max(s.iterations for s in st),
                          "max_rel_residual": max(s.rel_residual for s in st), "schedule": B.schedule()}
+    # the same 64 problems solved one after another with the single-problem solver (for comparison)
+    with torch.cuda.stream(stream):
+        for hp, fp, up in zip(B.problems, fs, us):
+            hp.solve(fp, up, rhs_kind=fe.FE_RHS_NODAL_F, rtol=1e-8, stream=stream)
+        ms_seq = time_launches(lambda: [hp.solve(fp, up, rtol=1e-8, stream=stream)
+                                        for hp, fp, up in zip(B.problems, fs, us)], stream, 3, flush)
+    out["batched_64"]["sequential_single_solves_ms"] = ms_seq
     B.close()
     return out
 
