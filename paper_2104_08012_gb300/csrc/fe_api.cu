@@ -466,7 +466,8 @@ static long long count_kernel_nodes(cudaGraph_t g);
 // linear).  The solution is left in the fine level's fx64.
 static void fmg_enqueue(fe_hierarchy* h, const double* b, int cycles, cudaStream_t s) {
   const int top = h->nlev - 1;
-  CUDA_CHECK(cudaMemcpyAsync(h->L[top].fb64, b, sizeof(double) * h->L[top].n, cudaMemcpyDeviceToDevice, s));
+  if (b != h->L[top].fb64.p)
+    CUDA_CHECK(cudaMemcpyAsync(h->L[top].fb64, b, sizeof(double) * h->L[top].n, cudaMemcpyDeviceToDevice, s));
   for (int l = top; l >= 1; --l) launch_restrict<double>(h, l, h->L[l].fb64, nullptr, h->L[l - 1].fb64, true, s);
   coarse_solve<double>(h, h->L[0].fb64, h->L[0].fx64, s);
   for (int l = 1; l <= top; ++l) {
