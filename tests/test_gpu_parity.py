@@ -262,6 +262,13 @@ def test_quadrature_load_vector(fe, k):
         h.solve(b, u2, rhs_kind=fe.FE_RHS_LOAD, rtol=1e-12)
         torch.cuda.synchronize()
         assert float(torch.linalg.norm(u1 - u2)) <= 1e-11 * float(torch.linalg.norm(u2))
+        # host pointers in and out (staged through the library's buffers) give the same results
+        bh = np.empty(L.n)
+        h.load_vector_quadrature(np.ascontiguousarray(fq), bh)
+        assert np.all(np.abs(bh - host(b)) <= 1e-13 * scale)  # atomics: summation order may differ
+        uh = np.empty(L.n)
+        h.solve(np.ascontiguousarray(fq), uh, rhs_kind=fe.FE_RHS_QUAD_F, rtol=1e-12)
+        assert np.linalg.norm(uh - host(u2)) <= 1e-11 * np.linalg.norm(host(u2))
 
 
 # ---------------------------------------------------------- full multigrid
