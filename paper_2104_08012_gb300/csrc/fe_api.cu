@@ -186,6 +186,8 @@ static void build_transfer_tables(TransferTables& t, int deg) {
   up(t.pro_start, t.h_pro_start);
   up(t.pro_off, t.h_pro_off);
   up(t.pro_w, t.h_pro_w);
+  up(t.pro_wf, std::vector<float>(t.h_pro_w.begin(), t.h_pro_w.end()));
+  up(t.res_wf, std::vector<float>(t.h_res_w.begin(), t.h_res_w.end()));
   up(t.res_start, t.h_res_start);
   up(t.res_off, t.h_res_off);
   up(t.res_w, t.h_res_w);

@@ -187,6 +187,7 @@ struct TransferTables {
   DBuf<int> pro_start, res_start;  // class -> first entry, size n_class+1
   DBuf<int4> pro_off, res_off;     // (dx,dy,dz,-) lattice offsets
   DBuf<double> pro_w, res_w;
+  DBuf<float> pro_wf, res_wf;      // the same weights in FP32 (exact: dyadic with small numerators)
   std::vector<int> h_pro_start, h_res_start;
   std::vector<int4> h_pro_off, h_res_off;
   std::vector<double> h_pro_w, h_res_w;

@@ -406,7 +406,7 @@ __global__ void k_check_positive(const double* __restrict__ v, int n, int* __res
 // k*c, weight) pairs built on the host by evaluating the coarse basis.
 template <int DEG, typename T>
 __global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __restrict__ start,
-                          const int4* __restrict__ off, const double* __restrict__ w, const T* __restrict__ xc,
+                          const int4* __restrict__ off, const T* __restrict__ w, const T* __restrict__ xc,
                           T* __restrict__ xf, int accumulate) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_f) return;
@@ -425,7 +425,7 @@ __global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __rest
     if (k < ne) {
       const int4 o = __ldg(off + e0 + k);
       const int j = lattice_to_dof(nc, DEG * cx + o.x, DEG * cy + o.y, DEG * cz + o.z);
-      s += (T)__ldg(w + e0 + k) * __ldg(xc + j);
+      s += __ldg(w + e0 + k) * __ldg(xc + j);
     }
   }
   xf[i] = accumulate ? xf[i] + s : s;
@@ -441,7 +441,7 @@ __global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __rest
 template <int DEG, typename T, int TPC>
 __global__ void __launch_bounds__(32 * TPC) k_restrict(Numbering nf, Numbering nc, int n_c,
                                                        const int* __restrict__ start, const int4* __restrict__ off,
-                                                       const double* __restrict__ w, const T* __restrict__ bf,
+                                                       const T* __restrict__ w, const T* __restrict__ bf,
                                                        const T* __restrict__ yf, T* __restrict__ rc, int zero_bd) {
   __shared__ T part[TPC][32];
   const int lane = threadIdx.x & 31, sub = threadIdx.x >> 5;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(32 * TPC) k_restrict(Numbering nf, Numbering n
         const int i = lattice_to_dof(nf, fx, fy, fz);
         T v = __ldg(bf + i);
         if (yf) v -= __ldg(yf + i);
-        s += (T)__ldg(w + e) * v;
+        s += __ldg(w + e) * v;
       }
     }
   }
@@ -636,16 +636,26 @@ int launch_check_positive(const double* v, int n, int* dflag, cudaStream_t s) {
   return hflag;
 }
 
+// Stencil weights in the precision of the vectors (exact in both).
+template <typename T>
+static const T* tt_weights(const DBuf<double>& wd, const DBuf<float>& wf);
+template <>
+const double* tt_weights<double>(const DBuf<double>& wd, const DBuf<float>&) { return wd.p; }
+template <>
+const float* tt_weights<float>(const DBuf<double>&, const DBuf<float>& wf) { return wf.p; }
+
 template <typename T>
 void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s) {
   const Level& F = h->L[lf];
   const Level& Cc = h->L[lf - 1];
   const TransferTables& t = h->tt;
   if (h->deg == 1)
-    k_prolong<1, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, F.n, t.pro_start, t.pro_off, t.pro_w, xc,
+    k_prolong<1, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, F.n, t.pro_start, t.pro_off,
+                                                            tt_weights<T>(t.pro_w, t.pro_wf), xc,
                                                             xf, accumulate);
   else
-    k_prolong<2, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, F.n, t.pro_start, t.pro_off, t.pro_w, xc,
+    k_prolong<2, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, F.n, t.pro_start, t.pro_off,
+                                                            tt_weights<T>(t.pro_w, t.pro_wf), xc,
                                                             xf, accumulate);
   LAUNCH_CHECK();
 }
@@ -656,10 +666,12 @@ void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T*
   const Level& Cc = h->L[lf - 1];
   const TransferTables& t = h->tt;
   if (h->deg == 1)
-    k_restrict<1, T, 4><<<ceil_div(Cc.n, 32), 32 * 4, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off, t.res_w, bf,
+    k_restrict<1, T, 4><<<ceil_div(Cc.n, 32), 32 * 4, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off,
+                                                              tt_weights<T>(t.res_w, t.res_wf), bf,
                                                               yf, rc, zero_bd);
   else
-    k_restrict<2, T, 8><<<ceil_div(Cc.n, 32), 32 * 8, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off, t.res_w, bf,
+    k_restrict<2, T, 8><<<ceil_div(Cc.n, 32), 32 * 8, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off,
+                                                              tt_weights<T>(t.res_w, t.res_wf), bf,
                                                               yf, rc, zero_bd);
   LAUNCH_CHECK();
 }
