@@ -110,6 +110,62 @@ static void finish_out(T* user, const T* dev, size_t n, cudaStream_t s) {
 
 static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
+// Transfer index tables.  A stencil entry names the lattice point
+// (k X + ox, k Y + oy, k Z + oz) of numbering `num` for a base point (X, Y, Z):
+// the restriction's fine points 2 Xc + o, the prolongation's coarse points
+// DEG c + o.  Its dof is then affine in (X, Y, Z): P1 numbers the lattice
+// lexicographically, P2 numbers each parity class lexicographically by
+// halved coordinates, and for k = 2 the class of k X + o is that of o.  The
+// entry stores (dof at X = Y = Z = 0, y stride, z stride, o packed as three
+// bytes biased by 8); the x stride is k for P1 and 1 for P2.
+static int4 entry_index(const Numbering& num, int k, int ox, int oy, int oz) {
+  FE_REQUIRE(ox >= -8 && ox < 8 && oy >= -8 && oy < 8 && oz >= -8 && oz < 8, FE_ERR_UNSUPPORTED,
+             "transfer offset out of the packed range");
+  const int packed = (ox + 8) | ((oy + 8) << 8) | ((oz + 8) << 16);
+  if (num.deg == 1) {
+    const int n1 = num.N + 1;
+    return make_int4(ox + n1 * (oy + n1 * oz), k * n1, k * n1 * n1, packed);
+  }
+  FE_REQUIRE(k == 2, FE_ERR_UNSUPPORTED, "P2 transfer base points sit on even lattice coordinates");
+  const int code = (ox & 1) | ((oy & 1) << 1) | ((oz & 1) << 2);
+  const int c = code == 3 ? 4 : code == 4 ? 3 : code;
+  const int sx = num.sx[c], sy = num.sy[c];
+  const int dx = ox >> 1, dy = oy >> 1, dz = oz >> 1;  // floor halving (offsets may be negative)
+  return make_int4(num.off[c] + dx + sx * (dy + sy * dz), sx, sx * sy, packed);
+}
+
+static void build_level_transfer_index(Level& F, const Level& Cc, const TransferTables& t) {
+  std::vector<int4> r(t.h_res_off.size()), p(t.h_pro_off.size());
+  for (size_t e = 0; e < r.size(); ++e) {
+    const int4 o = t.h_res_off[e];  // fine point 2 Xc + o of level F
+    r[e] = entry_index(F.num, 2, o.x, o.y, o.z);
+  }
+  for (size_t e = 0; e < p.size(); ++e) {
+    const int4 o = t.h_pro_off[e];  // coarse point DEG c + o of level Cc
+    p[e] = entry_index(Cc.num, F.deg == 1 ? 1 : 2, o.x, o.y, o.z);
+  }
+  // the affine forms against the numbering itself, at base points near both
+  // ends of each axis (host only, once per hierarchy)
+  auto check = [](const Numbering& num, int k, const std::vector<int4>& off, const std::vector<int4>& tab,
+                  int kx, int bmax) {
+    const int B[4] = {0, 1, bmax - 1, bmax};
+    for (size_t e = 0; e < off.size(); ++e)
+      for (int a = 0; a < 64; ++a) {
+        const int X = B[a & 3], Y = B[(a >> 2) & 3], Z = B[a >> 4];
+        const int x = k * X + off[e].x, y = k * Y + off[e].y, z = k * Z + off[e].z;
+        if (X < 0 || Y < 0 || Z < 0 || x < 0 || y < 0 || z < 0 || x > num.m || y > num.m || z > num.m) continue;
+        FE_REQUIRE(tab[e].x + kx * X + tab[e].y * Y + tab[e].z * Z == lattice_to_dof(num, x, y, z), FE_ERR_CUDA,
+                   "transfer index table disagrees with the numbering");
+      }
+  };
+  check(F.num, 2, t.h_res_off, r, F.deg == 1 ? 2 : 1, Cc.num.m);
+  check(Cc.num, F.deg == 1 ? 1 : 2, t.h_pro_off, p, 1, Cc.num.N);
+  F.rtab.alloc(r.size());
+  CUDA_CHECK(cudaMemcpy(F.rtab, r.data(), sizeof(int4) * r.size(), cudaMemcpyHostToDevice));
+  F.ptab.alloc(p.size());
+  CUDA_CHECK(cudaMemcpy(F.ptab, p.data(), sizeof(int4) * p.size(), cudaMemcpyHostToDevice));
+}
+
 // -------------------------------------------------- transfer stencils
 // Prolongation class o in [0,2k)^3 of a fine lattice point (position o/(2k)
 // inside its coarse cube): the containing Kuhn tet is found by sorting the
@@ -174,6 +230,11 @@ static void build_transfer_tables(TransferTables& t, int deg) {
     }
     t.h_res_start.push_back((int)t.h_res_off.size());
   }
+  // coarse points with every coordinate in [margin, m - margin] have all their
+  // fine points inside the lattice (2 X + o in [0, 2 m] for |o| <= 2 margin)
+  int omax = 0;
+  for (const int4& o : t.h_res_off) omax = std::max({omax, std::abs(o.x), std::abs(o.y), std::abs(o.z)});
+  t.res_margin = (omax + 1) / 2;
   // the prolongation kernel unrolls at most 2 (P1) or 10 (P2) entries per fine point
   for (int c = 0; c < t.n_pro_class; ++c)
     FE_REQUIRE(t.h_pro_start[c + 1] - t.h_pro_start[c] <= (deg == 1 ? 2 : 10), FE_ERR_UNSUPPORTED,
@@ -949,6 +1010,7 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     launch_build_level(L, s);
   }
   build_transfer_tables(h->tt, degree);
+  for (int l = 1; l < h->nlev; ++l) build_level_transfer_index(h->L[l], h->L[l - 1], h->tt);
   std::vector<int> ch = build_children();
   h->children.alloc(48);
   CUDA_CHECK(cudaMemcpy(h->children, ch.data(), sizeof(int) * 48, cudaMemcpyHostToDevice));

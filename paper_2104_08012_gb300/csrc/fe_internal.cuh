@@ -177,6 +177,11 @@ struct Level {
   // V-cycle work vectors (level-owned so the cycle can be captured in a graph)
   DBuf<double> b64, x64, y64, d64, w64;
   DBuf<double> fb64, fx64;  // full multigrid: this level's right-hand side and solution
+  // Transfer index tables (levels >= 1), one int4 per stencil entry of the
+  // restriction to level-1 (fine dofs of this level around a coarse point) and
+  // of the prolongation from level-1 (coarse dofs around a coarse cube): the
+  // entry's dof at base point 0, its y and z strides, the packed lattice offset.
+  DBuf<int4> rtab, ptab;
   DBuf<float> b32, x32, y32, d32;
 };
 
@@ -184,6 +189,7 @@ struct Level {
 struct TransferTables {
   int deg = 0;
   int n_pro_class = 0, n_res_class = 0;
+  int res_margin = 0;  // coarse points this far from the boundary need no bounds checks
   DBuf<int> pro_start, res_start;  // class -> first entry, size n_class+1
   DBuf<int4> pro_off, res_off;     // (dx,dy,dz,-) lattice offsets
   DBuf<double> pro_w, res_w;

@@ -402,12 +402,13 @@ __global__ void k_check_positive(const double* __restrict__ v, int n, int* __res
 
 // ----------------------------------------------------------- transfers
 // Prolongation: fine lattice point L splits as L = 2k*c + o (c the coarse cube,
-// o in [0,2k)^3); the class o selects a stencil of (coarse lattice offset from
-// k*c, weight) pairs built on the host by evaluating the coarse basis.
+// o in [0,2k)^3); the class o selects a stencil of (coarse lattice point
+// DEG*c + offset, weight) pairs built on the host by evaluating the coarse
+// basis.  The per-level index table gives each entry's coarse dof as
+// t.x + cx + t.y cy + t.z cz (affine in the cube coordinates).
 template <int DEG, typename T>
-__global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __restrict__ start,
-                          const int4* __restrict__ off, const T* __restrict__ w, const T* __restrict__ xc,
-                          T* __restrict__ xf, int accumulate) {
+__global__ void k_prolong(Numbering nf, int n_f, const int* __restrict__ start, const int4* __restrict__ tab,
+                          const T* __restrict__ w, const T* __restrict__ xc, T* __restrict__ xf, int accumulate) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_f) return;
   int x, y, z;
@@ -423,8 +424,8 @@ __global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __rest
 #pragma unroll
   for (int k = 0; k < MAXE; ++k) {
     if (k < ne) {
-      const int4 o = __ldg(off + e0 + k);
-      const int j = lattice_to_dof(nc, DEG * cx + o.x, DEG * cy + o.y, DEG * cz + o.z);
+      const int4 t = __ldg(tab + e0 + k);
+      const int j = t.x + cx + t.y * cy + t.z * cz;
       s += __ldg(w + e0 + k) * __ldg(xc + j);
     }
   }
@@ -432,35 +433,43 @@ __global__ void k_prolong(Numbering nf, Numbering nc, int n_f, const int* __rest
 }
 
 // Restriction = exact transpose: coarse point Lc gathers fine points
-// 2 Lc + f_off for the stencil entries of its parity class.  With yf != null
-// the restricted vector is the residual bf - yf.  A block holds 32 consecutive
-// coarse points (one per lane, so every gather of a warp reads consecutive
-// fine entries of one class array) and TPC warps: warp w takes every TPC-th
-// stencil entry (a P2 vertex gathers 125 fine points) and the partial sums
-// meet in shared memory.
+// 2 Lc + o for the stencil entries of its parity class; the index table gives
+// the fine dof as t.x + KX X + t.y Y + t.z Z (KX = 2 for P1, 1 for P2) and the
+// offset o packed in t.w, unpacked for the bounds test only by coarse points
+// within `margin` of the boundary.  With yf != null the restricted vector is
+// the residual bf - yf.  A block holds 32 consecutive coarse points (one per
+// lane, so every gather of a warp reads consecutive fine entries of one class
+// array) and TPC warps: warp w takes every TPC-th stencil entry (a P2 vertex
+// gathers 125 fine points) and the partial sums meet in shared memory.
 template <int DEG, typename T, int TPC>
-__global__ void __launch_bounds__(32 * TPC) k_restrict(Numbering nf, Numbering nc, int n_c,
-                                                       const int* __restrict__ start, const int4* __restrict__ off,
+__global__ void __launch_bounds__(32 * TPC) k_restrict(int mf, Numbering nc, int n_c, int margin,
+                                                       const int* __restrict__ start, const int4* __restrict__ tab,
                                                        const T* __restrict__ w, const T* __restrict__ bf,
                                                        const T* __restrict__ yf, T* __restrict__ rc, int zero_bd) {
   __shared__ T part[TPC][32];
+  constexpr int KX = DEG == 1 ? 2 : 1;
   const int lane = threadIdx.x & 31, sub = threadIdx.x >> 5;
   const int J = blockIdx.x * 32 + lane;
   T s = T(0);
   if (J < n_c) {
     int X, Y, Z;
     dof_to_lattice(nc, J, X, Y, Z);
-    const bool bd = X == 0 || Y == 0 || Z == 0 || X == nc.m || Y == nc.m || Z == nc.m;
+    const int mc = nc.m;
+    const bool bd = X == 0 || Y == 0 || Z == 0 || X == mc || Y == mc || Z == mc;
     if (!(bd && zero_bd)) {
+      const bool near = min(min(X, Y), Z) < margin || max(max(X, Y), Z) > mc - margin;
       const int cls = DEG == 2 ? ((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2)) : 0;
       const int e1 = __ldg(start + cls + 1);
-      const int mf = nf.m;
+      const int base = KX * X;
 #pragma unroll 2
       for (int e = __ldg(start + cls) + sub; e < e1; e += TPC) {
-        const int4 o = __ldg(off + e);
-        const int fx = 2 * X + o.x, fy = 2 * Y + o.y, fz = 2 * Z + o.z;
-        if (fx < 0 || fy < 0 || fz < 0 || fx > mf || fy > mf || fz > mf) continue;
-        const int i = lattice_to_dof(nf, fx, fy, fz);
+        const int4 t = __ldg(tab + e);
+        if (near) {
+          const int fx = 2 * X + (t.w & 255) - 8, fy = 2 * Y + ((t.w >> 8) & 255) - 8,
+                    fz = 2 * Z + ((t.w >> 16) & 255) - 8;
+          if (fx < 0 || fy < 0 || fz < 0 || fx > mf || fy > mf || fz > mf) continue;
+        }
+        const int i = t.x + base + t.y * Y + t.z * Z;
         T v = __ldg(bf + i);
         if (yf) v -= __ldg(yf + i);
         s += __ldg(w + e) * v;
@@ -647,16 +656,13 @@ const float* tt_weights<float>(const DBuf<double>&, const DBuf<float>& wf) { ret
 template <typename T>
 void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s) {
   const Level& F = h->L[lf];
-  const Level& Cc = h->L[lf - 1];
   const TransferTables& t = h->tt;
   if (h->deg == 1)
-    k_prolong<1, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, F.n, t.pro_start, t.pro_off,
-                                                            tt_weights<T>(t.pro_w, t.pro_wf), xc,
-                                                            xf, accumulate);
+    k_prolong<1, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, F.n, t.pro_start, F.ptab,
+                                                            tt_weights<T>(t.pro_w, t.pro_wf), xc, xf, accumulate);
   else
-    k_prolong<2, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, Cc.num, F.n, t.pro_start, t.pro_off,
-                                                            tt_weights<T>(t.pro_w, t.pro_wf), xc,
-                                                            xf, accumulate);
+    k_prolong<2, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, F.n, t.pro_start, F.ptab,
+                                                            tt_weights<T>(t.pro_w, t.pro_wf), xc, xf, accumulate);
   LAUNCH_CHECK();
 }
 
@@ -666,12 +672,12 @@ void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T*
   const Level& Cc = h->L[lf - 1];
   const TransferTables& t = h->tt;
   if (h->deg == 1)
-    k_restrict<1, T, 4><<<ceil_div(Cc.n, 32), 32 * 4, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off,
-                                                              tt_weights<T>(t.res_w, t.res_wf), bf,
+    k_restrict<1, T, 4><<<ceil_div(Cc.n, 32), 32 * 4, 0, s>>>(F.num.m, Cc.num, Cc.n, t.res_margin, t.res_start,
+                                                              F.rtab, tt_weights<T>(t.res_w, t.res_wf), bf,
                                                               yf, rc, zero_bd);
   else
-    k_restrict<2, T, 8><<<ceil_div(Cc.n, 32), 32 * 8, 0, s>>>(F.num, Cc.num, Cc.n, t.res_start, t.res_off,
-                                                              tt_weights<T>(t.res_w, t.res_wf), bf,
+    k_restrict<2, T, 8><<<ceil_div(Cc.n, 32), 32 * 8, 0, s>>>(F.num.m, Cc.num, Cc.n, t.res_margin, t.res_start,
+                                                              F.rtab, tt_weights<T>(t.res_w, t.res_wf), bf,
                                                               yf, rc, zero_bd);
   LAUNCH_CHECK();
 }
