@@ -195,6 +195,20 @@ int fe_apply_operator(const fe_hierarchy* h, int level, const void* x, void* y, 
  * other step stay FP64. */
 int fe_set_f64_mode(fe_hierarchy* h, int mode);
 
+/* Chebyshev-Jacobi smoothing (Sec. 3: two Chebyshev iterations per level
+ * visit) with the operator fused (on = 1) or not (on = 0, the default).
+ * Fused, each smoothing step that needs y = A x is one launch: every interior
+ * dof carries a countdown of the tets (or cubes) that scatter into it, and
+ * the thread whose contribution ends it applies d = c1 d + c2 D^-1 (b - y),
+ * x += d to that dof, so no separate vector kernel streams y, x and d again.
+ * On GB300 the countdown atomics (one per scattered value, with the result
+ * returned) cost about three times the operator itself, so the default is the
+ * operator kernel followed by one vector kernel.  The fused forms exist for
+ * the FP32 operator and the float-pair FP64 operators; native-FP64 and bf16
+ * smoothing always use two kernels.  Results agree up to the rounding order
+ * of the atomic sums. */
+int fe_set_smoother_fusion(fe_hierarchy* h, int on);
+
 /* y = M_l x with the consistent mass matrix (all dofs, no boundary change). */
 int fe_apply_mass(const fe_hierarchy* h, int level, const double* x, double* y, void* stream);
 

@@ -30,7 +30,7 @@ EXPORTED = (
     "fe_diagonal", "fe_lambda_max", "fe_prolong", "fe_restrict", "fe_smooth", "fe_coarse_solve", "fe_vcycle",
     "fe_load_vector", "fe_quadrature_points", "fe_load_vector_quadrature", "fe_solve_poisson", "fe_adjoint_gradient",
     "fe_objective", "fe_dot_noalloc",
-    "fe_set_f64_mode", "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
+    "fe_set_f64_mode", "fe_set_smoother_fusion", "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
 )
 
 
@@ -105,6 +105,7 @@ def load():
         "fe_objective": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
         "fe_dot_noalloc": (i, [vp, vp, ll, vp, vp]),
         "fe_set_f64_mode": (i, [vp, i]),
+        "fe_set_smoother_fusion": (i, [vp, i]),
         "fe_batch_create": (i, [i, vp, vp, vp, ctypes.POINTER(vp)]),
         "fe_batch_destroy": (None, [vp]),
         "fe_batch_hierarchy": (i, [vp, i, ctypes.POINTER(vp)]),
@@ -357,6 +358,10 @@ class Hierarchy:
     # -- operations on caller-owned vectors (torch tensors or numpy arrays)
     def set_f64_mode(self, mode):
         _check(self._L.fe_set_f64_mode(self.h, mode))
+
+    def set_smoother_fusion(self, on):
+        """Chebyshev update fused into the operator launch (True) or a separate vector kernel (False, default)."""
+        _check(self._L.fe_set_smoother_fusion(self.h, 1 if on else 0))
 
     def set_coefficient(self, kappa=None, stream=None):
         fe_set_coefficient(self.h, kappa, stream)

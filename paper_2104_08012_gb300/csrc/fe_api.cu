@@ -404,6 +404,35 @@ void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int
     FE_FAIL(FE_ERR_ARG, "unknown dtype");
 }
 
+// y = A x followed by the Chebyshev update of every dof: with fusion on, one
+// launch when the operator kernel of this precision and mode has the fused
+// form (FP32 cube kernel, float-pair tet and cube kernels); otherwise the
+// operator kernel and the vector kernel.
+template <typename T>
+static void apply_cheb_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d, double c1, double c2,
+                               bool store_d, int dtype, cudaStream_t s) {
+  Level& L = h->L[l];
+  if (h->fuse_smoother && L.cnt_tet.p) {
+    const bool cube = h->f64_mode == FE_F64_DOUBLE_FLOAT_CUBE || (h->f64_mode == FE_F64_DOUBLE_FLOAT && L.deg == 1);
+    if constexpr (sizeof(T) == 8) {
+      if (dtype == FE_F64 && h->f64_mode != FE_F64_NATIVE) {
+        if (cube)
+          launch_apply_cheb64_cube_df(L, b, x, y, d, c1, c2, store_d, s);
+        else
+          launch_apply_cheb64_df(L, b, x, y, d, c1, c2, store_d, s);
+        return;
+      }
+    } else {
+      if (dtype == FE_F32) {
+        launch_apply_cheb32(L, b, x, y, d, c1, c2, store_d, s);
+        return;
+      }
+    }
+  }
+  apply_enqueue(h, l, x, y, dtype, s);
+  launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, c1, c2, false, s, store_d);
+}
+
 // Chebyshev iterations on level l (same recurrence as the oracle's).
 template <typename T>
 static void smooth_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d, int steps, double lo, double hi,
@@ -415,16 +444,13 @@ static void smooth_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d,
   for (int k = 0; k < steps; ++k) {
     const bool last = k + 1 == steps;  // its direction d is not used again
     if (k == 0) {
-      if (x_zero) {
+      if (x_zero)
         launch_cheb_step<T>(L.n, b, nullptr, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, true, s, !last);
-      } else {
-        apply_enqueue(h, l, x, y, dtype, s);
-        launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, false, s, !last);
-      }
+      else
+        apply_cheb_enqueue<T>(h, l, b, x, y, d, 0.0, 1.0 / theta, !last, dtype, s);
     } else {
       const double rn = 1.0 / (2.0 * sigma - rho);
-      apply_enqueue(h, l, x, y, dtype, s);
-      launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, rn * rho, 2.0 * rn / delta, false, s, !last);
+      apply_cheb_enqueue<T>(h, l, b, x, y, d, rn * rho, 2.0 * rn / delta, !last, dtype, s);
       rho = rn;
     }
   }
@@ -1010,7 +1036,10 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     launch_build_level(L, s);
   }
   build_transfer_tables(h->tt, degree);
-  for (int l = 1; l < h->nlev; ++l) build_level_transfer_index(h->L[l], h->L[l - 1], h->tt);
+  for (int l = 0; l < h->nlev; ++l) {
+    if (l > 0) build_level_transfer_index(h->L[l], h->L[l - 1], h->tt);
+    launch_build_valence(h->L[l], s);
+  }
   std::vector<int> ch = build_children();
   h->children.alloc(48);
   CUDA_CHECK(cudaMemcpy(h->children, ch.data(), sizeof(int) * 48, cudaMemcpyHostToDevice));
@@ -1192,6 +1221,18 @@ int fe_set_f64_mode(fe_hierarchy* h, int mode) {
   if (h->f64_mode != mode) {
     CUDA_CHECK(cudaDeviceSynchronize());
     h->f64_mode = mode;
+    invalidate_graphs(h);
+  }
+  API_END
+}
+
+int fe_set_smoother_fusion(fe_hierarchy* h, int on) {
+  API_BEGIN
+  FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
+  FE_REQUIRE(on == 0 || on == 1, FE_ERR_ARG, "fusion flag must be 0 or 1");
+  if (h->fuse_smoother != on) {
+    CUDA_CHECK(cudaDeviceSynchronize());
+    h->fuse_smoother = on;
     invalidate_graphs(h);
   }
   API_END

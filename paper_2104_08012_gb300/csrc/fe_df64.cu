@@ -22,16 +22,52 @@ namespace {
 using namespace fe_df;
 constexpr int kBlock = 256;
 
+// The dofs whose countdown this thread ended (count returned 1): every other
+// contribution was fenced before its countdown, so after an acquiring fence
+// y_i in L2 is complete.
+template <int ND>
+__device__ __forceinline__ void finish_dofs(const int* pidx, const unsigned* prev, const double* y,
+                                            const ChebFuse<double>& cf) {
+#pragma unroll
+  for (int j = 0; j < ND; ++j)
+    if (prev[j] == 1u) {
+      fence_acq_rel_gpu();
+      const int i = pidx[j];
+      cf.cnt[i] = __ldg(cf.val + i);
+      cheb_update(i, __ldcg(y + i), cf.b, cf.dinv, cf.x, cf.d, cf.c1, cf.c2, cf.store_d);
+    }
+}
+
 // Persistent grid-stride loop over tets: while one tet is contracted, the
 // map rows, dofs and geometric factors of the thread's next tet are already
 // in flight (the kernel is otherwise bound by the latency of its gathers).
-template <int DEG>
+//
+// With FUSE the launch also performs the Chebyshev smoother step on its
+// input: each interior dof's countdown (its number of tets) is decremented
+// after the tet's contributions are issued and fenced; the thread that ends
+// it (it looks at the returned counts one tet later, so the atomics' latency
+// overlaps the next tet's arithmetic) reads the complete y_i from L2 and
+// updates d_i and x_i in place.  Every tet
+// gathers x before it scatters, so x_i only changes once all its readers are
+// done.  Dirichlet rows (y = x) are updated by the threads that write them.
+template <int DEG, bool FUSE>
 __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
-                                                        const float2* __restrict__ geo, const double* __restrict__ x,
-                                                        double* __restrict__ y, int nb, const int* __restrict__ bnd) {
+                                                        const float2* __restrict__ geo, const double* x,
+                                                        double* __restrict__ y, int nb, const int* __restrict__ bnd,
+                                                        ChebFuse<double> cf) {
   constexpr int ND = DEG == 1 ? 4 : 10;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  for (int i = tid; i < nb; i += stride) y[bnd[i]] = x[bnd[i]];  // Dirichlet rows: identity
+  for (int i = tid; i < nb; i += stride) {  // Dirichlet rows: identity
+    const int k = bnd[i];
+    const double xk = x[k];
+    y[k] = xk;
+    if constexpr (FUSE) cheb_update(k, xk, cf.b, cf.dinv, cf.x, cf.d, cf.c1, cf.c2, cf.store_d);
+  }
+  // with FUSE, x changes during the launch: plain loads instead of the read-only path
+  auto ldx = [&](int i) { return FUSE ? x[i] : __ldg(x + i); };
+  int pidx[FUSE ? ND : 1];
+  unsigned prev[FUSE ? ND : 1];
+  bool have_prev = false;
   int c = tid;
   if (c >= C) return;
   int idx[ND];
@@ -40,7 +76,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int
 #pragma unroll
   for (int j = 0; j < ND; ++j) idx[j] = __ldg(map + (size_t)j * Cs + c);
 #pragma unroll
-  for (int j = 0; j < ND; ++j) xv[j] = idx[j] >= 0 ? __ldg(x + idx[j]) : 0.0;
+  for (int j = 0; j < ND; ++j) xv[j] = idx[j] >= 0 ? ldx(idx[j]) : 0.0;
 #pragma unroll
   for (int a = 0; a < 6; ++a) gv[a] = __ldg(geo + (size_t)a * Cs + c);
   while (true) {
@@ -53,7 +89,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int
 #pragma unroll
       for (int j = 0; j < ND; ++j) idn[j] = __ldg(map + (size_t)j * Cs + cn);
 #pragma unroll
-      for (int j = 0; j < ND; ++j) xn[j] = idn[j] >= 0 ? __ldg(x + idn[j]) : 0.0;
+      for (int j = 0; j < ND; ++j) xn[j] = idn[j] >= 0 ? ldx(idn[j]) : 0.0;
 #pragma unroll
       for (int a = 0; a < 6; ++a) gn[a] = __ldg(geo + (size_t)a * Cs + cn);
     }
@@ -68,6 +104,17 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int
 #pragma unroll
     for (int j = 0; j < ND; ++j)
       if (idx[j] >= 0) atomicAdd(y + idx[j], widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
+    if constexpr (FUSE) {
+      // the previous tet's countdowns have returned by now: finish its dofs
+      if (have_prev) finish_dofs<ND>(pidx, prev, y, cf);
+      fence_acq_rel_gpu();  // this tet's contributions before its countdowns
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        pidx[j] = idx[j];
+        prev[j] = idx[j] >= 0 ? atomicSub(cf.cnt + idx[j], 1u) : 0u;
+      }
+      have_prev = true;
+    }
     if (!more) break;
     c = cn;
 #pragma unroll
@@ -78,26 +125,34 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int
 #pragma unroll
     for (int a = 0; a < 6; ++a) gv[a] = gn[a];
   }
+  if constexpr (FUSE)
+    if (have_prev) finish_dofs<ND>(pidx, prev, y, cf);
 }
 
 // Cube-aggregated variant: one thread per cube splits the cube's (k+1)^3 dofs
 // once (scaled by their largest exponent), applies its six Kuhn tets into
 // float-pair accumulators and widens/scatters (k+1)^3 values: 27 splits, 27
 // FP64 adds and 27 atomics per cube for P2 instead of 60 of each.
-template <int DEG>
+// FUSE: the Chebyshev step as in k_apply_df, with cube countdowns.
+template <int DEG, bool FUSE>
 __global__ void __launch_bounds__(kBlock, 1) k_apply_cube_df(int Q, int Qs, int Cs, const int* __restrict__ cmap,
-                                                             const float2* __restrict__ geo,
-                                                             const double* __restrict__ x, double* __restrict__ y,
-                                                             int nb, const int* __restrict__ bnd) {
+                                                             const float2* __restrict__ geo, const double* x,
+                                                             double* __restrict__ y, int nb,
+                                                             const int* __restrict__ bnd, ChebFuse<double> cf) {
   constexpr int NL = DEG == 1 ? 8 : 27, ND = DEG == 1 ? 4 : 10;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  for (int i = tid; i < nb; i += stride) y[bnd[i]] = x[bnd[i]];  // Dirichlet rows: identity
+  for (int i = tid; i < nb; i += stride) {  // Dirichlet rows: identity
+    const int k = bnd[i];
+    const double xk = x[k];
+    y[k] = xk;
+    if constexpr (FUSE) cheb_update(k, xk, cf.b, cf.dinv, cf.x, cf.d, cf.c1, cf.c2, cf.store_d);
+  }
   for (int q = tid; q < Q; q += stride) {
     double xv[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       const int i = __ldg(cmap + (size_t)l * Qs + q);
-      xv[l] = i >= 0 ? __ldg(x + i) : 0.0;
+      xv[l] = i >= 0 ? (FUSE ? x[i] : __ldg(x + i)) : 0.0;
     }
     const int emax = block_exponent<NL>(xv);
     DF uc[NL], acc[NL];
@@ -125,6 +180,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_apply_cube_df(int Q, int Qs, int 
     for (int l = 0; l < NL; ++l) {
       const int i = __ldg(cmap + (size_t)l * Qs + q);
       if (i >= 0) atomicAdd(y + i, widen_scaled(acc[l].hi, emax) + widen_scaled(acc[l].lo, emax));
+    }
+    if constexpr (FUSE) {
+      fence_acq_rel_gpu();
+      for (int l = 0; l < NL; ++l) {
+        const int i = __ldg(cmap + (size_t)l * Qs + q);
+        if (i >= 0 && atomicSub(cf.cnt + i, 1u) == 1u) {
+          fence_acq_rel_gpu();
+          cf.cnt[i] = __ldg(cf.val + i);
+          cheb_update(i, __ldcg(y + i), cf.b, cf.dinv, cf.x, cf.d, cf.c1, cf.c2, cf.store_d);
+        }
+      }
     }
   }
 }
@@ -207,34 +273,55 @@ static int resident_grid(K kernel, int block, int work_items) {
   return need < g ? (need > 0 ? need : 1) : g;
 }
 
-void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s) {
+template <bool FUSE>
+static void apply_cube_df(const Level& L, const double* x, double* y, const ChebFuse<double>& cf, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
   if (L.deg == 1) {
     static int g1 = 0;
-    if (!g1) g1 = resident_grid(k_apply_cube_df<1>, kBlock, 1 << 30);
-    k_apply_cube_df<1><<<std::min(g1, ceil_div(std::max(L.Q, L.nb), kBlock)), kBlock, 0, s>>>(
-        L.Q, L.Qs, L.Cs, L.cmap, L.geodf, x, y, L.nb, L.bnd);
+    if (!g1) g1 = resident_grid(k_apply_cube_df<1, FUSE>, kBlock, 1 << 30);
+    k_apply_cube_df<1, FUSE><<<std::min(g1, ceil_div(std::max(L.Q, L.nb), kBlock)), kBlock, 0, s>>>(
+        L.Q, L.Qs, L.Cs, L.cmap, L.geodf, x, y, L.nb, L.bnd, cf);
   } else {
     static int g2 = 0;
-    if (!g2) g2 = resident_grid(k_apply_cube_df<2>, kBlock, 1 << 30);
-    k_apply_cube_df<2><<<std::min(g2, ceil_div(std::max(L.Q, L.nb), kBlock)), kBlock, 0, s>>>(
-        L.Q, L.Qs, L.Cs, L.cmap, L.geodf, x, y, L.nb, L.bnd);
+    if (!g2) g2 = resident_grid(k_apply_cube_df<2, FUSE>, kBlock, 1 << 30);
+    k_apply_cube_df<2, FUSE><<<std::min(g2, ceil_div(std::max(L.Q, L.nb), kBlock)), kBlock, 0, s>>>(
+        L.Q, L.Qs, L.Cs, L.cmap, L.geodf, x, y, L.nb, L.bnd, cf);
   }
   LAUNCH_CHECK();
 }
 
-void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s) {
+template <bool FUSE>
+static void apply_df(const Level& L, const double* x, double* y, const ChebFuse<double>& cf, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
   if (L.deg == 1) {
     static int g1 = 0;
-    if (!g1) g1 = resident_grid(k_apply_df<1>, kBlock, 1 << 30);
-    k_apply_df<1><<<std::min(g1, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geodf, x,
-                                                                                          y, L.nb, L.bnd);
+    if (!g1) g1 = resident_grid(k_apply_df<1, FUSE>, kBlock, 1 << 30);
+    k_apply_df<1, FUSE><<<std::min(g1, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(
+        L.C, L.Cs, L.map, L.geodf, x, y, L.nb, L.bnd, cf);
   } else {
     static int g2 = 0;
-    if (!g2) g2 = resident_grid(k_apply_df<2>, kBlock, 1 << 30);
-    k_apply_df<2><<<std::min(g2, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geodf, x,
-                                                                                          y, L.nb, L.bnd);
+    if (!g2) g2 = resident_grid(k_apply_df<2, FUSE>, kBlock, 1 << 30);
+    k_apply_df<2, FUSE><<<std::min(g2, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(
+        L.C, L.Cs, L.map, L.geodf, x, y, L.nb, L.bnd, cf);
   }
   LAUNCH_CHECK();
+}
+
+void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s) {
+  apply_cube_df<false>(L, x, y, ChebFuse<double>{}, s);
+}
+
+void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s) {
+  apply_df<false>(L, x, y, ChebFuse<double>{}, s);
+}
+
+void launch_apply_cheb64_df(const Level& L, const double* b, double* x, double* y, double* d, double c1, double c2,
+                            bool store_d, cudaStream_t s) {
+  apply_df<true>(L, x, y, ChebFuse<double>{b, L.dinv64, x, d, L.val_tet, L.cnt_tet, c1, c2, store_d ? 1 : 0}, s);
+}
+
+void launch_apply_cheb64_cube_df(const Level& L, const double* b, double* x, double* y, double* d, double c1,
+                                 double c2, bool store_d, cudaStream_t s) {
+  apply_cube_df<true>(L, x, y, ChebFuse<double>{b, L.dinv64, x, d, L.val_cube, L.cnt_cube, c1, c2, store_d ? 1 : 0},
+                      s);
 }

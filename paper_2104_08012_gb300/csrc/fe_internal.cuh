@@ -154,6 +154,37 @@ __host__ __device__ constexpr int cube_local(int deg, int t, int j) {
                                  9 * (((kuhn_vmask(t, edge_a(j)) >> 2) & 1) + ((kuhn_vmask(t, edge_b(j)) >> 2) & 1)));
 }
 
+// ------------------------------------------------- Chebyshev update ---
+// One step of the Chebyshev semi-iteration on D^-1 A for one dof:
+// d = c1 d + c2 D^-1 (b - y), x += d (c1 = 0: the previous d is not read).
+// The same function serves the stand-alone vector kernel and the operator
+// kernels that fuse the update (ChebFuse), so both give the same arithmetic.
+template <typename T>
+__device__ __forceinline__ void cheb_update(int i, T yi, const T* b, const T* dinv, T* x, T* d, T c1, T c2,
+                                            int store_d) {
+  const T r = b[i] - yi;
+  const T dn = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * dinv[i] * r;
+  if (store_d) d[i] = dn;  // the last step of a sweep does not need d again
+  x[i] += dn;
+}
+
+// Release/acquire fence at GPU scope (orders this thread's earlier memory
+// operations before its later ones as seen by other threads of the device).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Arguments of an operator kernel that finishes the smoother step itself.
+template <typename T>
+struct ChebFuse {
+  const T* b;
+  const T* dinv;
+  T* x;  // the operator's input, updated in place by each dof's last contributor
+  T* d;
+  const unsigned* val;  // contributors per dof
+  unsigned* cnt;        // countdown, equal to val between launches
+  T c1, c2;
+  int store_d;
+};
+
 // ---------------------------------------------------------- level data ---
 struct Level {
   int N = 0, deg = 0, nd = 0;
@@ -183,6 +214,12 @@ struct Level {
   // entry's dof at base point 0, its y and z strides, the packed lattice offset.
   DBuf<int4> rtab, ptab;
   DBuf<float> b32, x32, y32, d32;
+  // Smoother fused with the operator (levels >= 1): per interior dof the number
+  // of tets (val_tet) and of cubes (val_cube) that scatter into it, and the
+  // countdown copies the apply kernels decrement; the thread that takes a
+  // dof's count to zero holds its complete y_i and performs the Chebyshev
+  // update of that dof, then restores the count.
+  DBuf<unsigned> val_tet, cnt_tet, val_cube, cnt_cube;
 };
 
 // Host-built transfer stencils (exact dyadic weights).
@@ -265,6 +302,7 @@ struct fe_hierarchy {
   DBuf<int> cgctl;        // loop counters
   bool lmax_valid = false;
   int f64_mode = FE_F64_DOUBLE_FLOAT;  // arithmetic of FP64 operator applications
+  int fuse_smoother = 0;               // Chebyshev update fused into the operator kernel (measured slower on GB300)
 };
 
 // ------------------------------------------------------- launch wrappers ---
@@ -275,6 +313,15 @@ void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s);
 void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s);
+// The same operator kernels with the Chebyshev update fused (y = A x, then
+// d = c1 d + c2 D^-1 (b - y), x += d per dof, in one launch).
+void launch_apply_cheb32(const Level& L, const float* b, float* x, float* y, float* d, double c1, double c2,
+                         bool store_d, cudaStream_t s);
+void launch_apply_cheb64_df(const Level& L, const double* b, double* x, double* y, double* d, double c1, double c2,
+                            bool store_d, cudaStream_t s);
+void launch_apply_cheb64_cube_df(const Level& L, const double* b, double* x, double* y, double* d, double c1,
+                                 double c2, bool store_d, cudaStream_t s);
+void launch_build_valence(Level& L, cudaStream_t s);
 void launch_split_geometry(Level& L, cudaStream_t s);
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_mass_df(const Level& L, const double* x, double* y, cudaStream_t s);

@@ -138,12 +138,12 @@ __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const
 // (k+1)^3 atomics instead of 6 * nd (27 instead of 60 for P2).
 constexpr int kCubeBlock = 128;  // 4 blocks of 128 per SM at 128 registers: 5% faster than 2 of 256
 
-template <int DEG>
+template <int DEG, bool FUSE>
 __global__ void __launch_bounds__(kCubeBlock, 4) k_apply_cube(int Q, int Qs, int Cs, int Qpad,
                                                             const int* __restrict__ cmap,
-                                                            const float* __restrict__ geo,
-                                                            const float* __restrict__ x, float* __restrict__ y,
-                                                            int nb, const int* __restrict__ bnd) {
+                                                            const float* __restrict__ geo, const float* x,
+                                                            float* __restrict__ y, int nb, const int* __restrict__ bnd,
+                                                            ChebFuse<float> cf) {
   constexpr int NL = DEG == 1 ? 8 : 27, ND = DEG == 1 ? 4 : 10;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < Q) {
@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(kCubeBlock, 4) k_apply_cube(int Q, int Qs, int
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       const int i = __ldg(cmap + (size_t)l * Qs + q);
-      xv[l] = i >= 0 ? __ldg(x + i) : 0.0f;
+      // with FUSE, x changes during the launch (each dof once, after its last reader)
+      xv[l] = i >= 0 ? (FUSE ? x[i] : __ldg(x + i)) : 0.0f;
       acc[l] = 0.0f;
     }
     // The cube's six tets are cells 6q .. 6q+5, contiguous in every row of
@@ -177,9 +178,34 @@ __global__ void __launch_bounds__(kCubeBlock, 4) k_apply_cube(int Q, int Qs, int
       const int i = __ldg(cmap + (size_t)l * Qs + q);
       if (i >= 0) atomicAdd(y + i, acc[l]);
     }
+    if constexpr (FUSE) {
+      // this cube's contributions reach L2 before its countdowns do; the cube
+      // that ends a dof's countdown therefore reads the complete y_i
+      fence_acq_rel_gpu();
+      for (int l = 0; l < NL; ++l) {
+        const int i = __ldg(cmap + (size_t)l * Qs + q);
+        if (i >= 0 && atomicSub(cf.cnt + i, 1u) == 1u) {
+          fence_acq_rel_gpu();
+          cf.cnt[i] = __ldg(cf.val + i);
+          cheb_update(i, __ldcg(y + i), cf.b, cf.dinv, cf.x, cf.d, cf.c1, cf.c2, cf.store_d);
+        }
+      }
+    }
   } else if (q >= Qpad && q - Qpad < nb) {
     const int i = bnd[q - Qpad];
-    y[i] = x[i];
+    const float xi = x[i];
+    y[i] = xi;
+    if constexpr (FUSE) cheb_update(i, xi, cf.b, cf.dinv, cf.x, cf.d, cf.c1, cf.c2, cf.store_d);
+  }
+}
+
+// Contributors per interior dof: cells (nd map rows) or cubes (cube map rows).
+__global__ void k_valence(int C, int Cs, int rows, const int* __restrict__ map, unsigned* __restrict__ v) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  for (int j = 0; j < rows; ++j) {
+    const int m = map[(size_t)j * Cs + c];
+    if (m >= 0) atomicAdd(v + m, 1u);
   }
 }
 
@@ -499,10 +525,7 @@ __global__ void k_cheb_step(int n, const T* __restrict__ b, const T* __restrict_
     if (store_d) d[i] = dn;
     x[i] = dn;
   } else {
-    const T r = b[i] - y[i];
-    const T dn = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * dinv[i] * r;
-    if (store_d) d[i] = dn;  // the last step of a sweep does not need d again
-    x[i] += dn;
+    cheb_update(i, y[i], b, dinv, x, d, c1, c2, store_d);
   }
 }
 
@@ -569,19 +592,44 @@ static void apply_impl(const Level& L, const T* geo, const T* x, T* y, cudaStrea
   LAUNCH_CHECK();
 }
 
-static void apply_cube32(const Level& L, const float* x, float* y, cudaStream_t s) {
+template <bool FUSE>
+static void apply_cube32(const Level& L, const float* x, float* y, const ChebFuse<float>& cf, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)L.n, s));
   const int Qpad = ceil_div(L.Q, kCubeBlock) * kCubeBlock;
   const int grid = ceil_div((long long)Qpad + L.nb, kCubeBlock);
   if (L.deg == 1)
-    k_apply_cube<1><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd);
+    k_apply_cube<1, FUSE><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd, cf);
   else
-    k_apply_cube<2><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd);
+    k_apply_cube<2, FUSE><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd, cf);
   LAUNCH_CHECK();
 }
 
+void launch_apply_cheb32(const Level& L, const float* b, float* x, float* y, float* d, double c1, double c2,
+                         bool store_d, cudaStream_t s) {
+  const ChebFuse<float> cf{b, L.dinv32, x, d, L.val_cube, L.cnt_cube, (float)c1, (float)c2, store_d ? 1 : 0};
+  apply_cube32<true>(L, x, y, cf, s);
+}
+
+void launch_build_valence(Level& L, cudaStream_t s) {
+  L.val_tet.alloc(L.n);
+  L.cnt_tet.alloc(L.n);
+  L.val_cube.alloc(L.n);
+  L.cnt_cube.alloc(L.n);
+  CUDA_CHECK(cudaMemsetAsync(L.val_tet, 0, sizeof(unsigned) * (size_t)L.n, s));
+  CUDA_CHECK(cudaMemsetAsync(L.val_cube, 0, sizeof(unsigned) * (size_t)L.n, s));
+  k_valence<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.nd, L.map, L.val_tet);
+  LAUNCH_CHECK();
+  const int K = L.deg + 1;
+  k_valence<<<ceil_div(L.Q, kBlock), kBlock, 0, s>>>(L.Q, L.Qs, K * K * K, L.cmap, L.val_cube);
+  LAUNCH_CHECK();
+  CUDA_CHECK(cudaMemcpyAsync(L.cnt_tet, L.val_tet, sizeof(unsigned) * (size_t)L.n, cudaMemcpyDeviceToDevice, s));
+  CUDA_CHECK(cudaMemcpyAsync(L.cnt_cube, L.val_cube, sizeof(unsigned) * (size_t)L.n, cudaMemcpyDeviceToDevice, s));
+}
+
 void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s) { apply_impl<double>(L, L.geo64, x, y, s); }
-void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) { apply_cube32(L, x, y, s); }
+void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) {
+  apply_cube32<false>(L, x, y, ChebFuse<float>{}, s);
+}
 
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));

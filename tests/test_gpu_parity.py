@@ -189,6 +189,42 @@ def test_chebyshev_smoother(fe, k, steps):
         assert np.linalg.norm(host(x) - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("mode", ["df", "df_tet", "df_cube", "f32"])
+def test_fused_smoother(fe, k, mode):
+    """Smoothing with the Chebyshev update fused into the operator launch (per-dof countdowns) against the
+    oracle's Chebyshev iteration and against the unfused kernels, on a fine and a coarse level, applied twice in a
+    row (the countdowns must be restored for the second call)."""
+    f64_mode = {"df": fe.FE_F64_DOUBLE_FLOAT, "df_tet": fe.FE_F64_DOUBLE_FLOAT_TET,
+                "df_cube": fe.FE_F64_DOUBLE_FLOAT_CUBE, "f32": fe.FE_F64_DOUBLE_FLOAT}[mode]
+    dtype, tdt = (fe.FE_F32, torch.float32) if mode == "f32" else (fe.FE_F64, torch.float64)
+    tol = 1e-5 if mode == "f32" else 1e-12
+    with fe.Hierarchy(3, 1, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=12)
+        h.set_coefficient(dt(kappa))
+        h.set_f64_mode(f64_mode)
+        oh = O.Hierarchy(3, 1, k, kappa)
+        for lev in (1, 0):
+            L = oh.levels[lev]
+            lm = h.lambda_max(lev)
+            b, x0 = I.random_vector(L.n, 30 + lev), I.random_vector(L.n, 40 + lev)
+            ref = x0
+            for _ in range(2):
+                ref = O.chebyshev(lambda v: L.A @ v, L.diag, b, ref, 0.1 * lm, 1.1 * lm, 3)
+            got = {}
+            for fused in (True, False):
+                h.set_smoother_fusion(fused)
+                x = dt(x0, tdt)
+                for _ in range(2):
+                    h.smooth(dt(b, tdt), x, level=lev, steps=3, lo=0.1, hi=1.1, dtype=dtype)
+                torch.cuda.synchronize()
+                got[fused] = host(x)
+                err = np.linalg.norm(got[fused] - ref) / np.linalg.norm(ref)
+                assert err <= tol, (lev, fused, err)
+            h.set_smoother_fusion(True)
+            assert np.linalg.norm(got[True] - got[False]) <= tol * np.linalg.norm(ref)
+
+
 def test_lambda_max_p1_closed_form(fe):
     """Lanczos estimate of lambda_max(D^-1 A) for P1 against 1 + cos(pi h) (Kuhn P1 = h x 7-point)."""
     for N in (4, 8, 16):
