@@ -70,6 +70,7 @@ extern "C" {
                                        out, with the faster layout per degree (P1: per cube, P2: per tet) */
 #define FE_F64_DOUBLE_FLOAT_TET 2   /* the same arithmetic, one thread per tet (persistent, prefetching) */
 #define FE_F64_DOUBLE_FLOAT_CUBE 3  /* the same arithmetic, one thread per cube (27/8 dofs split and scattered once) */
+#define FE_F64_DOUBLE_FLOAT_PAIR 4  /* P2: the same arithmetic, two tets per thread in packed FP32x2 instructions */
 
 /* ---- preconditioners and precision modes of fe_solve_poisson ---- */
 #define FE_PC_JACOBI 0

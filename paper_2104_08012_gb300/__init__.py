@@ -16,7 +16,8 @@ from . import build as _build
 FE_OK = 0
 FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_NOMEM, FE_ERR_NO_CONVERGENCE, FE_ERR_NAN, FE_ERR_TIMEOUT, FE_ERR_UNSUPPORTED = range(-1, -8, -1)
 FE_F64, FE_F32, FE_BF16 = 0, 1, 2
-FE_F64_NATIVE, FE_F64_DOUBLE_FLOAT, FE_F64_DOUBLE_FLOAT_TET, FE_F64_DOUBLE_FLOAT_CUBE = 0, 1, 2, 3
+FE_F64_NATIVE, FE_F64_DOUBLE_FLOAT, FE_F64_DOUBLE_FLOAT_TET, FE_F64_DOUBLE_FLOAT_CUBE, FE_F64_DOUBLE_FLOAT_PAIR = \
+    0, 1, 2, 3, 4
 FE_PC_JACOBI, FE_PC_GMG, FE_PC_FMG = 0, 1, 2
 FE_QUAD_POINTS = 27
 FE_PREC_F64, FE_PREC_MIXED_F32, FE_PREC_MIXED_BF16 = 0, 1, 2

@@ -390,7 +390,9 @@ void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int
   // measured on GB300 (P*64^3): P1 per cube 0.025 ms vs per tet 0.041 ms; P2 per tet 0.139 ms vs per cube
   // 0.209 ms (the P2 cube kernel needs 254 registers, i.e. 8 warps per SM)
   const bool cube = h->f64_mode == FE_F64_DOUBLE_FLOAT_CUBE || (h->f64_mode == FE_F64_DOUBLE_FLOAT && L.deg == 1);
-  if (dtype == FE_F64 && h->f64_mode != FE_F64_NATIVE && cube)
+  if (dtype == FE_F64 && h->f64_mode == FE_F64_DOUBLE_FLOAT_PAIR && L.deg == 2)
+    launch_apply64_df2(L, (const double*)x, (double*)y, s);
+  else if (dtype == FE_F64 && h->f64_mode != FE_F64_NATIVE && cube)
     launch_apply64_cube_df(L, (const double*)x, (double*)y, s);
   else if (dtype == FE_F64 && h->f64_mode != FE_F64_NATIVE)
     launch_apply64_df(L, (const double*)x, (double*)y, s);
@@ -1217,7 +1219,7 @@ int fe_apply_operator(const fe_hierarchy* hc, int level, const void* x, void* y,
 int fe_set_f64_mode(fe_hierarchy* h, int mode) {
   API_BEGIN
   FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
-  FE_REQUIRE(mode >= FE_F64_NATIVE && mode <= FE_F64_DOUBLE_FLOAT_CUBE, FE_ERR_ARG, "unknown FP64 mode");
+  FE_REQUIRE(mode >= FE_F64_NATIVE && mode <= FE_F64_DOUBLE_FLOAT_PAIR, FE_ERR_ARG, "unknown FP64 mode");
   if (h->f64_mode != mode) {
     CUDA_CHECK(cudaDeviceSynchronize());
     h->f64_mode = mode;

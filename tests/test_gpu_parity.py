@@ -60,13 +60,14 @@ def test_mesh_queries_match_oracle(fe, k, N):
 @pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("N", [1, 2, 3, 5, 8])
 @pytest.mark.parametrize("coef", ["one", "grf"])
-@pytest.mark.parametrize("mode", ["native", "double_float_tet", "double_float_cube"])
+@pytest.mark.parametrize("mode", ["native", "double_float_tet", "double_float_cube", "double_float_pair"])
 def test_apply_f64(fe, k, N, coef, mode):
     """FP64 operator in both arithmetics: FP64 FMAs and float-pair (~48-bit) on the FP32 pipes
-    (per cube and per tet)."""
+    (per cube, per tet, and two tets per thread in packed FP32x2 instructions)."""
     with fe.Hierarchy(N, 0, k) as h:
         h.set_f64_mode({"native": fe.FE_F64_NATIVE, "double_float_cube": fe.FE_F64_DOUBLE_FLOAT_CUBE,
-                        "double_float_tet": fe.FE_F64_DOUBLE_FLOAT_TET}[mode])
+                        "double_float_tet": fe.FE_F64_DOUBLE_FLOAT_TET,
+                        "double_float_pair": fe.FE_F64_DOUBLE_FLOAT_PAIR}[mode])
         kappa = None if coef == "one" else I.grf_kappa(h.cell_centroids(), seed=N)
         h.set_coefficient(None if kappa is None else dt(kappa))
         L = O.Level(N, k, kappa)
@@ -97,13 +98,14 @@ def test_apply_f32(fe, k, N, variable_kappa):
 
 
 @pytest.mark.parametrize("scale", [1e-250, 1e-30, 1e-8, 1.0, 1e8, 1e30, 1e250])
-@pytest.mark.parametrize("mode", ["double_float_cube", "double_float_tet"])
+@pytest.mark.parametrize("mode", ["double_float_cube", "double_float_tet", "double_float_pair"])
 def test_double_float_value_range(fe, scale, mode):
     """The float-pair split/widen keep FP64-class accuracy over the whole FP64 range (each
     tet's dofs are scaled by a power of two first), with exact zeros and sign changes,
     and NaN dofs propagate."""
     with fe.Hierarchy(3, 0, 2) as h:
-        h.set_f64_mode(fe.FE_F64_DOUBLE_FLOAT_CUBE if mode == "double_float_cube" else fe.FE_F64_DOUBLE_FLOAT_TET)
+        h.set_f64_mode({"double_float_cube": fe.FE_F64_DOUBLE_FLOAT_CUBE, "double_float_tet": fe.FE_F64_DOUBLE_FLOAT_TET,
+                        "double_float_pair": fe.FE_F64_DOUBLE_FLOAT_PAIR}[mode])
         L = O.Level(3, 2)
         x = I.random_vector(L.n, 77) * scale
         x[::7] = 0.0
@@ -116,6 +118,24 @@ def test_double_float_value_range(fe, scale, mode):
         xn[np.nonzero(~L.space.boundary)[0][0]] = np.nan
         h.apply_operator(dt(xn), y)
         assert torch.isnan(y).any()
+
+
+def test_paired_float_pair_kernel_matches_per_tet(fe):
+    """The packed two-tets-per-thread kernel evaluates the per-tet kernel's element formula lane by lane (the
+    negations are arranged to be exact), so both give the same contributions; the sums differ only by the
+    order of the atomic additions."""
+    with fe.Hierarchy(12, 0, 2) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=5)
+        h.set_coefficient(dt(kappa))
+        x = dt(I.random_vector(h.n_dofs(), 21))
+        ys = {}
+        for mode in (fe.FE_F64_DOUBLE_FLOAT_TET, fe.FE_F64_DOUBLE_FLOAT_PAIR):
+            h.set_f64_mode(mode)
+            ys[mode] = torch.empty_like(x)
+            h.apply_operator(x, ys[mode])
+        torch.cuda.synchronize()
+        d = (ys[fe.FE_F64_DOUBLE_FLOAT_TET] - ys[fe.FE_F64_DOUBLE_FLOAT_PAIR]).abs().max().item()
+        assert d <= 1e-15 * ys[fe.FE_F64_DOUBLE_FLOAT_TET].abs().max().item()
 
 
 def test_apply_host_pointers_match_device(fe):
