@@ -11,7 +11,7 @@ What it computes, written out from the definitions in the paper:
 * the Poisson problem -div(kappa grad u) = f on the unit cube with homogeneous
   (or given) Dirichlet data on all six faces (Section 2, Eq. 1, and the boundary
   conditions of the paper's Poisson script);
-* its Galerkin discretisation in continuous Lagrange P1/P2 on a tetrahedral
+* its Galerkin discretisation in continuous Lagrange P1/P2/P3 on a tetrahedral
   ``UnitCubeMesh`` (Section 2, the weak form Eq. 4): the global stiffness
   A_ij = int kappa grad(phi_j) . grad(phi_i) dx and mass M_ij = int phi_j phi_i dx
   are ASSEMBLED into CSR matrices (the paper's PETSc path uses assembled AIJ
@@ -51,6 +51,11 @@ P2_EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
 # mesh vertices, then x-, y-, z-edge midpoints, then xy-, xz-, yz-face
 # diagonals, then body diagonals.
 PARITY_CLASSES = ((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1))
+
+# Local P3 node order inside a tet: the 4 vertices, then for each edge (a, b) of
+# ``P2_EDGES`` the node at 2/3 lam_a + 1/3 lam_b and then the one at 1/3 lam_a +
+# 2/3 lam_b, then the centroid of each face, the face opposite vertex 0, 1, 2, 3.
+P3_FACES = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))
 
 _UNIT = np.eye(3, dtype=np.int64)
 
@@ -115,16 +120,17 @@ def dof_count(N, degree):
 def lattice_dof_index(L, N, degree):
     """Global dof number of the lattice points L (m,3) of the (degree*N)-lattice.
 
-    P1: lexicographic (x fastest).  P2: points grouped by the parity class of
-    their lattice coordinates (``PARITY_CLASSES`` order), lexicographic inside
-    a class over the sub-lattice a = (L - parity)/2 of extent N+1-parity.
+    P1 and P3: lexicographic (x fastest) over the (kN+1)^3 lattice.  P2: points
+    grouped by the parity class of their lattice coordinates (``PARITY_CLASSES``
+    order), lexicographic inside a class over the sub-lattice a = (L - parity)/2
+    of extent N+1-parity.
     """
     L = np.asarray(L, dtype=np.int64)
-    if degree == 1:
-        n1 = N + 1
+    if degree in (1, 3):
+        n1 = degree * N + 1
         return L[:, 0] + n1 * (L[:, 1] + n1 * L[:, 2])
     if degree != 2:
-        raise ValueError("degree must be 1 or 2")
+        raise ValueError("degree must be 1, 2 or 3")
     par = L % 2
     code = par[:, 0] + 2 * par[:, 1] + 4 * par[:, 2]
     code_to_class = np.empty(8, dtype=np.int64)
@@ -140,7 +146,11 @@ def lattice_dof_index(L, N, degree):
 
 
 class Space:
-    """Continuous Lagrange P1 or P2 on a ``Mesh`` (``FunctionSpace(mesh, "CG", k)``)."""
+    """Continuous Lagrange P1, P2 or P3 on a ``Mesh`` (``FunctionSpace(mesh, "CG", k)``).
+
+    Every P_k node of a Kuhn tet lies on the kN lattice: a node with barycentrics
+    (i0, i1, i2, i3)/k sits at sum_v i_v * vertex_v on the N lattice, scaled by k.
+    """
 
     def __init__(self, mesh, degree):
         self.mesh = mesh
@@ -150,10 +160,18 @@ class Space:
         vl = mesh.cell_vertex_lattice  # (C,4,3) on the N lattice
         if degree == 1:
             lat = vl
-        else:
+        elif degree == 2:
             v2 = 2 * vl
             edges = np.stack([vl[:, a] + vl[:, b] for a, b in P2_EDGES], axis=1)
             lat = np.concatenate([v2, edges], axis=1)  # (C,10,3) on the 2N lattice
+        elif degree == 3:
+            v3 = 3 * vl
+            edges = np.stack([2 * vl[:, a] + vl[:, b] if near_a else vl[:, a] + 2 * vl[:, b]
+                              for a, b in P2_EDGES for near_a in (True, False)], axis=1)
+            faces = np.stack([vl[:, a] + vl[:, b] + vl[:, c] for a, b, c in P3_FACES], axis=1)
+            lat = np.concatenate([v3, edges, faces], axis=1)  # (C,20,3) on the 3N lattice
+        else:
+            raise ValueError("degree must be 1, 2 or 3")
         self.cell_lattice = lat
         C, nd = lat.shape[:2]
         self.ndof_cell = nd
@@ -188,11 +206,15 @@ def tet_quadrature(n):
 
 
 def ref_basis(degree, xi):
-    """Values (m,nd) and reference gradients (m,nd,3) of the P1/P2 basis at points xi (m,3).
+    """Values (m,nd) and reference gradients (m,nd,3) of the P1/P2/P3 basis at points xi (m,3).
 
     Barycentrics lam = (1-xi-eta-zeta, xi, eta, zeta).  P1: phi_v = lam_v.
     P2: phi_v = lam_v (2 lam_v - 1) for the vertices, phi_ab = 4 lam_a lam_b for
-    the edges in ``P2_EDGES`` order.
+    the edges in ``P2_EDGES`` order.  P3 (node order of ``P3_FACES``' comment):
+    phi_v = lam_v (3 lam_v - 1)(3 lam_v - 2) / 2, the edge node nearer a
+    phi = 9/2 lam_a lam_b (3 lam_a - 1), the face node of (a, b, c)
+    phi = 27 lam_a lam_b lam_c: each is the cubic that is 1 at its node and 0 at
+    the other 19 (it vanishes on the planes lam = 0, 1/3, 2/3 through them).
     """
     xi = np.atleast_2d(xi)
     m = xi.shape[0]
@@ -200,6 +222,25 @@ def ref_basis(degree, xi):
     dlam = np.array([[-1.0, -1.0, -1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
     if degree == 1:
         return lam, np.broadcast_to(dlam, (m, 4, 3)).copy()
+    if degree == 3:
+        phi = np.empty((m, 20))
+        dphi = np.empty((m, 20, 3))
+        for v in range(4):
+            L = lam[:, v]
+            phi[:, v] = 0.5 * L * (3 * L - 1) * (3 * L - 2)
+            dphi[:, v] = (0.5 * (27 * L * L - 18 * L + 2))[:, None] * dlam[v]
+        for e, (a, b) in enumerate(P2_EDGES):
+            for h, (p, q) in enumerate(((a, b), (b, a))):  # node nearer p
+                Lp, Lq = lam[:, p], lam[:, q]
+                phi[:, 4 + 2 * e + h] = 4.5 * Lp * Lq * (3 * Lp - 1)
+                dphi[:, 4 + 2 * e + h] = 4.5 * ((Lq * (6 * Lp - 1))[:, None] * dlam[p]
+                                               + (Lp * (3 * Lp - 1))[:, None] * dlam[q])
+        for f, (a, b, c) in enumerate(P3_FACES):
+            La, Lb, Lc = lam[:, a], lam[:, b], lam[:, c]
+            phi[:, 16 + f] = 27 * La * Lb * Lc
+            dphi[:, 16 + f] = 27 * ((Lb * Lc)[:, None] * dlam[a] + (La * Lc)[:, None] * dlam[b]
+                                    + (La * Lb)[:, None] * dlam[c])
+        return phi, dphi
     phi = np.empty((m, 10))
     dphi = np.empty((m, 10, 3))
     for v in range(4):
@@ -212,12 +253,13 @@ def ref_basis(degree, xi):
 
 
 # ------------------------------------------------------- element matrices ---
-def element_stiffness(mesh, degree, kappa=None, sel=slice(None), nq=3):
+def element_stiffness(mesh, degree, kappa=None, sel=slice(None), nq=None):
     """A_K[i,j] = kappa_K * sum_q w_q |det J| (J^-T grad phi_j) . (J^-T grad phi_i).
 
-    The n=3 conical rule is exact for the degree-2 P2 integrand.
+    The integrand has degree 2(k-1); the n=3 conical rule (exact to degree 3)
+    covers P1/P2, n=4 (exact to degree 5) P3.
     """
-    xi, w = tet_quadrature(nq)
+    xi, w = tet_quadrature(nq if nq is not None else max(3, degree + 1))
     _, dphi = ref_basis(degree, xi)
     J = mesh.jacobians(sel)
     det = np.linalg.det(J)
@@ -229,9 +271,10 @@ def element_stiffness(mesh, degree, kappa=None, sel=slice(None), nq=3):
     return A
 
 
-def element_mass(mesh, degree, sel=slice(None), nq=4):
-    """M_K[i,j] = sum_q w_q |det J| phi_i phi_j (the n=4 rule is exact for P2 x P2)."""
-    xi, w = tet_quadrature(nq)
+def element_mass(mesh, degree, sel=slice(None), nq=None):
+    """M_K[i,j] = sum_q w_q |det J| phi_i phi_j (degree 2k: the n=4 rule, exact to
+    degree 5, for P1/P2; n=5, exact to degree 7, for P3)."""
+    xi, w = tet_quadrature(nq if nq is not None else max(4, degree + 2))
     phi, _ = ref_basis(degree, xi)
     det = np.abs(np.linalg.det(mesh.jacobians(sel)))
     ref = np.einsum("q,qd,qe->de", w, phi, phi)

@@ -38,7 +38,7 @@ def test_volumes_and_orientation(N):
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4])
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_unique_dofs_match_lattice_count(N, k):
     s = O.Space(O.Mesh(N), k)
     assert np.unique(s.cell_dofs).size == (k * N + 1) ** 3 == s.n
@@ -84,11 +84,16 @@ def test_quadrature_exact_on_monomials(n):
                 assert abs(got - exact) < 1e-15, (a, b, c)
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_basis_is_nodal_and_partition_of_unity(k):
     nodes = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
     if k == 2:
         nodes = np.concatenate([nodes, [(nodes[a] + nodes[b]) / 2 for a, b in O.P2_EDGES]])
+    if k == 3:  # edge nodes at 1/3 and 2/3 (nearer a first), then the face centroids
+        edge = [(2 * nodes[a] + nodes[b]) / 3 if h == 0 else (nodes[a] + 2 * nodes[b]) / 3
+                for a, b in O.P2_EDGES for h in (0, 1)]
+        face = [(nodes[a] + nodes[b] + nodes[c]) / 3 for a, b, c in O.P3_FACES]
+        nodes = np.concatenate([nodes, edge, face])
     phi, dphi = O.ref_basis(k, nodes)
     assert np.allclose(phi, np.eye(len(nodes)), atol=1e-15)
     pts = np.random.default_rng(0).dirichlet(np.ones(4), 50)[:, 1:]
@@ -102,3 +107,18 @@ def test_basis_is_nodal_and_partition_of_unity(k):
         e[a] = h
         fd = (O.ref_basis(k, pts + e)[0] - O.ref_basis(k, pts - e)[0]) / (2 * h)
         assert np.allclose(fd, dphi[:, :, a], atol=1e-8)
+
+
+def test_p3_nodes_on_the_3n_lattice():
+    """P3 (the paper's degree): vertex dofs sit at the mesh vertices, edge dofs at the thirds of the edges
+    (nearer the first vertex first), face dofs at the face centroids."""
+    m = O.Mesh(2)
+    s = O.Space(m, 3)
+    assert s.ndof_cell == 20
+    P = m.coords[m.cells]  # (C,4,3)
+    assert np.allclose(s.coords[s.cell_dofs[:, :4]], P)
+    for e, (a, b) in enumerate(O.P2_EDGES):
+        assert np.allclose(s.coords[s.cell_dofs[:, 4 + 2 * e]], (2 * P[:, a] + P[:, b]) / 3)
+        assert np.allclose(s.coords[s.cell_dofs[:, 5 + 2 * e]], (P[:, a] + 2 * P[:, b]) / 3)
+    for f, (a, b, c) in enumerate(O.P3_FACES):
+        assert np.allclose(s.coords[s.cell_dofs[:, 16 + f]], (P[:, a] + P[:, b] + P[:, c]) / 3)

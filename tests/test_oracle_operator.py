@@ -19,13 +19,20 @@ def _perm_local_dofs(k, pi):
     if k == 1:
         return list(pi)
     out = list(pi)
+    if k == 2:
+        for a, b in O.P2_EDGES:
+            pa, pb = sorted((pi[a], pi[b]))
+            out.append(4 + O.P2_EDGES.index((pa, pb)))
+        return out
     for a, b in O.P2_EDGES:
-        pa, pb = sorted((pi[a], pi[b]))
-        out.append(4 + O.P2_EDGES.index((pa, pb)))
+        for near in (a, b):  # P3: the node nearer `near` on edge (a, b)
+            pa, pb = sorted((pi[a], pi[b]))
+            out.append(4 + 2 * O.P2_EDGES.index((pa, pb)) + (0 if pi[near] == pa else 1))
+    out += [16 + pi[f] for f in range(4)]  # face f is the face opposite vertex f
     return out
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_element_stiffness_invariants(k):
     m = O.Mesh(2)
     kap = I.grf_kappa(m.centroids(), seed=3)
@@ -79,7 +86,7 @@ def test_p1_jacobi_spectrum_closed_form():
     assert abs(O.estimate_lambda_max(L.A, L.diag, 30) - (1 + np.cos(np.pi * h))) < 1e-8
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_global_matrix_invariants(k):
     L = O.Level(3, k, I.grf_kappa(O.Mesh(3).centroids()))
     A = L.A_free
@@ -92,7 +99,7 @@ def test_global_matrix_invariants(k):
     assert np.abs(Abc[bd][:, ~bd]).max() == 0
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_mass_matrix(k):
     L = O.Level(3, k)
     M = L.M
@@ -105,7 +112,7 @@ def test_mass_matrix(k):
     assert abs(M - M.T).max() < 1e-16
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_apply_rows_matches_assembled(k):
     L = O.Level(4, k, I.grf_kappa(O.Mesh(4).centroids()))
     x = I.random_vector(L.n, 5)
@@ -113,7 +120,7 @@ def test_apply_rows_matches_assembled(k):
     assert np.allclose(O.apply_rows(L.space, L.kappa, x, rows), (L.A @ x)[rows], atol=1e-14)
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_apply_rows_mass_matches_assembled(k):
     L = O.Level(4, k)
     x = I.random_vector(L.n, 6)
@@ -121,26 +128,30 @@ def test_apply_rows_mass_matches_assembled(k):
     assert np.allclose(O.apply_rows_mass(L.space, x, rows), (L.M @ x)[rows], atol=1e-15)
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_prolongation_reproduces_polynomials(k):
     c, f = O.Level(2, k), O.Level(4, k)
     P = O.prolongation(c, f)
     assert np.allclose(P @ np.ones(c.n), 1.0, atol=1e-15)
     rng = np.random.default_rng(0)
     for _ in range(3):
-        a = rng.normal(size=10)
+        a = rng.normal(size=20)
 
         def p(X):
             x, y, z = X[:, 0], X[:, 1], X[:, 2]
             val = a[0] + a[1] * x + a[2] * y + a[3] * z
-            if k == 2:
+            if k >= 2:
                 val = val + a[4] * x * x + a[5] * y * y + a[6] * z * z + a[7] * x * y + a[8] * x * z + a[9] * y * z
+            if k >= 3:
+                val = val + (a[10] * x ** 3 + a[11] * y ** 3 + a[12] * z ** 3 + a[13] * x * x * y + a[14] * x * x * z
+                             + a[15] * y * y * x + a[16] * y * y * z + a[17] * z * z * x + a[18] * z * z * y
+                             + a[19] * x * y * z)
             return val
 
         assert np.allclose(P @ p(c.space.coords), p(f.space.coords), atol=1e-13)
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_galerkin_identity(k):
     c, f = O.Level(2, k), O.Level(4, k)
     P = O.prolongation(c, f)
@@ -188,3 +199,20 @@ def test_quadrature_load_vector_converges():
         b = O.load_vector_quadrature(L, I.sin_product_rhs(O.quadrature_points(L.space.mesh).reshape(-1, 3)).reshape(-1, 27))
         errs.append(O.l2_error(L.space, O.direct_solve(L, b), I.sin_product))
     assert 2.6 <= np.log2(errs[0] / errs[1]) <= 3.4, errs
+
+
+def test_p3_energies_of_polynomials():
+    """P3 stiffness and mass reproduce exact integrals of polynomials in the space (unit cube, kappa = 1):
+    |grad x^3|^2 -> 9/5, |grad (x^2 y)|^2 -> 4/9 + 1/5, (x^3)^2 -> 1/7, x^3 * 1 -> 1/4, (xyz)^2 -> 1/27."""
+    L = O.Level(2, 3)
+    X = L.space.coords
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    A, M = L.A_free, L.M
+    u = x ** 3
+    assert abs(u @ (A @ u) - 9 / 5) < 1e-12
+    v = x * x * y  # grad = (2xy, x^2, 0): int 4 x^2 y^2 + x^4 = 4/9 + 1/5
+    assert abs(v @ (A @ v) - (4 / 9 + 1 / 5)) < 1e-12
+    assert abs(u @ (M @ u) - 1 / 7) < 1e-13
+    assert abs(np.ones(L.n) @ (M @ u) - 1 / 4) < 1e-13
+    w = x * y * z
+    assert abs(w @ (M @ w) - 1 / 27) < 1e-13

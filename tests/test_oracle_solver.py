@@ -9,7 +9,7 @@ from oracle import fe_oracle as O
 import fe_inputs as I
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 @pytest.mark.parametrize("N", [2, 4])
 def test_brute_force_dense_solve(k, N):
     h = O.Hierarchy(max(1, N // 2), 1, k)
@@ -21,15 +21,19 @@ def test_brute_force_dense_solve(k, N):
         assert np.linalg.norm(u - dense) <= 1e-12 * np.linalg.norm(dense)
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_patch_test_exact(k):
-    """Linear (P1) / quadratic (P2) solutions with matching Dirichlet data are nodally exact."""
+    """Linear (P1) / quadratic (P2) / cubic (P3) solutions with matching Dirichlet data are nodally exact."""
     h = O.Hierarchy(2, 1, k)
     L = h.fine
     X = L.space.coords
     if k == 1:
         u = 1 + 2 * X[:, 0] - 3 * X[:, 1] + 0.5 * X[:, 2]
         f = np.zeros(L.n)
+    elif k == 3:
+        x, y, z = X[:, 0], X[:, 1], X[:, 2]
+        u = x ** 3 - 2 * y * y * z + x * y * z + 0.5 * z ** 3 - x * x + 1
+        f = -(6 * x - 4 * z + 3 * z - 2)  # -Laplace(u), linear: its P3 interpolant is exact
     else:
         u = X[:, 0] ** 2 + 2 * X[:, 1] ** 2 - X[:, 2] ** 2 + X[:, 0] * X[:, 1] - X[:, 1] * X[:, 2] + 3 * X[:, 0]
         f = np.full(L.n, -4.0)  # -Laplace(u)
@@ -38,7 +42,7 @@ def test_patch_test_exact(k):
     assert np.abs(uh - u).max() < 1e-12
 
 
-@pytest.mark.parametrize("k,Ns,order", [(1, (8, 16), 2.0), (2, (8, 16), 3.0)])
+@pytest.mark.parametrize("k,Ns,order", [(1, (8, 16), 2.0), (2, (8, 16), 3.0), (3, (4, 8), 4.0)])
 def test_convergence_rates(k, Ns, order):
     errs = []
     for N in Ns:
