@@ -150,10 +150,17 @@ long long fe_kernel_launches(void);
 int fe_mesh_create(int nx, int ny, int nz, fe_mesh** out);
 void fe_mesh_destroy(fe_mesh* mesh);
 
-/* Refine `coarse` uniformly `nrefine` times (0..8) and build the degree-1 or
- * degree-2 Lagrange space on every level, uploading the levels to the current
- * CUDA device.  Level 0 is the coarse mesh, level nrefine the finest.  The
- * coefficient is kappa = 1 until fe_set_coefficient() is called. */
+/* Refine `coarse` uniformly `nrefine` times (0..8) and build the degree-1, 2
+ * or 3 Lagrange space on every level (Sec. 2; degree 3 is the paper's),
+ * uploading the levels to the current CUDA device; other degrees give
+ * FE_ERR_UNSUPPORTED.  Level 0 is the coarse mesh, level nrefine the finest.
+ * The coefficient is kappa = 1 until fe_set_coefficient() is called.
+ * Degree 3 (20 dofs per tet, dofs numbered lexicographically on the 3N
+ * lattice): the operator applies its element matrix, formed per tet from the
+ * six geometric factors and reference coefficients, in FP64 FMAs (every
+ * fe_set_f64_mode setting) or FP32; the bf16 tensor-core operator, the
+ * quadrature load vector (FE_RHS_QUAD_F) and the batched solver are P1/P2
+ * only and return FE_ERR_UNSUPPORTED for a degree-3 hierarchy. */
 int fe_hierarchy_refine(const fe_mesh* coarse, int nrefine, int degree, fe_hierarchy** out);
 void fe_hierarchy_destroy(fe_hierarchy* h);
 

@@ -49,11 +49,11 @@ Numbering make_numbering(int N, int deg) {
   nb.N = N;
   nb.deg = deg;
   nb.m = deg * N;
-  if (deg == 1) {
-    const int n = (N + 1) * (N + 1) * (N + 1);
+  if (deg != 2) {  // P1, P3: one lexicographic class over the (kN+1)^3 lattice
+    const int n1 = deg * N + 1, n = n1 * n1 * n1;
     nb.off[0] = 0;
     for (int k = 1; k < 9; ++k) nb.off[k] = n;
-    for (int k = 0; k < 8; ++k) nb.sx[k] = nb.sy[k] = nb.sz[k] = N + 1;
+    for (int k = 0; k < 8; ++k) nb.sx[k] = nb.sy[k] = nb.sz[k] = n1;
     return nb;
   }
   int acc = 0;
@@ -117,13 +117,13 @@ static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 // lexicographically, P2 numbers each parity class lexicographically by
 // halved coordinates, and for k = 2 the class of k X + o is that of o.  The
 // entry stores (dof at X = Y = Z = 0, y stride, z stride, o packed as three
-// bytes biased by 8); the x stride is k for P1 and 1 for P2.
+// bytes biased by 8); the x stride is k for P1/P3 and 1 for P2.
 static int4 entry_index(const Numbering& num, int k, int ox, int oy, int oz) {
   FE_REQUIRE(ox >= -8 && ox < 8 && oy >= -8 && oy < 8 && oz >= -8 && oz < 8, FE_ERR_UNSUPPORTED,
              "transfer offset out of the packed range");
   const int packed = (ox + 8) | ((oy + 8) << 8) | ((oz + 8) << 16);
-  if (num.deg == 1) {
-    const int n1 = num.N + 1;
+  if (num.deg != 2) {  // lexicographic (P1, P3): x stride k
+    const int n1 = num.m + 1;
     return make_int4(ox + n1 * (oy + n1 * oz), k * n1, k * n1 * n1, packed);
   }
   FE_REQUIRE(k == 2, FE_ERR_UNSUPPORTED, "P2 transfer base points sit on even lattice coordinates");
@@ -142,7 +142,7 @@ static void build_level_transfer_index(Level& F, const Level& Cc, const Transfer
   }
   for (size_t e = 0; e < p.size(); ++e) {
     const int4 o = t.h_pro_off[e];  // coarse point DEG c + o of level Cc
-    p[e] = entry_index(Cc.num, F.deg == 1 ? 1 : 2, o.x, o.y, o.z);
+    p[e] = entry_index(Cc.num, F.deg, o.x, o.y, o.z);
   }
   // the affine forms against the numbering itself, at base points near both
   // ends of each axis (host only, once per hierarchy)
@@ -158,8 +158,8 @@ static void build_level_transfer_index(Level& F, const Level& Cc, const Transfer
                    "transfer index table disagrees with the numbering");
       }
   };
-  check(F.num, 2, t.h_res_off, r, F.deg == 1 ? 2 : 1, Cc.num.m);
-  check(Cc.num, F.deg == 1 ? 1 : 2, t.h_pro_off, p, 1, Cc.num.N);
+  check(F.num, 2, t.h_res_off, r, F.deg == 2 ? 1 : 2, Cc.num.m);
+  check(Cc.num, F.deg, t.h_pro_off, p, F.deg == 3 ? 3 : 1, Cc.num.N);
   F.rtab.alloc(r.size());
   CUDA_CHECK(cudaMemcpy(F.rtab, r.data(), sizeof(int4) * r.size(), cudaMemcpyHostToDevice));
   F.ptab.alloc(p.size());
@@ -200,6 +200,29 @@ static void build_transfer_tables(TransferTables& t, int deg) {
         };
         if (deg == 1) {
           for (int i = 0; i < 4; ++i) push(v[i], lam[i]);
+        } else if (deg == 3) {
+          // barycentrics l/6 with integer l: the P3 basis values are l-polynomials over
+          // powers of two (vertex l(l-2)(l-4)/48, edge l_p l_q (l_p - 2)/16, face
+          // l_a l_b l_c / 8), so the weights and their zeros are exact
+          int sv[3] = {o[0], o[1], o[2]};
+          std::sort(sv, sv + 3, [](int a, int b) { return a > b; });
+          const int l[4] = {K2 - sv[0], sv[0] - sv[1], sv[1] - sv[2], sv[2]};
+          for (int i = 0; i < 4; ++i) {
+            const int d[3] = {3 * v[i][0], 3 * v[i][1], 3 * v[i][2]};
+            push(d, (double)(l[i] * (l[i] - 2) * (l[i] - 4)) / 48.0);
+          }
+          for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+              for (int h = 0; h < 2; ++h) {
+                const int pp = h ? b : a, q = h ? a : b;
+                const int d[3] = {2 * v[pp][0] + v[q][0], 2 * v[pp][1] + v[q][1], 2 * v[pp][2] + v[q][2]};
+                push(d, (double)(l[pp] * l[q] * (l[pp] - 2)) / 16.0);
+              }
+          for (int f = 0; f < 4; ++f) {
+            const int a = p3_face_vertex(f, 0), b = p3_face_vertex(f, 1), c = p3_face_vertex(f, 2);
+            const int d[3] = {v[a][0] + v[b][0] + v[c][0], v[a][1] + v[b][1] + v[c][1], v[a][2] + v[b][2] + v[c][2]};
+            push(d, (double)(l[a] * l[b] * l[c]) / 8.0);
+          }
         } else {
           for (int i = 0; i < 4; ++i) {
             const int d[3] = {2 * v[i][0], 2 * v[i][1], 2 * v[i][2]};
@@ -214,17 +237,16 @@ static void build_transfer_tables(TransferTables& t, int deg) {
         t.h_pro_start.push_back((int)t.h_pro_off.size());
       }
   // Restriction: coarse point Lc receives w * r_f(2 Lc + o - 2 d) from every
-  // entry (o, d, w) with d = Lc (mod k); classes indexed by the parity code of Lc.
-  t.n_res_class = deg == 2 ? 8 : 1;
+  // entry (o, d, w) with d = Lc (mod k); classes indexed by the code
+  // (Lc_x mod k) + k (Lc_y mod k) + k^2 (Lc_z mod k).
+  t.n_res_class = deg * deg * deg;
   t.h_res_start.assign(1, 0);
   t.h_res_off.clear();
   t.h_res_w.clear();
   for (int cls = 0; cls < t.n_res_class; ++cls) {
     for (const Ent& e : all) {
-      if (deg == 2) {
-        const int code = (e.d[0] & 1) | ((e.d[1] & 1) << 1) | ((e.d[2] & 1) << 2);
-        if (code != cls) continue;
-      }
+      const int code = (e.d[0] % deg) + deg * ((e.d[1] % deg) + deg * (e.d[2] % deg));
+      if (code != cls) continue;
       t.h_res_off.push_back(make_int4(e.o[0] - 2 * e.d[0], e.o[1] - 2 * e.d[1], e.o[2] - 2 * e.d[2], 0));
       t.h_res_w.push_back(e.w);
     }
@@ -235,9 +257,9 @@ static void build_transfer_tables(TransferTables& t, int deg) {
   int omax = 0;
   for (const int4& o : t.h_res_off) omax = std::max({omax, std::abs(o.x), std::abs(o.y), std::abs(o.z)});
   t.res_margin = (omax + 1) / 2;
-  // the prolongation kernel unrolls at most 2 (P1) or 10 (P2) entries per fine point
+  // the prolongation kernel unrolls at most 2 (P1), 10 (P2) or 20 (P3) entries per fine point
   for (int c = 0; c < t.n_pro_class; ++c)
-    FE_REQUIRE(t.h_pro_start[c + 1] - t.h_pro_start[c] <= (deg == 1 ? 2 : 10), FE_ERR_UNSUPPORTED,
+    FE_REQUIRE(t.h_pro_start[c + 1] - t.h_pro_start[c] <= (deg == 1 ? 2 : tet_ndof(deg)), FE_ERR_UNSUPPORTED,
                "prolongation stencil longer than the kernel's bound");
   auto up = [](auto& dbuf, const auto& vec) {
     using T = typename std::decay_t<decltype(vec)>::value_type;
@@ -379,7 +401,7 @@ template <> const float* lv_dinv<float>(const Level& L) { return L.dinv32; }
 // Consistent mass y = M x in FP64: float-pair arithmetic unless the hierarchy
 // is in native-FP64 mode (the operator's mode decides both).
 static void mass_enqueue(const fe_hierarchy* h, const Level& L, const double* x, double* y, cudaStream_t s) {
-  if (h->f64_mode == FE_F64_NATIVE)
+  if (h->f64_mode == FE_F64_NATIVE || L.deg == 3)
     launch_mass(L, x, y, s);
   else
     launch_mass_df(L, x, y, s);
@@ -387,6 +409,16 @@ static void mass_enqueue(const fe_hierarchy* h, const Level& L, const double* x,
 
 void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s) {
   const Level& L = h->L[level];
+  if (L.deg == 3) {  // P3: reference-matrix kernel, one tet per thread, FP64 FMAs or FP32
+    FE_REQUIRE(dtype != FE_BF16, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
+    if (dtype == FE_F64)
+      launch_apply64(L, (const double*)x, (double*)y, s);
+    else if (dtype == FE_F32)
+      launch_apply32(L, (const float*)x, (float*)y, s);
+    else
+      FE_FAIL(FE_ERR_ARG, "unknown dtype");
+    return;
+  }
   // measured on GB300 (P*64^3): P1 per cube 0.025 ms vs per tet 0.041 ms; P2 per tet 0.139 ms vs per cube
   // 0.209 ms (the P2 cube kernel needs 254 registers, i.e. 8 warps per SM)
   const bool cube = h->f64_mode == FE_F64_DOUBLE_FLOAT_CUBE || (h->f64_mode == FE_F64_DOUBLE_FLOAT && L.deg == 1);
@@ -414,7 +446,7 @@ template <typename T>
 static void apply_cheb_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d, double c1, double c2,
                                bool store_d, int dtype, cudaStream_t s) {
   Level& L = h->L[l];
-  if (h->fuse_smoother && L.cnt_tet.p) {
+  if (h->fuse_smoother && L.cnt_tet.p && L.deg <= 2) {
     const bool cube = h->f64_mode == FE_F64_DOUBLE_FLOAT_CUBE || (h->f64_mode == FE_F64_DOUBLE_FLOAT && L.deg == 1);
     if constexpr (sizeof(T) == 8) {
       if (dtype == FE_F64 && h->f64_mode != FE_F64_NATIVE) {
@@ -940,6 +972,7 @@ static const double* rhs_to_load(fe_hierarchy* h, const double* rhs, int kind, c
   Level& F = h->L[h->nlev - 1];
   const double* rd = stage_in<double>(h, 1, rhs, kind == FE_RHS_QUAD_F ? (size_t)F.C * FE_QUAD_POINTS : F.n, s);
   if (kind == FE_RHS_QUAD_F) {
+    FE_REQUIRE(F.deg <= 2, FE_ERR_UNSUPPORTED, "the quadrature load vector is tabulated for P1/P2");
     launch_load_quadrature(F, rd, h->b, s);
     launch_zero_boundary64(F, h->b, s);
   } else if (kind == FE_RHS_LOAD) {
@@ -976,7 +1009,7 @@ static fe_solver_opts resolve_opts(const fe_solver_opts* o) {
 fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
   FE_REQUIRE(N0 >= 1, FE_ERR_ARG, "mesh size must be >= 1");
   FE_REQUIRE(nrefine >= 0 && nrefine <= 8, FE_ERR_ARG, "nrefine must be in [0, 8]");
-  FE_REQUIRE(degree == 1 || degree == 2, FE_ERR_UNSUPPORTED, "degree must be 1 or 2");
+  FE_REQUIRE(degree >= 1 && degree <= 3, FE_ERR_UNSUPPORTED, "degree must be 1, 2 or 3");
   const long long Nf = (long long)N0 << nrefine;
   const long long nf = (long long)(degree * Nf + 1) * (degree * Nf + 1) * (degree * Nf + 1);
   FE_REQUIRE(6 * Nf * Nf * Nf < (1ll << 31) && nf < (1ll << 31), FE_ERR_ARG, "finest level too large for 32-bit indices");
@@ -996,7 +1029,7 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     Level& L = h->L[l];
     L.N = N0 << l;
     L.deg = degree;
-    L.nd = degree == 1 ? 4 : 10;
+    L.nd = tet_ndof(degree);
     L.num = make_numbering(L.N, degree);
     const int m = degree * L.N;
     L.n = (m + 1) * (m + 1) * (m + 1);
@@ -1008,9 +1041,11 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     L.cmap.alloc((size_t)(degree + 1) * (degree + 1) * (degree + 1) * L.Qs);
     L.map.alloc((size_t)L.nd * L.Cs);
     CUDA_CHECK(cudaMemset(L.map, 0, sizeof(int) * (size_t)L.nd * L.Cs));
-    L.vx.alloc(L.V);
-    L.vy.alloc(L.V);
-    L.vz.alloc(L.V);
+    // P3 vertex dofs are not numbered first: coordinates of every dof instead
+    const int ncoord = degree == 3 ? L.n : L.V;
+    L.vx.alloc(ncoord);
+    L.vy.alloc(ncoord);
+    L.vz.alloc(ncoord);
     L.detj.alloc(L.C);
     L.kappa.alloc(L.C);
     L.geo64.alloc((size_t)6 * L.Cs);
@@ -1198,6 +1233,7 @@ int fe_apply_operator(const fe_hierarchy* hc, int level, const void* x, void* y,
   FE_REQUIRE(x && y && x != y, FE_ERR_ARG, "x and y must be distinct non-null vectors");
   FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32 || dtype == FE_BF16, FE_ERR_ARG, "unknown dtype");
   if (dtype == FE_BF16) FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
+  if (dtype == FE_BF16) FE_REQUIRE(hc->deg <= 2, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
   fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
   const Level& L = h->L[level];
   cudaStream_t s = as_stream(stream);
@@ -1313,6 +1349,7 @@ int fe_smooth(const fe_hierarchy* hc, int level, const void* b, void* x, int ste
   FE_REQUIRE(b && x && steps >= 1 && hi > lo && lo > 0, FE_ERR_ARG, "invalid smoother arguments");
   FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32 || dtype == FE_BF16, FE_ERR_ARG, "unknown dtype");
   if (dtype == FE_BF16) FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
+  if (dtype == FE_BF16) FE_REQUIRE(hc->deg <= 2, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
   fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
   Level& L = h->L[level];
   cudaStream_t s = as_stream(stream);
@@ -1352,6 +1389,7 @@ int fe_vcycle(const fe_hierarchy* hc, const void* b, void* x, int dtype, void* s
   FE_REQUIRE(b && x, FE_ERR_ARG, "null vector");
   FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32 || dtype == FE_BF16, FE_ERR_ARG, "unknown dtype");
   if (dtype == FE_BF16) FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
+  if (dtype == FE_BF16) FE_REQUIRE(hc->deg <= 2, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
   fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
   Level& F = h->L[h->nlev - 1];
   cudaStream_t s = as_stream(stream);
@@ -1411,8 +1449,10 @@ int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_
   FE_REQUIRE(h && rhs && u, FE_ERR_ARG, "null argument");
   const fe_solver_opts o = resolve_opts(opts);
   FE_REQUIRE(o.precision == FE_PREC_F64 || o.precond == FE_PC_GMG, FE_ERR_ARG, "mixed precision needs the GMG preconditioner");
-  if (o.precision == FE_PREC_MIXED_BF16)
+  if (o.precision == FE_PREC_MIXED_BF16) {
     FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
+    FE_REQUIRE(h->deg <= 2, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
+  }
   FE_REQUIRE(o.precision == FE_PREC_F64 || h->nlev > 1, FE_ERR_ARG, "mixed precision needs at least 2 levels");
   cudaStream_t s = as_stream(stream);
   const Level& F = h->L[h->nlev - 1];

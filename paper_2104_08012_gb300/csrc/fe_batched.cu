@@ -762,6 +762,7 @@ int fe_batch_create(int nprob, const int* N0, const int* nrefine, const int* deg
     for (int p = 0; p < nprob; ++p) {
       FE_REQUIRE(nrefine[p] >= 1 && nrefine[p] + 1 <= kMaxLev, FE_ERR_ARG, "each problem needs 2..6 levels");
       FE_REQUIRE(p == 0 || nrefine[p] == nrefine[0], FE_ERR_UNSUPPORTED, "all problems of a batch need the same level count");
+      FE_REQUIRE(degree[p] == 1 || degree[p] == 2, FE_ERR_UNSUPPORTED, "the batched solver is for P1/P2");
       B->hs.push_back(hierarchy_create(N0[p], nrefine[p], degree[p]));
     }
     B->nlev = nrefine[0] + 1;

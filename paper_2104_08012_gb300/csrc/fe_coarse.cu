@@ -278,11 +278,15 @@ void coarse_setup(fe_hierarchy* h, cudaStream_t s) {
   }
   const size_t nn = (size_t)nci * nci;
   CUDA_CHECK(cudaMemsetAsync(cs.A, 0, sizeof(double) * nn, s));
-  if (L0.deg == 1)
+  if (L0.deg == 1) {
     k_coarse_assemble<1><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci, cs.A);
-  else
+    LAUNCH_CHECK();
+  } else if (L0.deg == 2) {
     k_coarse_assemble<2><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci, cs.A);
-  LAUNCH_CHECK();
+    LAUNCH_CHECK();
+  } else {
+    launch_coarse_assemble_p3(L0, cs.dof2int, nci, cs.A, s);
+  }
   const int w = cs.band;
   for (int j = 0; j + 1 < nci; ++j) {
     const int wl = std::min(w, nci - 1 - j);

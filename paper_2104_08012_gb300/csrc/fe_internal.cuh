@@ -95,7 +95,7 @@ __host__ __device__ inline int class_parity_y(int c) { return (c == 2 || c == 4 
 __host__ __device__ inline int class_parity_z(int c) { return (c == 3 || c == 5 || c == 6 || c == 7) ? 1 : 0; }
 
 __host__ __device__ inline int lattice_to_dof(const Numbering& nb, int x, int y, int z) {
-  if (nb.deg == 1) return x + (nb.N + 1) * (y + (nb.N + 1) * z);
+  if (nb.deg != 2) return x + (nb.m + 1) * (y + (nb.m + 1) * z);  // P1, P3: lexicographic
   const int code = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
   // code (px + 2py + 4pz) -> class index in the order above
   const int c = (code == 3) ? 4 : (code == 4) ? 3 : code;
@@ -103,8 +103,8 @@ __host__ __device__ inline int lattice_to_dof(const Numbering& nb, int x, int y,
 }
 
 __host__ __device__ inline void dof_to_lattice(const Numbering& nb, int i, int& x, int& y, int& z) {
-  if (nb.deg == 1) {
-    const int n1 = nb.N + 1;
+  if (nb.deg != 2) {
+    const int n1 = nb.m + 1;
     x = i % n1;
     const int r = i / n1;
     y = r % n1;
@@ -323,6 +323,7 @@ void launch_apply_cheb64_df(const Level& L, const double* b, double* x, double* 
 void launch_apply_cheb64_cube_df(const Level& L, const double* b, double* x, double* y, double* d, double c1,
                                  double c2, bool store_d, cudaStream_t s);
 void launch_build_valence(Level& L, cudaStream_t s);
+void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, double* A, cudaStream_t s);
 void launch_split_geometry(Level& L, cudaStream_t s);
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_mass_df(const Level& L, const double* x, double* y, cudaStream_t s);
@@ -492,12 +493,26 @@ __host__ __device__ inline void p2_element(const T* u, const T* g, T* y) {
   y[9] = four * (b23 + b32);
 }
 
+// P1/P2 element formulas; the P3 element (reference matrices in constant
+// memory) is p3_element in fe_kernels.cu.
 template <int DEG, typename T>
 __host__ __device__ inline void element_apply(const T* u, const T* g, T* y) {
+  static_assert(DEG == 1 || DEG == 2, "P3 uses p3_element (fe_kernels.cu)");
   if constexpr (DEG == 1)
     p1_element<T>(u, g, y);
   else
     p2_element<T>(u, g, y);
+}
+
+// Dofs of one tet: 4 (P1), 10 (P2), 20 (P3).
+__host__ __device__ constexpr int tet_ndof(int deg) { return deg == 1 ? 4 : deg == 2 ? 10 : 20; }
+
+// P3 local dofs: vertices 0..3; edge e = (a, b), a < b, in the P2 edge order
+// (p2_edge - 4) holds node 4 + 2e, the one nearer a (lattice 2 v_a + v_b), and
+// node 4 + 2e + 1 (v_a + 2 v_b); the face opposite vertex f holds node 16 + f
+// (the sum of its three vertices).
+__host__ __device__ constexpr int p3_face_vertex(int f, int k) {  // k-th vertex of the face opposite f
+  return k + (k >= f ? 1 : 0);
 }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -2,12 +2,21 @@
 // mass, diagonal, adjoint cell gradient, mesh construction, and the
 // multigrid transfer and smoother vector kernels (paper Section 3).
 #include <cmath>
+#include <type_traits>
 
 #include "fe_internal.cuh"
 
-// Reference P1/P2 mass matrices int_ref phi_i phi_j, filled by fe_api.cu.
+// Reference P1/P2/P3 mass matrices int_ref phi_i phi_j, filled by fe_api.cu.
 __constant__ double c_mref1[16];
 __constant__ double c_mref2[100];
+__constant__ double c_mref3[400];
+// P3 reference stiffness: for the symmetric pairs p = (i <= j) of the 20
+// local dofs (row-major packed upper triangle), the coefficients of the six
+// components (00, 01, 02, 11, 12, 22) of G = |det J| J^-1 J^-T:
+// A_K[i][j] = kappa_K sum_k G_k c_K3[p][k], with c_K3[p][k] = int_ref
+// d_a phi_i d_b phi_j (+ d_b phi_i d_a phi_j for a != b).
+__constant__ double c_K3[210][6];
+__constant__ float c_K3f[210][6];
 // Quadrature rule of the load vector (conical-product Gauss, 3 points per
 // direction, FE_QUAD_POINTS = 27 per tet): reference points, weights, basis values.
 __constant__ double c_qxi[FE_QUAD_POINTS][3];
@@ -23,6 +32,52 @@ __device__ __forceinline__ int decode(int m, bool& bd) {
   bd = m < 0;
   return bd ? -1 - m : m;
 }
+
+template <typename T>
+__device__ __forceinline__ T k3(int p, int k);
+template <>
+__device__ __forceinline__ double k3<double>(int p, int k) { return c_K3[p][k]; }
+template <>
+__device__ __forceinline__ float k3<float>(int p, int k) { return c_K3f[p][k]; }
+
+// P3 tet: y = A_K u over the 210 symmetric pairs, each entry formed from the
+// six geometric factors (g = kappa G) and used for both (i, j) and (j, i):
+// 8 FMAs per pair, the reference coefficients read as constant operands.
+template <typename T>
+__device__ __forceinline__ void p3_element(const T* u, const T* g, T* y) {
+#pragma unroll
+  for (int i = 0; i < 20; ++i) y[i] = T(0);
+#pragma unroll
+  for (int i = 0; i < 20; ++i)
+#pragma unroll
+    for (int j = i; j < 20; ++j) {
+      const int p = 20 * i - i * (i - 1) / 2 + (j - i);
+      const T a = g[0] * k3<T>(p, 0) + g[1] * k3<T>(p, 1) + g[2] * k3<T>(p, 2) + g[3] * k3<T>(p, 3) +
+                  g[4] * k3<T>(p, 4) + g[5] * k3<T>(p, 5);
+      y[i] += a * u[j];
+      if (j != i) y[j] += a * u[i];
+    }
+}
+
+// Diagonal entry A_K[i][i] of the P3 element.
+__device__ __forceinline__ double p3_diag_entry(const double* g, int i) {
+  const int p = 20 * i - i * (i - 1) / 2;
+  return g[0] * c_K3[p][0] + g[1] * c_K3[p][1] + g[2] * c_K3[p][2] + g[3] * c_K3[p][3] + g[4] * c_K3[p][4] +
+         g[5] * c_K3[p][5];
+}
+
+template <int DEG, typename T>
+__device__ __forceinline__ void tet_element(const T* u, const T* g, T* y) {
+  if constexpr (DEG == 3)
+    p3_element<T>(u, g, y);
+  else
+    element_apply<DEG, T>(u, g, y);
+}
+
+// Geometric factors are stored as kappa G / w: w = 6 (P1) and 120 (P2) fold
+// the element formulas' reference integrals; P3 keeps them in c_K3 (w = 1).
+template <int DEG>
+__host__ __device__ constexpr double geo_weight() { return DEG == 1 ? 6.0 : DEG == 2 ? 120.0 : 1.0; }
 
 // ------------------------------------------------------ mesh construction
 template <int DEG>
@@ -51,6 +106,22 @@ __global__ void k_build_map(Numbering num, int C, int Cs, int* __restrict__ map)
   if (DEG == 1) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) put(k, v[k][0], v[k][1], v[k][2]);
+  } else if (DEG == 3) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) put(k, 3 * v[k][0], 3 * v[k][1], 3 * v[k][2]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a + 1; b < 4; ++b) {
+        const int e = p2_edge(a, b) - 4;
+        put(4 + 2 * e, 2 * v[a][0] + v[b][0], 2 * v[a][1] + v[b][1], 2 * v[a][2] + v[b][2]);
+        put(5 + 2 * e, v[a][0] + 2 * v[b][0], v[a][1] + 2 * v[b][1], v[a][2] + 2 * v[b][2]);
+      }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int a = p3_face_vertex(f, 0), b = p3_face_vertex(f, 1), d = p3_face_vertex(f, 2);
+      put(16 + f, v[a][0] + v[b][0] + v[d][0], v[a][1] + v[b][1] + v[d][1], v[a][2] + v[b][2] + v[d][2]);
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < 4; ++k) put(k, 2 * v[k][0], 2 * v[k][1], 2 * v[k][2]);
@@ -60,6 +131,20 @@ __global__ void k_build_map(Numbering num, int C, int Cs, int* __restrict__ map)
       for (int b = a + 1; b < 4; ++b)
         put(p2_edge(a, b), v[a][0] + v[b][0], v[a][1] + v[b][1], v[a][2] + v[b][2]);
   }
+}
+
+// P3: coordinates of every lattice point indexed by its dof, so that the map
+// rows of the tet vertices index them as they index the vertices for P1/P2.
+__global__ void k_build_coords_lattice(Numbering num, int n, double* __restrict__ vx, double* __restrict__ vy,
+                                       double* __restrict__ vz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x, y, z;
+  dof_to_lattice(num, i, x, y, z);
+  const double m = (double)num.m;
+  vx[i] = x / m;
+  vy[i] = y / m;
+  vz[i] = z / m;
 }
 
 __global__ void k_build_coords(int N, int V, double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz) {
@@ -91,7 +176,7 @@ __global__ void k_geometry(int C, int Cs, const int* __restrict__ map, const dou
   }
   double g[6], adet;
   tet_metric<double>(p, g, adet);
-  const double s = kappa[c] / (DEG == 1 ? 6.0 : 120.0);
+  const double s = kappa[c] / geo_weight<DEG>();
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
     geo64[(size_t)a * Cs + c] = g[a] * s;
@@ -109,7 +194,7 @@ template <int DEG, typename T>
 __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const int* __restrict__ map,
                                                   const T* __restrict__ geo, const T* __restrict__ x,
                                                   T* __restrict__ y, int nb, const int* __restrict__ bnd) {
-  constexpr int ND = DEG == 1 ? 4 : 10;
+  constexpr int ND = tet_ndof(DEG);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < C) {
     int idx[ND];
@@ -123,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const
 #pragma unroll
     for (int a = 0; a < 6; ++a) g[a] = __ldg(geo + (size_t)a * Cs + t);
     T out[ND];
-    element_apply<DEG, T>(u, g, out);
+    tet_element<DEG, T>(u, g, out);
 #pragma unroll
     for (int j = 0; j < ND; ++j)
       if (idx[j] >= 0) atomicAdd(y + idx[j], out[j]);
@@ -228,7 +313,7 @@ __global__ void k_build_cube_map(Numbering num, int Q, int Qs, int* __restrict__
 template <int DEG>
 __global__ void k_mass(int C, int Cs, const int* __restrict__ map, const double* __restrict__ detj,
                        const double* __restrict__ x, double* __restrict__ y) {
-  constexpr int ND = DEG == 1 ? 4 : 10;
+  constexpr int ND = tet_ndof(DEG);
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   int idx[ND];
@@ -240,7 +325,7 @@ __global__ void k_mass(int C, int Cs, const int* __restrict__ map, const double*
     u[j] = x[idx[j]];
   }
   const double s = detj[c];
-  const double* M = DEG == 1 ? c_mref1 : c_mref2;
+  const double* M = DEG == 1 ? c_mref1 : DEG == 2 ? c_mref2 : c_mref3;
 #pragma unroll
   for (int i = 0; i < ND; ++i) {
     double acc = 0.0;
@@ -299,19 +384,26 @@ __global__ void k_load_quad(int C, int Cs, const int* __restrict__ map, const do
 // ------------------------------------------------------------ diagonal
 template <int DEG>
 __global__ void k_diag(int C, int Cs, const int* __restrict__ map, const double* __restrict__ geo, double* __restrict__ diag) {
-  constexpr int ND = DEG == 1 ? 4 : 10;
+  constexpr int ND = tet_ndof(DEG);
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   double g[6];
 #pragma unroll
   for (int a = 0; a < 6; ++a) g[a] = geo[(size_t)a * Cs + c];
+  if constexpr (DEG == 3) {
+    for (int i = 0; i < ND; ++i) {
+      const int m = map[(size_t)i * Cs + c];
+      if (m >= 0) atomicAdd(diag + m, p3_diag_entry(g, i));
+    }
+    return;
+  }
   for (int i = 0; i < ND; ++i) {
     const int m = map[(size_t)i * Cs + c];
     if (m < 0) continue;
     double u[ND], out[ND];
 #pragma unroll
     for (int j = 0; j < ND; ++j) u[j] = (j == i) ? 1.0 : 0.0;
-    element_apply<DEG, double>(u, g, out);
+    tet_element<DEG, double>(u, g, out);
     atomicAdd(diag + m, out[i]);
   }
 }
@@ -336,7 +428,7 @@ template <int DEG>
 __global__ void k_gradient(int C, int Cs, const int* __restrict__ map, const double* __restrict__ vx,
                            const double* __restrict__ vy, const double* __restrict__ vz, const double* __restrict__ u,
                            const double* __restrict__ lam, double* __restrict__ g) {
-  constexpr int ND = DEG == 1 ? 4 : 10;
+  constexpr int ND = tet_ndof(DEG);
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   double uu[ND], ll[ND];
@@ -355,11 +447,11 @@ __global__ void k_gradient(int C, int Cs, const int* __restrict__ map, const dou
   }
   double G[6], adet;
   tet_metric<double>(p, G, adet);
-  const double s = 1.0 / (DEG == 1 ? 6.0 : 120.0);
+  const double s = 1.0 / geo_weight<DEG>();
 #pragma unroll
   for (int a = 0; a < 6; ++a) G[a] *= s;
   double out[ND];
-  element_apply<DEG, double>(uu, G, out);
+  tet_element<DEG, double>(uu, G, out);
   double acc = 0.0;
 #pragma unroll
   for (int j = 0; j < ND; ++j) acc += ll[j] * out[j];
@@ -444,14 +536,17 @@ __global__ void k_prolong(Numbering nf, int n_f, const int* __restrict__ start, 
   const int cls = (x - K2 * cx) + K2 * ((y - K2 * cy) + K2 * (z - K2 * cz));
   T s = T(0);
   const int e0 = __ldg(start + cls), ne = __ldg(start + cls + 1) - e0;
-  // at most 10 coarse P2 dofs (2 for P1) per fine dof: unrolled and predicated,
-  // so all the gathers of a fine dof are in flight together
-  constexpr int MAXE = DEG == 1 ? 2 : 10;
+  // at most 2 (P1), 10 (P2), 20 (P3) coarse dofs per fine dof: unrolled and
+  // predicated, so all the gathers of a fine dof are in flight together
+  constexpr int MAXE = tet_ndof(DEG) == 4 ? 2 : tet_ndof(DEG);
+  // x stride of the coarse dof in the cube index: P1 and P2 (halved
+  // coordinates of its class) 1, P3 (lexicographic, base point 3 c) 3
+  constexpr int KP = DEG == 3 ? 3 : 1;
 #pragma unroll
   for (int k = 0; k < MAXE; ++k) {
     if (k < ne) {
       const int4 t = __ldg(tab + e0 + k);
-      const int j = t.x + cx + t.y * cy + t.z * cz;
+      const int j = t.x + KP * cx + t.y * cy + t.z * cz;
       s += __ldg(w + e0 + k) * __ldg(xc + j);
     }
   }
@@ -459,8 +554,9 @@ __global__ void k_prolong(Numbering nf, int n_f, const int* __restrict__ start, 
 }
 
 // Restriction = exact transpose: coarse point Lc gathers fine points
-// 2 Lc + o for the stencil entries of its parity class; the index table gives
-// the fine dof as t.x + KX X + t.y Y + t.z Z (KX = 2 for P1, 1 for P2) and the
+// 2 Lc + o for the stencil entries of its class (Lc mod k per axis); the index
+// table gives the fine dof as t.x + KX X + t.y Y + t.z Z (KX = 1 for P2, whose
+// classes halve the coordinates, 2 for the lexicographic P1/P3) and the
 // offset o packed in t.w, unpacked for the bounds test only by coarse points
 // within `margin` of the boundary.  With yf != null the restricted vector is
 // the residual bf - yf.  A block holds 32 consecutive coarse points (one per
@@ -473,7 +569,7 @@ __global__ void __launch_bounds__(32 * TPC) k_restrict(int mf, Numbering nc, int
                                                        const T* __restrict__ w, const T* __restrict__ bf,
                                                        const T* __restrict__ yf, T* __restrict__ rc, int zero_bd) {
   __shared__ T part[TPC][32];
-  constexpr int KX = DEG == 1 ? 2 : 1;
+  constexpr int KX = DEG == 2 ? 1 : 2;
   const int lane = threadIdx.x & 31, sub = threadIdx.x >> 5;
   const int J = blockIdx.x * 32 + lane;
   T s = T(0);
@@ -484,7 +580,7 @@ __global__ void __launch_bounds__(32 * TPC) k_restrict(int mf, Numbering nc, int
     const bool bd = X == 0 || Y == 0 || Z == 0 || X == mc || Y == mc || Z == mc;
     if (!(bd && zero_bd)) {
       const bool near = min(min(X, Y), Z) < margin || max(max(X, Y), Z) > mc - margin;
-      const int cls = DEG == 2 ? ((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2)) : 0;
+      const int cls = DEG == 1 ? 0 : (X % DEG) + DEG * ((Y % DEG) + DEG * (Z % DEG));
       const int e1 = __ldg(start + cls + 1);
       const int base = KX * X;
 #pragma unroll 2
@@ -552,31 +648,71 @@ __global__ void k_random(int n, uint64_t seed, double* __restrict__ v) {
   v[i] = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
 }
 
+// Dense interior coarse operator, P3: A[ii][jj] += A_K[i][j] straight from
+// the reference coefficients (the P1/P2 assembly in fe_coarse.cu applies the
+// element to unit vectors).
+__global__ void k_coarse_assemble_p3(int C, int Cs, const int* __restrict__ map, const double* __restrict__ geo,
+                                     const int* __restrict__ dof2int, int nci, double* __restrict__ A) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  int ii[20];
+  double g[6];
+  for (int j = 0; j < 20; ++j) {
+    const int m = map[(size_t)j * Cs + c];
+    ii[j] = m >= 0 ? dof2int[m] : -1;
+  }
+  for (int a = 0; a < 6; ++a) g[a] = geo[(size_t)a * Cs + c];
+  for (int i = 0; i < 20; ++i) {
+    if (ii[i] < 0) continue;
+    for (int j = 0; j < 20; ++j) {
+      if (ii[j] < 0) continue;
+      const int lo = min(i, j), hi = max(i, j);
+      const int p = 20 * lo - lo * (lo - 1) / 2 + (hi - lo);
+      double a = 0.0;
+      for (int k = 0; k < 6; ++k) a += g[k] * c_K3[p][k];
+      atomicAdd(A + (size_t)ii[i] * nci + ii[j], a);
+    }
+  }
+}
+
 }  // namespace
 
 // ===================================================================== host
+void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, double* A, cudaStream_t s) {
+  k_coarse_assemble_p3<<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, dof2int, nci, A);
+  LAUNCH_CHECK();
+}
+
+// Calls f with std::integral_constant<int, deg> for deg = 1, 2, 3.
+template <class F>
+static void by_degree(int deg, F&& f) {
+  if (deg == 1)
+    f(std::integral_constant<int, 1>{});
+  else if (deg == 2)
+    f(std::integral_constant<int, 2>{});
+  else
+    f(std::integral_constant<int, 3>{});
+}
+
 void launch_build_level(Level& L, cudaStream_t s) {
-  if (L.deg == 1)
-    k_build_map<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.Cs, L.map);
+  by_degree(L.deg, [&](auto D) {
+    k_build_map<D.value><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.Cs, L.map);
+    LAUNCH_CHECK();
+    k_build_cube_map<D.value><<<ceil_div(L.Q, kBlock), kBlock, 0, s>>>(L.num, L.Q, L.Qs, L.cmap);
+    LAUNCH_CHECK();
+  });
+  if (L.deg == 3)  // coordinates of every lattice point, indexed by dof (the vertices' dofs are not 0..V-1)
+    k_build_coords_lattice<<<ceil_div(L.n, kBlock), kBlock, 0, s>>>(L.num, L.n, L.vx, L.vy, L.vz);
   else
-    k_build_map<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.num, L.C, L.Cs, L.map);
-  LAUNCH_CHECK();
-  if (L.deg == 1)
-    k_build_cube_map<1><<<ceil_div(L.Q, kBlock), kBlock, 0, s>>>(L.num, L.Q, L.Qs, L.cmap);
-  else
-    k_build_cube_map<2><<<ceil_div(L.Q, kBlock), kBlock, 0, s>>>(L.num, L.Q, L.Qs, L.cmap);
-  LAUNCH_CHECK();
-  k_build_coords<<<ceil_div(L.V, kBlock), kBlock, 0, s>>>(L.N, L.V, L.vx, L.vy, L.vz);
+    k_build_coords<<<ceil_div(L.V, kBlock), kBlock, 0, s>>>(L.N, L.V, L.vx, L.vy, L.vz);
   LAUNCH_CHECK();
 }
 
 void launch_geometry(Level& L, cudaStream_t s) {
-  if (L.deg == 1)
-    k_geometry<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64, L.geo32,
-                                                          L.detj);
-  else
-    k_geometry<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64, L.geo32,
-                                                          L.detj);
+  by_degree(L.deg, [&](auto D) {
+    k_geometry<D.value><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64,
+                                                                L.geo32, L.detj);
+  });
   LAUNCH_CHECK();
 }
 
@@ -585,10 +721,9 @@ static void apply_impl(const Level& L, const T* geo, const T* x, T* y, cudaStrea
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)L.n, s));
   const int Cpad = ceil_div(L.C, kBlock) * kBlock;
   const int grid = ceil_div((long long)Cpad + L.nb, kBlock);
-  if (L.deg == 1)
-    k_apply<1, T><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, geo, x, y, L.nb, L.bnd);
-  else
-    k_apply<2, T><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, geo, x, y, L.nb, L.bnd);
+  by_degree(L.deg, [&](auto D) {
+    k_apply<D.value, T><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, geo, x, y, L.nb, L.bnd);
+  });
   LAUNCH_CHECK();
 }
 
@@ -628,24 +763,25 @@ void launch_build_valence(Level& L, cudaStream_t s) {
 
 void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s) { apply_impl<double>(L, L.geo64, x, y, s); }
 void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) {
-  apply_cube32<false>(L, x, y, ChebFuse<float>{}, s);
+  if (L.deg == 3)  // P3: one thread per tet (a P3 cube holds 64 dofs and 6 x 20 x 20 products)
+    apply_impl<float>(L, L.geo32, x, y, s);
+  else
+    apply_cube32<false>(L, x, y, ChebFuse<float>{}, s);
 }
 
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
-  if (L.deg == 1)
-    k_mass<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, x, y);
-  else
-    k_mass<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, x, y);
+  by_degree(L.deg, [&](auto D) {
+    k_mass<D.value><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, x, y);
+  });
   LAUNCH_CHECK();
 }
 
 void launch_diag(Level& L, double* diag, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(diag, 0, sizeof(double) * (size_t)L.n, s));
-  if (L.deg == 1)
-    k_diag<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geo64, diag);
-  else
-    k_diag<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geo64, diag);
+  by_degree(L.deg, [&](auto D) {
+    k_diag<D.value><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geo64, diag);
+  });
   LAUNCH_CHECK();
   if (L.nb > 0) {
     k_diag_finish<<<ceil_div(L.nb, kBlock), kBlock, 0, s>>>(L.n, L.nb, L.bnd, diag);
@@ -656,10 +792,9 @@ void launch_diag(Level& L, double* diag, cudaStream_t s) {
 }
 
 void launch_gradient(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s) {
-  if (L.deg == 1)
-    k_gradient<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, u, lam, g);
-  else
-    k_gradient<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, u, lam, g);
+  by_degree(L.deg, [&](auto D) {
+    k_gradient<D.value><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, u, lam, g);
+  });
   LAUNCH_CHECK();
 }
 
@@ -705,12 +840,10 @@ template <typename T>
 void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s) {
   const Level& F = h->L[lf];
   const TransferTables& t = h->tt;
-  if (h->deg == 1)
-    k_prolong<1, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, F.n, t.pro_start, F.ptab,
-                                                            tt_weights<T>(t.pro_w, t.pro_wf), xc, xf, accumulate);
-  else
-    k_prolong<2, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, F.n, t.pro_start, F.ptab,
-                                                            tt_weights<T>(t.pro_w, t.pro_wf), xc, xf, accumulate);
+  by_degree(h->deg, [&](auto D) {
+    k_prolong<D.value, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, F.n, t.pro_start, F.ptab,
+                                                                  tt_weights<T>(t.pro_w, t.pro_wf), xc, xf, accumulate);
+  });
   LAUNCH_CHECK();
 }
 
@@ -723,8 +856,12 @@ void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T*
     k_restrict<1, T, 4><<<ceil_div(Cc.n, 32), 32 * 4, 0, s>>>(F.num.m, Cc.num, Cc.n, t.res_margin, t.res_start,
                                                               F.rtab, tt_weights<T>(t.res_w, t.res_wf), bf,
                                                               yf, rc, zero_bd);
-  else
+  else if (h->deg == 2)
     k_restrict<2, T, 8><<<ceil_div(Cc.n, 32), 32 * 8, 0, s>>>(F.num.m, Cc.num, Cc.n, t.res_margin, t.res_start,
+                                                              F.rtab, tt_weights<T>(t.res_w, t.res_wf), bf,
+                                                              yf, rc, zero_bd);
+  else
+    k_restrict<3, T, 8><<<ceil_div(Cc.n, 32), 32 * 8, 0, s>>>(F.num.m, Cc.num, Cc.n, t.res_margin, t.res_start,
                                                               F.rtab, tt_weights<T>(t.res_w, t.res_wf), bf,
                                                               yf, rc, zero_bd);
   LAUNCH_CHECK();
@@ -810,11 +947,101 @@ void quad_tables_host(double xi[FE_QUAD_POINTS][3], double w[FE_QUAD_POINTS], do
       }
 }
 
+// Gauss-Legendre nodes and weights on [0, 1] (Newton's method on the
+// three-term Legendre recurrence, P_n'(x) = n (x P_n - P_{n-1}) / (x^2 - 1)).
+static void gauss_legendre01(int n, double* t, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    t[i] = 0.5 * (x + 1.0);
+    w[i] = 1.0 / ((1.0 - x * x) * dp * dp);  // half the [-1, 1] weight 2 / ((1 - x^2) P_n'(x)^2)
+  }
+}
+
+// P3 Lagrange basis on the reference tet at xi, local order of k_build_map<3>:
+// vertex v: lam (3 lam - 1)(3 lam - 2) / 2; the edge node nearer p on edge
+// (p, q): 9/2 lam_p lam_q (3 lam_p - 1); face (a, b, c): 27 lam_a lam_b lam_c.
+static void p3_basis_host(const double xi[3], double phi[20], double dphi[20][3]) {
+  const double lam[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
+  const double dl[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int v = 0; v < 4; ++v) {
+    const double L = lam[v];
+    phi[v] = 0.5 * L * (3 * L - 1) * (3 * L - 2);
+    for (int a = 0; a < 3; ++a) dphi[v][a] = 0.5 * (27 * L * L - 18 * L + 2) * dl[v][a];
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = a + 1; b < 4; ++b) {
+      const int e = p2_edge(a, b) - 4;
+      for (int h = 0; h < 2; ++h) {
+        const int p = h ? b : a, q = h ? a : b, i = 4 + 2 * e + h;
+        phi[i] = 4.5 * lam[p] * lam[q] * (3 * lam[p] - 1);
+        for (int c = 0; c < 3; ++c)
+          dphi[i][c] = 4.5 * (lam[q] * (6 * lam[p] - 1) * dl[p][c] + lam[p] * (3 * lam[p] - 1) * dl[q][c]);
+      }
+    }
+  for (int f = 0; f < 4; ++f) {
+    const int a = p3_face_vertex(f, 0), b = p3_face_vertex(f, 1), c = p3_face_vertex(f, 2);
+    phi[16 + f] = 27 * lam[a] * lam[b] * lam[c];
+    for (int d = 0; d < 3; ++d)
+      dphi[16 + f][d] = 27 * (lam[b] * lam[c] * dl[a][d] + lam[a] * lam[c] * dl[b][d] + lam[a] * lam[b] * dl[c][d]);
+  }
+}
+
+// Reference P3 stiffness coefficients (see c_K3) and mass matrix, by the
+// conical-product Gauss rule with 5 points per direction (exact to degree 7;
+// the integrands have degree 4 and 6).
+void p3_tables_host(double K[210][6], double M[400]) {
+  double t[5], w[5];
+  gauss_legendre01(5, t, w);
+  for (int p = 0; p < 210; ++p)
+    for (int k = 0; k < 6; ++k) K[p][k] = 0.0;
+  for (int i = 0; i < 400; ++i) M[i] = 0.0;
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b)
+      for (int c = 0; c < 5; ++c) {
+        const double u = t[a], v = t[b], z = t[c];
+        const double xi[3] = {u, (1 - u) * v, (1 - u) * (1 - v) * z};
+        const double wq = w[a] * w[b] * w[c] * (1 - u) * (1 - u) * (1 - v);
+        double phi[20], d[20][3];
+        p3_basis_host(xi, phi, d);
+        for (int i = 0, p = 0; i < 20; ++i)
+          for (int j = i; j < 20; ++j, ++p) {
+            K[p][0] += wq * d[i][0] * d[j][0];
+            K[p][1] += wq * (d[i][0] * d[j][1] + d[i][1] * d[j][0]);
+            K[p][2] += wq * (d[i][0] * d[j][2] + d[i][2] * d[j][0]);
+            K[p][3] += wq * d[i][1] * d[j][1];
+            K[p][4] += wq * (d[i][1] * d[j][2] + d[i][2] * d[j][1]);
+            K[p][5] += wq * d[i][2] * d[j][2];
+          }
+        for (int i = 0; i < 20; ++i)
+          for (int j = 0; j < 20; ++j) M[i * 20 + j] += wq * phi[i] * phi[j];
+      }
+}
+
 void upload_mass_tables() {
   double m1[16], m2[100];
   mass_tables_host(m1, m2);
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref1, m1, sizeof(m1)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref2, m2, sizeof(m2)));
+  static double K3[210][6], M3[400];
+  static float K3f[210][6];
+  p3_tables_host(K3, M3);
+  for (int p = 0; p < 210; ++p)
+    for (int k = 0; k < 6; ++k) K3f[p][k] = (float)K3[p][k];
+  CUDA_CHECK(cudaMemcpyToSymbol(c_K3, K3, sizeof(K3)));
+  CUDA_CHECK(cudaMemcpyToSymbol(c_K3f, K3f, sizeof(K3f)));
+  CUDA_CHECK(cudaMemcpyToSymbol(c_mref3, M3, sizeof(M3)));
   double xi[FE_QUAD_POINTS][3], w[FE_QUAD_POINTS], p1[FE_QUAD_POINTS][4], p2[FE_QUAD_POINTS][10];
   quad_tables_host(xi, w, p1, p2);
   CUDA_CHECK(cudaMemcpyToSymbol(c_qxi, xi, sizeof(xi)));

@@ -53,7 +53,7 @@ def test_argument_validation(lib):
     assert e.value.code == fe.FE_ERR_ARG
     m = fe.fe_mesh_create(2)
     with pytest.raises(fe.FeError) as e:
-        fe.fe_hierarchy_refine(m, 1, 3)
+        fe.fe_hierarchy_refine(m, 1, 4)
     assert e.value.code == fe.FE_ERR_UNSUPPORTED
     with pytest.raises(fe.FeError) as e:
         fe.fe_hierarchy_refine(m, 9, 1)
