@@ -243,6 +243,35 @@ def extras(fe, I, h, dev, stream, flush):
                                         for hp, fp, up in zip(B.problems, fs, us)], stream, 3, flush)
     out["batched_64"]["sequential_single_solves_ms"] = ms_seq
     B.close()
+    # ---- P3 (the paper's degree) on UnitCubeMesh 32^3, 4 levels: operator rates and solves
+    h4 = fe.Hierarchy(4, 3, 3)
+    n4, C4 = h4.n_dofs(), h4.n_cells()
+    p3 = {"workload": "P3 UnitCubeMesh 32^3, 4 levels (coarse 4^3), rtol 1e-8", "dofs": n4, "cells": C4}
+    fma_per_cell = 210 * 8  # 210 symmetric element-matrix pairs: 6 FMAs to form the entry, 2 to apply it
+    for name, dtp, tdt in (("apply_f64", fe.FE_F64, torch.float64), ("apply_f32", fe.FE_F32, torch.float32)):
+        x4 = torch.rand(n4, dtype=tdt, device=dev)
+        y4 = torch.empty_like(x4)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                h4.apply_operator(x4, y4, dtype=dtp, stream=stream)
+            ms = time_launches(lambda: h4.apply_operator(x4, y4, dtype=dtp, stream=stream), stream, 10, flush)
+        tf = 2 * fma_per_cell * C4 / (ms * 1e-3) / 1e12
+        p3[name] = {"ms": ms, "GDoF_per_s": n4 / (ms * 1e-3) / 1e9, "TFLOP_per_s": tf}
+    p3["apply_f64"]["frac_of_nominal_fp64_peak"] = p3["apply_f64"]["TFLOP_per_s"] / FP64_PEAK_TFLOPS
+    p3["apply_f32"]["frac_of_nominal_fp32_peak"] = p3["apply_f32"]["TFLOP_per_s"] / (2 * FP32_PEAK_TOPS)
+    f4 = torch.from_numpy(I.sin_product_rhs(h4.dof_coordinates())).to(dev)
+    u4 = torch.empty_like(f4)
+    for name, prec in (("solve_f64", fe.FE_PREC_F64), ("solve_mixed_f32", fe.FE_PREC_MIXED_F32)):
+        with torch.cuda.stream(stream):
+            h4.solve(f4, u4, rtol=1e-8, precision=prec, stream=stream)
+            ms = time_launches(lambda: h4.solve(f4, u4, rtol=1e-8, precision=prec, stream=stream), stream, 3, flush)
+            st = h4.solve(f4, u4, rtol=1e-8, precision=prec, stream=stream)
+        p3[name] = {"ms": ms, "DoF_per_s": n4 / (ms * 1e-3), "iterations": st.iterations,
+                    "outer": st.outer_iterations, "rel_residual": st.rel_residual,
+                    "max_nodal_error_vs_exact": float((u4.cpu() - torch.from_numpy(
+                        I.sin_product(h4.dof_coordinates()))).abs().max())}
+    out["p3_32cubed"] = p3
+    h4.close()
     return out
 
 

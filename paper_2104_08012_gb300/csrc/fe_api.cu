@@ -409,10 +409,12 @@ static void mass_enqueue(const fe_hierarchy* h, const Level& L, const double* x,
 
 void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s) {
   const Level& L = h->L[level];
-  if (L.deg == 3) {  // P3: reference-matrix kernel, one tet per thread, FP64 FMAs or FP32
+  if (L.deg == 3) {  // P3: element matrix per tet in FP64 FMAs, float pairs (default) or FP32
     FE_REQUIRE(dtype != FE_BF16, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
-    if (dtype == FE_F64)
+    if (dtype == FE_F64 && h->f64_mode == FE_F64_NATIVE)
       launch_apply64(L, (const double*)x, (double*)y, s);
+    else if (dtype == FE_F64)
+      launch_apply64_df3(L, (const double*)x, (double*)y, s);
     else if (dtype == FE_F32)
       launch_apply32(L, (const float*)x, (float*)y, s);
     else

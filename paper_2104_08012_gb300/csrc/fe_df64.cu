@@ -18,6 +18,10 @@
 #include "fe_df.cuh"
 #include "fe_df2.cuh"
 
+// P3 reference stiffness coefficients times 3360 (exact integers, |k| <= 1944,
+// so exact in FP32); the 1/3360 is folded into the float-pair geometric factors.
+__constant__ float c_K3i[210][6];
+
 namespace {
 
 using namespace fe_df;
@@ -197,6 +201,95 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df2(int P, int Cs, const in
   }
 }
 
+// sum_k g_k K_k for float-pair g and exact small-integer K (the P3 reference
+// coefficients of pair p): the six leading products summed by TwoSum, their
+// rounding errors (FMA) and the g.lo products gathered in one float.
+__device__ __forceinline__ DF dot6_k3(const DF (&g)[6], int p) {
+  float ph[6], e = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float K = c_K3i[p][k];
+    ph[k] = __fmul_rn(g[k].hi, K);
+    e = __fadd_rn(e, __fmaf_rn(g[k].lo, K, __fmaf_rn(g[k].hi, K, -ph[k])));
+  }
+  DF s = two_sum(ph[0], ph[1]);
+  float err = s.lo;
+#pragma unroll
+  for (int k = 2; k < 6; ++k) {
+    const DF t = two_sum(s.hi, ph[k]);
+    s.hi = t.hi;
+    err = __fadd_rn(err, t.lo);
+  }
+  return DF(s.hi, __fadd_rn(err, e));
+}
+
+// P3, one tet per thread (persistent grid-stride loop): the element matrix
+// entry of each of the 210 symmetric pairs is formed in float pairs from the
+// geometric factors (kappa G / 3360, split) and the integer coefficients, and
+// applied to both rows.  Row i is a runtime loop (a fully unrolled 210-pair
+// body, 19k instructions, ran out of the instruction cache: "no instruction"
+// stalls dominated); the columns j are unrolled behind warp-uniform tests, so
+// u_j and the column sums stay in registers while u_i comes from shared
+// memory and row i's own sum goes there.  Dofs split and contributions
+// widened per tet as in k_apply_df.
+constexpr int kBlockP3 = 128;
+__global__ void __launch_bounds__(kBlockP3, 4) k_apply_df3(int C, int Cs, const int* __restrict__ map,
+                                                           const float2* __restrict__ geo,
+                                                           const double* __restrict__ x, double* __restrict__ y,
+                                                           int nb, const int* __restrict__ bnd) {
+  constexpr int ND = 20;
+  __shared__ float2 su[ND][kBlockP3], srow[ND][kBlockP3];  // [dof][thread]: conflict-free
+  const int tx = threadIdx.x;
+  const int tid = blockIdx.x * blockDim.x + tx, stride = gridDim.x * blockDim.x;
+  for (int i = tid; i < nb; i += stride) y[bnd[i]] = x[bnd[i]];  // Dirichlet rows: identity
+  for (int c = tid; c < C; c += stride) {
+    double xv[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const int m = __ldg(map + (size_t)j * Cs + c);
+      xv[j] = m >= 0 ? __ldg(x + m) : 0.0;
+    }
+    DF g[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const float2 v = __ldg(geo + (size_t)a * Cs + c);
+      g[a] = DF(v.x, v.y);
+    }
+    const int emax = block_exponent<ND>(xv);
+    DF u[ND], acc[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      u[j] = split_scaled(xv[j], emax);
+      if (j == 0 && emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
+      su[j][tx] = make_float2(u[j].hi, u[j].lo);
+      acc[j] = DF(0.0f);
+    }
+#pragma unroll 1
+    for (int i = 0; i < ND; ++i) {
+      const float2 t = su[i][tx];
+      const DF ui(t.x, t.y);
+      const int base = 20 * i - i * (i - 1) / 2 - i;  // pair index of (i, j) is base + j
+      DF ai(0.0f);
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        if (j >= i) {
+          const DF a = dot6_k3(g, base + j);
+          ai = ai + mul(a, u[j]);
+          if (j > i) acc[j] = acc[j] + mul(a, ui);
+        }
+      }
+      srow[i][tx] = make_float2(ai.hi, ai.lo);
+    }
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const int m = __ldg(map + (size_t)j * Cs + c);
+      const float2 r = srow[j][tx];
+      const DF yj = acc[j] + DF(r.x, r.y);
+      if (m >= 0) atomicAdd(y + m, widen_scaled(yj.hi, emax) + widen_scaled(yj.lo, emax));
+    }
+  }
+}
+
 // Cube-aggregated variant: one thread per cube splits the cube's (k+1)^3 dofs
 // once (scaled by their largest exponent), applies its six Kuhn tets into
 // float-pair accumulators and widens/scatters (k+1)^3 values: 27 splits, 27
@@ -294,12 +387,13 @@ __global__ void __launch_bounds__(kBlock) k_mass_df(int C, int Cs, const int* __
   for (int j = 0; j < ND; ++j) atomicAdd(y + idx[j], widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
 }
 
-__global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, float2* __restrict__ geodf,
-                            const double* __restrict__ detj, double wmass, float2* __restrict__ mdf) {
+__global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, double gscale,
+                            float2* __restrict__ geodf, const double* __restrict__ detj, double wmass,
+                            float2* __restrict__ mdf) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   for (int a = 0; a < 6; ++a) {
-    const double g = geo64[(size_t)a * Cs + c];
+    const double g = geo64[(size_t)a * Cs + c] * gscale;
     const float hi = (float)g;
     geodf[(size_t)a * Cs + c] = make_float2(hi, (float)(g - (double)hi));
   }
@@ -311,8 +405,9 @@ __global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, flo
 }  // namespace
 
 void launch_split_geometry(Level& L, cudaStream_t s) {
-  k_split_geo<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, L.geodf, L.detj,
-                                                       L.deg == 1 ? 1.0 / 120.0 : 1.0 / 2520.0, L.massdf);
+  // P3: the float-pair kernel takes kappa G / 3360 (its coefficients are integers)
+  k_split_geo<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, L.deg == 3 ? 1.0 / 3360.0 : 1.0, L.geodf,
+                                                       L.detj, L.deg == 1 ? 1.0 / 120.0 : 1.0 / 2520.0, L.massdf);
   LAUNCH_CHECK();
 }
 
@@ -385,6 +480,21 @@ void launch_apply64_df2(const Level& L, const double* x, double* y, cudaStream_t
                                                                                  L.bnd);
   LAUNCH_CHECK();
 }
+
+void launch_apply64_df3(const Level& L, const double* x, double* y, cudaStream_t s) {
+  FE_REQUIRE(L.deg == 3, FE_ERR_UNSUPPORTED, "the float-pair P3 kernel needs a degree-3 level");
+  CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
+  static int g = 0;
+  if (!g) {  // 4 blocks of 40 KB shared memory per SM: prefer the largest shared-memory carveout
+    CUDA_CHECK(cudaFuncSetAttribute(k_apply_df3, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    g = resident_grid(k_apply_df3, kBlockP3, 1 << 30);
+  }
+  k_apply_df3<<<std::min(g, ceil_div(std::max(L.C, L.nb), kBlockP3)), kBlockP3, 0, s>>>(L.C, L.Cs, L.map, L.geodf, x,
+                                                                                       y, L.nb, L.bnd);
+  LAUNCH_CHECK();
+}
+
+void upload_p3_df_table(const float* k3i) { CUDA_CHECK(cudaMemcpyToSymbol(c_K3i, k3i, sizeof(float) * 210 * 6)); }
 
 void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s) {
   apply_cube_df<false>(L, x, y, ChebFuse<double>{}, s);

@@ -1039,6 +1039,15 @@ void upload_mass_tables() {
   p3_tables_host(K3, M3);
   for (int p = 0; p < 210; ++p)
     for (int k = 0; k < 6; ++k) K3f[p][k] = (float)K3[p][k];
+  // the coefficients are integers over 3360: exact FP32 copies for the float-pair kernel
+  static float K3i[210][6];
+  for (int p = 0; p < 210; ++p)
+    for (int k = 0; k < 6; ++k) {
+      const double v = K3[p][k] * 3360.0, r = std::nearbyint(v);
+      FE_REQUIRE(std::fabs(v - r) < 1e-8 && std::fabs(r) < (1 << 20), FE_ERR_CUDA, "P3 coefficients are not k/3360");
+      K3i[p][k] = (float)r;
+    }
+  upload_p3_df_table(&K3i[0][0]);
   CUDA_CHECK(cudaMemcpyToSymbol(c_K3, K3, sizeof(K3)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_K3f, K3f, sizeof(K3f)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref3, M3, sizeof(M3)));

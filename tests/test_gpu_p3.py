@@ -55,8 +55,11 @@ def test_p3_mesh_queries(fe, N):
 
 @pytest.mark.parametrize("N", [1, 2, 3, 5])
 @pytest.mark.parametrize("coef", ["one", "grf"])
-def test_p3_apply_f64_and_f32(fe, N, coef):
+@pytest.mark.parametrize("mode", ["double_float", "native"])
+def test_p3_apply_f64_and_f32(fe, N, coef, mode):
+    """FP64 operator in float pairs (default) and in FP64 FMAs, and the FP32 operator."""
     with fe.Hierarchy(N, 0, 3) as h:
+        h.set_f64_mode(fe.FE_F64_NATIVE if mode == "native" else fe.FE_F64_DOUBLE_FLOAT)
         kappa = None if coef == "one" else I.grf_kappa(h.cell_centroids(), seed=N)
         h.set_coefficient(None if kappa is None else dt(kappa))
         L = O.Level(N, 3, kappa)
@@ -145,9 +148,11 @@ def test_p3_smoother_and_vcycle(fe):
         assert np.linalg.norm(host(x) - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("N0,nref", [(1, 2), (2, 1), (2, 2)])
-def test_p3_gmg_pcg_solution_parity(fe, N0, nref):
+@pytest.mark.parametrize("N0,nref,mode", [(1, 2, "double_float"), (2, 1, "native"), (2, 2, "double_float"),
+                                          (2, 2, "native")])
+def test_p3_gmg_pcg_solution_parity(fe, N0, nref, mode):
     with fe.Hierarchy(N0, nref, 3) as h:
+        h.set_f64_mode(fe.FE_F64_NATIVE if mode == "native" else fe.FE_F64_DOUBLE_FLOAT)
         kappa = I.grf_kappa(h.cell_centroids(), seed=6)
         h.set_coefficient(dt(kappa))
         L = O.Level(N0 * 2 ** nref, 3, kappa)
