@@ -464,36 +464,102 @@ def lanczos_lambda_max(alphas, betas):
     return float(np.linalg.eigvalsh(T)[-1])
 
 
-def estimate_lambda_max(A, diag, n_steps=20, seed=0):
-    """lambda_max(D^-1 A) estimated from n_steps of Jacobi-PCG on a seeded random rhs."""
+def estimate_lambda_max(A, diag, n_steps=20, seed=0, prec=None):
+    """lambda_max(M^-1 A) estimated from n_steps of PCG on a seeded random rhs (M = D, Jacobi, unless
+    ``prec`` applies another M^-1)."""
     b = np.random.default_rng(seed).uniform(-1, 1, A.shape[0])
-    _, _, _, (al, be) = pcg(lambda v: A @ v, b, lambda v: v / diag, rtol=0.0, maxit=n_steps)
+    _, _, _, (al, be) = pcg(lambda v: A @ v, b, prec if prec is not None else (lambda v: v / diag),
+                            rtol=0.0, maxit=n_steps)
     return lanczos_lambda_max(al, be)
 
 
-def chebyshev(apply_A, diag, b, x, lo, hi, steps):
-    """Chebyshev semi-iteration for A x = b preconditioned by D^-1 on [lo, hi].
+def chebyshev(apply_A, diag, b, x, lo, hi, steps, prec=None):
+    """Chebyshev semi-iteration for A x = b preconditioned by M^-1 on [lo, hi] (M = D, Jacobi, unless
+    ``prec`` applies another M^-1, e.g. the vertex-star patch preconditioner).
 
-    theta = (hi+lo)/2, delta = (hi-lo)/2; d_0 = D^-1 r_0 / theta; then
+    theta = (hi+lo)/2, delta = (hi-lo)/2; d_0 = M^-1 r_0 / theta; then
     rho_k = 1/(2 theta/delta - rho_{k-1}),
-    d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) D^-1 r_k; x_{k+1} = x_k + d_k.
+    d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) M^-1 r_k; x_{k+1} = x_k + d_k.
     """
+    if prec is None:
+        prec = lambda v: v / diag  # noqa: E731
     theta = 0.5 * (hi + lo)
     delta = 0.5 * (hi - lo)
     sigma = theta / delta
     rho = 1.0 / sigma
     x = x.copy()
     r = b - apply_A(x)
-    d = r / diag / theta
+    d = prec(r) / theta
     for k in range(steps):
         x += d
         if k == steps - 1:
             break
         r = b - apply_A(x)
         rho_new = 1.0 / (2.0 * sigma - rho)
-        d = rho_new * rho * d + (2.0 * rho_new / delta) * (r / diag)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * prec(r)
         rho = rho_new
     return x
+
+
+# ------------------------------------------------- vertex-star patches -----
+def ref_node_barycentrics(degree):
+    """Barycentric coordinates (nd, 4) of the local Lagrange nodes in the local dof order of ``Space``."""
+    I4 = np.eye(4)
+    if degree == 1:
+        return I4.copy()
+    if degree == 2:
+        return np.concatenate([I4, [(I4[a] + I4[b]) / 2 for a, b in P2_EDGES]])
+    edge = [(2 * I4[a] + I4[b]) / 3 if near_a else (I4[a] + 2 * I4[b]) / 3 for a, b in P2_EDGES for near_a in (True, False)]
+    face = [(I4[a] + I4[b] + I4[c]) / 3 for a, b, c in P3_FACES]
+    return np.concatenate([I4, edge, face])
+
+
+def star_patches(level):
+    """Vertex-star patches (the paper's PatchPC with star construction around vertices, Section 3): for each mesh
+    vertex v, the dofs of the open star of v -- the mesh entities whose closure contains v, i.e. the nodes of the
+    cells around v whose barycentric coordinate for v is positive -- without the Dirichlet dofs.  Returns a list
+    of sorted dof arrays, one per vertex (empty ones dropped)."""
+    space, mesh = level.space, level.mesh
+    bary = ref_node_barycentrics(space.degree)
+    groups = [[] for _ in range(mesh.n_vertices)]
+    for a in range(4):
+        local = np.nonzero(bary[:, a] > 0)[0]
+        for K in range(mesh.n_cells):
+            groups[mesh.cells[K, a]].append(space.cell_dofs[K, local])
+    out = []
+    for g in groups:
+        d = np.unique(np.concatenate(g)) if g else np.empty(0, dtype=np.int64)
+        d = d[~space.boundary[d]]
+        if d.size:
+            out.append(d)
+    return out
+
+
+class PatchPreconditioner:
+    """Additive Schwarz over the vertex-star patches with exact local solves (PatchPC's default additive
+    combination and direct sub-solver): M^-1 r = sum_p R_p^T (R_p A R_p^T)^-1 R_p r on the free dofs, and
+    M^-1 r = r on the Dirichlet dofs (their rows are the identity, as for Jacobi)."""
+
+    def __init__(self, level):
+        self.level = level
+        self.patches = star_patches(level)
+        A = level.A_free
+        self.bd = level.space.boundary
+        self.by_size = {}
+        for p in self.patches:
+            self.by_size.setdefault(p.size, []).append(p)
+        self.blocks = []
+        for size, ps in self.by_size.items():
+            idx = np.stack(ps)  # (P, size)
+            Ap = np.stack([A[p][:, p].toarray() for p in ps])
+            self.blocks.append((idx, np.linalg.inv(Ap)))
+
+    def __call__(self, r):
+        z = np.zeros_like(r)
+        for idx, Ainv in self.blocks:
+            np.add.at(z, idx, np.einsum("pij,pj->pi", Ainv, r[idx]))
+        z[self.bd] = r[self.bd]
+        return z
 
 
 # -------------------------------------------------------- multigrid -------
@@ -501,7 +567,9 @@ class Hierarchy:
     """Nested levels UnitCubeMesh(N0 * 2^l), l = 0..nrefine (``MeshHierarchy``)."""
 
     def __init__(self, N0, nrefine, degree, kappa_fine=None, cheb_steps=2,
-                 cheb_lo=0.1, cheb_hi=1.1, eig_steps=20):
+                 cheb_lo=0.1, cheb_hi=1.1, eig_steps=20, smoother="jacobi"):
+        """smoother: "jacobi" (Chebyshev preconditioned by D^-1) or "patch" (by the vertex-star patches, the
+        paper's PatchPC choice)."""
         self.degree = degree
         Ns = [N0 * 2 ** l for l in range(nrefine + 1)]
         kappas = [None] * len(Ns)
@@ -512,7 +580,9 @@ class Hierarchy:
         self.levels = [Level(N, degree, k) for N, k in zip(Ns, kappas)]
         self.P = [None] + [prolongation(self.levels[l - 1], self.levels[l]) for l in range(1, len(Ns))]
         self.cheb_steps = cheb_steps
-        self.lmax = [estimate_lambda_max(L.A, L.diag, eig_steps) for L in self.levels]
+        self.prec = [PatchPreconditioner(L) if smoother == "patch" and l > 0 else None
+                     for l, L in enumerate(self.levels)]
+        self.lmax = [estimate_lambda_max(L.A, L.diag, eig_steps, prec=P) for L, P in zip(self.levels, self.prec)]
         self.cheb_lo, self.cheb_hi = cheb_lo, cheb_hi
         c = self.levels[0]
         self.coarse_interior = np.nonzero(~c.space.boundary)[0]
@@ -532,7 +602,8 @@ class Hierarchy:
     def smooth(self, l, b, x):
         L = self.levels[l]
         lm = self.lmax[l]
-        return chebyshev(lambda v: L.A @ v, L.diag, b, x, self.cheb_lo * lm, self.cheb_hi * lm, self.cheb_steps)
+        return chebyshev(lambda v: L.A @ v, L.diag, b, x, self.cheb_lo * lm, self.cheb_hi * lm, self.cheb_steps,
+                         prec=self.prec[l])
 
     def vcycle(self, b, l=None):
         """One V-cycle: pre-smooth from 0, restrict the residual, recurse, prolong, post-smooth."""
