@@ -148,8 +148,25 @@ def extras(fe, I, h, dev, stream, flush):
     h.set_smoother_fusion(False)
     out["fused_smoother_solve"] = {"ms": ms, "DoF_per_s": n / (ms * 1e-3), "iterations": st.iterations,
                                    "rel_residual": st.rel_residual}
-    # ---- full multigrid as the whole solve (the paper's outer solver) on the same problem
+    # ---- the paper's level smoother: Chebyshev preconditioned by vertex-star patches, CG and full multigrid
     ue = torch.from_numpy(I.sin_product(h.dof_coordinates()))
+    h.set_smoother(fe.FE_SMOOTHER_PATCH)
+    pt = {"what": "Chebyshev(2) preconditioned by vertex-star patches (additive, exact 15x15 local solves)",
+          "lambda_max": [h.lambda_max(l) for l in range(h.nlev)]}
+    with torch.cuda.stream(stream):
+        h.solve(f_n, u_n, rtol=1e-8, stream=stream)
+        ms = time_launches(lambda: h.solve(f_n, u_n, rtol=1e-8, stream=stream), stream, 3, flush)
+        st = h.solve(f_n, u_n, rtol=1e-8, stream=stream)
+        pt["gmg_pcg"] = {"ms": ms, "DoF_per_s": n / (ms * 1e-3), "iterations": st.iterations,
+                         "rel_residual": st.rel_residual}
+        h.solve(f_n, u_n, precond=fe.FE_PC_FMG, max_it=1, stream=stream)
+        ms = time_launches(lambda: h.solve(f_n, u_n, precond=fe.FE_PC_FMG, max_it=1, stream=stream), stream, 3, flush)
+        st = h.solve(f_n, u_n, precond=fe.FE_PC_FMG, max_it=1, stream=stream)
+        pt["full_multigrid_1_cycle"] = {"ms": ms, "rel_residual": st.rel_residual,
+                                        "max_nodal_error_vs_exact": float((u_n.cpu() - ue).abs().max())}
+    h.set_smoother(fe.FE_SMOOTHER_JACOBI)
+    out["patch_smoother_p2_64cubed"] = pt
+    # ---- full multigrid as the whole solve (the paper's outer solver) on the same problem
     fm = {"what": "one full-multigrid cycle (restrict b to all levels, coarse Cholesky, per finer level: "
                   "interpolate, V-cycles), P2 64^3, 4 levels",
           "cg_max_nodal_error_vs_exact": float((u_n.cpu() - ue).abs().max())}

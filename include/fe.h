@@ -203,6 +203,23 @@ int fe_apply_operator(const fe_hierarchy* h, int level, const void* x, void* y, 
  * other step stay FP64. */
 int fe_set_f64_mode(fe_hierarchy* h, int mode);
 
+/* ---- preconditioner of the Chebyshev level smoother (fe_set_smoother) ---- */
+#define FE_SMOOTHER_JACOBI 0  /* D^-1 (the default) */
+#define FE_SMOOTHER_PATCH 1   /* vertex-star patches, additive, exact local solves (Sec. 3, PatchPC star) */
+
+/* Precondition the Chebyshev smoother of every level >= 1 with D^-1
+ * (FE_SMOOTHER_JACOBI) or with the vertex-star patch preconditioner
+ * (FE_SMOOTHER_PATCH): M^-1 r = sum_p R_p^T (R_p A R_p^T)^-1 R_p r over one
+ * patch per mesh vertex, the dofs of the vertex's open star (the vertex and,
+ * for P2, the midpoints of its 14 Kuhn edges) without Dirichlet dofs, and
+ * M^-1 r = r on Dirichlet rows (Sec. 3: PatchPC with star patches around
+ * vertices as the preconditioner of the level smoother).  The Chebyshev
+ * interval becomes [lo, hi] * lambda_max(M^-1 A) (re-estimated here and after
+ * every fe_set_coefficient).  P2 builds one 15 x 15 local inverse per vertex
+ * (FP64 and FP32 copies); for P1 a star patch is its vertex alone and the
+ * patch preconditioner is exactly Jacobi; P3 returns FE_ERR_UNSUPPORTED. */
+int fe_set_smoother(fe_hierarchy* h, int smoother);
+
 /* Chebyshev-Jacobi smoothing (Sec. 3: two Chebyshev iterations per level
  * visit) with the operator fused (on = 1) or not (on = 0, the default).
  * Fused, each smoothing step that needs y = A x is one launch: every interior

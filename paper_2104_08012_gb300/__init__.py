@@ -19,6 +19,7 @@ FE_F64, FE_F32, FE_BF16 = 0, 1, 2
 FE_F64_NATIVE, FE_F64_DOUBLE_FLOAT, FE_F64_DOUBLE_FLOAT_TET, FE_F64_DOUBLE_FLOAT_CUBE, FE_F64_DOUBLE_FLOAT_PAIR = \
     0, 1, 2, 3, 4
 FE_PC_JACOBI, FE_PC_GMG, FE_PC_FMG = 0, 1, 2
+FE_SMOOTHER_JACOBI, FE_SMOOTHER_PATCH = 0, 1
 FE_QUAD_POINTS = 27
 FE_PREC_F64, FE_PREC_MIXED_F32, FE_PREC_MIXED_BF16 = 0, 1, 2
 FE_RHS_LOAD, FE_RHS_NODAL_F, FE_RHS_QUAD_F = 0, 1, 2
@@ -31,7 +32,7 @@ EXPORTED = (
     "fe_diagonal", "fe_lambda_max", "fe_prolong", "fe_restrict", "fe_smooth", "fe_coarse_solve", "fe_vcycle",
     "fe_load_vector", "fe_quadrature_points", "fe_load_vector_quadrature", "fe_solve_poisson", "fe_adjoint_gradient",
     "fe_objective", "fe_dot_noalloc",
-    "fe_set_f64_mode", "fe_set_smoother_fusion", "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
+    "fe_set_f64_mode", "fe_set_smoother_fusion", "fe_set_smoother", "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
 )
 
 
@@ -107,6 +108,7 @@ def load():
         "fe_dot_noalloc": (i, [vp, vp, ll, vp, vp]),
         "fe_set_f64_mode": (i, [vp, i]),
         "fe_set_smoother_fusion": (i, [vp, i]),
+        "fe_set_smoother": (i, [vp, i]),
         "fe_batch_create": (i, [i, vp, vp, vp, ctypes.POINTER(vp)]),
         "fe_batch_destroy": (None, [vp]),
         "fe_batch_hierarchy": (i, [vp, i, ctypes.POINTER(vp)]),
@@ -359,6 +361,10 @@ class Hierarchy:
     # -- operations on caller-owned vectors (torch tensors or numpy arrays)
     def set_f64_mode(self, mode):
         _check(self._L.fe_set_f64_mode(self.h, mode))
+
+    def set_smoother(self, smoother):
+        """FE_SMOOTHER_JACOBI (default) or FE_SMOOTHER_PATCH (vertex-star patches) as the Chebyshev preconditioner."""
+        _check(self._L.fe_set_smoother(self.h, smoother))
 
     def set_smoother_fusion(self, on):
         """Chebyshev update fused into the operator launch (True) or a separate vector kernel (False, default)."""

@@ -337,16 +337,30 @@ static double tridiag_max_eig(const std::vector<double>& a, const std::vector<do
 
 // lambda_max(D^-1 A_l) from `steps` Jacobi-PCG iterations on a seeded random
 // right-hand side: the CG coefficients define the Lanczos tridiagonal.
+// Whether level l smooths with the vertex-star patches (P2 levels >= 1; for P1
+// the patches are single vertices and the preconditioner is Jacobi).
+static bool use_patch(const fe_hierarchy* h, int l) {
+  return h->smoother == FE_SMOOTHER_PATCH && h->deg == 2 && l >= 1 && h->L[l].pdof.p;
+}
+
+// lambda_max(M^-1 A) from the Lanczos tridiagonal of `steps` PCG iterations
+// (M = D, or the patch preconditioner on patch-smoothed levels).
 static double estimate_lmax(fe_hierarchy* h, int l, int steps, cudaStream_t s) {
   Level& L = h->L[l];
   const int n = L.n;
   ReduceCtx& R = h->red;
   double *b = h->b, *x = h->x, *r = h->r, *z = h->z, *p = h->p, *q = h->q;
+  const bool patch = use_patch(h, l);
   launch_random(n, 0x2104080120210416ull + (uint64_t)l, b, s);
   launch_zero_boundary64(L, b, s);
   CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   CUDA_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  launch_cheb_step<double>(n, r, nullptr, L.dinv64, p, z, 0.0, 1.0, true, s);  // z = p = D^-1 r
+  if (patch) {
+    launch_patch_apply<double>(L, r, nullptr, z, s);  // z = M^-1 r
+    CUDA_CHECK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    launch_cheb_step<double>(n, r, nullptr, L.dinv64, p, z, 0.0, 1.0, true, s);  // z = p = D^-1 r
+  }
   launch_dot<double>(R, n, r, z, S_RZ, s);
   CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
   CUDA_CHECK(cudaStreamSynchronize(s));
@@ -355,7 +369,13 @@ static double estimate_lmax(fe_hierarchy* h, int l, int steps, cudaStream_t s) {
   for (int it = 0; it < steps; ++it) {
     apply_enqueue(h, l, p, q, FE_F64, s);
     launch_cg_alpha<double>(R, n, p, q, s);
-    launch_cg_update<double>(R, n, x, r, p, q, L.dinv64, z, s);
+    if (patch) {
+      launch_cg_update<double>(R, n, x, r, p, q, nullptr, nullptr, s);
+      launch_patch_apply<double>(L, r, nullptr, z, s);
+      launch_cg_beta<double>(R, n, r, z, s);
+    } else {
+      launch_cg_update<double>(R, n, x, r, p, q, L.dinv64, z, s);
+    }
     launch_cg_update_p<double>(R, n, p, z, s);
     CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
     CUDA_CHECK(cudaStreamSynchronize(s));
@@ -397,6 +417,9 @@ template <> float* lv_x<float>(Level& L) { return L.x32; }
 template <> float* lv_y<float>(Level& L) { return L.y32; }
 template <> float* lv_d<float>(Level& L) { return L.d32; }
 template <> const float* lv_dinv<float>(const Level& L) { return L.dinv32; }
+template <typename T> static T* lv_z(Level& L);
+template <> double* lv_z<double>(Level& L) { return L.z64; }
+template <> float* lv_z<float>(Level& L) { return L.z32; }
 
 // Consistent mass y = M x in FP64: float-pair arithmetic unless the hierarchy
 // is in native-FP64 mode (the operator's mode decides both).
@@ -477,6 +500,23 @@ static void smooth_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d,
   const double a = lo * L.lmax, bmax = hi * L.lmax;
   const double theta = 0.5 * (bmax + a), delta = 0.5 * (bmax - a), sigma = theta / delta;
   double rho = 1.0 / sigma;
+  if (use_patch(h, l)) {  // z = M^-1 (b - A x) by the vertex-star patches, then d = c1 d + c2 z, x += d
+    T* z = lv_z<T>(L);
+    for (int k = 0; k < steps; ++k) {
+      const bool last = k + 1 == steps;
+      const bool from_zero = k == 0 && x_zero;
+      if (!from_zero) apply_enqueue(h, l, x, y, dtype, s);
+      launch_patch_apply<T>(L, b, from_zero ? nullptr : y, z, s);
+      if (k == 0) {
+        launch_cheb_pc<T>(L.n, z, x, d, 0.0, 1.0 / theta, from_zero, !last, s);
+      } else {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        launch_cheb_pc<T>(L.n, z, x, d, rn * rho, 2.0 * rn / delta, false, !last, s);
+        rho = rn;
+      }
+    }
+    return;
+  }
   for (int k = 0; k < steps; ++k) {
     const bool last = k + 1 == steps;  // its direction d is not used again
     if (k == 0) {
@@ -964,6 +1004,8 @@ static void set_coefficient_impl(fe_hierarchy* h, const double* kappa, cudaStrea
     launch_split_geometry(h->L[l], s);
     launch_diag(h->L[l], h->tmp, s);
   }
+  if (h->smoother == FE_SMOOTHER_PATCH && h->deg == 2)
+    for (int l = 1; l < h->nlev; ++l) launch_patch_setup(h->L[l], s);
   for (int l = 0; l < h->nlev; ++l) h->L[l].lmax = estimate_lmax(h, l, 20, s);
   if (h->nlev > 1) coarse_setup(h, s);
   invalidate_graphs(h);
@@ -1262,6 +1304,32 @@ int fe_set_f64_mode(fe_hierarchy* h, int mode) {
     CUDA_CHECK(cudaDeviceSynchronize());
     h->f64_mode = mode;
     invalidate_graphs(h);
+  }
+  API_END
+}
+
+int fe_set_smoother(fe_hierarchy* h, int smoother) {
+  API_BEGIN
+  FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
+  FE_REQUIRE(smoother == FE_SMOOTHER_JACOBI || smoother == FE_SMOOTHER_PATCH, FE_ERR_ARG, "unknown smoother");
+  FE_REQUIRE(smoother == FE_SMOOTHER_JACOBI || h->deg <= 2, FE_ERR_UNSUPPORTED,
+             "the vertex-star patch smoother is built for P1/P2");
+  if (h->smoother != smoother) {
+    CUDA_CHECK(cudaDeviceSynchronize());
+    cudaStream_t s = 0;
+    h->smoother = smoother;
+    if (smoother == FE_SMOOTHER_PATCH && h->deg == 2)
+      for (int l = 1; l < h->nlev; ++l) {
+        Level& L = h->L[l];
+        launch_patch_setup(L, s);
+        if (!L.z64.p) {
+          L.z64.alloc(L.n);
+          L.z32.alloc(L.n);
+        }
+      }
+    for (int l = 0; l < h->nlev; ++l) h->L[l].lmax = estimate_lmax(h, l, 20, s);
+    invalidate_graphs(h);
+    CUDA_CHECK(cudaStreamSynchronize(s));
   }
   API_END
 }

@@ -220,6 +220,12 @@ struct Level {
   // dof's count to zero holds its complete y_i and performs the Chebyshev
   // update of that dof, then restores the count.
   DBuf<unsigned> val_tet, cnt_tet, val_cube, cnt_cube;
+  // Vertex-star patch smoother (P2, levels >= 1, built by fe_set_smoother):
+  // slot dofs [15][Pp], packed A_p^-1 [120][Pp] (FP64 and FP32), and the
+  // preconditioned residuals z of the smoother.
+  DBuf<int> pdof;
+  DBuf<double> pinv, z64;
+  DBuf<float> pinv32, z32;
 };
 
 // Host-built transfer stencils (exact dyadic weights).
@@ -303,6 +309,7 @@ struct fe_hierarchy {
   bool lmax_valid = false;
   int f64_mode = FE_F64_DOUBLE_FLOAT;  // arithmetic of FP64 operator applications
   int fuse_smoother = 0;               // Chebyshev update fused into the operator kernel (measured slower on GB300)
+  int smoother = FE_SMOOTHER_JACOBI;   // preconditioner of the Chebyshev smoother
 };
 
 // ------------------------------------------------------- launch wrappers ---
@@ -326,6 +333,13 @@ void launch_apply_cheb64_cube_df(const Level& L, const double* b, double* x, dou
                                  double c2, bool store_d, cudaStream_t s);
 void launch_build_valence(Level& L, cudaStream_t s);
 void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, double* A, cudaStream_t s);
+// Vertex-star patch smoother (fe_patch.cu)
+void launch_patch_setup(Level& L, cudaStream_t s);
+template <typename T>
+void launch_patch_apply(const Level& L, const T* b, const T* y, T* z, cudaStream_t s);
+template <typename T>
+void launch_cheb_pc(int n, const T* z, T* x, T* d, double c1, double c2, bool first_from_zero, bool store_d,
+                    cudaStream_t s);
 void launch_split_geometry(Level& L, cudaStream_t s);
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_mass_df(const Level& L, const double* x, double* y, cudaStream_t s);
