@@ -356,7 +356,7 @@ static double estimate_lmax(fe_hierarchy* h, int l, int steps, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   CUDA_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   if (patch) {
-    launch_patch_apply<double>(L, r, nullptr, z, s);  // z = M^-1 r
+    launch_patch_apply<double>(L, r, nullptr, z, h->f64_mode != FE_F64_NATIVE, s);  // z = M^-1 r
     CUDA_CHECK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   } else {
     launch_cheb_step<double>(n, r, nullptr, L.dinv64, p, z, 0.0, 1.0, true, s);  // z = p = D^-1 r
@@ -371,7 +371,7 @@ static double estimate_lmax(fe_hierarchy* h, int l, int steps, cudaStream_t s) {
     launch_cg_alpha<double>(R, n, p, q, s);
     if (patch) {
       launch_cg_update<double>(R, n, x, r, p, q, nullptr, nullptr, s);
-      launch_patch_apply<double>(L, r, nullptr, z, s);
+      launch_patch_apply<double>(L, r, nullptr, z, h->f64_mode != FE_F64_NATIVE, s);
       launch_cg_beta<double>(R, n, r, z, s);
     } else {
       launch_cg_update<double>(R, n, x, r, p, q, L.dinv64, z, s);
@@ -506,7 +506,7 @@ static void smooth_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d,
       const bool last = k + 1 == steps;
       const bool from_zero = k == 0 && x_zero;
       if (!from_zero) apply_enqueue(h, l, x, y, dtype, s);
-      launch_patch_apply<T>(L, b, from_zero ? nullptr : y, z, s);
+      launch_patch_apply<T>(L, b, from_zero ? nullptr : y, z, h->f64_mode != FE_F64_NATIVE, s);
       if (k == 0) {
         launch_cheb_pc<T>(L.n, z, x, d, 0.0, 1.0 / theta, from_zero, !last, s);
       } else {

@@ -225,6 +225,7 @@ struct Level {
   // preconditioned residuals z of the smoother.
   DBuf<int> pdof;
   DBuf<double> pinv, z64;
+  DBuf<float2> pinvdf;  // A_p^-1 as float pairs for the FP64 smoother's float-pair product
   DBuf<float> pinv32, z32;
 };
 
@@ -336,7 +337,7 @@ void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, dou
 // Vertex-star patch smoother (fe_patch.cu)
 void launch_patch_setup(Level& L, cudaStream_t s);
 template <typename T>
-void launch_patch_apply(const Level& L, const T* b, const T* y, T* z, cudaStream_t s);
+void launch_patch_apply(const Level& L, const T* b, const T* y, T* z, bool df, cudaStream_t s);
 template <typename T>
 void launch_cheb_pc(int n, const T* z, T* x, T* d, double c1, double c2, bool first_from_zero, bool store_d,
                     cudaStream_t s);

@@ -13,7 +13,9 @@
 // gets an identity row so that A_p stays invertible and its r and z stay 0.
 // M^-1 r = sum_p R_p^T A_p^-1 R_p r is one thread per patch (gather r = b - y,
 // 120-entry symmetric product, atomic scatter); Dirichlet rows take z = r.
-#include "fe_internal.cuh"
+// The FP64 product runs in float pairs (k_patch_apply_df) unless the
+// hierarchy's FP64 mode is native.
+#include "fe_df.cuh"
 
 namespace {
 
@@ -31,8 +33,8 @@ __device__ int slot_of(int dx, int dy, int dz) {
 }
 
 __global__ void k_patch_setup(Numbering num, int P, int Pp, int Cs, const double* __restrict__ geo64,
-                              int* __restrict__ pdof, double* __restrict__ pinv, float* __restrict__ pinv32,
-                              int* __restrict__ flag) {
+                              int* __restrict__ pdof, double* __restrict__ pinv, float2* __restrict__ pinvdf,
+                              float* __restrict__ pinv32, int* __restrict__ flag) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= P) return;
   const int N = num.N, n1 = N + 1, m = num.m;
@@ -118,7 +120,9 @@ __global__ void k_patch_setup(Numbering num, int P, int Pp, int Cs, const double
     for (int j = i; j < NS; ++j, ++p) {
       const double e = 0.5 * (B[i * NS + j] + B[j * NS + i]);  // symmetric up to rounding
       pinv[(size_t)p * Pp + v] = e;
-      pinv32[(size_t)p * Pp + v] = (float)e;
+      const float hi = (float)e;
+      pinvdf[(size_t)p * Pp + v] = make_float2(hi, (float)(e - (double)hi));
+      pinv32[(size_t)p * Pp + v] = hi;
     }
 }
 
@@ -157,6 +161,50 @@ __global__ void __launch_bounds__(kBlock) k_patch_apply(int P, int Pp, int Ppad,
   }
 }
 
+// The FP64 product in float pairs on the FP32 pipes (as the operator): the
+// residual r = b - y (FP64) is scaled by the patch's largest power of two and
+// split, A_p^-1 is read as (hi, lo) pairs, and z is widened back per slot.
+__global__ void __launch_bounds__(kBlock) k_patch_apply_df(int P, int Pp, int Ppad, const int* __restrict__ pdof,
+                                                           const float2* __restrict__ pinv, const double* __restrict__ b,
+                                                           const double* __restrict__ y, double* __restrict__ z,
+                                                           int nb, const int* __restrict__ bnd) {
+  using namespace fe_df;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < P) {
+    int dof[NS];
+    double rd[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      dof[s] = __ldg(pdof + (size_t)s * Pp + v);
+      rd[s] = dof[s] >= 0 ? __ldg(b + dof[s]) - (y ? __ldg(y + dof[s]) : 0.0) : 0.0;
+    }
+    const int emax = block_exponent<NS>(rd);
+    DF r[NS], zz[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      r[s] = split_scaled(rd[s], emax);
+      zz[s] = DF(0.0f);
+    }
+    if (emax == 0x7FF) r[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf residuals
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+      for (int j = i; j < NS; ++j) {
+        const int p = NS * i - i * (i - 1) / 2 + (j - i);
+        const float2 e = __ldg(pinv + (size_t)p * Pp + v);
+        const DF a(e.x, e.y);
+        zz[i] = zz[i] + mul(a, r[j]);
+        if (j != i) zz[j] = zz[j] + mul(a, r[i]);
+      }
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (dof[s] >= 0) atomicAdd(z + dof[s], widen_scaled(zz[s].hi, emax) + widen_scaled(zz[s].lo, emax));
+  } else if (v >= Ppad && v - Ppad < nb) {
+    const int i = bnd[v - Ppad];
+    z[i] = b[i] - (y ? y[i] : 0.0);
+  }
+}
+
 // Chebyshev step with a preconditioned residual z: d = c1 d + c2 z, x += d
 // (first_from_zero: x = d = c2 z).
 template <typename T>
@@ -184,12 +232,14 @@ void launch_patch_setup(Level& L, cudaStream_t s) {
   if (L.pdof.n != (size_t)NS * Pp) {
     L.pdof.alloc((size_t)NS * Pp);
     L.pinv.alloc((size_t)NP * Pp);
+    L.pinvdf.alloc((size_t)NP * Pp);
     L.pinv32.alloc((size_t)NP * Pp);
   }
   DBuf<int> flag;
   flag.alloc(1);
   CUDA_CHECK(cudaMemsetAsync(flag, 0, sizeof(int), s));
-  k_patch_setup<<<ceil_div(P, 128), 128, 0, s>>>(L.num, P, Pp, L.Cs, L.geo64, L.pdof, L.pinv, L.pinv32, flag);
+  k_patch_setup<<<ceil_div(P, 128), 128, 0, s>>>(L.num, P, Pp, L.Cs, L.geo64, L.pdof, L.pinv, L.pinvdf, L.pinv32,
+                                                  flag);
   LAUNCH_CHECK();
   int hflag = 0;
   CUDA_CHECK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -198,11 +248,18 @@ void launch_patch_setup(Level& L, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_patch_apply(const Level& L, const T* b, const T* y, T* z, cudaStream_t s) {
+void launch_patch_apply(const Level& L, const T* b, const T* y, T* z, bool df, cudaStream_t s) {
   const int P = L.V, Pp = (P + 127) / 128 * 128, Ppad = ceil_div(P, kBlock) * kBlock;
   CUDA_CHECK(cudaMemsetAsync(z, 0, sizeof(T) * (size_t)L.n, s));
-  k_patch_apply<T><<<ceil_div((long long)Ppad + L.nb, kBlock), kBlock, 0, s>>>(P, Pp, Ppad, L.pdof, patch_inv<T>(L), b,
-                                                                              y, z, L.nb, L.bnd);
+  const int grid = ceil_div((long long)Ppad + L.nb, kBlock);
+  if constexpr (sizeof(T) == 8) {
+    if (df) {
+      k_patch_apply_df<<<grid, kBlock, 0, s>>>(P, Pp, Ppad, L.pdof, L.pinvdf, b, y, z, L.nb, L.bnd);
+      LAUNCH_CHECK();
+      return;
+    }
+  }
+  k_patch_apply<T><<<grid, kBlock, 0, s>>>(P, Pp, Ppad, L.pdof, patch_inv<T>(L), b, y, z, L.nb, L.bnd);
   LAUNCH_CHECK();
 }
 
@@ -214,7 +271,7 @@ void launch_cheb_pc(int n, const T* z, T* x, T* d, double c1, double c2, bool fi
   LAUNCH_CHECK();
 }
 
-template void launch_patch_apply<double>(const Level&, const double*, const double*, double*, cudaStream_t);
-template void launch_patch_apply<float>(const Level&, const float*, const float*, float*, cudaStream_t);
+template void launch_patch_apply<double>(const Level&, const double*, const double*, double*, bool, cudaStream_t);
+template void launch_patch_apply<float>(const Level&, const float*, const float*, float*, bool, cudaStream_t);
 template void launch_cheb_pc<double>(int, const double*, double*, double*, double, double, bool, bool, cudaStream_t);
 template void launch_cheb_pc<float>(int, const float*, float*, float*, double, double, bool, bool, cudaStream_t);

@@ -36,8 +36,11 @@ def host(t):
 
 @pytest.mark.parametrize("N0", [1, 2, 3])
 @pytest.mark.parametrize("steps", [1, 2, 3])
-def test_patch_smoother_matches_oracle(fe, N0, steps):
+@pytest.mark.parametrize("mode", ["double_float", "native"])
+def test_patch_smoother_matches_oracle(fe, N0, steps, mode):
+    """FP64 patch products in float pairs (default) and in FP64 FMAs, and the FP32 product."""
     with fe.Hierarchy(N0, 1, 2) as h:
+        h.set_f64_mode(fe.FE_F64_NATIVE if mode == "native" else fe.FE_F64_DOUBLE_FLOAT)
         kappa = I.grf_kappa(h.cell_centroids(), seed=3)
         h.set_coefficient(dt(kappa))
         h.set_smoother(fe.FE_SMOOTHER_PATCH)
