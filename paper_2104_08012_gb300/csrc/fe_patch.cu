@@ -7,7 +7,8 @@
 // +-(e_y+e_z), +-(1,1,1)); Dirichlet dofs are left out.  Every patch has these
 // 15 slots (a slot outside the domain or on its boundary is inactive), so the
 // patch data is uniform: slot dofs [15][Pp] and the packed upper triangle of
-// A_p^-1 [120][Pp], one column per vertex (a warp reads consecutive entries).
+// A_p^-1 [120][Pp], one column per vertex (a warp reads consecutive entries;
+// the float-pair copy holds entries 2k and 2k+1 together in [60][Pp] float4).
 // A_p is assembled from the element matrices of the 24 (fewer at the
 // boundary) tets around V and inverted once per coefficient; an inactive slot
 // gets an identity row so that A_p stays invertible and its r and z stay 0.
@@ -121,7 +122,8 @@ __global__ void k_patch_setup(Numbering num, int P, int Pp, int Cs, const double
       const double e = 0.5 * (B[i * NS + j] + B[j * NS + i]);  // symmetric up to rounding
       pinv[(size_t)p * Pp + v] = e;
       const float hi = (float)e;
-      pinvdf[(size_t)p * Pp + v] = make_float2(hi, (float)(e - (double)hi));
+      // float pairs of entries 2k and 2k+1 share one 16-byte slot [k][Pp] (one float4 load)
+      pinvdf[((size_t)(p >> 1) * Pp + v) * 2 + (p & 1)] = make_float2(hi, (float)(e - (double)hi));
       pinv32[(size_t)p * Pp + v] = hi;
     }
 }
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_patch_apply(int P, int Pp, int Ppad,
 // residual r = b - y (FP64) is scaled by the patch's largest power of two and
 // split, A_p^-1 is read as (hi, lo) pairs, and z is widened back per slot.
 __global__ void __launch_bounds__(kBlock) k_patch_apply_df(int P, int Pp, int Ppad, const int* __restrict__ pdof,
-                                                           const float2* __restrict__ pinv, const double* __restrict__ b,
+                                                           const float4* __restrict__ pinv, const double* __restrict__ b,
                                                            const double* __restrict__ y, double* __restrict__ z,
                                                            int nb, const int* __restrict__ bnd) {
   using namespace fe_df;
@@ -186,13 +188,14 @@ __global__ void __launch_bounds__(kBlock) k_patch_apply_df(int P, int Pp, int Pp
       zz[s] = DF(0.0f);
     }
     if (emax == 0x7FF) r[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf residuals
+    float4 e;
 #pragma unroll
     for (int i = 0; i < NS; ++i)
 #pragma unroll
       for (int j = i; j < NS; ++j) {
         const int p = NS * i - i * (i - 1) / 2 + (j - i);
-        const float2 e = __ldg(pinv + (size_t)p * Pp + v);
-        const DF a(e.x, e.y);
+        if ((p & 1) == 0) e = __ldg(pinv + (size_t)(p >> 1) * Pp + v);
+        const DF a = (p & 1) ? DF(e.z, e.w) : DF(e.x, e.y);
         zz[i] = zz[i] + mul(a, r[j]);
         if (j != i) zz[j] = zz[j] + mul(a, r[i]);
       }
@@ -254,7 +257,8 @@ void launch_patch_apply(const Level& L, const T* b, const T* y, T* z, bool df, c
   const int grid = ceil_div((long long)Ppad + L.nb, kBlock);
   if constexpr (sizeof(T) == 8) {
     if (df) {
-      k_patch_apply_df<<<grid, kBlock, 0, s>>>(P, Pp, Ppad, L.pdof, L.pinvdf, b, y, z, L.nb, L.bnd);
+      k_patch_apply_df<<<grid, kBlock, 0, s>>>(P, Pp, Ppad, L.pdof, reinterpret_cast<const float4*>(L.pinvdf.p), b,
+                                               y, z, L.nb, L.bnd);
       LAUNCH_CHECK();
       return;
     }

@@ -21,7 +21,10 @@ def main():
     ap.add_argument("--nrefine", type=int, default=0)
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--f64-mode", type=int, default=None, help="0 native, 1 double-float (best layout), 2 per tet, 3 per cube")
+    ap.add_argument("--f64-mode", type=int, default=None,
+                    help="0 native, 1 double-float (best layout), 2 per tet, 3 per cube, 4 two tets per thread (P2)")
+    ap.add_argument("--smoother", choices=["jacobi", "patch"], default="jacobi",
+                    help="preconditioner of the Chebyshev smoother (--op vcycle)")
     a = ap.parse_args()
     import numpy as np
     import torch
@@ -35,6 +38,8 @@ def main():
     h = fe.Hierarchy(N0, a.nrefine, a.degree)
     if a.f64_mode is not None:
         h.set_f64_mode(a.f64_mode)
+    if a.smoother == "patch":
+        h.set_smoother(fe.FE_SMOOTHER_PATCH)
     n = h.n_dofs()
     x = torch.from_numpy(np.random.default_rng(0).uniform(-1, 1, n)).to("cuda", tdt)
     y = torch.empty_like(x)
