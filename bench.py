@@ -294,6 +294,29 @@ def extras(fe, I, h, dev, stream, flush):
                     "outer": st.outer_iterations, "rel_residual": st.rel_residual,
                     "max_nodal_error_vs_exact": float((u4.cpu() - torch.from_numpy(
                         I.sin_product(h4.dof_coordinates()))).abs().max())}
+    # the paper's solver on P3: full multigrid (1 or 2 V-cycles per level) smoothed by Chebyshev(2) with
+    # vertex-star patches, direct coarse solve; error against the exact solution vs. the discretisation error
+    ue4 = torch.from_numpy(I.sin_product(h4.dof_coordinates()))
+    fmg = {}
+    for sm_name, sm in (("jacobi", fe.FE_SMOOTHER_JACOBI), ("patch", fe.FE_SMOOTHER_PATCH)):
+        h4.set_smoother(sm)
+        for cyc in (1, 2):
+            with torch.cuda.stream(stream):
+                h4.solve(f4, u4, precond=fe.FE_PC_FMG, max_it=cyc, stream=stream)
+                ms = time_launches(lambda: h4.solve(f4, u4, precond=fe.FE_PC_FMG, max_it=cyc, stream=stream),
+                                   stream, 3, flush)
+                st = h4.solve(f4, u4, precond=fe.FE_PC_FMG, max_it=cyc, stream=stream)
+            fmg[f"{sm_name}_{cyc}_cycles"] = {"ms": ms, "rel_residual": st.rel_residual,
+                                              "max_nodal_error_vs_exact": float((u4.cpu() - ue4).abs().max())}
+        with torch.cuda.stream(stream):
+            h4.solve(f4, u4, rtol=1e-8, stream=stream)
+            ms = time_launches(lambda: h4.solve(f4, u4, rtol=1e-8, stream=stream), stream, 3, flush)
+            st = h4.solve(f4, u4, rtol=1e-8, stream=stream)
+        fmg[f"{sm_name}_gmg_pcg_1e-8"] = {"ms": ms, "iterations": st.iterations,
+                                         "max_nodal_error_vs_exact": float((u4.cpu() - ue4).abs().max())}
+    h4.set_smoother(fe.FE_SMOOTHER_JACOBI)
+    p3["paper_solver"] = dict(fmg, what="full multigrid (the paper's outer solver) and GMG-PCG, each with Jacobi "
+                                         "or vertex-star patch (the paper's PatchPC) Chebyshev(2) smoothing")
     out["p3_32cubed"] = p3
     h4.close()
     return out

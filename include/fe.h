@@ -215,9 +215,11 @@ int fe_set_f64_mode(fe_hierarchy* h, int mode);
  * M^-1 r = r on Dirichlet rows (Sec. 3: PatchPC with star patches around
  * vertices as the preconditioner of the level smoother).  The Chebyshev
  * interval becomes [lo, hi] * lambda_max(M^-1 A) (re-estimated here and after
- * every fe_set_coefficient).  P2 builds one 15 x 15 local inverse per vertex
- * (FP64 and FP32 copies); for P1 a star patch is its vertex alone and the
- * patch preconditioner is exactly Jacobi; P3 returns FE_ERR_UNSUPPORTED. */
+ * every fe_set_coefficient).  P2 builds one 15 x 15 local inverse per vertex,
+ * P3 one 65 x 65 (the vertex, the 2 nodes of each of its 14 edges, its 36 face
+ * centroids), in FP64 with float-pair and FP32 copies (P3 at UnitCubeMesh 32^3:
+ * 1.5 GB); for P1 a star patch is its vertex alone and the patch
+ * preconditioner is exactly Jacobi. */
 int fe_set_smoother(fe_hierarchy* h, int smoother);
 
 /* Chebyshev-Jacobi smoothing (Sec. 3: two Chebyshev iterations per level

@@ -340,7 +340,7 @@ static double tridiag_max_eig(const std::vector<double>& a, const std::vector<do
 // Whether level l smooths with the vertex-star patches (P2 levels >= 1; for P1
 // the patches are single vertices and the preconditioner is Jacobi).
 static bool use_patch(const fe_hierarchy* h, int l) {
-  return h->smoother == FE_SMOOTHER_PATCH && h->deg == 2 && l >= 1 && h->L[l].pdof.p;
+  return h->smoother == FE_SMOOTHER_PATCH && h->deg >= 2 && l >= 1 && h->L[l].pdof.p;
 }
 
 // lambda_max(M^-1 A) from the Lanczos tridiagonal of `steps` PCG iterations
@@ -1004,7 +1004,7 @@ static void set_coefficient_impl(fe_hierarchy* h, const double* kappa, cudaStrea
     launch_split_geometry(h->L[l], s);
     launch_diag(h->L[l], h->tmp, s);
   }
-  if (h->smoother == FE_SMOOTHER_PATCH && h->deg == 2)
+  if (h->smoother == FE_SMOOTHER_PATCH && h->deg >= 2)
     for (int l = 1; l < h->nlev; ++l) launch_patch_setup(h->L[l], s);
   for (int l = 0; l < h->nlev; ++l) h->L[l].lmax = estimate_lmax(h, l, 20, s);
   if (h->nlev > 1) coarse_setup(h, s);
@@ -1312,13 +1312,12 @@ int fe_set_smoother(fe_hierarchy* h, int smoother) {
   API_BEGIN
   FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
   FE_REQUIRE(smoother == FE_SMOOTHER_JACOBI || smoother == FE_SMOOTHER_PATCH, FE_ERR_ARG, "unknown smoother");
-  FE_REQUIRE(smoother == FE_SMOOTHER_JACOBI || h->deg <= 2, FE_ERR_UNSUPPORTED,
-             "the vertex-star patch smoother is built for P1/P2");
+
   if (h->smoother != smoother) {
     CUDA_CHECK(cudaDeviceSynchronize());
     cudaStream_t s = 0;
     h->smoother = smoother;
-    if (smoother == FE_SMOOTHER_PATCH && h->deg == 2)
+    if (smoother == FE_SMOOTHER_PATCH && h->deg >= 2)
       for (int l = 1; l < h->nlev; ++l) {
         Level& L = h->L[l];
         launch_patch_setup(L, s);

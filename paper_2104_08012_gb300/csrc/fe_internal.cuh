@@ -334,8 +334,9 @@ void launch_apply_cheb64_cube_df(const Level& L, const double* b, double* x, dou
                                  double c2, bool store_d, cudaStream_t s);
 void launch_build_valence(Level& L, cudaStream_t s);
 void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, double* A, cudaStream_t s);
-// Vertex-star patch smoother (fe_patch.cu)
+// Vertex-star patch smoother (fe_patch.cu; P3 setup in fe_kernels.cu)
 void launch_patch_setup(Level& L, cudaStream_t s);
+void launch_patch_setup_p3(Level& L, cudaStream_t s);
 template <typename T>
 void launch_patch_apply(const Level& L, const T* b, const T* y, T* z, bool df, cudaStream_t s);
 template <typename T>

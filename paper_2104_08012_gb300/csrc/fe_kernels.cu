@@ -1,7 +1,9 @@
 // Cell-loop kernels of the matrix-free operator (paper Section 2, Eq. 4),
 // mass, diagonal, adjoint cell gradient, mesh construction, and the
 // multigrid transfer and smoother vector kernels (paper Section 3).
+#include <array>
 #include <cmath>
+#include <vector>
 #include <type_traits>
 
 #include "fe_internal.cuh"
@@ -17,6 +19,10 @@ __constant__ double c_mref3[400];
 // d_a phi_i d_b phi_j (+ d_b phi_i d_a phi_j for a != b).
 __constant__ double c_K3[210][6];
 __constant__ float c_K3f[210][6];
+// P3 vertex-star patch slots: lattice offsets from 3 V on the 3N lattice of
+// the vertex (0), the two nodes of each of its 14 edges (d, 2 d) and the
+// centroids of its 36 faces (d1 + d2); filled by launch_patch_setup_p3.
+__constant__ int c_p3slot[65][3];
 // Quadrature rule of the load vector (conical-product Gauss, 3 points per
 // direction, FE_QUAD_POINTS = 27 per tet): reference points, weights, basis values.
 __constant__ double c_qxi[FE_QUAD_POINTS][3];
@@ -675,9 +681,188 @@ __global__ void k_coarse_assemble_p3(int C, int Cs, const int* __restrict__ map,
   }
 }
 
+// P3 vertex-star patch: one block per vertex assembles A_p (65 x 65, shared
+// memory) from the element-matrix entries of the tets around V that couple two
+// dofs of V's open star (per tet: V, the 6 nodes of its 3 edges at V, the 3
+// face nodes of its faces at V), gives inactive slots (outside, Dirichlet) an
+// identity row, inverts A_p in place by Gauss-Jordan (SPD: no pivoting) and
+// stores the packed upper triangle patch-major [P][2145] (FP64, float pairs,
+// FP32) for the warp-per-patch product.
+constexpr int kNS3 = 65, kNP3 = kNS3 * (kNS3 + 1) / 2;
+__device__ int p3_slot_of(int dx, int dy, int dz) {
+  for (int s = 0; s < kNS3; ++s)
+    if (c_p3slot[s][0] == dx && c_p3slot[s][1] == dy && c_p3slot[s][2] == dz) return s;
+  return -1;
+}
+
+__global__ void __launch_bounds__(128) k_patch_setup_p3(Numbering num, int P, int Cs, const double* __restrict__ geo64,
+                                                        int* __restrict__ pdof, double* __restrict__ pinv,
+                                                        float2* __restrict__ pinvdf, float* __restrict__ pinv32,
+                                                        int* __restrict__ flag) {
+  __shared__ double A[kNS3][kNS3];
+  __shared__ double fcol[kNS3];
+  __shared__ int sdof[kNS3];
+  __shared__ int bad;
+  const int v = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int N = num.N, n1 = N + 1, m = num.m;
+  const int V[3] = {v % n1, (v / n1) % n1, v / (n1 * n1)};
+  if (tid == 0) bad = 0;
+  for (int sl = tid; sl < kNS3; sl += nt) {
+    const int x = 3 * V[0] + c_p3slot[sl][0], y = 3 * V[1] + c_p3slot[sl][1], z = 3 * V[2] + c_p3slot[sl][2];
+    const bool active = x > 0 && y > 0 && z > 0 && x < m && y < m && z < m;
+    sdof[sl] = active ? lattice_to_dof(num, x, y, z) : -1;
+    pdof[(size_t)v * kNS3 + sl] = sdof[sl];
+  }
+  for (int e = tid; e < kNS3 * kNS3; e += nt) A[e / kNS3][e % kNS3] = 0.0;
+  __syncthreads();
+  // work item: (cube around V, tet, pair of the tet's 10 star dofs)
+  for (int item = tid; item < 8 * 6 * 100; item += nt) {
+    const int c8 = item / 600, t = (item / 100) % 6, pr = item % 100;
+    const int ox = V[0] - 1 + (c8 & 1), oy = V[1] - 1 + ((c8 >> 1) & 1), oz = V[2] - 1 + (c8 >> 2);
+    if (ox < 0 || oy < 0 || oz < 0 || ox >= N || oy >= N || oz >= N) continue;
+    int p0, p1, p2;
+    kuhn_perm(t, p0, p1, p2);
+    int w[4][3] = {{ox, oy, oz}, {ox, oy, oz}, {ox, oy, oz}, {ox + 1, oy + 1, oz + 1}};
+    w[1][p0] += 1;
+    w[2][p0] += 1;
+    w[2][p1] += 1;
+    int a = -1;
+    for (int k = 0; k < 4; ++k)
+      if (w[k][0] == V[0] && w[k][1] == V[1] && w[k][2] == V[2]) a = k;
+    if (a < 0) continue;
+    // the tet's 10 star dofs: local index and lattice offset from 3 V
+    int loc[10], off[10][3], n = 0;
+    loc[n] = a;
+    off[n][0] = off[n][1] = off[n][2] = 0;
+    ++n;
+    for (int b = 0; b < 4; ++b) {
+      if (b == a) continue;
+      const int lo = min(a, b), hi = max(a, b), e = p2_edge(lo, hi) - 4;
+      for (int h = 0; h < 2; ++h) {  // node 4 + 2e + h at (2 - h) w_lo + (1 + h) w_hi
+        loc[n] = 4 + 2 * e + h;
+        for (int d = 0; d < 3; ++d) off[n][d] = (2 - h) * w[lo][d] + (1 + h) * w[hi][d] - 3 * V[d];
+        ++n;
+      }
+    }
+    for (int f = 0; f < 4; ++f) {
+      if (f == a) continue;
+      loc[n] = 16 + f;
+      for (int d = 0; d < 3; ++d)
+        off[n][d] = w[p3_face_vertex(f, 0)][d] + w[p3_face_vertex(f, 1)][d] + w[p3_face_vertex(f, 2)][d] - 3 * V[d];
+      ++n;
+    }
+    const int ii = pr / 10, jj = pr % 10;
+    const int si = p3_slot_of(off[ii][0], off[ii][1], off[ii][2]), sj = p3_slot_of(off[jj][0], off[jj][1], off[jj][2]);
+    if (si < 0 || sj < 0) {
+      atomicOr(flag, 1);
+      continue;
+    }
+    if (sdof[si] < 0 || sdof[sj] < 0) continue;
+    const int lo = min(loc[ii], loc[jj]), hi = max(loc[ii], loc[jj]);
+    const int p = 20 * lo - lo * (lo - 1) / 2 + (hi - lo);
+    const int cell = 6 * (ox + N * (oy + N * oz)) + t;
+    double aij = 0.0;
+    for (int k = 0; k < 6; ++k) aij += geo64[(size_t)k * Cs + cell] * c_K3[p][k];
+    atomicAdd(&A[si][sj], aij);
+  }
+  __syncthreads();
+  for (int sl = tid; sl < kNS3; sl += nt)
+    if (sdof[sl] < 0) A[sl][sl] = 1.0;
+  __syncthreads();
+  for (int k = 0; k < kNS3; ++k) {
+    const double pk = A[k][k];
+    if (!(pk > 0.0)) {  // uniform: every thread reads the same pivot
+      if (tid == 0) atomicOr(flag, 2);
+      return;
+    }
+    __syncthreads();
+    for (int j = tid; j < kNS3; j += nt) A[k][j] = (j == k ? 1.0 : A[k][j]) / pk;
+    for (int i = tid; i < kNS3; i += nt) fcol[i] = i == k ? 0.0 : A[i][k];
+    __syncthreads();
+    for (int e = tid; e < kNS3 * kNS3; e += nt) {
+      const int i = e / kNS3, j = e % kNS3;
+      if (i != k) A[i][j] = (j == k ? 0.0 : A[i][j]) - fcol[i] * A[k][j];
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < kNS3; ++i)
+    for (int j = i + tid; j < kNS3; j += nt) {
+      const int p = kNS3 * i - i * (i - 1) / 2 + (j - i);
+      const double e = 0.5 * (A[i][j] + A[j][i]);
+      const size_t o = (size_t)v * kNP3 + p;
+      pinv[o] = e;
+      const float h = (float)e;
+      pinvdf[o] = make_float2(h, (float)(e - (double)h));
+      pinv32[o] = h;
+    }
+  (void)bad;
+}
+
 }  // namespace
 
 // ===================================================================== host
+void launch_patch_setup_p3(Level& L, cudaStream_t s) {
+  static bool slots = false;
+  if (!slots) {  // the 65 slot offsets of a Kuhn vertex star, from the six tets of the 8 cubes around it
+    int tab[65][3] = {{0, 0, 0}};
+    int ns = 1;
+    std::vector<std::array<int, 3>> edges, faces;
+    auto add = [](std::vector<std::array<int, 3>>& v, std::array<int, 3> d) {
+      for (auto& x : v)
+        if (x == d) return;
+      v.push_back(d);
+    };
+    for (int c8 = 0; c8 < 8; ++c8)
+      for (int t = 0; t < 6; ++t) {
+        const int o[3] = {-1 + (c8 & 1), -1 + ((c8 >> 1) & 1), -1 + (c8 >> 2)};
+        int p0, p1, p2;
+        kuhn_perm(t, p0, p1, p2);
+        int w[4][3] = {{o[0], o[1], o[2]}, {o[0], o[1], o[2]}, {o[0], o[1], o[2]}, {o[0] + 1, o[1] + 1, o[2] + 1}};
+        w[1][p0] += 1;
+        w[2][p0] += 1;
+        w[2][p1] += 1;
+        int a = -1;
+        for (int k = 0; k < 4; ++k)
+          if (w[k][0] == 0 && w[k][1] == 0 && w[k][2] == 0) a = k;
+        if (a < 0) continue;
+        for (int b = 0; b < 4; ++b)
+          if (b != a) add(edges, {w[b][0], w[b][1], w[b][2]});
+        for (int b = 0; b < 4; ++b)
+          for (int c = b + 1; c < 4; ++c)
+            if (b != a && c != a) add(faces, {w[b][0] + w[c][0], w[b][1] + w[c][1], w[b][2] + w[c][2]});
+      }
+    FE_REQUIRE(edges.size() == 14 && faces.size() == 36, FE_ERR_CUDA, "unexpected Kuhn vertex star");
+    for (auto& d : edges) {
+      for (int k = 0; k < 3; ++k) tab[ns][k] = d[k];
+      ++ns;
+      for (int k = 0; k < 3; ++k) tab[ns][k] = 2 * d[k];
+      ++ns;
+    }
+    for (auto& d : faces) {
+      for (int k = 0; k < 3; ++k) tab[ns][k] = d[k];
+      ++ns;
+    }
+    CUDA_CHECK(cudaMemcpyToSymbol(c_p3slot, tab, sizeof(tab)));
+    slots = true;
+  }
+  const int P = L.V;
+  if (L.pdof.n != (size_t)kNS3 * P) {
+    L.pdof.alloc((size_t)kNS3 * P);
+    L.pinv.alloc((size_t)kNP3 * P);
+    L.pinvdf.alloc((size_t)kNP3 * P);
+    L.pinv32.alloc((size_t)kNP3 * P);
+  }
+  DBuf<int> flag;
+  flag.alloc(1);
+  CUDA_CHECK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  k_patch_setup_p3<<<P, 128, 0, s>>>(L.num, P, L.Cs, L.geo64, L.pdof, L.pinv, L.pinvdf, L.pinv32, flag);
+  LAUNCH_CHECK();
+  int hflag = 0;
+  CUDA_CHECK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  FE_REQUIRE(hflag == 0, FE_ERR_CUDA, "P3 patch setup failed (non-positive pivot or unknown star node)");
+}
+
 void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, double* A, cudaStream_t s) {
   k_coarse_assemble_p3<<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, dof2int, nci, A);
   LAUNCH_CHECK();

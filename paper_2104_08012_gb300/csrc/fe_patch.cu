@@ -15,7 +15,10 @@
 // M^-1 r = sum_p R_p^T A_p^-1 R_p r is one thread per patch (gather r = b - y,
 // 120-entry symmetric product, atomic scatter); Dirichlet rows take z = r.
 // The FP64 product runs in float pairs (k_patch_apply_df) unless the
-// hierarchy's FP64 mode is native.
+// hierarchy's FP64 mode is native.  P3 stars hold 65 dofs (the vertex, the 2
+// nodes of each of its 14 edges, its 36 face centroids): a block per patch
+// builds A_p^-1 (k_patch_setup_p3, fe_kernels.cu) and a warp per patch applies
+// it (k_patch_apply_p3).
 #include "fe_df.cuh"
 
 namespace {
@@ -208,6 +211,85 @@ __global__ void __launch_bounds__(kBlock) k_patch_apply_df(int P, int Pp, int Pp
   }
 }
 
+// P3 (65 slots, packed inverse patch-major [P][2145]): one warp per patch.  Each
+// lane owns rows lane, lane + 32 and lane + 64 (< 65); r = b - y is split into
+// float pairs with the warp's largest exponent and shared through shared
+// memory; z_i = sum_j (A_p^-1)_ij r_j reads the packed upper triangle, whose
+// 17 KB per patch the warp streams through L1.  T = double: float-pair
+// arithmetic; T = float: FP32 with the FP32 copy.
+constexpr int NS3 = 65, NP3 = NS3 * (NS3 + 1) / 2, kWarpsP3 = 4;
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarpsP3) k_patch_apply_p3(int P, const int* __restrict__ pdof,
+                                                                  const float2* __restrict__ pinvdf,
+                                                                  const float* __restrict__ pinv32,
+                                                                  const T* __restrict__ b, const T* __restrict__ y,
+                                                                  T* __restrict__ z, int nb,
+                                                                  const int* __restrict__ bnd) {
+  using namespace fe_df;
+  __shared__ float2 rs[kWarpsP3][NS3];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int v = blockIdx.x * kWarpsP3 + wib;
+  const int nwarps = gridDim.x * kWarpsP3;
+  // Dirichlet rows: z = r (a grid-stride loop over all threads)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int k = bnd[i];
+    z[k] = b[k] - (y ? y[k] : T(0));
+  }
+  if (v >= P) return;
+  (void)nwarps;
+  int dof[3];
+  T rr[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int sl = lane + 32 * q;
+    dof[q] = sl < NS3 ? __ldg(pdof + (size_t)v * NS3 + sl) : -1;
+    rr[q] = dof[q] >= 0 ? __ldg(b + dof[q]) - (y ? __ldg(y + dof[q]) : T(0)) : T(0);
+  }
+  int emax = 0;
+  if constexpr (sizeof(T) == 8) {
+    emax = block_exponent<3>(rr);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int sl = lane + 32 * q;
+    if (sl < NS3) {
+      if constexpr (sizeof(T) == 8) {
+        DF d = split_scaled((double)rr[q], emax);
+        if (q == 0 && lane == 0 && emax == 0x7FF) d = DF(__int_as_float(0x7fc00000), 0.0f);
+        rs[wib][sl] = make_float2(d.hi, d.lo);
+      } else {
+        rs[wib][sl] = make_float2((float)rr[q], 0.0f);
+      }
+    }
+  }
+  __syncwarp();
+  const size_t base = (size_t)v * NP3;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int i = lane + 32 * q;
+    if (i >= NS3) continue;
+    if constexpr (sizeof(T) == 8) {
+      DF acc(0.0f);
+      for (int j = 0; j < NS3; ++j) {
+        const int lo = min(i, j), hi = max(i, j);
+        const float2 e = __ldg(pinvdf + base + NS3 * lo - lo * (lo - 1) / 2 + (hi - lo));
+        const float2 r = rs[wib][j];
+        acc = acc + mul(DF(e.x, e.y), DF(r.x, r.y));
+      }
+      if (dof[q] >= 0) atomicAdd(z + dof[q], (T)(widen_scaled(acc.hi, emax) + widen_scaled(acc.lo, emax)));
+    } else {
+      float acc = 0.0f;
+      for (int j = 0; j < NS3; ++j) {
+        const int lo = min(i, j), hi = max(i, j);
+        acc += __ldg(pinv32 + base + NS3 * lo - lo * (lo - 1) / 2 + (hi - lo)) * rs[wib][j].x;
+      }
+      if (dof[q] >= 0) atomicAdd(z + dof[q], (T)acc);
+    }
+  }
+}
+
 // Chebyshev step with a preconditioned residual z: d = c1 d + c2 z, x += d
 // (first_from_zero: x = d = c2 z).
 template <typename T>
@@ -230,7 +312,11 @@ const float* patch_inv<float>(const Level& L) { return L.pinv32; }
 }  // namespace
 
 void launch_patch_setup(Level& L, cudaStream_t s) {
-  FE_REQUIRE(L.deg == 2, FE_ERR_UNSUPPORTED, "the GPU patch setup is for P2 (P1 patches are Jacobi)");
+  if (L.deg == 3) {
+    launch_patch_setup_p3(L, s);
+    return;
+  }
+  FE_REQUIRE(L.deg == 2, FE_ERR_UNSUPPORTED, "the GPU patch setup is for P2/P3 (P1 patches are Jacobi)");
   const int P = L.V, Pp = (P + 127) / 128 * 128;
   if (L.pdof.n != (size_t)NS * Pp) {
     L.pdof.alloc((size_t)NS * Pp);
@@ -254,6 +340,13 @@ template <typename T>
 void launch_patch_apply(const Level& L, const T* b, const T* y, T* z, bool df, cudaStream_t s) {
   const int P = L.V, Pp = (P + 127) / 128 * 128, Ppad = ceil_div(P, kBlock) * kBlock;
   CUDA_CHECK(cudaMemsetAsync(z, 0, sizeof(T) * (size_t)L.n, s));
+  if (L.deg == 3) {  // P3: the FP64 product always in float pairs
+    (void)df;
+    k_patch_apply_p3<T><<<ceil_div(P, kWarpsP3), 32 * kWarpsP3, 0, s>>>(P, L.pdof, L.pinvdf, L.pinv32, b, y, z, L.nb,
+                                                                       L.bnd);
+    LAUNCH_CHECK();
+    return;
+  }
   const int grid = ceil_div((long long)Ppad + L.nb, kBlock);
   if constexpr (sizeof(T) == 8) {
     if (df) {
