@@ -319,6 +319,36 @@ def extras(fe, I, h, dev, stream, flush):
                                          "or vertex-star patch (the paper's PatchPC) Chebyshev(2) smoothing")
     out["p3_32cubed"] = p3
     h4.close()
+    # ---- the paper's Poisson problem at full size: P3 on UnitCubeMesh 128^3 (57,066,625 dofs), 5 levels from 8^3
+    t0 = time.perf_counter()
+    h5 = fe.Hierarchy(8, 4, 3)
+    pw = {"workload": "P3 UnitCubeMesh 128^3 (the paper's Poisson problem), 5 levels from 8^3, f = 3 pi^2 sin sin sin",
+          "dofs": h5.n_dofs(), "cells": h5.n_cells(), "setup_s": time.perf_counter() - t0}
+    X5 = h5.dof_coordinates()
+    f5 = torch.from_numpy(I.sin_product_rhs(X5)).to(dev)
+    ue5 = torch.from_numpy(I.sin_product(X5)).to(dev)
+    del X5
+    u5 = torch.empty_like(f5)
+
+    def run5(name, reps=2, **kw):
+        with torch.cuda.stream(stream):
+            st = h5.solve(f5, u5, stream=stream, **kw)
+            ms = time_launches(lambda: h5.solve(f5, u5, stream=stream, **kw), stream, reps, flush)
+        pw[name] = {"ms": ms, "DoF_per_s": h5.n_dofs() / (ms * 1e-3), "iterations": st.iterations,
+                    "max_nodal_error_vs_exact": float((u5 - ue5).abs().max())}
+
+    run5("jacobi_gmg_pcg_1e-8", rtol=1e-8)
+    run5("mixed_f32_gmg_pcg_1e-8", rtol=1e-8, precision=fe.FE_PREC_MIXED_F32)
+    run5("jacobi_full_multigrid_2_cycles", precond=fe.FE_PC_FMG, max_it=2)
+    t0 = time.perf_counter()
+    h5.set_smoother(fe.FE_SMOOTHER_PATCH)
+    torch.cuda.synchronize()
+    pw["patch_setup_s"] = time.perf_counter() - t0
+    run5("paper_solver_full_multigrid_patch_1_cycle", precond=fe.FE_PC_FMG, max_it=1)
+    run5("paper_solver_full_multigrid_patch_2_cycles", precond=fe.FE_PC_FMG, max_it=2)
+    out["paper_poisson_p3_128cubed"] = pw
+    h5.close()
+    del f5, ue5, u5
     return out
 
 

@@ -217,9 +217,9 @@ int fe_set_f64_mode(fe_hierarchy* h, int mode);
  * interval becomes [lo, hi] * lambda_max(M^-1 A) (re-estimated here and after
  * every fe_set_coefficient).  P2 builds one 15 x 15 local inverse per vertex,
  * P3 one 65 x 65 (the vertex, the 2 nodes of each of its 14 edges, its 36 face
- * centroids), in FP64 with float-pair and FP32 copies (P3 at UnitCubeMesh 32^3:
- * 1.5 GB); for P1 a star patch is its vertex alone and the patch
- * preconditioner is exactly Jacobi. */
+ * centroids), stored in FP64 (P2 only), float pairs and FP32 (P3: 25.7 KB per
+ * vertex, 0.9 GB at UnitCubeMesh 32^3); for P1 a star patch is its vertex
+ * alone and the patch preconditioner is exactly Jacobi. */
 int fe_set_smoother(fe_hierarchy* h, int smoother);
 
 /* Chebyshev-Jacobi smoothing (Sec. 3: two Chebyshev iterations per level

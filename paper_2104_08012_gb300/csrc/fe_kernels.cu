@@ -686,8 +686,8 @@ __global__ void k_coarse_assemble_p3(int C, int Cs, const int* __restrict__ map,
 // dofs of V's open star (per tet: V, the 6 nodes of its 3 edges at V, the 3
 // face nodes of its faces at V), gives inactive slots (outside, Dirichlet) an
 // identity row, inverts A_p in place by Gauss-Jordan (SPD: no pivoting) and
-// stores the packed upper triangle patch-major [P][2145] (FP64, float pairs,
-// FP32) for the warp-per-patch product.
+// stores the packed upper triangle patch-major [P][2145] as float pairs (the
+// FP64 product) and FP32 for the warp-per-patch product.
 constexpr int kNS3 = 65, kNP3 = kNS3 * (kNS3 + 1) / 2;
 __device__ int p3_slot_of(int dx, int dy, int dz) {
   for (int s = 0; s < kNS3; ++s)
@@ -696,9 +696,8 @@ __device__ int p3_slot_of(int dx, int dy, int dz) {
 }
 
 __global__ void __launch_bounds__(128) k_patch_setup_p3(Numbering num, int P, int Cs, const double* __restrict__ geo64,
-                                                        int* __restrict__ pdof, double* __restrict__ pinv,
-                                                        float2* __restrict__ pinvdf, float* __restrict__ pinv32,
-                                                        int* __restrict__ flag) {
+                                                        int* __restrict__ pdof, float2* __restrict__ pinvdf,
+                                                        float* __restrict__ pinv32, int* __restrict__ flag) {
   __shared__ double A[kNS3][kNS3];
   __shared__ double fcol[kNS3];
   __shared__ int sdof[kNS3];
@@ -790,8 +789,7 @@ __global__ void __launch_bounds__(128) k_patch_setup_p3(Numbering num, int P, in
       const int p = kNS3 * i - i * (i - 1) / 2 + (j - i);
       const double e = 0.5 * (A[i][j] + A[j][i]);
       const size_t o = (size_t)v * kNP3 + p;
-      pinv[o] = e;
-      const float h = (float)e;
+      const float h = (float)e;  // P3 products use the float-pair and FP32 copies only
       pinvdf[o] = make_float2(h, (float)(e - (double)h));
       pinv32[o] = h;
     }
@@ -848,14 +846,13 @@ void launch_patch_setup_p3(Level& L, cudaStream_t s) {
   const int P = L.V;
   if (L.pdof.n != (size_t)kNS3 * P) {
     L.pdof.alloc((size_t)kNS3 * P);
-    L.pinv.alloc((size_t)kNP3 * P);
     L.pinvdf.alloc((size_t)kNP3 * P);
     L.pinv32.alloc((size_t)kNP3 * P);
   }
   DBuf<int> flag;
   flag.alloc(1);
   CUDA_CHECK(cudaMemsetAsync(flag, 0, sizeof(int), s));
-  k_patch_setup_p3<<<P, 128, 0, s>>>(L.num, P, L.Cs, L.geo64, L.pdof, L.pinv, L.pinvdf, L.pinv32, flag);
+  k_patch_setup_p3<<<P, 128, 0, s>>>(L.num, P, L.Cs, L.geo64, L.pdof, L.pinvdf, L.pinv32, flag);
   LAUNCH_CHECK();
   int hflag = 0;
   CUDA_CHECK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
