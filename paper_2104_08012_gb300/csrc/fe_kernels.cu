@@ -701,11 +701,9 @@ __global__ void __launch_bounds__(128) k_patch_setup_p3(Numbering num, int P, in
   __shared__ double A[kNS3][kNS3];
   __shared__ double fcol[kNS3];
   __shared__ int sdof[kNS3];
-  __shared__ int bad;
   const int v = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int N = num.N, n1 = N + 1, m = num.m;
   const int V[3] = {v % n1, (v / n1) % n1, v / (n1 * n1)};
-  if (tid == 0) bad = 0;
   for (int sl = tid; sl < kNS3; sl += nt) {
     const int x = 3 * V[0] + c_p3slot[sl][0], y = 3 * V[1] + c_p3slot[sl][1], z = 3 * V[2] + c_p3slot[sl][2];
     const bool active = x > 0 && y > 0 && z > 0 && x < m && y < m && z < m;
@@ -793,7 +791,6 @@ __global__ void __launch_bounds__(128) k_patch_setup_p3(Numbering num, int P, in
       pinvdf[o] = make_float2(h, (float)(e - (double)h));
       pinv32[o] = h;
     }
-  (void)bad;
 }
 
 }  // namespace

@@ -229,14 +229,12 @@ __global__ void __launch_bounds__(32 * kWarpsP3) k_patch_apply_p3(int P, const i
   __shared__ float2 rs[kWarpsP3][NS3];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int v = blockIdx.x * kWarpsP3 + wib;
-  const int nwarps = gridDim.x * kWarpsP3;
   // Dirichlet rows: z = r (a grid-stride loop over all threads)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
     const int k = bnd[i];
     z[k] = b[k] - (y ? y[k] : T(0));
   }
   if (v >= P) return;
-  (void)nwarps;
   int dof[3];
   T rr[3];
 #pragma unroll
