@@ -15,7 +15,9 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["apply", "vcycle", "mass"], default="apply")
+    ap.add_argument("--op", choices=["apply", "vcycle", "mass", "fmg"], default="apply",
+                    help="fmg: one full-multigrid solve of the sin-product problem (the paper's outer solver)")
+    ap.add_argument("--cycles", type=int, default=1, help="V-cycles per level of --op fmg")
     ap.add_argument("--degree", type=int, default=2)
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--nrefine", type=int, default=0)
@@ -41,7 +43,12 @@ def main():
     if a.smoother == "patch":
         h.set_smoother(fe.FE_SMOOTHER_PATCH)
     n = h.n_dofs()
-    x = torch.from_numpy(np.random.default_rng(0).uniform(-1, 1, n)).to("cuda", tdt)
+    if a.op == "fmg":
+        import fe_inputs as I
+        x = torch.from_numpy(I.sin_product_rhs(h.dof_coordinates())).to("cuda", torch.float64)
+        h.solve(x, torch.empty_like(x), precond=fe.FE_PC_FMG, max_it=a.cycles)  # build the graph outside the range
+    else:
+        x = torch.from_numpy(np.random.default_rng(0).uniform(-1, 1, n)).to("cuda", tdt)
     y = torch.empty_like(x)
     s = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]
@@ -53,6 +60,8 @@ def main():
             h.apply_operator(x, y, dtype=dt, stream=s)
         elif a.op == "mass":
             h.apply_mass(x, y, stream=s)
+        elif a.op == "fmg":
+            h.solve(x, y, precond=fe.FE_PC_FMG, max_it=a.cycles, stream=s)
         else:
             h.vcycle(x, y, dtype=dt, stream=s)
         e1.record(s)
