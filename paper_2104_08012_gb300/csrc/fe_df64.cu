@@ -17,15 +17,13 @@
 
 #include "fe_df.cuh"
 #include "fe_df2.cuh"
-
-// P3 reference stiffness coefficients times 3360 (exact integers, |k| <= 1944,
-// so exact in FP32); the 1/3360 is folded into the float-pair geometric factors.
-__constant__ float c_K3i[210][6];
+#include "fe_p3.cuh"
 
 namespace {
 
 using namespace fe_df;
 constexpr int kBlock = 256;
+constexpr int kBlockP3 = 128;
 
 // The dofs whose countdown this thread ended (count returned 1): every other
 // contribution was fenced before its countdown, so after an acquiring fence
@@ -201,46 +199,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df2(int P, int Cs, const in
   }
 }
 
-// sum_k g_k K_k for float-pair g and exact small-integer K (the P3 reference
-// coefficients of pair p): the six leading products summed by TwoSum, their
-// rounding errors (FMA) and the g.lo products gathered in one float.
-__device__ __forceinline__ DF dot6_k3(const DF (&g)[6], int p) {
-  float ph[6], e = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const float K = c_K3i[p][k];
-    ph[k] = __fmul_rn(g[k].hi, K);
-    e = __fadd_rn(e, __fmaf_rn(g[k].lo, K, __fmaf_rn(g[k].hi, K, -ph[k])));
-  }
-  DF s = two_sum(ph[0], ph[1]);
-  float err = s.lo;
-#pragma unroll
-  for (int k = 2; k < 6; ++k) {
-    const DF t = two_sum(s.hi, ph[k]);
-    s.hi = t.hi;
-    err = __fadd_rn(err, t.lo);
-  }
-  return DF(s.hi, __fadd_rn(err, e));
-}
-
-// P3, one tet per thread (persistent grid-stride loop): the element matrix
-// entry of each of the 210 symmetric pairs is formed in float pairs from the
-// geometric factors (kappa G / 3360, split) and the integer coefficients, and
-// applied to both rows.  Row i is a runtime loop (a fully unrolled 210-pair
-// body, 19k instructions, ran out of the instruction cache: "no instruction"
-// stalls dominated); the columns j are unrolled behind warp-uniform tests, so
-// u_j and the column sums stay in registers while u_i comes from shared
-// memory and row i's own sum goes there.  Dofs split and contributions
+// P3, one tet per thread (persistent grid-stride loop): the element through
+// the gradient at the P2 nodes (fe_p3.cuh) in float pairs, on the geometric
+// factors kappa G / 161280 split once per tet; dofs split and contributions
 // widened per tet as in k_apply_df.
-constexpr int kBlockP3 = 128;
-__global__ void __launch_bounds__(kBlockP3, 4) k_apply_df3(int C, int Cs, const int* __restrict__ map,
+__global__ void __launch_bounds__(kBlockP3, 2) k_apply_df3(int C, int Cs, const int* __restrict__ map,
                                                            const float2* __restrict__ geo,
                                                            const double* __restrict__ x, double* __restrict__ y,
                                                            int nb, const int* __restrict__ bnd) {
   constexpr int ND = 20;
-  __shared__ float2 su[ND][kBlockP3], srow[ND][kBlockP3];  // [dof][thread]: conflict-free
-  const int tx = threadIdx.x;
-  const int tid = blockIdx.x * blockDim.x + tx, stride = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   for (int i = tid; i < nb; i += stride) y[bnd[i]] = x[bnd[i]];  // Dirichlet rows: identity
   for (int c = tid; c < C; c += stride) {
     double xv[ND];
@@ -256,36 +224,15 @@ __global__ void __launch_bounds__(kBlockP3, 4) k_apply_df3(int C, int Cs, const 
       g[a] = DF(v.x, v.y);
     }
     const int emax = block_exponent<ND>(xv);
-    DF u[ND], acc[ND];
+    DF u[ND], out[ND];
 #pragma unroll
-    for (int j = 0; j < ND; ++j) {
-      u[j] = split_scaled(xv[j], emax);
-      if (j == 0 && emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
-      su[j][tx] = make_float2(u[j].hi, u[j].lo);
-      acc[j] = DF(0.0f);
-    }
-#pragma unroll 1
-    for (int i = 0; i < ND; ++i) {
-      const float2 t = su[i][tx];
-      const DF ui(t.x, t.y);
-      const int base = 20 * i - i * (i - 1) / 2 - i;  // pair index of (i, j) is base + j
-      DF ai(0.0f);
-#pragma unroll
-      for (int j = 0; j < ND; ++j) {
-        if (j >= i) {
-          const DF a = dot6_k3(g, base + j);
-          ai = ai + mul(a, u[j]);
-          if (j > i) acc[j] = acc[j] + mul(a, ui);
-        }
-      }
-      srow[i][tx] = make_float2(ai.hi, ai.lo);
-    }
+    for (int j = 0; j < ND; ++j) u[j] = split_scaled(xv[j], emax);
+    if (emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
+    fe_p3::p3_element_grad<fe_p3::DFOps>(u, g, out);
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
       const int m = __ldg(map + (size_t)j * Cs + c);
-      const float2 r = srow[j][tx];
-      const DF yj = acc[j] + DF(r.x, r.y);
-      if (m >= 0) atomicAdd(y + m, widen_scaled(yj.hi, emax) + widen_scaled(yj.lo, emax));
+      if (m >= 0) atomicAdd(y + m, widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
     }
   }
 }
@@ -405,8 +352,7 @@ __global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, dou
 }  // namespace
 
 void launch_split_geometry(Level& L, cudaStream_t s) {
-  // P3: the float-pair kernel takes kappa G / 3360 (its coefficients are integers)
-  k_split_geo<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, L.deg == 3 ? 1.0 / 3360.0 : 1.0, L.geodf,
+  k_split_geo<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, 1.0, L.geodf,
                                                        L.detj, L.deg == 1 ? 1.0 / 120.0 : 1.0 / 2520.0, L.massdf);
   LAUNCH_CHECK();
 }
@@ -485,16 +431,11 @@ void launch_apply64_df3(const Level& L, const double* x, double* y, cudaStream_t
   FE_REQUIRE(L.deg == 3, FE_ERR_UNSUPPORTED, "the float-pair P3 kernel needs a degree-3 level");
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
   static int g = 0;
-  if (!g) {  // 4 blocks of 40 KB shared memory per SM: prefer the largest shared-memory carveout
-    CUDA_CHECK(cudaFuncSetAttribute(k_apply_df3, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    g = resident_grid(k_apply_df3, kBlockP3, 1 << 30);
-  }
+  if (!g) g = resident_grid(k_apply_df3, kBlockP3, 1 << 30);
   k_apply_df3<<<std::min(g, ceil_div(std::max(L.C, L.nb), kBlockP3)), kBlockP3, 0, s>>>(L.C, L.Cs, L.map, L.geodf, x,
                                                                                        y, L.nb, L.bnd);
   LAUNCH_CHECK();
 }
-
-void upload_p3_df_table(const float* k3i) { CUDA_CHECK(cudaMemcpyToSymbol(c_K3i, k3i, sizeof(float) * 210 * 6)); }
 
 void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s) {
   apply_cube_df<false>(L, x, y, ChebFuse<double>{}, s);

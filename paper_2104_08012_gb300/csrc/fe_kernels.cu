@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "fe_internal.cuh"
+#include "fe_p3.cuh"
 
 // Reference P1/P2/P3 mass matrices int_ref phi_i phi_j, filled by fe_api.cu.
 __constant__ double c_mref1[16];
@@ -16,9 +17,10 @@ __constant__ double c_mref3[400];
 // local dofs (row-major packed upper triangle), the coefficients of the six
 // components (00, 01, 02, 11, 12, 22) of G = |det J| J^-1 J^-T:
 // A_K[i][j] = kappa_K sum_k G_k c_K3[p][k], with c_K3[p][k] = int_ref
-// d_a phi_i d_b phi_j (+ d_b phi_i d_a phi_j for a != b).
+// d_a phi_i d_b phi_j (+ d_b phi_i d_a phi_j for a != b).  The operator applies
+// the element through the gradient at the P2 nodes (fe_p3.cuh); these entries
+// serve the diagonal, the coarse assembly and the patch matrices.
 __constant__ double c_K3[210][6];
-__constant__ float c_K3f[210][6];
 // P3 vertex-star patch slots: lattice offsets from 3 V on the 3N lattice of
 // the vertex (0), the two nodes of each of its 14 edges (d, 2 d) and the
 // centroids of its 36 faces (d1 + d2); filled by launch_patch_setup_p3.
@@ -39,51 +41,27 @@ __device__ __forceinline__ int decode(int m, bool& bd) {
   return bd ? -1 - m : m;
 }
 
-template <typename T>
-__device__ __forceinline__ T k3(int p, int k);
-template <>
-__device__ __forceinline__ double k3<double>(int p, int k) { return c_K3[p][k]; }
-template <>
-__device__ __forceinline__ float k3<float>(int p, int k) { return c_K3f[p][k]; }
-
-// P3 tet: y = A_K u over the 210 symmetric pairs, each entry formed from the
-// six geometric factors (g = kappa G) and used for both (i, j) and (j, i):
-// 8 FMAs per pair, the reference coefficients read as constant operands.
-template <typename T>
-__device__ __forceinline__ void p3_element(const T* u, const T* g, T* y) {
-#pragma unroll
-  for (int i = 0; i < 20; ++i) y[i] = T(0);
-#pragma unroll
-  for (int i = 0; i < 20; ++i)
-#pragma unroll
-    for (int j = i; j < 20; ++j) {
-      const int p = 20 * i - i * (i - 1) / 2 + (j - i);
-      const T a = g[0] * k3<T>(p, 0) + g[1] * k3<T>(p, 1) + g[2] * k3<T>(p, 2) + g[3] * k3<T>(p, 3) +
-                  g[4] * k3<T>(p, 4) + g[5] * k3<T>(p, 5);
-      y[i] += a * u[j];
-      if (j != i) y[j] += a * u[i];
-    }
-}
-
-// Diagonal entry A_K[i][i] of the P3 element.
+// Diagonal entry A_K[i][i] of the P3 element (g = kappa G / 161280 as stored).
 __device__ __forceinline__ double p3_diag_entry(const double* g, int i) {
   const int p = 20 * i - i * (i - 1) / 2;
-  return g[0] * c_K3[p][0] + g[1] * c_K3[p][1] + g[2] * c_K3[p][2] + g[3] * c_K3[p][3] + g[4] * c_K3[p][4] +
-         g[5] * c_K3[p][5];
+  return 161280.0 * (g[0] * c_K3[p][0] + g[1] * c_K3[p][1] + g[2] * c_K3[p][2] + g[3] * c_K3[p][3] +
+                     g[4] * c_K3[p][4] + g[5] * c_K3[p][5]);
 }
 
 template <int DEG, typename T>
 __device__ __forceinline__ void tet_element(const T* u, const T* g, T* y) {
-  if constexpr (DEG == 3)
-    p3_element<T>(u, g, y);
-  else
+  if constexpr (DEG == 3) {
+    const T gg[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
+    fe_p3::p3_element_grad<fe_p3::PlainOps<T>>(u, gg, y);
+  } else {
     element_apply<DEG, T>(u, g, y);
+  }
 }
 
-// Geometric factors are stored as kappa G / w: w = 6 (P1) and 120 (P2) fold
-// the element formulas' reference integrals; P3 keeps them in c_K3 (w = 1).
+// Geometric factors are stored as kappa G / w: w = 6 (P1), 120 (P2) and
+// 161280 = 64 x 2520 (P3) fold the element formulas' reference integrals.
 template <int DEG>
-__host__ __device__ constexpr double geo_weight() { return DEG == 1 ? 6.0 : DEG == 2 ? 120.0 : 1.0; }
+__host__ __device__ constexpr double geo_weight() { return DEG == 1 ? 6.0 : DEG == 2 ? 120.0 : 161280.0; }
 
 // ------------------------------------------------------ mesh construction
 template <int DEG>
@@ -676,7 +654,7 @@ __global__ void k_coarse_assemble_p3(int C, int Cs, const int* __restrict__ map,
       const int p = 20 * lo - lo * (lo - 1) / 2 + (hi - lo);
       double a = 0.0;
       for (int k = 0; k < 6; ++k) a += g[k] * c_K3[p][k];
-      atomicAdd(A + (size_t)ii[i] * nci + ii[j], a);
+      atomicAdd(A + (size_t)ii[i] * nci + ii[j], 161280.0 * a);  // g = kappa G / 161280
     }
   }
 }
@@ -760,7 +738,7 @@ __global__ void __launch_bounds__(128) k_patch_setup_p3(Numbering num, int P, in
     const int cell = 6 * (ox + N * (oy + N * oz)) + t;
     double aij = 0.0;
     for (int k = 0; k < 6; ++k) aij += geo64[(size_t)k * Cs + cell] * c_K3[p][k];
-    atomicAdd(&A[si][sj], aij);
+    atomicAdd(&A[si][sj], 161280.0 * aij);  // geo64 = kappa G / 161280
   }
   __syncthreads();
   for (int sl = tid; sl < kNS3; sl += nt)
@@ -1214,21 +1192,8 @@ void upload_mass_tables() {
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref1, m1, sizeof(m1)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref2, m2, sizeof(m2)));
   static double K3[210][6], M3[400];
-  static float K3f[210][6];
   p3_tables_host(K3, M3);
-  for (int p = 0; p < 210; ++p)
-    for (int k = 0; k < 6; ++k) K3f[p][k] = (float)K3[p][k];
-  // the coefficients are integers over 3360: exact FP32 copies for the float-pair kernel
-  static float K3i[210][6];
-  for (int p = 0; p < 210; ++p)
-    for (int k = 0; k < 6; ++k) {
-      const double v = K3[p][k] * 3360.0, r = std::nearbyint(v);
-      FE_REQUIRE(std::fabs(v - r) < 1e-8 && std::fabs(r) < (1 << 20), FE_ERR_CUDA, "P3 coefficients are not k/3360");
-      K3i[p][k] = (float)r;
-    }
-  upload_p3_df_table(&K3i[0][0]);
   CUDA_CHECK(cudaMemcpyToSymbol(c_K3, K3, sizeof(K3)));
-  CUDA_CHECK(cudaMemcpyToSymbol(c_K3f, K3f, sizeof(K3f)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref3, M3, sizeof(M3)));
   double xi[FE_QUAD_POINTS][3], w[FE_QUAD_POINTS], p1[FE_QUAD_POINTS][4], p2[FE_QUAD_POINTS][10];
   quad_tables_host(xi, w, p1, p2);
