@@ -35,8 +35,9 @@ WORKLOAD = {"workload": "poisson_p2_unitcube64_gmg4_fp64", "mesh": "UnitCubeMesh
 SAMPLE = {"N0": 8, "nrefine": 2, "degree": 2}  # oracle bounded sample: P2 32^3, 3 levels
 F64_MODE = 1  # FE_F64_DOUBLE_FLOAT: the library default for FP64 operator applications
 # DRAM bytes per launch of the dominant kernel on this workload from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by FP64 mode; None until captured
-TRAFFIC = {0: 188.2e6, 1: 183.6e6, 2: 183.6e6}
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean of 2 launches of the P2 64^3 kernel case,
+# profiles/k_apply_df_p2_64cubed.md), keyed by FP64 mode; None until captured
+TRAFFIC = {0: 182.4e6, 1: 181.9e6, 2: 181.9e6}
 # Arithmetic of one P2 element application (c, d, S, four G-products, transpose),
 # per tet: 151 flops in the FP64 formula (an FMA counts 2).  The float-pair form
 # of the same formula issues 976 FP32 operations (an add, mul or FMA counts 1):
