@@ -424,7 +424,7 @@ template <> float* lv_z<float>(Level& L) { return L.z32; }
 // Consistent mass y = M x in FP64: float-pair arithmetic unless the hierarchy
 // is in native-FP64 mode (the operator's mode decides both).
 static void mass_enqueue(const fe_hierarchy* h, const Level& L, const double* x, double* y, cudaStream_t s) {
-  if (h->f64_mode == FE_F64_NATIVE || L.deg == 3)
+  if (h->f64_mode == FE_F64_NATIVE)
     launch_mass(L, x, y, s);
   else
     launch_mass_df(L, x, y, s);

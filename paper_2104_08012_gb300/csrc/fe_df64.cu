@@ -19,6 +19,10 @@
 #include "fe_df2.cuh"
 #include "fe_p3.cuh"
 
+// P3 reference mass matrix times 26880 (exact integers, |k| <= 432, so exact in
+// FP32); the 1/26880 is folded into the float-pair |det J| factor.
+__constant__ float c_M3i[400];
+
 namespace {
 
 using namespace fe_df;
@@ -334,6 +338,44 @@ __global__ void __launch_bounds__(kBlock) k_mass_df(int C, int Cs, const int* __
   for (int j = 0; j < ND; ++j) atomicAdd(y + idx[j], widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
 }
 
+// P3 consistent mass in float pairs, one tet per thread: (K u)_i with the
+// integer matrix K row by row (a runtime loop over rows keeps the code small;
+// the columns are unrolled), exact products by the integers (TwoProd of the
+// leading term), then times |det J| / 26880; every dof takes part.
+__global__ void __launch_bounds__(kBlock) k_mass_df3(int C, int Cs, const int* __restrict__ map,
+                                                     const float2* __restrict__ mdf, const double* __restrict__ x,
+                                                     double* __restrict__ y) {
+  constexpr int ND = 20;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double xv[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const int m = __ldg(map + (size_t)j * Cs + c);
+    xv[j] = __ldg(x + (m < 0 ? -1 - m : m));
+  }
+  const int emax = block_exponent<ND>(xv);
+  DF u[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) u[j] = split_scaled(xv[j], emax);
+  if (emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
+  const float2 sv = __ldg(mdf + c);
+  const DF sdet(sv.x, sv.y);
+#pragma unroll 1
+  for (int i = 0; i < ND; ++i) {
+    DF acc(0.0f);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const float k = c_M3i[i * ND + j];
+      const float p = __fmul_rn(u[j].hi, k);
+      acc = acc + DF(p, __fmaf_rn(u[j].lo, k, __fmaf_rn(u[j].hi, k, -p)));
+    }
+    const DF yi = mul(sdet, acc);
+    const int m = __ldg(map + (size_t)i * Cs + c);
+    atomicAdd(y + (m < 0 ? -1 - m : m), widen_scaled(yi.hi, emax) + widen_scaled(yi.lo, emax));
+  }
+}
+
 __global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, double gscale,
                             float2* __restrict__ geodf, const double* __restrict__ detj, double wmass,
                             float2* __restrict__ mdf) {
@@ -352,14 +394,19 @@ __global__ void k_split_geo(int C, int Cs, const double* __restrict__ geo64, dou
 }  // namespace
 
 void launch_split_geometry(Level& L, cudaStream_t s) {
-  k_split_geo<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, 1.0, L.geodf,
-                                                       L.detj, L.deg == 1 ? 1.0 / 120.0 : 1.0 / 2520.0, L.massdf);
+  k_split_geo<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(
+      L.C, L.Cs, L.geo64, 1.0, L.geodf, L.detj, L.deg == 1 ? 1.0 / 120.0 : L.deg == 2 ? 1.0 / 2520.0 : 1.0 / 26880.0,
+      L.massdf);
   LAUNCH_CHECK();
 }
 
+void upload_p3_mass_table(const float* m3i) { CUDA_CHECK(cudaMemcpyToSymbol(c_M3i, m3i, sizeof(float) * 400)); }
+
 void launch_mass_df(const Level& L, const double* x, double* y, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
-  if (L.deg == 1)
+  if (L.deg == 3)
+    k_mass_df3<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.massdf, x, y);
+  else if (L.deg == 1)
     k_mass_df<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.massdf, x, y);
   else
     k_mass_df<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.massdf, x, y);

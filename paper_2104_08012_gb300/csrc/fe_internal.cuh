@@ -323,6 +323,7 @@ void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t 
 void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply64_df2(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply64_df3(const Level& L, const double* x, double* y, cudaStream_t s);
+void upload_p3_mass_table(const float* m3i);
 // The same operator kernels with the Chebyshev update fused (y = A x, then
 // d = c1 d + c2 D^-1 (b - y), x += d per dof, in one launch).
 void launch_apply_cheb32(const Level& L, const float* b, float* x, float* y, float* d, double c1, double c2,

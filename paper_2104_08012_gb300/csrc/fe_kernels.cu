@@ -1195,6 +1195,14 @@ void upload_mass_tables() {
   p3_tables_host(K3, M3);
   CUDA_CHECK(cudaMemcpyToSymbol(c_K3, K3, sizeof(K3)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref3, M3, sizeof(M3)));
+  // the P3 mass entries are integers over 26880: exact FP32 copies for the float-pair mass kernel
+  static float M3i[400];
+  for (int i = 0; i < 400; ++i) {
+    const double v = M3[i] * 26880.0, r = std::nearbyint(v);
+    FE_REQUIRE(std::fabs(v - r) < 1e-8 && std::fabs(r) < 4096, FE_ERR_CUDA, "P3 mass entries are not k/26880");
+    M3i[i] = (float)r;
+  }
+  upload_p3_mass_table(M3i);
   double xi[FE_QUAD_POINTS][3], w[FE_QUAD_POINTS], p1[FE_QUAD_POINTS][4], p2[FE_QUAD_POINTS][10];
   quad_tables_host(xi, w, p1, p2);
   CUDA_CHECK(cudaMemcpyToSymbol(c_qxi, xi, sizeof(xi)));

@@ -75,9 +75,12 @@ def test_p3_apply_f64_and_f32(fe, N, coef, mode):
         assert_rowwise(host(y32), L.A @ xd, abs(L.A) @ np.abs(xd), 1e-5, "P3 fp32 apply")
 
 
-def test_p3_mass_and_diagonal(fe):
+@pytest.mark.parametrize("mode", ["double_float", "native"])
+def test_p3_mass_and_diagonal(fe, mode):
+    """P3 mass in float pairs (integer reference matrix, default) and in FP64; the diagonal."""
     N = 3
     with fe.Hierarchy(N, 0, 3) as h:
+        h.set_f64_mode(fe.FE_F64_NATIVE if mode == "native" else fe.FE_F64_DOUBLE_FLOAT)
         kappa = I.grf_kappa(h.cell_centroids(), seed=5)
         h.set_coefficient(dt(kappa))
         L = O.Level(N, 3, kappa)
