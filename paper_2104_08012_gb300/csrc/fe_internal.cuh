@@ -511,11 +511,11 @@ __host__ __device__ inline void p2_element(const T* u, const T* g, T* y) {
   y[9] = four * (b23 + b32);
 }
 
-// P1/P2 element formulas; the P3 element (reference matrices in constant
-// memory) is p3_element in fe_kernels.cu.
+// P1/P2 element formulas; the P3 element (through the gradient at the P2
+// nodes) is fe_p3::p3_element_grad in fe_p3.cuh.
 template <int DEG, typename T>
 __host__ __device__ inline void element_apply(const T* u, const T* g, T* y) {
-  static_assert(DEG == 1 || DEG == 2, "P3 uses p3_element (fe_kernels.cu)");
+  static_assert(DEG == 1 || DEG == 2, "P3 uses fe_p3::p3_element_grad (fe_p3.cuh)");
   if constexpr (DEG == 1)
     p1_element<T>(u, g, y);
   else
