@@ -374,21 +374,21 @@ __global__ void k_diag(int C, int Cs, const int* __restrict__ map, const double*
   double g[6];
 #pragma unroll
   for (int a = 0; a < 6; ++a) g[a] = geo[(size_t)a * Cs + c];
-  if constexpr (DEG == 3) {
+  if constexpr (DEG == 3) {  // straight from the reference coefficients
     for (int i = 0; i < ND; ++i) {
       const int m = map[(size_t)i * Cs + c];
       if (m >= 0) atomicAdd(diag + m, p3_diag_entry(g, i));
     }
-    return;
-  }
-  for (int i = 0; i < ND; ++i) {
-    const int m = map[(size_t)i * Cs + c];
-    if (m < 0) continue;
-    double u[ND], out[ND];
+  } else {  // the element applied to unit vectors
+    for (int i = 0; i < ND; ++i) {
+      const int m = map[(size_t)i * Cs + c];
+      if (m < 0) continue;
+      double u[ND], out[ND];
 #pragma unroll
-    for (int j = 0; j < ND; ++j) u[j] = (j == i) ? 1.0 : 0.0;
-    tet_element<DEG, double>(u, g, out);
-    atomicAdd(diag + m, out[i]);
+      for (int j = 0; j < ND; ++j) u[j] = (j == i) ? 1.0 : 0.0;
+      tet_element<DEG, double>(u, g, out);
+      atomicAdd(diag + m, out[i]);
+    }
   }
 }
 
