@@ -158,9 +158,9 @@ void fe_mesh_destroy(fe_mesh* mesh);
  * Degree 3 (20 dofs per tet, dofs numbered lexicographically on the 3N
  * lattice): the operator applies each tet's element through the gradient at
  * its 10 P2 nodes (677 operations), in float pairs (FP64 default), FP64
- * (FE_F64_NATIVE) or FP32; the bf16 tensor-core operator, the quadrature load
- * vector (FE_RHS_QUAD_F) and the batched solver are P1/P2 only and return
- * FE_ERR_UNSUPPORTED for a degree-3 hierarchy. */
+ * (FE_F64_NATIVE) or FP32; the bf16 tensor-core operator and the batched
+ * solver are P1/P2 only and return FE_ERR_UNSUPPORTED for a degree-3
+ * hierarchy. */
 int fe_hierarchy_refine(const fe_mesh* coarse, int nrefine, int degree, fe_hierarchy** out);
 void fe_hierarchy_destroy(fe_hierarchy* h);
 

@@ -1016,7 +1016,6 @@ static const double* rhs_to_load(fe_hierarchy* h, const double* rhs, int kind, c
   Level& F = h->L[h->nlev - 1];
   const double* rd = stage_in<double>(h, 1, rhs, kind == FE_RHS_QUAD_F ? (size_t)F.C * FE_QUAD_POINTS : F.n, s);
   if (kind == FE_RHS_QUAD_F) {
-    FE_REQUIRE(F.deg <= 2, FE_ERR_UNSUPPORTED, "the quadrature load vector is tabulated for P1/P2");
     launch_load_quadrature(F, rd, h->b, s);
     launch_zero_boundary64(F, h->b, s);
   } else if (kind == FE_RHS_LOAD) {

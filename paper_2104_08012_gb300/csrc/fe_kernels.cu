@@ -31,6 +31,7 @@ __constant__ double c_qxi[FE_QUAD_POINTS][3];
 __constant__ double c_qw[FE_QUAD_POINTS];
 __constant__ double c_qphi1[FE_QUAD_POINTS][4];
 __constant__ double c_qphi2[FE_QUAD_POINTS][10];
+__constant__ double c_qphi3[FE_QUAD_POINTS][20];
 
 namespace {
 
@@ -344,9 +345,19 @@ __global__ void k_quad_points(int C, int Cs, const int* __restrict__ map, const 
 
 // b_i += sum_q w_q |det J| f(x_q) phi_i(xi_q) for the cell's dofs (boundary rows are zeroed afterwards).
 template <int DEG>
+__device__ __forceinline__ double qphi(int q, int i) {
+  if constexpr (DEG == 1)
+    return c_qphi1[q][i];
+  else if constexpr (DEG == 2)
+    return c_qphi2[q][i];
+  else
+    return c_qphi3[q][i];
+}
+
+template <int DEG>
 __global__ void k_load_quad(int C, int Cs, const int* __restrict__ map, const double* __restrict__ detj,
                             const double* __restrict__ fq, double* __restrict__ b) {
-  constexpr int ND = DEG == 1 ? 4 : 10;
+  constexpr int ND = tet_ndof(DEG);
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   double acc[ND];
@@ -356,7 +367,7 @@ __global__ void k_load_quad(int C, int Cs, const int* __restrict__ map, const do
   for (int q = 0; q < FE_QUAD_POINTS; ++q) {
     const double sq = c_qw[q] * dj * __ldg(fq + (size_t)c * FE_QUAD_POINTS + q);
 #pragma unroll
-    for (int i = 0; i < ND; ++i) acc[i] += sq * (DEG == 1 ? c_qphi1[q][i] : c_qphi2[q][i]);
+    for (int i = 0; i < ND; ++i) acc[i] += sq * qphi<DEG>(q, i);
   }
 #pragma unroll
   for (int i = 0; i < ND; ++i) {
@@ -1209,6 +1220,12 @@ void upload_mass_tables() {
   CUDA_CHECK(cudaMemcpyToSymbol(c_qw, w, sizeof(w)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_qphi1, p1, sizeof(p1)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_qphi2, p2, sizeof(p2)));
+  double p3[FE_QUAD_POINTS][20];
+  for (int q = 0; q < FE_QUAD_POINTS; ++q) {
+    double d[20][3];
+    p3_basis_host(xi[q], p3[q], d);
+  }
+  CUDA_CHECK(cudaMemcpyToSymbol(c_qphi3, p3, sizeof(p3)));
 }
 
 void launch_quad_points(const Level& L, double* xyz, cudaStream_t s) {
@@ -1218,10 +1235,9 @@ void launch_quad_points(const Level& L, double* xyz, cudaStream_t s) {
 
 void launch_load_quadrature(const Level& L, const double* fq, double* b, cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(b, 0, sizeof(double) * (size_t)L.n, s));
-  if (L.deg == 1)
-    k_load_quad<1><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, fq, b);
-  else
-    k_load_quad<2><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, fq, b);
+  by_degree(L.deg, [&](auto D) {
+    k_load_quad<D.value><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, fq, b);
+  });
   LAUNCH_CHECK();
 }
 

@@ -220,8 +220,5 @@ def test_p3_unsupported_forms_fail_loudly(fe):
         y = torch.empty_like(x)
         with pytest.raises(fe.FeError):
             h.apply_operator(x, y, dtype=fe.FE_BF16)
-        fq = torch.zeros(h.n_cells() * fe.FE_QUAD_POINTS, dtype=torch.float64, device=DEV)
-        with pytest.raises(fe.FeError):
-            h.load_vector_quadrature(fq, torch.empty(n, dtype=torch.float64, device=DEV))
     with pytest.raises(fe.FeError):
         fe.Batch([(2, 1, 3)])

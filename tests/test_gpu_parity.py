@@ -287,7 +287,7 @@ def test_vcycle_matches_oracle(fe, k):
 
 
 # ---------------------------------------------------- quadrature load vector
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_quadrature_load_vector(fe, k):
     """fe_quadrature_points and fe_load_vector_quadrature against the oracle (points to 1e-15,
     load vector rowwise 1e-13), and a solve with FE_RHS_QUAD_F equals a solve with the assembled

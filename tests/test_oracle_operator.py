@@ -174,21 +174,28 @@ def test_coarsen_kappa_has_eight_children():
 
 
 # ---------------------------------------------------- quadrature load vector
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_quadrature_load_vector_exact_cases(k):
-    """The 27-point rule is exact to degree 3: for f = 1 and for f linear (P_k x f of degree <= 3)
-    the quadrature load vector equals M I_h f on the interior rows (I_h f = f); the points lie
-    inside their cells (barycentric coordinates in [0, 1])."""
+    """The 27-point rule is exact to degree 3: for f = 1 (P_k x f of degree <= 3) and, for P1/P2, f linear the
+    quadrature load vector equals M I_h f on the interior rows (I_h f = f).  For P3 x linear (degree 4) the
+    64-point rule of the same family (exact to degree 5) does.  The points lie inside their cells (barycentric
+    coordinates in [0, 1])."""
     L = O.Level(3, k)
     P = O.quadrature_points(L.space.mesh)
     assert P.shape == (L.space.mesh.n_cells, 27, 3)
     inside = L.space.mesh.coords[L.space.mesh.cells].min(axis=1)[:, None, :] <= P + 1e-15
     assert inside.all()
     X = L.space.coords
-    for f, fx in ((lambda p: np.ones(p.shape[:-1]), np.ones(len(X))),
-                  (lambda p: 0.3 + 2 * p[..., 0] - p[..., 1] + 0.5 * p[..., 2], 0.3 + 2 * X[:, 0] - X[:, 1] + 0.5 * X[:, 2])):
-        b = O.load_vector_quadrature(L, f(P))
+    lin_n = O.QUAD_N if k <= 2 else 4
+    for f, fx, n in ((lambda p: np.ones(p.shape[:-1]), np.ones(len(X)), O.QUAD_N),
+                     (lambda p: 0.3 + 2 * p[..., 0] - p[..., 1] + 0.5 * p[..., 2],
+                      0.3 + 2 * X[:, 0] - X[:, 1] + 0.5 * X[:, 2], lin_n)):
+        b = O.load_vector_quadrature(L, f(O.quadrature_points(L.space.mesh, n)), n)
         assert np.allclose(b, O.load_vector(L, fx), rtol=0, atol=1e-15)
+    if k == 3:
+        # the 27-point rule is not exact for P3 x linear: the pin above really needs the finer rule
+        b27 = O.load_vector_quadrature(L, 0.3 + 2 * P[..., 0] - P[..., 1] + 0.5 * P[..., 2])
+        assert np.abs(b27 - O.load_vector(L, 0.3 + 2 * X[:, 0] - X[:, 1] + 0.5 * X[:, 2])).max() > 1e-10
 
 
 def test_quadrature_load_vector_converges():
