@@ -198,14 +198,15 @@ def test_quadrature_load_vector_exact_cases(k):
         assert np.abs(b27 - O.load_vector(L, 0.3 + 2 * X[:, 0] - X[:, 1] + 0.5 * X[:, 2])).max() > 1e-10
 
 
-def test_quadrature_load_vector_converges():
-    """Solving with the quadrature load vector of the sin-product f converges at the P2 rate."""
+@pytest.mark.parametrize("k", [2, 3])
+def test_quadrature_load_vector_converges(k):
+    """Solving with the quadrature load vector of the sin-product f converges at the P_k rate h^(k+1) in L2."""
     errs = []
     for N in (4, 8):
-        L = O.Level(N, 2)
+        L = O.Level(N, k)
         b = O.load_vector_quadrature(L, I.sin_product_rhs(O.quadrature_points(L.space.mesh).reshape(-1, 3)).reshape(-1, 27))
         errs.append(O.l2_error(L.space, O.direct_solve(L, b), I.sin_product))
-    assert 2.6 <= np.log2(errs[0] / errs[1]) <= 3.4, errs
+    assert k + 0.6 <= np.log2(errs[0] / errs[1]) <= k + 1.4, errs
 
 
 def test_p3_energies_of_polynomials():
