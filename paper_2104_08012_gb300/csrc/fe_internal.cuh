@@ -220,9 +220,10 @@ struct Level {
   // dof's count to zero holds its complete y_i and performs the Chebyshev
   // update of that dof, then restores the count.
   DBuf<unsigned> val_tet, cnt_tet, val_cube, cnt_cube;
-  // Vertex-star patch smoother (P2, levels >= 1, built by fe_set_smoother):
-  // slot dofs [15][Pp], packed A_p^-1 [120][Pp] (FP64 and FP32), and the
-  // preconditioned residuals z of the smoother.
+  // Vertex-star patch smoother (levels >= 1, built by fe_set_smoother), one
+  // patch per vertex.  P2: slot dofs [15][Pp], packed A_p^-1 [120][Pp] (FP64,
+  // float pairs, FP32).  P3: patch-major slot dofs [P][65] and packed A_p^-1
+  // [P][2145] (float pairs, FP32).  z: the preconditioned residuals.
   DBuf<int> pdof;
   DBuf<double> pinv, z64;
   DBuf<float2> pinvdf;  // A_p^-1 as float pairs for the FP64 smoother's float-pair product
