@@ -15,7 +15,7 @@ flushed between steps.
 host cores on a bounded sample of the same workload (P2 UnitCubeMesh 32^3,
 3 levels, same f and rtol), since the paper ships no runnable code.
 
-Multi-GPU (torchrun, N>1): the solve does not shard in this build; every rank
+Multi-GPU (torchrun, N>1): the solve does not shard; every rank
 solves its own replica (weak scaling, no collective on the data path).
 """
 import argparse

@@ -57,7 +57,7 @@ extern "C" {
 #define FE_ERR_NO_CONVERGENCE (-4)  /* the iteration limit was reached before the tolerance */
 #define FE_ERR_NAN (-5)             /* a residual norm became NaN or Inf */
 #define FE_ERR_TIMEOUT (-6)         /* a bounded device-side wait gave up */
-#define FE_ERR_UNSUPPORTED (-7)     /* valid request that this build does not support */
+#define FE_ERR_UNSUPPORTED (-7)     /* valid request that the library does not support */
 
 /* ---- arithmetic types of an operator application ---- */
 #define FE_F64 0   /* vectors double, arithmetic FP64 */
@@ -145,7 +145,7 @@ long long fe_kernel_launches(void);
 
 /* ---- mesh and hierarchy (paper Section 2: UnitCubeMesh, MeshHierarchy, FunctionSpace) ---- */
 
-/* Create UnitCubeMesh(nx, ny, nz).  This build supports cubes only:
+/* Create UnitCubeMesh(nx, ny, nz).  The library supports cubes only:
  * nx == ny == nz >= 1, else FE_ERR_UNSUPPORTED / FE_ERR_ARG.  Host-only. */
 int fe_mesh_create(int nx, int ny, int nz, fe_mesh** out);
 void fe_mesh_destroy(fe_mesh* mesh);

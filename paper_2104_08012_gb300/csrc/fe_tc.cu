@@ -467,7 +467,7 @@ bool bf16_supported() {
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  return major == 10 && minor == 3;  // this build carries sm_103a code only
+  return major == 10 && minor == 3;  // the library carries sm_103a code only
 }
 
 void apply_bf16_enqueue(const Level& L, const float* x, float* y, cudaStream_t s) {
