@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "fe_internal.cuh"
+#include "fe_stencils.h"
 
 void upload_mass_tables();
 void launch_fill64(size_t n, double v, double* p, cudaStream_t s);
@@ -167,90 +168,27 @@ static void build_level_transfer_index(Level& F, const Level& Cc, const Transfer
 }
 
 // -------------------------------------------------- transfer stencils
-// Prolongation class o in [0,2k)^3 of a fine lattice point (position o/(2k)
-// inside its coarse cube): the containing Kuhn tet is found by sorting the
-// position's coordinates, its barycentrics are exact dyadic numbers, and the
-// coarse basis functions of that tet give the stencil weights.
+// The stencils of fe_stencils.h as per-class device tables (FP64 and FP32
+// weights: dyadic with small numerators, so the FP32 copies are exact).
 static void build_transfer_tables(TransferTables& t, int deg) {
-  const int K2 = 2 * deg;
   t.deg = deg;
-  t.n_pro_class = K2 * K2 * K2;
-  t.h_pro_start.assign(1, 0);
+  t.n_pro_class = 8 * deg * deg * deg;
+  t.n_res_class = deg * deg * deg;
+  std::vector<fe_stencil::Entry> pro;
+  fe_stencil::prolongation(deg, t.h_pro_start, pro);
   t.h_pro_off.clear();
   t.h_pro_w.clear();
-  struct Ent { int o[3]; int d[3]; double w; };
-  std::vector<Ent> all;
-  for (int oz = 0; oz < K2; ++oz)
-    for (int oy = 0; oy < K2; ++oy)
-      for (int ox = 0; ox < K2; ++ox) {
-        const int o[3] = {ox, oy, oz};
-        const double s[3] = {ox / (double)K2, oy / (double)K2, oz / (double)K2};
-        int sig[3] = {0, 1, 2};
-        std::stable_sort(sig, sig + 3, [&](int a, int b) { return s[a] > s[b]; });
-        const double lam[4] = {1.0 - s[sig[0]], s[sig[0]] - s[sig[1]], s[sig[1]] - s[sig[2]], s[sig[2]]};
-        int v[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {1, 1, 1}};
-        v[1][sig[0]] = 1;
-        v[2][sig[0]] = 1;
-        v[2][sig[1]] = 1;
-        auto push = [&](const int d[3], double w) {
-          if (w == 0.0) return;
-          t.h_pro_off.push_back(make_int4(d[0], d[1], d[2], 0));
-          t.h_pro_w.push_back(w);
-          all.push_back(Ent{{o[0], o[1], o[2]}, {d[0], d[1], d[2]}, w});
-        };
-        if (deg == 1) {
-          for (int i = 0; i < 4; ++i) push(v[i], lam[i]);
-        } else if (deg == 3) {
-          // barycentrics l/6 with integer l: the P3 basis values are l-polynomials over
-          // powers of two (vertex l(l-2)(l-4)/48, edge l_p l_q (l_p - 2)/16, face
-          // l_a l_b l_c / 8), so the weights and their zeros are exact
-          int sv[3] = {o[0], o[1], o[2]};
-          std::sort(sv, sv + 3, [](int a, int b) { return a > b; });
-          const int l[4] = {K2 - sv[0], sv[0] - sv[1], sv[1] - sv[2], sv[2]};
-          for (int i = 0; i < 4; ++i) {
-            const int d[3] = {3 * v[i][0], 3 * v[i][1], 3 * v[i][2]};
-            push(d, (double)(l[i] * (l[i] - 2) * (l[i] - 4)) / 48.0);
-          }
-          for (int a = 0; a < 4; ++a)
-            for (int b = a + 1; b < 4; ++b)
-              for (int h = 0; h < 2; ++h) {
-                const int pp = h ? b : a, q = h ? a : b;
-                const int d[3] = {2 * v[pp][0] + v[q][0], 2 * v[pp][1] + v[q][1], 2 * v[pp][2] + v[q][2]};
-                push(d, (double)(l[pp] * l[q] * (l[pp] - 2)) / 16.0);
-              }
-          for (int f = 0; f < 4; ++f) {
-            const int a = p3_face_vertex(f, 0), b = p3_face_vertex(f, 1), c = p3_face_vertex(f, 2);
-            const int d[3] = {v[a][0] + v[b][0] + v[c][0], v[a][1] + v[b][1] + v[c][1], v[a][2] + v[b][2] + v[c][2]};
-            push(d, (double)(l[a] * l[b] * l[c]) / 8.0);
-          }
-        } else {
-          for (int i = 0; i < 4; ++i) {
-            const int d[3] = {2 * v[i][0], 2 * v[i][1], 2 * v[i][2]};
-            push(d, lam[i] * (2.0 * lam[i] - 1.0));
-          }
-          for (int a = 0; a < 4; ++a)
-            for (int b = a + 1; b < 4; ++b) {
-              const int d[3] = {v[a][0] + v[b][0], v[a][1] + v[b][1], v[a][2] + v[b][2]};
-              push(d, 4.0 * lam[a] * lam[b]);
-            }
-        }
-        t.h_pro_start.push_back((int)t.h_pro_off.size());
-      }
-  // Restriction: coarse point Lc receives w * r_f(2 Lc + o - 2 d) from every
-  // entry (o, d, w) with d = Lc (mod k); classes indexed by the code
-  // (Lc_x mod k) + k (Lc_y mod k) + k^2 (Lc_z mod k).
-  t.n_res_class = deg * deg * deg;
-  t.h_res_start.assign(1, 0);
+  for (const auto& e : pro) {
+    t.h_pro_off.push_back(make_int4(e.d[0], e.d[1], e.d[2], 0));
+    t.h_pro_w.push_back(e.w);
+  }
+  std::vector<fe_stencil::Tap> res;
+  fe_stencil::restriction(deg, pro, t.h_res_start, res);
   t.h_res_off.clear();
   t.h_res_w.clear();
-  for (int cls = 0; cls < t.n_res_class; ++cls) {
-    for (const Ent& e : all) {
-      const int code = (e.d[0] % deg) + deg * ((e.d[1] % deg) + deg * (e.d[2] % deg));
-      if (code != cls) continue;
-      t.h_res_off.push_back(make_int4(e.o[0] - 2 * e.d[0], e.o[1] - 2 * e.d[1], e.o[2] - 2 * e.d[2], 0));
-      t.h_res_w.push_back(e.w);
-    }
-    t.h_res_start.push_back((int)t.h_res_off.size());
+  for (const auto& r : res) {
+    t.h_res_off.push_back(make_int4(r.off[0], r.off[1], r.off[2], 0));
+    t.h_res_w.push_back(r.w);
   }
   // coarse points with every coordinate in [margin, m - margin] have all their
   // fine points inside the lattice (2 X + o in [0, 2 m] for |o| <= 2 margin)
