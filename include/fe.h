@@ -2,12 +2,14 @@
  * fe.h -- C ABI of the GB300 matrix-free finite element Poisson library.
  *
  * The library solves -div(kappa grad u) = f on the unit cube with Dirichlet
- * conditions on all six faces, discretised with continuous Lagrange P1 or P2
- * elements on a tetrahedral UnitCubeMesh, by conjugate gradients preconditioned
- * with a geometric multigrid V-cycle over a nested mesh hierarchy.  This is the
- * Poisson model problem of the paper (Section 2, Eqs. 1-4: mesh, function
- * space, Dirichlet BCs, right-hand side, bilinear form; Section 3: multigrid
- * with two Chebyshev smoothing iterations per level and a direct coarse solve).
+ * conditions on all six faces, discretised with continuous Lagrange P1, P2 or
+ * P3 elements on a tetrahedral UnitCubeMesh, by conjugate gradients
+ * preconditioned with a geometric multigrid V-cycle over a nested mesh
+ * hierarchy, or by full multigrid.  This is the Poisson model problem of the
+ * paper (Section 2, Eqs. 1-4: mesh, function space, Dirichlet BCs, right-hand
+ * side, bilinear form; Section 3: multigrid with two Chebyshev smoothing
+ * iterations per level, Jacobi or vertex-star patch preconditioned, and a
+ * direct coarse solve).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -35,7 +37,9 @@
  *   vertex order, followed by edge midpoints grouped by the parity class of
  *   their lattice coordinates in the order (1,0,0),(0,1,0),(0,0,1),(1,1,0),
  *   (1,0,1),(0,1,1),(1,1,1); inside a class the sub-lattice (L - parity)/2 is
- *   numbered x fastest.  Use fe_dof_coordinates() to evaluate fields.
+ *   numbered x fastest.  P3 dofs are the points of the 3N lattice numbered
+ *   lexicographically (x fastest).  Use fe_dof_coordinates() to evaluate
+ *   fields.
  * Boundary: a dof is a boundary dof if any lattice coordinate is 0 or kN.  The
  *   operator is the symmetric elimination of the Dirichlet dofs: boundary
  *   rows and columns of A are replaced by the identity.
@@ -242,7 +246,8 @@ int fe_apply_mass(const fe_hierarchy* h, int level, const double* x, double* y, 
 /* diag = diagonal of A_l (boundary entries 1), n_dofs doubles. */
 int fe_diagonal(const fe_hierarchy* h, int level, double* diag, void* stream);
 
-/* Largest eigenvalue estimate of D^-1 A_l used by the Chebyshev smoother. */
+/* Largest eigenvalue estimate of D^-1 A_l (or of M^-1 A_l with the patch
+ * smoother) that scales the Chebyshev interval of `level`. */
 int fe_lambda_max(const fe_hierarchy* h, int level, double* lmax);
 
 /* ---- multigrid components (paper Section 3: MG with Chebyshev smoothing, direct coarse solve) ---- */
@@ -256,9 +261,10 @@ int fe_prolong(const fe_hierarchy* h, int level_fine, const double* xc, double* 
  * fe_prolong).  zero_boundary != 0 sets the coarse boundary entries to 0. */
 int fe_restrict(const fe_hierarchy* h, int level_fine, const double* rf, double* rc, int zero_boundary, void* stream);
 
-/* `steps` Chebyshev iterations for A_l x = b with the Jacobi preconditioner
- * on [cheb_lo, cheb_hi] * lambda_max, starting from x (in/out).  dtype
- * FE_F64 (double vectors) or FE_F32/FE_BF16 (float vectors). */
+/* `steps` Chebyshev iterations for A_l x = b preconditioned as chosen by
+ * fe_set_smoother (Jacobi by default) on [cheb_lo, cheb_hi] * lambda_max,
+ * starting from x (in/out).  dtype FE_F64 (double vectors) or FE_F32/FE_BF16
+ * (float vectors). */
 int fe_smooth(const fe_hierarchy* h, int level, const void* b, void* x, int steps, double cheb_lo, double cheb_hi,
               int dtype, void* stream);
 
@@ -288,10 +294,11 @@ int fe_quadrature_points(const fe_hierarchy* h, double* xyz);
  * the boundary.  FP64 accumulation; host or device pointers. */
 int fe_load_vector_quadrature(const fe_hierarchy* h, const double* f_qp, double* b, void* stream);
 
-/* Solve A u = b on the finest level by PCG (Jacobi or GMG V-cycle), or by
- * FP64 iterative refinement around a reduced-precision GMG-PCG.  rhs:
- * FE_RHS_LOAD or FE_RHS_NODAL_F (see above).  u: in = initial guess
- * (ignored, taken as 0), out = solution.  Synchronises `stream`.  Returns
+/* Solve A u = b on the finest level by PCG (Jacobi or GMG V-cycle), by full
+ * multigrid (FE_PC_FMG), or by FP64 iterative refinement around a
+ * reduced-precision GMG-PCG.  rhs: FE_RHS_LOAD, FE_RHS_NODAL_F or
+ * FE_RHS_QUAD_F (see above).  u: in = initial guess (ignored, taken as 0),
+ * out = solution.  Synchronises `stream`.  Returns
  * FE_ERR_NO_CONVERGENCE if max_it is reached (u holds the last iterate) and
  * FE_ERR_NAN on a non-finite residual.  opts NULL = defaults; stats may be NULL. */
 int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_solver_opts* opts, double* u,
