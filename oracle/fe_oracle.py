@@ -22,12 +22,15 @@ What it computes, written out from the definitions in the paper:
   Section 2 and Section 3) with prolongation = exact interpolation of the coarse
   finite element function at the fine nodes and restriction = its transpose,
   rediscretised coarse operators, Chebyshev smoothing with two iterations per
-  level (the level-smoother options of the paper's FMG listing, here with a
-  Jacobi preconditioner instead of PatchPC), and a direct Cholesky coarse solve
+  level (the level-smoother options of the paper's FMG listing), preconditioned
+  by Jacobi or by additive vertex-star patches with exact local solves (the
+  paper's PatchPC with star patches), and a direct Cholesky coarse solve
   (Section 3 factorises the coarsest level directly);
-* conjugate gradients (Jacobi- or V-cycle-preconditioned), the L2 error against an
-  analytic solution (Section 2 measures the error against the exact solution), and
-  the discrete adjoint gradient dJ/dkappa of J = (u-u_d)^T M (u-u_d).
+* conjugate gradients (Jacobi- or V-cycle-preconditioned), full multigrid as the
+  whole solve (the paper's outer solver), the load vector of f by quadrature, the
+  L2 error against an analytic solution (Section 2 measures the error against the
+  exact solution), and the discrete adjoint gradient dJ/dkappa of
+  J = (u-u_d)^T M (u-u_d).
 
 Readings where the paper is silent (each also listed in the design notes):
 Kuhn 6-tet split of each cube; level l of the hierarchy is the Kuhn mesh of
