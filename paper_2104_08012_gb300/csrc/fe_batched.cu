@@ -23,8 +23,7 @@
 #include <memory>
 
 #include "fe_df.cuh"
-
-void mass_tables_host(double m1[16], double m2[100]);
+#include "fe_reftables.h"
 
 namespace {
 
@@ -774,7 +773,7 @@ int fe_batch_create(int nprob, const int* N0, const int* nrefine, const int* deg
     B->dbar.alloc(1);
     CUDA_CHECK(cudaMemset(B->dsc.p, 0, sizeof(BScal) * nprob));
     double m1[16], m2[100];
-    mass_tables_host(m1, m2);
+    fe_ref::mass_tables(m1, m2);
     B->mref1.alloc(16);
     B->mref2.alloc(100);
     CUDA_CHECK(cudaMemcpy(B->mref1.p, m1, sizeof(m1), cudaMemcpyHostToDevice));

@@ -8,6 +8,7 @@
 
 #include "fe_internal.cuh"
 #include "fe_p3.cuh"
+#include "fe_reftables.h"
 
 // Reference P1/P2/P3 mass matrices int_ref phi_i phi_j, filled by fe_api.cu.
 __constant__ double c_mref1[16];
@@ -1074,136 +1075,15 @@ void launch_random(int n, uint64_t seed, double* v, cudaStream_t s) {
   LAUNCH_CHECK();
 }
 
-// ------------------------------------------------------- mass tables
-// int_ref phi_i phi_j on the reference tet.  Every P1/P2 basis function is a
-// homogeneous polynomial in the barycentrics (P1: lambda_i; P2: lambda_v^2 -
-// sum_{w!=v} lambda_v lambda_w and 4 lambda_a lambda_b), and
-// int_ref lambda^alpha = alpha! / (|alpha| + 3)!.
-static double fact(int k) {
-  double f = 1.0;
-  for (int i = 2; i <= k; ++i) f *= i;
-  return f;
-}
-
-void mass_tables_host(double m1[16], double m2[100]);
-
-// The load vector's rule: Gauss-Legendre with 3 nodes on [0, 1] per direction,
-// collapsed to the reference tet (xi = u, eta = (1-u) v, zeta = (1-u)(1-v) w,
-// weight w_u w_v w_w (1-u)^2 (1-v)), points ordered u slowest, w fastest.
-void quad_tables_host(double xi[FE_QUAD_POINTS][3], double w[FE_QUAD_POINTS], double phi1[FE_QUAD_POINTS][4],
-                      double phi2[FE_QUAD_POINTS][10]) {
-  const double r = std::sqrt(0.6);
-  const double t[3] = {0.5 * (1.0 - r), 0.5, 0.5 * (1.0 + r)};
-  const double wt[3] = {0.5 * 5.0 / 9.0, 0.5 * 8.0 / 9.0, 0.5 * 5.0 / 9.0};
-  int q = 0;
-  for (int iu = 0; iu < 3; ++iu)
-    for (int iv = 0; iv < 3; ++iv)
-      for (int iw = 0; iw < 3; ++iw, ++q) {
-        const double u = t[iu], v = t[iv], ww = t[iw];
-        xi[q][0] = u;
-        xi[q][1] = (1.0 - u) * v;
-        xi[q][2] = (1.0 - u) * (1.0 - v) * ww;
-        w[q] = wt[iu] * wt[iv] * wt[iw] * (1.0 - u) * (1.0 - u) * (1.0 - v);
-        const double lam[4] = {1.0 - xi[q][0] - xi[q][1] - xi[q][2], xi[q][0], xi[q][1], xi[q][2]};
-        for (int k = 0; k < 4; ++k) {
-          phi1[q][k] = lam[k];
-          phi2[q][k] = lam[k] * (2.0 * lam[k] - 1.0);
-        }
-        int e = 4;
-        for (int a = 0; a < 4; ++a)
-          for (int b2 = a + 1; b2 < 4; ++b2) phi2[q][e++] = 4.0 * lam[a] * lam[b2];
-      }
-}
-
-// Gauss-Legendre nodes and weights on [0, 1] (Newton's method on the
-// three-term Legendre recurrence, P_n'(x) = n (x P_n - P_{n-1}) / (x^2 - 1)).
-static void gauss_legendre01(int n, double* t, double* w) {
-  for (int i = 0; i < n; ++i) {
-    double x = std::cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5)), dp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = x;
-      for (int k = 2; k <= n; ++k) {
-        const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      dp = n * (x * p1 - p0) / (x * x - 1.0);
-      const double dx = p1 / dp;
-      x -= dx;
-      if (std::fabs(dx) < 1e-16) break;
-    }
-    t[i] = 0.5 * (x + 1.0);
-    w[i] = 1.0 / ((1.0 - x * x) * dp * dp);  // half the [-1, 1] weight 2 / ((1 - x^2) P_n'(x)^2)
-  }
-}
-
-// P3 Lagrange basis on the reference tet at xi, local order of k_build_map<3>:
-// vertex v: lam (3 lam - 1)(3 lam - 2) / 2; the edge node nearer p on edge
-// (p, q): 9/2 lam_p lam_q (3 lam_p - 1); face (a, b, c): 27 lam_a lam_b lam_c.
-static void p3_basis_host(const double xi[3], double phi[20], double dphi[20][3]) {
-  const double lam[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
-  const double dl[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-  for (int v = 0; v < 4; ++v) {
-    const double L = lam[v];
-    phi[v] = 0.5 * L * (3 * L - 1) * (3 * L - 2);
-    for (int a = 0; a < 3; ++a) dphi[v][a] = 0.5 * (27 * L * L - 18 * L + 2) * dl[v][a];
-  }
-  for (int a = 0; a < 4; ++a)
-    for (int b = a + 1; b < 4; ++b) {
-      const int e = p2_edge(a, b) - 4;
-      for (int h = 0; h < 2; ++h) {
-        const int p = h ? b : a, q = h ? a : b, i = 4 + 2 * e + h;
-        phi[i] = 4.5 * lam[p] * lam[q] * (3 * lam[p] - 1);
-        for (int c = 0; c < 3; ++c)
-          dphi[i][c] = 4.5 * (lam[q] * (6 * lam[p] - 1) * dl[p][c] + lam[p] * (3 * lam[p] - 1) * dl[q][c]);
-      }
-    }
-  for (int f = 0; f < 4; ++f) {
-    const int a = p3_face_vertex(f, 0), b = p3_face_vertex(f, 1), c = p3_face_vertex(f, 2);
-    phi[16 + f] = 27 * lam[a] * lam[b] * lam[c];
-    for (int d = 0; d < 3; ++d)
-      dphi[16 + f][d] = 27 * (lam[b] * lam[c] * dl[a][d] + lam[a] * lam[c] * dl[b][d] + lam[a] * lam[b] * dl[c][d]);
-  }
-}
-
-// Reference P3 stiffness coefficients (see c_K3) and mass matrix, by the
-// conical-product Gauss rule with 5 points per direction (exact to degree 7;
-// the integrands have degree 4 and 6).
-void p3_tables_host(double K[210][6], double M[400]) {
-  double t[5], w[5];
-  gauss_legendre01(5, t, w);
-  for (int p = 0; p < 210; ++p)
-    for (int k = 0; k < 6; ++k) K[p][k] = 0.0;
-  for (int i = 0; i < 400; ++i) M[i] = 0.0;
-  for (int a = 0; a < 5; ++a)
-    for (int b = 0; b < 5; ++b)
-      for (int c = 0; c < 5; ++c) {
-        const double u = t[a], v = t[b], z = t[c];
-        const double xi[3] = {u, (1 - u) * v, (1 - u) * (1 - v) * z};
-        const double wq = w[a] * w[b] * w[c] * (1 - u) * (1 - u) * (1 - v);
-        double phi[20], d[20][3];
-        p3_basis_host(xi, phi, d);
-        for (int i = 0, p = 0; i < 20; ++i)
-          for (int j = i; j < 20; ++j, ++p) {
-            K[p][0] += wq * d[i][0] * d[j][0];
-            K[p][1] += wq * (d[i][0] * d[j][1] + d[i][1] * d[j][0]);
-            K[p][2] += wq * (d[i][0] * d[j][2] + d[i][2] * d[j][0]);
-            K[p][3] += wq * d[i][1] * d[j][1];
-            K[p][4] += wq * (d[i][1] * d[j][2] + d[i][2] * d[j][1]);
-            K[p][5] += wq * d[i][2] * d[j][2];
-          }
-        for (int i = 0; i < 20; ++i)
-          for (int j = 0; j < 20; ++j) M[i * 20 + j] += wq * phi[i] * phi[j];
-      }
-}
-
+// ------------------------------------------------------- reference tables
+// (host code in fe_reftables.h)
 void upload_mass_tables() {
   double m1[16], m2[100];
-  mass_tables_host(m1, m2);
+  fe_ref::mass_tables(m1, m2);
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref1, m1, sizeof(m1)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref2, m2, sizeof(m2)));
   static double K3[210][6], M3[400];
-  p3_tables_host(K3, M3);
+  fe_ref::p3_tables(K3, M3);
   CUDA_CHECK(cudaMemcpyToSymbol(c_K3, K3, sizeof(K3)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_mref3, M3, sizeof(M3)));
   // the P3 mass entries are integers over 26880: exact FP32 copies for the float-pair mass kernel
@@ -1215,16 +1095,12 @@ void upload_mass_tables() {
   }
   upload_p3_mass_table(M3i);
   double xi[FE_QUAD_POINTS][3], w[FE_QUAD_POINTS], p1[FE_QUAD_POINTS][4], p2[FE_QUAD_POINTS][10];
-  quad_tables_host(xi, w, p1, p2);
+  double p3[FE_QUAD_POINTS][20];
+  fe_ref::quad_tables(xi, w, p1, p2, p3);
   CUDA_CHECK(cudaMemcpyToSymbol(c_qxi, xi, sizeof(xi)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_qw, w, sizeof(w)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_qphi1, p1, sizeof(p1)));
   CUDA_CHECK(cudaMemcpyToSymbol(c_qphi2, p2, sizeof(p2)));
-  double p3[FE_QUAD_POINTS][20];
-  for (int q = 0; q < FE_QUAD_POINTS; ++q) {
-    double d[20][3];
-    p3_basis_host(xi[q], p3[q], d);
-  }
   CUDA_CHECK(cudaMemcpyToSymbol(c_qphi3, p3, sizeof(p3)));
 }
 
@@ -1239,45 +1115,6 @@ void launch_load_quadrature(const Level& L, const double* fq, double* b, cudaStr
     k_load_quad<D.value><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.detj, fq, b);
   });
   LAUNCH_CHECK();
-}
-
-void mass_tables_host(double m1[16], double m2[100]) {
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) m1[i * 4 + j] = (i == j ? 2.0 : 1.0) / 120.0;
-  // P2 basis as symmetric quadratic forms Q[i][a][b] in the barycentrics
-  double Q[10][4][4] = {};
-  for (int v = 0; v < 4; ++v) {
-    Q[v][v][v] = 1.0;
-    for (int w = 0; w < 4; ++w)
-      if (w != v) {
-        Q[v][v][w] -= 0.5;
-        Q[v][w][v] -= 0.5;
-      }
-  }
-  for (int a = 0; a < 4; ++a)
-    for (int b = a + 1; b < 4; ++b) {
-      const int e = p2_edge(a, b);
-      Q[e][a][b] = 2.0;
-      Q[e][b][a] = 2.0;
-    }
-  for (int i = 0; i < 10; ++i)
-    for (int j = 0; j < 10; ++j) {
-      double s = 0.0;
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b)
-          for (int c = 0; c < 4; ++c)
-            for (int d = 0; d < 4; ++d) {
-              const double q = Q[i][a][b] * Q[j][c][d];
-              if (q == 0.0) continue;
-              int al[4] = {0, 0, 0, 0};
-              al[a]++;
-              al[b]++;
-              al[c]++;
-              al[d]++;
-              s += q * fact(al[0]) * fact(al[1]) * fact(al[2]) * fact(al[3]) / fact(7);
-            }
-      m2[i * 10 + j] = s;
-    }
 }
 
 namespace {
