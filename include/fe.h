@@ -25,8 +25,11 @@
  *   return before device-side work finishes unless stated otherwise.
  * Ownership: handles are created and owned by the library and released with
  *   the matching *_destroy.  Vectors are owned by the caller.  A hierarchy
- *   holds device workspace; calls on the same hierarchy must not run
- *   concurrently (from several host threads or on several streams at once).
+ *   holds device workspace on the device that was current when it was
+ *   created, which must be current for every call on it; calls on the same
+ *   hierarchy must not run concurrently (from several host threads or on
+ *   several streams at once).  Hierarchies on different devices of one
+ *   process are independent.
  * Mesh: UnitCubeMesh(N,N,N), vertex (i,j,k) at (i,j,k)/N with index
  *   i + (N+1)(j + (N+1)k); cube (ci,cj,ck) has index q = ci + N(cj + N ck) and
  *   is split into the six Kuhn tetrahedra 6q..6q+5 that share its main

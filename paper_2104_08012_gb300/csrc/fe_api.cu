@@ -999,8 +999,17 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
   int dev = 0;
   CUDA_CHECK(cudaGetDevice(&dev));
   CUDA_CHECK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
-  static std::once_flag mass_once;
-  std::call_once(mass_once, upload_mass_tables);
+  {
+    // constant-memory tables live in each device's context: upload them once per device
+    static std::mutex mu;
+    static std::vector<char> uploaded;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= (int)uploaded.size()) uploaded.resize(dev + 1, 0);
+    if (!uploaded[dev]) {
+      upload_mass_tables();
+      uploaded[dev] = 1;
+    }
+  }
   h->N0 = N0;
   h->nlev = nrefine + 1;
   h->deg = degree;

@@ -3,6 +3,7 @@
 // multigrid transfer and smoother vector kernels (paper Section 3).
 #include <array>
 #include <cmath>
+#include <mutex>
 #include <vector>
 #include <type_traits>
 
@@ -787,8 +788,13 @@ __global__ void __launch_bounds__(128) k_patch_setup_p3(Numbering num, int P, in
 
 // ===================================================================== host
 void launch_patch_setup_p3(Level& L, cudaStream_t s) {
-  static bool slots = false;
-  if (!slots) {  // the 65 slot offsets of a Kuhn vertex star, from the six tets of the 8 cubes around it
+  static std::mutex mu;
+  static std::vector<char> uploaded;  // per device: constant memory lives in each device's context
+  int dev = 0;
+  CUDA_CHECK(cudaGetDevice(&dev));
+  std::unique_lock<std::mutex> lock(mu);
+  if (dev >= (int)uploaded.size()) uploaded.resize(dev + 1, 0);
+  if (!uploaded[dev]) {  // the 65 slot offsets of a Kuhn vertex star, from the six tets of the 8 cubes around it
     int tab[65][3] = {{0, 0, 0}};
     int ns = 1;
     std::vector<std::array<int, 3>> edges, faces;
@@ -828,8 +834,9 @@ void launch_patch_setup_p3(Level& L, cudaStream_t s) {
       ++ns;
     }
     CUDA_CHECK(cudaMemcpyToSymbol(c_p3slot, tab, sizeof(tab)));
-    slots = true;
+    uploaded[dev] = 1;
   }
+  lock.unlock();
   const int P = L.V;
   if (L.pdof.n != (size_t)kNS3 * P) {
     L.pdof.alloc((size_t)kNS3 * P);
