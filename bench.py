@@ -107,6 +107,26 @@ def time_launches(fn, stream, reps, flush):
     return ms[len(ms) // 2]
 
 
+def quadrature_rhs_rate(fe, I, hh, nd, dev, stream, flush):
+    """fe_load_vector_quadrature on the finest level of ``hh`` (f given at the 27 points of every tet, b assembled
+    by the one-thread-per-tet kernel): time per call and its algorithmic bytes (f values, map, |det J|, b zero-fill
+    and write) against the measured HBM bandwidth."""
+    import torch
+    C, n = hh.n_cells(), hh.n_dofs()
+    P = hh.quadrature_points()
+    fq = torch.from_numpy(I.sin_product_rhs(P.reshape(-1, 3)).reshape(C, -1)).to(dev)
+    del P
+    b = torch.empty(n, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            hh.load_vector_quadrature(fq, b, stream=stream)
+        ms = time_launches(lambda: hh.load_vector_quadrature(fq, b, stream=stream), stream, 10, flush)
+    byt = C * (fe.FE_QUAD_POINTS * 8 + nd * 4 + 8) + 2 * 8 * n
+    peak, src = hbm_peak()
+    return {"ms": ms, "cells": C, "dofs": n, "algorithmic_bytes": byt, "GB_per_s": byt / (ms * 1e-3) / 1e9,
+            "hbm_frac": byt / (ms * 1e-3) / 1e9 / peak, "hbm_peak_source": src}
+
+
 def extras(fe, I, h, dev, stream, flush):
     """Side measurements: matvec rates, mixed precision (128^3), adjoint (96^3 P1), batched (64 problems)."""
     import numpy as np
@@ -129,6 +149,11 @@ def extras(fe, I, h, dev, stream, flush):
         mv[name] = {"ms": ms, "GDoF_per_s": n / (ms * 1e-3) / 1e9, "GB_per_s": byt / (ms * 1e-3) / 1e9,
                     "hbm_frac": byt / (ms * 1e-3) / 1e9 / peak, "bytes_per_dof": byt / n}
     out["matvec_p2_64cubed"] = dict(mv, hbm_peak_gbs=peak, hbm_peak_source=src)
+    # ---- the load vector by quadrature (f at the 27 points of every tet) on the same level
+    try:
+        out["quadrature_load_vector_p2_64cubed"] = quadrature_rhs_rate(fe, I, h, 10, dev, stream, flush)
+    except Exception as exc:  # a side measurement never stops the others
+        out["quadrature_load_vector_p2_64cubed"] = {"error": repr(exc)[:300]}
     # ---- the benchmark solve with the native FP64 operator, for comparison
     u_n = torch.empty(n, dtype=torch.float64, device=dev)
     f_n = torch.from_numpy(I.sin_product_rhs(h.dof_coordinates())).to(dev)
@@ -280,6 +305,10 @@ def extras(fe, I, h, dev, stream, flush):
         tops = ops_per_cell * C4 / (ms * 1e-3) / 1e12
         p3[name] = {"ms": ms, "GDoF_per_s": n4 / (ms * 1e-3) / 1e9, "element_T_ops_per_s": tops}
     h4.set_f64_mode(F64_MODE)
+    try:
+        p3["quadrature_load_vector"] = quadrature_rhs_rate(fe, I, h4, 20, dev, stream, flush)
+    except Exception as exc:
+        p3["quadrature_load_vector"] = {"error": repr(exc)[:300]}
     p3["element_ops_per_tet"] = ops_per_cell
     p3["apply_f64"]["arithmetic"] = "float pairs on the FP32 pipes (k_apply_df3)"
     p3["apply_f64_native"]["arithmetic"] = "FP64 (k_apply<3, double>)"
