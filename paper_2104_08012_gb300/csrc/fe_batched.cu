@@ -1,6 +1,9 @@
 // Batched GMG-PCG: many independent variable-coefficient Poisson problems on
 // meshes of different sizes (P1 and P2 mixed) solved by ONE persistent
-// cooperative kernel launch, replayed from a captured CUDA graph.
+// cooperative kernel launch, replayed from a captured CUDA graph.  Each is the
+// Poisson problem of the paper's Section 2 (Eqs. 1-4) solved by the
+// multigrid-preconditioned method of Section 3; batching them is an extension
+// beyond the paper.
 //
 // Every problem is an ordinary hierarchy (same setup path as the single
 // solver: maps, geometric factors, Jacobi diagonals, Chebyshev eigenvalue

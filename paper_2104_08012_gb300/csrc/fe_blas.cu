@@ -1,4 +1,6 @@
-// BLAS-1 kernels of conjugate gradients with deterministic grid reductions.
+// BLAS-1 kernels of conjugate gradients (the Krylov solve around the
+// multigrid preconditioner, paper Section 3) with deterministic grid
+// reductions.
 //
 // Every reduction runs on a fixed grid (ReduceCtx::grid blocks): each block
 // reduces its grid-stride slice with warp shuffles, writes one partial, and

@@ -1,4 +1,5 @@
-// FP64-accurate operator application computed on the FP32 pipes.
+// FP64-accurate operator application (the bilinear form of the paper's
+// Section 2, Eq. 4) computed on the FP32 pipes.
 //
 // GB300 issues about 2 FP64 FMAs per clock per SM against 128 FP32 operations,
 // so the FP64 element contraction (124 FP64 instructions per P2 tet) is bound

@@ -1,6 +1,8 @@
 // Internal declarations of the GB300 finite element library: error handling,
 // device buffers, the dof numbering, the per-level device data and the
-// element kernels' arithmetic.  Not part of the public ABI (see include/fe.h).
+// element kernels' arithmetic (the P1/P2 element actions of the bilinear form
+// of the paper's Section 2, Eq. 4).  Not part of the public ABI (see
+// include/fe.h).
 #pragma once
 
 #include <cuda_runtime.h>

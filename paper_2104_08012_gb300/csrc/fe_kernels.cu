@@ -11,7 +11,8 @@
 #include "fe_p3.cuh"
 #include "fe_reftables.h"
 
-// Reference P1/P2/P3 mass matrices int_ref phi_i phi_j, filled by fe_api.cu.
+// Reference P1/P2/P3 mass matrices int_ref phi_i phi_j (fe_reftables.h),
+// uploaded when the first hierarchy is created on each device.
 __constant__ double c_mref1[16];
 __constant__ double c_mref2[100];
 __constant__ double c_mref3[400];

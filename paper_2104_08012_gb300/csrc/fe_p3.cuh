@@ -1,4 +1,5 @@
-// P3 element action through the gradient at the P2 nodes.
+// P3 element action through the gradient at the P2 nodes (degree 3 is the
+// paper's Poisson discretisation, Section 2; the bilinear form is Eq. 4).
 //
 // For u in P3 the reference gradient is quadratic, so it equals its P2
 // interpolant: grad u = sum_n psi_n d_n over the 10 P2 nodes n (vertices, edge

@@ -1,7 +1,8 @@
-// Reference-element tables of the Lagrange P1/P2/P3 bases (host code, no CUDA
-// types): the consistent mass matrices of the reference tet, the reference P3
-// stiffness coefficients, and the quadrature rule of the load vector with the
-// basis values at its points.  fe_kernels.cu uploads them to constant memory.
+// Reference-element tables of the Lagrange P1/P2/P3 bases of the paper's
+// function spaces (Section 2); host code, no CUDA types: the consistent mass
+// matrices of the reference tet, the reference P3 stiffness coefficients, and
+// the quadrature rule of the load vector with the basis values at its points.
+// fe_kernels.cu uploads them to constant memory.
 //
 // Local dof order: vertices 0..3; P2 edges (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)
 // as dofs 4..9; P3 per edge in that order the node nearer its first vertex,

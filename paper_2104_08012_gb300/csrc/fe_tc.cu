@@ -1,4 +1,5 @@
-// bf16 tensor-core operator apply (5th-generation tensor cores: tcgen05 + TMA).
+// bf16 tensor-core operator apply (5th-generation tensor cores: tcgen05 + TMA)
+// of the bilinear form of the paper's Section 2, Eq. 4.
 //
 // The element contraction y_K = sum_p G_p S_p x_K (p over the 6 entries of the
 // symmetric metric G, S_p the reference stiffness tensors, symmetric) is recast
