@@ -430,7 +430,9 @@ static void apply_cheb_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T
   launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, c1, c2, false, s, store_d);
 }
 
-// Chebyshev iterations on level l (same recurrence as the oracle's).
+// Chebyshev iterations on level l (the level smoother of Section 3): the
+// three-term Chebyshev semi-iteration for the preconditioned operator on
+// [lo, hi] * lambda_max, theta = centre, delta = half-width of the interval.
 template <typename T>
 static void smooth_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d, int steps, double lo, double hi,
                            bool x_zero, int dtype, cudaStream_t s) {
