@@ -45,6 +45,9 @@ TRAFFIC = {0: 182.4e6, 1: 181.9e6, 2: 181.9e6}
 # 8 small-integer scalings x 6, 12 power-of-two scalings x 2.
 FLOPS_PER_CELL_P2_F64 = 151
 OPS_PER_CELL_P2_DF = 976
+# Operations of one P3 element application through the gradient at the P2 nodes (fe_p3.cuh; an FMA counts 1):
+# 206 additions, 165 multiplications, 284 FMAs, 22 negations (counted by tests/test_p3_element_host.py)
+OPS_PER_CELL_P3 = 677
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64: 152 SMs x 2 FMA/clk/SM x 2 flops x 2.07 GHz (recipe table)
 FP32_PEAK_TOPS = 40.3  # 152 SMs x 128 FP32 lanes x 1 operation/clk x 2.07 GHz (recipe unit counts and clock)
 
@@ -290,7 +293,7 @@ def extras(fe, I, h, dev, stream, flush):
     h4 = fe.Hierarchy(4, 3, 3)
     n4, C4 = h4.n_dofs(), h4.n_cells()
     p3 = {"workload": "P3 UnitCubeMesh 32^3, 4 levels (coarse 4^3), rtol 1e-8", "dofs": n4, "cells": C4}
-    ops_per_cell = 677  # the element through the gradient at the P2 nodes (fe_p3.cuh), an FMA counting 1
+    ops_per_cell = OPS_PER_CELL_P3  # the element through the gradient at the P2 nodes (fe_p3.cuh)
     for name, dtp, tdt, mode in (("apply_f64", fe.FE_F64, torch.float64, F64_MODE),
                                  ("apply_f64_native", fe.FE_F64, torch.float64, fe.FE_F64_NATIVE),
                                  ("apply_f32", fe.FE_F32, torch.float32, F64_MODE)):

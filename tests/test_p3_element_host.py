@@ -44,3 +44,20 @@ def test_p3_gradient_form_matches_oracle_element_matrices(exe):
     scale = np.einsum("cij,cj->ci", np.abs(A), np.abs(u))
     assert y.shape == ref.shape
     assert np.all(np.abs(y - ref) <= 1e-13 * scale), np.max(np.abs(y - ref) / scale)
+
+
+def test_p3_operation_count_matches_the_benchmark_constant(tmp_path):
+    """The operation count the benchmark's P3 roofline uses (ops per tet) is the formula's own: the element run
+    once with a tallying arithmetic type."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path / "p3_opcount_host")
+    subprocess.check_call([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-O1",
+                           "-I", os.path.join(ROOT, "include"),
+                           "-I", os.path.join(ROOT, "paper_2104_08012_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "host", "p3_opcount_host.cu"), "-o", out])
+    add, mul, fma, neg = map(int, subprocess.run([out], capture_output=True, text=True, check=True).stdout.split())
+    import bench
+    assert add + mul + fma + neg == bench.OPS_PER_CELL_P3 == 677
+    assert (add, mul, fma, neg) == (206, 165, 284, 22)
