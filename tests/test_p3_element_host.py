@@ -1,6 +1,7 @@
 """The library's P3 element formula (gradient at the P2 nodes, fe_p3.cuh) compiled for the host and compared with
 the oracle's P3 element stiffness matrices (conical Gauss quadrature of the physical basis gradients) on the tets
-of a mesh with a random coefficient.  CPU only: nvcc compiles the header as host code."""
+of a mesh with a random coefficient; and the operation counts the benchmark's rooflines use, counted from the P2
+and P3 element formulas themselves.  CPU only: nvcc compiles the headers as host code."""
 import os
 import shutil
 import subprocess
@@ -61,3 +62,20 @@ def test_p3_operation_count_matches_the_benchmark_constant(tmp_path):
     import bench
     assert add + mul + fma + neg == bench.OPS_PER_CELL_P3 == 677
     assert (add, mul, fma, neg) == (206, 165, 284, 22)
+
+
+def test_p2_flop_count_matches_the_benchmark_constant(tmp_path):
+    """The FP64 flop count of the P2 element formula that the benchmark's roofline for the native FP64 operator uses
+    (151 per tet: additions and multiplications, an FMA counting 2) is the formula's own."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path / "p2_opcount_host")
+    subprocess.check_call([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-O1",
+                           "-I", os.path.join(ROOT, "include"),
+                           "-I", os.path.join(ROOT, "paper_2104_08012_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "host", "p2_opcount_host.cu"), "-o", out])
+    add, mul, neg = map(int, subprocess.run([out], capture_output=True, text=True, check=True).stdout.split())
+    import bench
+    assert add + mul == bench.FLOPS_PER_CELL_P2_F64 == 151
+    assert (add, mul, neg) == (95, 56, 4)
