@@ -700,8 +700,11 @@ def direct_solve(level, b):
 
 
 # ------------------------------------------------------------- errors -----
-def l2_error(space, u_h, u_exact, nq=6, chunk=1 << 15):
-    """||u_h - u||_{L2} by the conical-product rule with nq points per direction."""
+def l2_error(space, u_h, u_exact, nq=None, chunk=1 << 15):
+    """||u_h - u||_{L2} by the conical-product rule with nq points per direction (default max(6, k + 4): exact to
+    degree 2 nq - 3 >= 2k + 4 for P_k, beyond the degree 2k of (u_h)^2)."""
+    if nq is None:
+        nq = max(6, space.degree + 4)
     xi, w = tet_quadrature(nq)
     phi, _ = ref_basis(space.degree, xi)
     mesh = space.mesh
