@@ -68,6 +68,18 @@ def test_paper_manufactured_pair():
     assert np.allclose(-lap, I.paper_rhs(X), rtol=1e-5, atol=1e-5)
 
 
+def test_paper_problem_p3_converges_at_h4():
+    """The paper's Poisson problem as it states it (Section 2, Eqs. 2-3: its u and f, P3 as in its script): the
+    discrete solution's L2 error falls at the P3 rate h^4 (N = 4 -> 8)."""
+    errs = []
+    for N in (4, 8):
+        L = O.Level(N, 3)
+        X = L.space.coords
+        u = O.direct_solve(L, O.load_vector(L, I.paper_rhs(X)))
+        errs.append(O.l2_error(L.space, u, I.paper_solution))
+    assert 3.6 <= np.log2(errs[0] / errs[1]) <= 4.4, errs
+
+
 @pytest.mark.parametrize("steps", [1, 2, 3])
 def test_chebyshev_polynomial_identity(steps):
     """x_k - x* = p_k(D^-1 A)(x_0 - x*), p_k(t) = T_k((theta-t)/delta) / T_k(theta/delta)."""
