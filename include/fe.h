@@ -48,6 +48,10 @@
  *   rows and columns of A are replaced by the identity.
  * Coefficient: kappa is one FP64 value per fine cell (NULL means kappa = 1);
  *   coarse levels use the arithmetic mean of the 8 child cells.
+ * Debug checks: with FE_DEBUG_CHECKS=1 in the environment, fe_hierarchy_refine
+ *   also reads every level's tet->dof and cube->dof maps back to the host and
+ *   checks them (dofs in range, Dirichlet encoding consistent with the
+ *   boundary, no dof repeated within a cell), failing with FE_ERR_CUDA.
  */
 #ifndef FE_GB300_H
 #define FE_GB300_H

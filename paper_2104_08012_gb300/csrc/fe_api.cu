@@ -8,10 +8,12 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
 
+#include "fe_checks.h"
 #include "fe_internal.cuh"
 #include "fe_stencils.h"
 
@@ -70,6 +72,16 @@ Numbering make_numbering(int N, int deg) {
 }
 
 // ------------------------------------------------- host pointer staging
+// FE_DEBUG_CHECKS=1 in the environment turns on host-side consistency checks
+// of the device tables (read back once per hierarchy).
+static bool debug_checks() {
+  static const bool on = [] {
+    const char* v = std::getenv("FE_DEBUG_CHECKS");
+    return v != nullptr && v[0] != '\0' && std::strcmp(v, "0") != 0;
+  }();
+  return on;
+}
+
 static bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -1063,6 +1075,17 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     L.bnd.alloc(L.nb);
     CUDA_CHECK(cudaMemcpy(L.bnd, bnd.data(), sizeof(int) * L.nb, cudaMemcpyHostToDevice));
     launch_build_level(L, s);
+    if (debug_checks()) {  // FE_DEBUG_CHECKS=1: bounds and boundary check of both maps on the host
+      CUDA_CHECK(cudaStreamSynchronize(s));
+      const int nq = (degree + 1) * (degree + 1) * (degree + 1);
+      std::vector<int> hm((size_t)std::max(L.nd * (size_t)L.Cs, nq * (size_t)L.Qs));
+      CUDA_CHECK(cudaMemcpy(hm.data(), L.map, sizeof(int) * (size_t)L.nd * L.Cs, cudaMemcpyDeviceToHost));
+      FE_REQUIRE(fe_check::bad_map_entries(hm.data(), L.nd, L.C, L.Cs, L.n, bnd) == 0, FE_ERR_CUDA,
+                 "tet->dof map failed its consistency check");
+      CUDA_CHECK(cudaMemcpy(hm.data(), L.cmap, sizeof(int) * (size_t)nq * L.Qs, cudaMemcpyDeviceToHost));
+      FE_REQUIRE(fe_check::bad_map_entries(hm.data(), nq, L.Q, L.Qs, L.n, bnd) == 0, FE_ERR_CUDA,
+                 "cube->dof map failed its consistency check");
+    }
   }
   build_transfer_tables(h->tt, degree);
   for (int l = 0; l < h->nlev; ++l) {
