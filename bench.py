@@ -11,9 +11,12 @@ reused across right-hand sides).  Metric: solved DoF/s (all (2N+1)^3 dofs)
 per step; steps are timed with CUDA events on the solve's stream, with L2
 flushed between steps.
 
---impl reference times the CPU FP64 oracle (assembled CSR + GMG-PCG) on the
-host cores on a bounded sample of the same workload (P2 UnitCubeMesh 32^3,
-3 levels, same f and rtol), since the paper ships no runnable code.
+--impl reference times the CPU FP64 oracle (assembled CSR + GMG-PCG, the CSR
+products split over the host's cores) on the same workload, since the paper
+ships no runnable code.
+
+--case OP runs one kernel case a few times inside the NVTX range "case" (for
+profilers: ``ncu --nvtx --nvtx-include case/``) and prints its mean time.
 
 Multi-GPU (torchrun, N>1): the solve does not shard; every rank
 solves its own replica (weak scaling, no collective on the data path).
@@ -32,11 +35,14 @@ sys.path.insert(0, ROOT)
 WORKLOAD = {"workload": "poisson_p2_unitcube64_gmg4_fp64", "mesh": "UnitCubeMesh(64,64,64) Kuhn 6-tet",
             "degree": 2, "levels": 4, "coarse_mesh": 8, "cells": 1572864, "dofs": 2146689, "rtol": 1e-8,
             "preconditioner": "GMG V(2,2) Chebyshev-Jacobi + FP64 Cholesky coarse", "l2_between_steps": "flushed"}
-SAMPLE = {"N0": 8, "nrefine": 2, "degree": 2}  # oracle bounded sample: P2 32^3, 3 levels
 F64_MODE = 1  # FE_F64_DOUBLE_FLOAT: the library default for FP64 operator applications
-# DRAM bytes per launch of the dominant kernel on this workload from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, mean of 2 launches of the P2 64^3 kernel case,
-# profiles/k_apply_df_p2_64cubed.md), keyed by FP64 mode; None until captured
+# Algorithmic bytes per dof of one matrix-free application (each array counted once; P2, kappa = 1):
+# x read + y write (8 + 8 in FP64, 4 + 4 in FP32), tet->dof map (0.75 tets/dof x 10 x 4 B = 30 B),
+# vertex coordinates (1/8 vertex per dof x 24 B = 3 B).
+BYTES_PER_DOF_P2 = {"f64": 49.0, "f32": 41.0}
+# DRAM bytes per launch of the FP64 operator kernel on this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the single-kernel P2 64^3 case, mean of 2 launches),
+# keyed by FP64 mode; None where the kernel changed after the last capture.
 TRAFFIC = {0: 182.4e6, 1: 181.9e6, 2: 181.9e6}
 # Arithmetic of one P2 element application (c, d, S, four G-products, transpose),
 # per tet: 151 flops in the FP64 formula (an FMA counts 2).  The float-pair form
@@ -63,6 +69,19 @@ def parse():
     p.add_argument("--host-loop", action="store_true",
                    help="drive the CG iterations from the host in the timed solves (same kernels; for profilers "
                         "that do not follow launches inside conditional graph nodes)")
+    c = p.add_argument_group("single-kernel case (--case): no JSON line, one timing line")
+    c.add_argument("--case", choices=["apply", "vcycle", "mass", "fmg"], default=None,
+                   help="fmg: one full-multigrid solve of the sin-product problem (the paper's outer solver)")
+    c.add_argument("--cycles", type=int, default=1, help="V-cycles per level of --case fmg")
+    c.add_argument("--degree", type=int, default=2)
+    c.add_argument("--N", type=int, default=64)
+    c.add_argument("--nrefine", type=int, default=0)
+    c.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64")
+    c.add_argument("--reps", type=int, default=3)
+    c.add_argument("--f64-mode", type=int, default=None,
+                   help="0 native, 1 float pairs (best layout), 2 per tet, 3 per cube, 4 two tets per thread (P2)")
+    c.add_argument("--smoother", choices=["jacobi", "patch"], default="jacobi",
+                   help="preconditioner of the Chebyshev smoother (--case vcycle)")
     return p.parse_args()
 
 
@@ -80,6 +99,19 @@ def max_over_ranks(values, device=None):
 def job_throughput(units_per_rank, steps, world, total_ms):
     """Whole-job rate: the units every rank processed over the slowest rank's time."""
     return world * units_per_rank * steps / (total_ms * 1e-3)
+
+
+PHASES = ("apply", "smooth", "transfer", "coarse", "blas1")
+
+
+def phase_summary(st):
+    """Per-phase, per-level device time of one profiled solve (ms), from fe_solve_stats."""
+    nl = max(1, st.levels_timed)
+    out = {}
+    for p, name in enumerate(PHASES):
+        per_level = [st.phase_ms[p][l] for l in range(nl)]
+        out[name] = {"total": sum(per_level), "per_level_coarse_to_fine": per_level}
+    return out
 
 
 def hbm_peak():
@@ -149,8 +181,11 @@ def extras(fe, I, h, dev, stream, flush):
                 h.apply_operator(x, y, dtype=dt, stream=stream)
             ms = time_launches(lambda: h.apply_operator(x, y, dtype=dt, stream=stream), stream, 10, flush)
         byt = apply_bytes_per_launch(n, C, 10, vb, gb, cube)
-        mv[name] = {"ms": ms, "GDoF_per_s": n / (ms * 1e-3) / 1e9, "GB_per_s": byt / (ms * 1e-3) / 1e9,
-                    "hbm_frac": byt / (ms * 1e-3) / 1e9 / peak, "bytes_per_dof": byt / n}
+        sb = BYTES_PER_DOF_P2["f64" if vb == 8 else "f32"] * n
+        mv[name] = {"ms": ms, "GDoF_per_s": n / (ms * 1e-3) / 1e9,
+                    "hbm_frac_survey_bytes": sb / (ms * 1e-3) / 1e9 / peak,
+                    "GB_per_s_kernel_bytes": byt / (ms * 1e-3) / 1e9,
+                    "hbm_frac_kernel_bytes": byt / (ms * 1e-3) / 1e9 / peak, "kernel_bytes_per_dof": byt / n}
     out["matvec_p2_64cubed"] = dict(mv, hbm_peak_gbs=peak, hbm_peak_source=src)
     # ---- the load vector by quadrature (f at the 27 points of every tet) on the same level
     try:
@@ -223,8 +258,14 @@ def extras(fe, I, h, dev, stream, flush):
             h2.apply_operator(x32, y32, dtype=fe.FE_F32, stream=stream)
         ms = time_launches(lambda: h2.apply_operator(x32, y32, dtype=fe.FE_F32, stream=stream), stream, 10, flush)
     byt = apply_bytes_per_launch(n2, h2.n_cells(), 10, 4, 4, cube_map=True)
-    out["matvec_p2_128cubed_f32"] = {"ms": ms, "GDoF_per_s": n2 / (ms * 1e-3) / 1e9, "GB_per_s": byt / (ms * 1e-3) / 1e9,
-                                     "hbm_frac": byt / (ms * 1e-3) / 1e9 / peak, "bytes_per_dof": byt / n2,
+    sb = BYTES_PER_DOF_P2["f32"] * n2
+    out["matvec_p2_128cubed_f32"] = {"ms": ms, "GDoF_per_s": n2 / (ms * 1e-3) / 1e9,
+                                     "hbm_frac_survey_bytes": sb / (ms * 1e-3) / 1e9 / peak,
+                                     "survey_bytes_per_dof": BYTES_PER_DOF_P2["f32"],
+                                     "kernel_bytes_per_dof": byt / n2, "GB_per_s_kernel_bytes": byt / (ms * 1e-3) / 1e9,
+                                     "hbm_frac_kernel_bytes": byt / (ms * 1e-3) / 1e9 / peak,
+                                     "kernel_bytes_model": "x 4 + y zero-fill and write 8 + cube->dof map 27 x 4 per "
+                                                           "cube + per-tet geometric factors 6 x 4 per tet",
                                      "hbm_peak_gbs": peak, "hbm_peak_source": src}
     del x32, y32
     for name, prec in (("f64", fe.FE_PREC_F64), ("mixed_f32", fe.FE_PREC_MIXED_F32),
@@ -429,58 +470,155 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ cpu oracle
+# The oracle runs in its own interpreter (started before this process touches
+# the GPU): it builds the benchmark's hierarchy (assembled CSR on every level,
+# prolongations, Lanczos estimates, coarse Cholesky), then waits for one line
+# on stdin before its timed solves, so that its set-up overlaps the GPU run
+# and its solves do not share the host with it.
 ORACLE_SNIPPET = r"""
-import json, sys, time
+import json, os, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
+from oracle import build_oracle
+build_oracle.build()
 from oracle import fe_oracle as O
 import fe_inputs as I
 N0, nref, k, steps = {N0}, {nref}, {k}, {steps}
+cores = O.THREADS
 t0 = time.time()
 h = O.Hierarchy(N0, nref, k)
 L = h.fine
 b = O.load_vector(L, I.sin_product_rhs(L.space.coords))
 setup = time.time() - t0
+print(json.dumps({{"ready": True, "setup_s": setup}}), flush=True)
+sys.stdin.readline()
 times, its = [], []
 for s in range(steps):
     t = time.time()
     u, it, hist = O.solve(h, b, rtol=1e-8)
     times.append(time.time() - t)
     its.append(it)
+rel_res = hist[-1]
+err = float(np.abs(u - I.sin_product(L.space.coords)).max())
+# one more solve with the CSR products on a single thread
+O.THREADS = 1
+t = time.time()
+O.solve(h, b, rtol=1e-8)
+t1 = time.time() - t
+O.THREADS = cores
 # the assembled fine-level CSR product alone (the oracle's operator application)
 x = I.random_vector(L.n, 1)
-t = time.time()
-for _ in range(20):
-    y = L.A @ x
-spmv = (time.time() - t) / 20
-print(json.dumps({{"n": int(L.n), "setup_s": setup, "times": times, "iterations": its, "rel_res": hist[-1],
-                  "spmv_s": spmv, "nnz": int(L.A.nnz)}}))
+spmv = {{}}
+for th in (cores, 1):
+    O.matvec(L.A, x, threads=th)
+    t = time.time()
+    for _ in range(10):
+        O.matvec(L.A, x, threads=th)
+    spmv[th] = (time.time() - t) / 10
+print(json.dumps({{"n": int(L.n), "setup_s": setup, "times": times, "iterations": its, "rel_res": rel_res,
+                  "max_nodal_error_vs_exact": err, "time_1thread": t1, "spmv_s": spmv[cores],
+                  "spmv_1thread_s": spmv[1], "nnz": int(L.A.nnz), "cores": cores,
+                  "threaded_products": O._csr_lib() is not None}}))
 """
 
 
-def run_oracle(steps):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET.format(root=ROOT, N0=SAMPLE["N0"], nref=SAMPLE["nrefine"], k=SAMPLE["degree"], steps=steps)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+class OracleRun:
+    """The oracle on the benchmark's own workload in a subprocess; ``start`` before any GPU work."""
+
+    def __init__(self, steps):
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env.pop(k, None)
+        code = ORACLE_SNIPPET.format(root=ROOT, N0=WORKLOAD["coarse_mesh"], nref=WORKLOAD["levels"] - 1,
+                                     k=WORKLOAD["degree"], steps=steps)
+        self.proc = subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+                                     stderr=subprocess.PIPE, text=True, env=env)
+
+    def result(self, timeout=1800):
+        """Wait for the set-up, release the timed solves and return their record."""
+        p = self.proc
+        try:
+            line = p.stdout.readline()
+            if not line:
+                raise RuntimeError(p.stderr.read()[-2000:])
+            p.stdin.write("go\n")
+            p.stdin.flush()
+            out, err = p.communicate(timeout=timeout)
+        except Exception:
+            p.kill()
+            raise
+        if p.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        return json.loads(out.strip().splitlines()[-1])
 
 
 def oracle_details(r):
-    """Setup time, iterations and the CSR operator product rate of the oracle sample."""
-    return {"setup_s": r["setup_s"], "iterations": r["iterations"][-1],
-            "csr_spmv_dof_per_s": r["n"] / r["spmv_s"], "csr_nnz": r["nnz"]}
+    """Set-up time, iterations, 1-thread solve and the CSR operator product rates of the oracle run."""
+    return {"setup_s": r["setup_s"], "iterations": r["iterations"][-1], "rel_residual": r["rel_res"],
+            "max_nodal_error_vs_exact": r["max_nodal_error_vs_exact"],
+            "value_1thread": r["n"] / r["time_1thread"], "cores_1thread": 1,
+            "csr_spmv_dof_per_s": r["n"] / r["spmv_s"], "csr_spmv_dof_per_s_1thread": r["n"] / r["spmv_1thread_s"],
+            "csr_nnz": r["nnz"], "host_cores_in_affinity": r["cores"]}
 
 
 def sample_desc(r):
-    return (f"oracle GMG-PCG solve (assembled CSR, scipy SpMV) of the same problem on P2 UnitCubeMesh "
-            f"{SAMPLE['N0'] << SAMPLE['nrefine']}^3 ({r['n']} dofs, {SAMPLE['nrefine'] + 1} levels), rtol 1e-8, "
-            f"{len(r['times'])} solve(s), setup {r['setup_s']:.1f}s excluded")
+    thr = (f"CSR products on {r['cores']} OpenMP threads (the rest numpy/scipy, one thread)"
+           if r["threaded_products"] else "scipy CSR products on one thread")
+    return (f"oracle GMG-PCG solve of the benchmark workload itself (P2 UnitCubeMesh 64^3, {r['n']} dofs, 4 levels, "
+            f"assembled CSR), rtol 1e-8, {len(r['times'])} timed solve(s), set-up {r['setup_s']:.0f} s excluded; "
+            f"{thr}")
+
+
+# --------------------------------------------------------------- case
+def run_case(a):
+    """One kernel case a few times on a single mesh (or hierarchy) inside the NVTX range "case"."""
+    import numpy as np
+    import torch
+
+    from paper_2104_08012_gb300 import build as _build
+    _build.build()
+    import paper_2104_08012_gb300 as fe
+    dt = {"f64": fe.FE_F64, "f32": fe.FE_F32, "bf16": fe.FE_BF16}[a.dtype]
+    tdt = torch.float64 if a.dtype == "f64" else torch.float32
+    N0 = a.N >> a.nrefine
+    h = fe.Hierarchy(N0, a.nrefine, a.degree)
+    if a.f64_mode is not None:
+        h.set_f64_mode(a.f64_mode)
+    if a.smoother == "patch":
+        h.set_smoother(fe.FE_SMOOTHER_PATCH)
+    n = h.n_dofs()
+    if a.case == "fmg":
+        import fe_inputs as I
+        x = torch.from_numpy(I.sin_product_rhs(h.dof_coordinates())).to("cuda", torch.float64)
+        h.solve(x, torch.empty_like(x), precond=fe.FE_PC_FMG, max_it=a.cycles)  # build the graph outside the range
+    else:
+        x = torch.from_numpy(np.random.default_rng(0).uniform(-1, 1, n)).to("cuda", tdt)
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("case")
+    for e0, e1 in evs:
+        e0.record(s)
+        if a.case == "apply":
+            h.apply_operator(x, y, dtype=dt, stream=s)
+        elif a.case == "mass":
+            h.apply_mass(x, y, stream=s)
+        elif a.case == "fmg":
+            h.solve(x, y, precond=fe.FE_PC_FMG, max_it=a.cycles, stream=s)
+        else:
+            h.vcycle(x, y, dtype=dt, stream=s)
+        e1.record(s)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    print(f"{a.case} P{a.degree} N={a.N} {a.dtype}: n={n} cells={h.n_cells()} ms/launch={np.mean(ms):.4f} "
+          f"(min {np.min(ms):.4f})")
+    h.close()
 
 
 # --------------------------------------------------------------- ours
-def run_ours(args, rank, world, local_rank):
+def run_ours(args, rank, world, local_rank, oracle=None):
     import numpy as np
     import torch
 
@@ -549,11 +687,11 @@ def run_ours(args, rank, world, local_rank):
     te_ms = sum(a.elapsed_time(b) for a, b in eve)
     # operator-apply durations for the roofline: the same solves with CUDA events around
     # every fine-level application (host-driven CG loop), after the timed region
-    stats = []
+    pstats = []
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
-            stats.append(step(f, u, opts_prof))
+            pstats.append(step(f, u, opts_prof))
     torch.cuda.synchronize()
     # correctness of the last solve: relative residual reported by the FP64 recurrence and an
     # independent check of the error against the analytic solution at the nodes
@@ -568,78 +706,129 @@ def run_ours(args, rank, world, local_rank):
             extra = {"error": repr(exc)[:300]}
     if rank != 0:
         return None
-    apply_ms = sum(s.apply_ms for s in stats) / max(1, sum(s.apply_timed for s in stats))
+    apply_ms = sum(s.apply_ms for s in pstats) / max(1, sum(s.apply_timed for s in pstats))
+    peak_hbm, hsrc = hbm_peak()
+    # the bytes view of the scope table: algorithmic bytes per dof x dofs / event-timed launch duration
+    byt = BYTES_PER_DOF_P2["f64"] * n
+    achieved_gbs = byt / (apply_ms * 1e-3) / 1e9
     if F64_MODE == fe.FE_F64_DOUBLE_FLOAT:
-        kname, flops, peak, unit = ("k_apply_df<2> (FP64 operator in double-float on the FP32 pipes, persistent, "
-                                    "one tet per thread)", OPS_PER_CELL_P2_DF * C, FP32_PEAK_TOPS, "T FP32 op/s")
-        psrc = ("nominal FP32 issue rate: 152 SMs x 128 lanes x 1 operation/clk x 2.07 GHz (recipe unit counts and "
-                "clock); no measured FP32 peak")
+        kname = ("k_apply_df<2> (FP64 operator: float-pair element arithmetic on the FP32 pipes, persistent, one tet "
+                 "per thread)")
+        ops, opeak, ounit = OPS_PER_CELL_P2_DF * C, FP32_PEAK_TOPS, "T FP32 op/s"
+        oderiv = ("976 FP32 operations per tet of the float-pair element formula x cells / launch duration, against the "
+                  "nominal FP32 issue rate 152 SMs x 128 lanes x 1 op/clk x 2.07 GHz = 40.3 T op/s (no measured FP32 "
+                  "peak exists)")
     else:
-        kname, flops, peak, unit = ("k_apply<2,double> (native FP64 operator)", FLOPS_PER_CELL_P2_F64 * C,
-                                    FP64_PEAK_TFLOPS, "TFLOP/s")
-        psrc = "nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json"
-    achieved = flops / (apply_ms * 1e-3) / 1e12
+        kname = "k_apply<2,double> (native FP64 operator)"
+        ops, opeak, ounit = FLOPS_PER_CELL_P2_F64 * C, FP64_PEAK_TFLOPS, "TFLOP/s"
+        oderiv = "151 FP64 flops per tet x cells / launch duration, against the nominal 1.25 TFLOP/s FP64 rate"
     value = job_throughput(n, args.steps, world, t_ms)
     line = {
         "metric": "Poisson GMG-CG solve DoF/s at 1e-8 residual",
         "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (manufactured sin-product right-hand side, kappa = 1)",
+        "dtype": "f64 (float-pair operator)" if F64_MODE == fe.FE_F64_DOUBLE_FLOAT else "f64",
+        "data": "synthetic (manufactured sin-product right-hand side, kappa = 1)",
         "config": dict(WORKLOAD, parallelism=f"replicas{world}",
-                       f64_operator="double-float element arithmetic (~48 bits) on FP32 pipes; FP64 vectors, "
-                                    "reductions, transfers, smoother, coarse Cholesky" if F64_MODE == 1 else "native FP64"),
+                       f64_operator="float-pair (double-float, ~47-bit) element arithmetic on the FP32 pipes; FP64 "
+                                    "vectors, reductions, transfers, smoother updates, coarse Cholesky"
+                       if F64_MODE == 1 else "native FP64"),
         "iterations": stats[-1].iterations, "rel_residual": stats[-1].rel_residual,
         "max_nodal_error_vs_exact": nodal_err, "setup_s": setup_s,
         "e2e": {"value": job_throughput(n, args.steps, world, te_ms), "unit": "DoF/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "traffic": TRAFFIC.get(F64_MODE), "apply_ms": apply_ms,
-                     "ops_per_launch": flops, "fp64_formula_flops_per_launch": FLOPS_PER_CELL_P2_F64 * C,
+        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
+                     "frac": achieved_gbs / peak_hbm, "frac_hbm": achieved_gbs / peak_hbm,
+                     "traffic": TRAFFIC.get(F64_MODE), "apply_ms": apply_ms,
+                     "algorithmic_bytes_per_launch": byt, "bytes_per_dof": BYTES_PER_DOF_P2["f64"],
+                     "bytes_model": "x read 8 + y write 8 + tet->dof map 30 + vertex coordinates 3 B per dof (P2, "
+                                    "kappa = 1)",
+                     "peak_source": f"{hsrc} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hsrc == "measured"
+                     else "fallback 6.8 TB/s",
+                     "limiter": "instruction issue (float-pair arithmetic), not DRAM",
+                     "alu_issue_view_nominal": {"achieved": ops / (apply_ms * 1e-3) / 1e12, "peak": opeak,
+                                                "unit": ounit, "frac": ops / (apply_ms * 1e-3) / 1e12 / opeak,
+                                                "derivation": oderiv},
                      "apply_timing": "CUDA events around each fine-level apply of the same solves (host-driven "
-                                     "CG loop), run after the timed region",
-                     "peak_source": psrc},
+                                     "CG loop), run after the timed region"},
         "clocks": clk,
     }
+    if pstats and hasattr(pstats[-1], "phase_ms"):
+        line["phases_ms_per_solve"] = phase_summary(pstats[-1])
     if extra is not None:
         line["extras"] = extra
     return line
 
 
+def summary(line):
+    """The headline figures, gathered at the end of the line."""
+    ex = line.get("extras") or {}
+    out = {"solve_dofs_per_s": line["value"], "e2e_dofs_per_s": line["e2e"]["value"],
+           "fp64_apply_hbm_frac_survey_bytes": line["roofline"]["frac_hbm"]}
+    nat = ex.get("native_fp64_operator_solve", {})
+    if "DoF_per_s" in nat:
+        out["native_fp64_solve_dofs_per_s"] = nat["DoF_per_s"]
+    mv = ex.get("matvec_p2_128cubed_f32", {})
+    if "hbm_frac_survey_bytes" in mv:
+        out["matvec_f32_128_hbm_frac_survey_bytes"] = mv["hbm_frac_survey_bytes"]
+    mp = ex.get("mixed_precision_p2_128cubed", {})
+    for name, key in (("mixed_f32", "mixed_f32_speedup_vs_f64"), ("mixed_bf16_tensor_core", "mixed_bf16_speedup_vs_f64")):
+        if "ms" in mp.get("f64", {}) and "ms" in mp.get(name, {}):
+            out[key] = mp["f64"]["ms"] / mp[name]["ms"]
+            out[key.replace("speedup_vs_f64", "rel_l2_vs_fp64")] = mp[name].get("rel_l2_diff_vs_fp64_gpu_solution")
+    cb = line.get("cpu_baseline", {})
+    if "value" in cb:
+        out["oracle_dofs_per_s"] = cb["value"]
+        out["oracle_cores"] = cb.get("cores")
+        out["oracle_dofs_per_s_1thread"] = cb.get("value_1thread")
+    return out
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         if rank != 0:
             return
-        r = run_oracle(args.warmup + args.steps)
+        r = OracleRun(args.warmup + args.steps).result()
         times = r["times"][args.warmup:]
         value = r["n"] * len(times) / sum(times)
-        cb = {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample_desc(r),
-              **oracle_details(r)}
+        cb = {"value": value, "unit": "DoF/s", "cores": r["cores"] if r["threaded_products"] else 1,
+              "kind": "oracle", "sample": sample_desc(r), **oracle_details(r)}
         print(json.dumps({"impl": "reference", "metric": "Poisson GMG-CG solve DoF/s at 1e-8 residual",
                           "value": value, "unit": "DoF/s", "n_gpus": args.gpus, "steps": args.steps,
                           "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": dict(WORKLOAD, parallelism="cpu"),
-                          "cpu_baseline": cb,
+                          "data": "synthetic (manufactured sin-product right-hand side, kappa = 1)",
+                          "config": dict(WORKLOAD, parallelism="cpu"), "cpu_baseline": cb,
                           "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
+    oracle = None
+    if world == 1 and not args.no_cpu_baseline:
+        oracle = OracleRun(1)  # set-up overlaps the GPU run; its solve runs afterwards
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
     line = run_ours(args, rank, world, local_rank)
     if rank == 0 and line is not None:
-        if world == 1 and not args.no_cpu_baseline:
+        if oracle is not None:
             try:
-                r = run_oracle(1)
-                line["cpu_baseline"] = {"value": r["n"] / r["times"][0], "unit": "DoF/s", "cores": 1,
-                                        "kind": "oracle", "sample": sample_desc(r), **oracle_details(r)}
+                r = oracle.result()
+                line["cpu_baseline"] = {"value": r["n"] / r["times"][0], "unit": "DoF/s",
+                                        "cores": r["cores"] if r["threaded_products"] else 1, "kind": "oracle",
+                                        "sample": sample_desc(r), **oracle_details(r)}
             except Exception as exc:  # the GPU line is printed either way
                 line["cpu_baseline"] = {"error": repr(exc)[:300]}
+        line["summary"] = summary(line)
         print(json.dumps(line))
+    elif oracle is not None:
+        oracle.proc.kill()
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

@@ -106,6 +106,15 @@ extern "C" {
  * Legendre nodes of [0, 1], u slowest and w fastest. */
 #define FE_QUAD_POINTS 27
 
+/* ---- phases of the per-level solve timers (fe_solve_stats.phase_ms, with opts.profile) ---- */
+#define FE_MAX_LEVELS 9      /* levels of a hierarchy: nrefine <= 8 */
+#define FE_PHASE_APPLY 0     /* operator applications outside the smoother: CG's A p, multigrid residuals */
+#define FE_PHASE_SMOOTH 1    /* Chebyshev smoothing: its operator applications and vector (or patch) updates */
+#define FE_PHASE_TRANSFER 2  /* restriction and prolongation */
+#define FE_PHASE_COARSE 3    /* the direct coarse solve */
+#define FE_PHASE_BLAS1 4     /* dot products and vector updates of CG and of iterative refinement */
+#define FE_NUM_PHASES 5
+
 typedef struct fe_mesh fe_mesh;
 typedef struct fe_hierarchy fe_hierarchy;
 typedef struct fe_batch fe_batch;
@@ -122,7 +131,8 @@ typedef struct fe_solver_opts {
   double inner_rtol;  /* mixed precision: inner FP32 solve tolerance */
   int inner_max_it;   /* mixed precision: inner iteration limit per refinement step */
   int use_graph;      /* nonzero: replay each V-cycle from a captured CUDA graph */
-  int profile;        /* nonzero: time every CG operator application with CUDA events (stats.apply_ms) */
+  int profile;        /* nonzero: time every CG operator application (stats.apply_ms) and every phase of every
+                         level (stats.phase_ms) with CUDA events; graph replay is off while profiling */
   int wait_timeout_us; /* bound of every device-side wait of the persistent batched kernel (0 = 5 s) */
 } fe_solver_opts;
 
@@ -136,6 +146,9 @@ typedef struct fe_solve_stats {
   int fine_applies_low;  /* FP32/bf16 fine-level operator applications */
   double apply_ms;       /* profile: summed device time of the timed CG operator applications */
   int apply_timed;       /* profile: number of operator applications in apply_ms */
+  int levels_timed;      /* profile: levels with entries in phase_ms (the hierarchy's levels), else 0 */
+  double phase_ms[FE_NUM_PHASES][FE_MAX_LEVELS]; /* profile: device time (ms) of each phase FE_PHASE_* on each level
+                         (index 0 = coarsest), summed over the solve: the per-level multigrid log */
 } fe_solve_stats;
 
 /* Fill `opts` with the defaults: rtol 1e-8, max_it 500, GMG, FP64,
@@ -304,12 +317,19 @@ int fe_load_vector_quadrature(const fe_hierarchy* h, const double* f_qp, double*
 /* Solve A u = b on the finest level by PCG (Jacobi or GMG V-cycle), by full
  * multigrid (FE_PC_FMG), or by FP64 iterative refinement around a
  * reduced-precision GMG-PCG.  rhs: FE_RHS_LOAD, FE_RHS_NODAL_F or
- * FE_RHS_QUAD_F (see above).  u: in = initial guess (ignored, taken as 0),
- * out = solution.  Synchronises `stream`.  Returns
- * FE_ERR_NO_CONVERGENCE if max_it is reached (u holds the last iterate) and
- * FE_ERR_NAN on a non-finite residual.  opts NULL = defaults; stats may be NULL. */
-int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_solver_opts* opts, double* u,
-                     fe_solve_stats* stats, void* stream);
+ * FE_RHS_QUAD_F (see above).
+ * bc_values: Dirichlet data u = g on the boundary (Sec. 2, Eq. 1: the
+ *   boundary condition of the strong form), n_dofs doubles of which only the
+ *   boundary entries are read; NULL means g = 0.  The load is eliminated
+ *   symmetrically: b_i -= sum_j A_ij g_j over the boundary dofs j for every
+ *   interior row i, b_j = g_j on the boundary (with FE_RHS_LOAD the boundary
+ *   entries of rhs are then ignored), so u_j = g_j exactly on the boundary.
+ * u: in = initial guess (ignored, taken as 0), out = solution.  Synchronises
+ * `stream`.  Returns FE_ERR_NO_CONVERGENCE if max_it is reached (u holds the
+ * last iterate) and FE_ERR_NAN on a non-finite residual.  opts NULL =
+ * defaults; stats may be NULL. */
+int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const double* bc_values,
+                     const fe_solver_opts* opts, double* u, fe_solve_stats* stats, void* stream);
 
 /* Adjoint gradient of J(kappa) = (u - u_d)^T M (u - u_d) = int (u_h - I_h u_d)^2
  * where A(kappa) u = b: solves A u = b (unless u_ckpt != NULL, which is taken
@@ -364,15 +384,21 @@ int fe_batch_schedule(const fe_batch* batch, int* cell_block, int* dof_block, in
  * The call allocates nothing: its partial sums live in a static device array
  * of the library (16384 partials + 2 slots, 128.5 KiB, held by every GPU that
  * loads the library until the process exits).
- *   x, y: DEVICE pointers to n doubles (host pointers are rejected with
- *         FE_ERR_ARG, since staging them would need device memory).
+ *   x, y: DEVICE pointers of the current device to n doubles each (host
+ *         pointers and memory of another device are rejected with FE_ERR_ARG,
+ *         since staging them would need device memory).  The library cannot
+ *         see the length of a buffer: x and y must hold n doubles.
  *   n:    0 <= n <= 67,108,864 (4096 elements per partial sum); larger n is
  *         rejected with FE_ERR_ARG.
- *   out:  one double, device or host pointer; a host `out` makes the call
- *         synchronise `stream`.
+ *   out:  one double, device pointer of the current device or host pointer;
+ *         a host `out` makes the call synchronise `stream`.
  * The result does not depend on scheduling (fixed summation order).  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
+ * with that device current.  Under CUDA's default lazy module loading that
+ * first lookup also loads the library's device code on that device, which
+ * can itself allocate device memory and synchronise: make the first call
+ * during set-up, before any stream capture and before the code that must not
+ * allocate.
  * Every call shares the one array and overwrites it: calls that overlap on the
  * GPU (several streams, or several host threads) race and must be serialised
  * by the caller. */

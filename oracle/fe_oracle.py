@@ -41,6 +41,9 @@ Lanczos from CG; stopping on the unpreconditioned ||r||_2 <= rtol ||b||_2.
 Every function here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, invariants, brute force and convergence rates.
 """
+import ctypes
+import os
+
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
@@ -422,6 +425,45 @@ def coarsen_kappa(coarse_mesh, fine_mesh, kappa_fine):
     return s / c
 
 
+# ---------------------------------------------------------- products -----
+# The solves' CSR products go through csr_omp.c (the textbook row-by-row
+# product with the rows split over OpenMP threads) when it has been built by
+# oracle/build_oracle.py, else through scipy's product (one thread).  Both sum
+# every row in column order.
+THREADS = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+_CSR_LIB = []
+
+
+def _csr_lib():
+    if not _CSR_LIB:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liboracle_csr.so")
+        lib = None
+        if os.path.exists(path):
+            lib = ctypes.CDLL(path)
+            lib.oracle_csr_matvec.restype = None
+            lib.oracle_csr_matvec.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int]
+        _CSR_LIB.append(lib)
+    return _CSR_LIB[0]
+
+
+def matvec(A, x, threads=None):
+    """y = A x for a CSR matrix A (the solves' operator products)."""
+    lib = _csr_lib()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if lib is None or not sp.isspmatrix_csr(A) or A.indices.dtype != np.int32 or x.ndim != 1:
+        return A @ x
+    ip = getattr(A, "_oracle_indptr64", None)
+    if ip is None:
+        ip = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        A._oracle_indptr64 = ip
+    idx = np.ascontiguousarray(A.indices)
+    dat = np.ascontiguousarray(A.data, dtype=np.float64)
+    y = np.empty(A.shape[0])
+    lib.oracle_csr_matvec(A.shape[0], ip.ctypes.data, idx.ctypes.data, dat.ctypes.data, x.ctypes.data, y.ctypes.data,
+                          int(threads or THREADS))
+    return y
+
+
 # ----------------------------------------------------------- Krylov -------
 def pcg(apply_A, b, apply_M, rtol, maxit, x0=None):
     """Preconditioned conjugate gradients; stops on ||r||_2 <= rtol ||b||_2.
@@ -605,7 +647,7 @@ class Hierarchy:
     def smooth(self, l, b, x):
         L = self.levels[l]
         lm = self.lmax[l]
-        return chebyshev(lambda v: L.A @ v, L.diag, b, x, self.cheb_lo * lm, self.cheb_hi * lm, self.cheb_steps,
+        return chebyshev(lambda v: matvec(L.A, v), L.diag, b, x, self.cheb_lo * lm, self.cheb_hi * lm, self.cheb_steps,
                          prec=self.prec[l])
 
     def vcycle(self, b, l=None):
@@ -616,7 +658,7 @@ class Hierarchy:
             return self.coarse_solve(b)
         L = self.levels[l]
         x = self.smooth(l, b, np.zeros_like(b))
-        r = b - L.A @ x
+        r = b - matvec(L.A, x)
         rc = self.P[l].T @ r
         rc[self.levels[l - 1].space.boundary] = 0.0
         x = x + self.P[l] @ self.vcycle(rc, l - 1)
@@ -640,7 +682,7 @@ class Hierarchy:
             x = self.P[l] @ x
             A = self.levels[l].A
             for _ in range(cycles):
-                x = x + self.vcycle(bs[l] - A @ x, l)
+                x = x + self.vcycle(bs[l] - matvec(A, x), l)
         return x
 
 
@@ -689,7 +731,7 @@ def solve(hier_or_level, b, rtol=1e-10, maxit=2000, precond="gmg", x0=None):
     else:
         L = hier_or_level
         M = lambda v: v / L.diag
-    x, it, hist, _ = pcg(lambda v: L.A @ v, b, M, rtol, maxit, x0)
+    x, it, hist, _ = pcg(lambda v: matvec(L.A, v), b, M, rtol, maxit, x0)
     return x, it, hist
 
 

@@ -23,6 +23,9 @@ FE_SMOOTHER_JACOBI, FE_SMOOTHER_PATCH = 0, 1
 FE_QUAD_POINTS = 27
 FE_PREC_F64, FE_PREC_MIXED_F32, FE_PREC_MIXED_BF16 = 0, 1, 2
 FE_RHS_LOAD, FE_RHS_NODAL_F, FE_RHS_QUAD_F = 0, 1, 2
+FE_MAX_LEVELS = 9
+FE_PHASE_APPLY, FE_PHASE_SMOOTH, FE_PHASE_TRANSFER, FE_PHASE_COARSE, FE_PHASE_BLAS1 = range(5)
+FE_NUM_PHASES = 5
 
 # every symbol include/fe.h declares
 EXPORTED = (
@@ -52,10 +55,14 @@ class SolverOpts(ctypes.Structure):
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("bnorm", ctypes.c_double), ("solve_ms", ctypes.c_double), ("fine_applies_f64", ctypes.c_int),
-                ("fine_applies_low", ctypes.c_int), ("apply_ms", ctypes.c_double), ("apply_timed", ctypes.c_int)]
+                ("fine_applies_low", ctypes.c_int), ("apply_ms", ctypes.c_double), ("apply_timed", ctypes.c_int),
+                ("levels_timed", ctypes.c_int),
+                ("phase_ms", (ctypes.c_double * FE_MAX_LEVELS) * FE_NUM_PHASES)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
+        d["phase_ms"] = [list(row) for row in self.phase_ms]
+        return d
 
 
 _LIB = None
@@ -102,7 +109,7 @@ def load():
         "fe_load_vector": (i, [vp, vp, vp, vp]),
         "fe_quadrature_points": (i, [vp, vp]),
         "fe_load_vector_quadrature": (i, [vp, vp, vp, vp]),
-        "fe_solve_poisson": (i, [vp, vp, i, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(SolveStats), vp]),
+        "fe_solve_poisson": (i, [vp, vp, i, vp, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(SolveStats), vp]),
         "fe_adjoint_gradient": (i, [vp, vp, i, vp, vp, ctypes.POINTER(SolverOpts), vp, ctypes.POINTER(d), vp, vp]),
         "fe_objective": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
         "fe_dot_noalloc": (i, [vp, vp, ll, vp, vp]),
@@ -198,9 +205,10 @@ def fe_apply_operator(h, level, x, y, dtype=FE_F64, stream=None):
     _check(load().fe_apply_operator(h, level, _ptr(x), _ptr(y), dtype, _stream(stream)))
 
 
-def fe_solve_poisson(h, rhs, rhs_kind, opts, u, stream=None):
+def fe_solve_poisson(h, rhs, rhs_kind, opts, u, stream=None, bc_values=None):
     st = SolveStats()
-    rc = load().fe_solve_poisson(h, _ptr(rhs), rhs_kind, ctypes.byref(opts), _ptr(u), ctypes.byref(st), _stream(stream))
+    rc = load().fe_solve_poisson(h, _ptr(rhs), rhs_kind, _ptr(bc_values), ctypes.byref(opts), _ptr(u),
+                                 ctypes.byref(st), _stream(stream))
     _check(rc)
     return st
 
@@ -212,14 +220,43 @@ def fe_adjoint_gradient(h, rhs, rhs_kind, u_d, u_ckpt, opts, dJ, u_out=None, str
     return J.value
 
 
+def _torch_float64():
+    import torch  # only reached for tensor arguments, so torch is already imported by the caller
+    return torch.float64
+
+
 def fe_dot_noalloc(x, y, n=None, out=None, stream=None):
     """sum_i x[i] y[i] of two device vectors without any device allocation (see include/fe.h).
 
     ``out``: optional device tensor / host array of one double; returns the value when ``out`` is None.
     """
+    def count(a, name):
+        # the kernel reads n doubles from x and y and writes one to out: check what each buffer holds
+        if hasattr(a, "data_ptr"):
+            if a.dtype != _torch_float64() or not a.is_contiguous():
+                raise FeError(FE_ERR_ARG, f"{name} must be a contiguous float64 tensor")
+            return a.numel(), (a.device.type, a.device.index if a.device.type == "cuda" else None)
+        if isinstance(a, np.ndarray):
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise FeError(FE_ERR_ARG, f"{name} must be a C-contiguous float64 array")
+            return a.size, ("cpu", None)
+        raise FeError(FE_ERR_ARG, f"unsupported vector type {type(a)}")
+
+    nx, dx = count(x, "x")
+    ny, dy = count(y, "y")
     if n is None:
-        n = x.numel() if hasattr(x, "numel") else x.size
+        n = nx
     n = int(n)
+    if n < 0 or n > nx or n > ny:
+        raise FeError(FE_ERR_ARG, f"n = {n} exceeds the length of x ({nx}) or y ({ny})")
+    if dx != dy:
+        raise FeError(FE_ERR_ARG, "x and y must be on the same device")
+    if out is not None:
+        no, do = count(out, "out")
+        if no < 1:
+            raise FeError(FE_ERR_ARG, "out must hold at least one float64")
+        if do[0] == "cuda" and do != dx:
+            raise FeError(FE_ERR_ARG, "a device out must be on the device of x and y")
     if out is None:
         res = np.zeros(1)
         _check(load().fe_dot_noalloc(_ptr(x), _ptr(y), n, _ptr(res), _stream(stream)))
@@ -424,9 +461,10 @@ class Hierarchy:
         _check(self._L.fe_objective(self.h, _ptr(u), _ptr(u_d), ctypes.byref(J), _stream(stream)))
         return J.value
 
-    def solve(self, rhs, u, rhs_kind=FE_RHS_NODAL_F, opts=None, stream=None, **kw):
+    def solve(self, rhs, u, rhs_kind=FE_RHS_NODAL_F, opts=None, stream=None, bc_values=None, **kw):
+        """Solve with Dirichlet data ``bc_values`` on the boundary dofs (None: homogeneous)."""
         o = opts if opts is not None else default_opts(**kw)
-        return fe_solve_poisson(self.h, rhs, rhs_kind, o, u, stream)
+        return fe_solve_poisson(self.h, rhs, rhs_kind, o, u, stream, bc_values)
 
     def adjoint_gradient(self, rhs, u_d, dJ, rhs_kind=FE_RHS_NODAL_F, u_ckpt=None, u_out=None, opts=None,
                          stream=None, **kw):

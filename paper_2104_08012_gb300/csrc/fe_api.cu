@@ -346,6 +346,34 @@ static double estimate_lmax(fe_hierarchy* h, int l, int steps, cudaStream_t s) {
 }
 
 // -------------------------------------------------------- V-cycle
+// ------------------------------------------------ per-phase timers (profile)
+// With fe_solver_opts.profile set, each phase of the solve on each level is
+// bracketed by a pair of CUDA events; after the solve the elapsed times are
+// summed into fe_solve_stats.phase_ms (a per-level multigrid log).  Graph
+// replay is off while profiling, so every bracket holds real launches.
+static thread_local PhaseProf* g_prof = nullptr;
+
+struct PhaseScope {
+  PhaseProf* p;
+  cudaStream_t s;
+  size_t rec = 0;
+  PhaseScope(int phase, int level, cudaStream_t st) : p(g_capturing ? nullptr : g_prof), s(st) {
+    if (!p) return;
+    const int e0 = p->take();
+    CUDA_CHECK(cudaEventRecord(p->ev[e0], s));
+    rec = p->recs.size();
+    p->recs.push_back({phase, level, e0, -1});
+  }
+  ~PhaseScope() {
+    if (!p) return;
+    const int e1 = p->take();
+    p->recs[rec].e1 = e1;
+    cudaEventRecord(p->ev[e1], s);  // no throw from a destructor; a failed record shows up at the next check
+  }
+  PhaseScope(const PhaseScope&) = delete;
+  PhaseScope& operator=(const PhaseScope&) = delete;
+};
+
 struct SmootherParams {
   int steps = 2;
   double lo = 0.1, hi = 1.1;
@@ -380,7 +408,19 @@ static void mass_enqueue(const fe_hierarchy* h, const Level& L, const double* x,
     launch_mass_df(L, x, y, s);
 }
 
-void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s) {
+// Whether the FP64 operator on level l is the per-tet float-pair kernel that can
+// gather pre-split dofs (P1 in FE_F64_DOUBLE_FLOAT_TET mode, P2 in the default
+// mode), so that the vector kernels producing its inputs write float pairs too.
+// FE_F64_DOUBLE_FLOAT_TET keeps the split inside the operator kernel (for
+// comparison); the fused and patch smoothers update x without pairs.
+static bool presplit(const fe_hierarchy* h, int l) {
+  const Level& L = h->L[l];
+  return h->f64_mode == FE_F64_DOUBLE_FLOAT && L.deg == 2 && L.xs64.p && !h->fuse_smoother &&
+         !(h->smoother == FE_SMOOTHER_PATCH && h->deg >= 2 && l >= 1 && L.pdof.p);
+}
+
+void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s,
+                   const float2* xs) {
   const Level& L = h->L[level];
   if (L.deg == 3) {  // P3: element matrix per tet in FP64 FMAs, float pairs (default) or FP32
     FE_REQUIRE(dtype != FE_BF16, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
@@ -402,7 +442,7 @@ void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int
   else if (dtype == FE_F64 && h->f64_mode != FE_F64_NATIVE && cube)
     launch_apply64_cube_df(L, (const double*)x, (double*)y, s);
   else if (dtype == FE_F64 && h->f64_mode != FE_F64_NATIVE)
-    launch_apply64_df(L, (const double*)x, (double*)y, s);
+    launch_apply64_df(L, (const double*)x, (double*)y, s, h->f64_mode == FE_F64_DOUBLE_FLOAT ? xs : nullptr);
   else if (dtype == FE_F64)
     launch_apply64(L, (const double*)x, (double*)y, s);
   else if (dtype == FE_F32)
@@ -419,7 +459,8 @@ void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int
 // operator kernel and the vector kernel.
 template <typename T>
 static void apply_cheb_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d, double c1, double c2,
-                               bool store_d, int dtype, cudaStream_t s) {
+                               bool store_d, int dtype, cudaStream_t s, const float2* xs_in = nullptr,
+                               float2* xs_out = nullptr) {
   Level& L = h->L[l];
   if (h->fuse_smoother && L.cnt_tet.p && L.deg <= 2) {
     const bool cube = h->f64_mode == FE_F64_DOUBLE_FLOAT_CUBE || (h->f64_mode == FE_F64_DOUBLE_FLOAT && L.deg == 1);
@@ -438,16 +479,19 @@ static void apply_cheb_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T
       }
     }
   }
-  apply_enqueue(h, l, x, y, dtype, s);
-  launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, c1, c2, false, s, store_d);
+  apply_enqueue(h, l, x, y, dtype, s, xs_in);
+  launch_cheb_step<T>(L.n, b, y, lv_dinv<T>(L), x, d, c1, c2, false, s, store_d, xs_out);
 }
 
 // Chebyshev iterations on level l (the level smoother of Section 3): the
 // three-term Chebyshev semi-iteration for the preconditioned operator on
 // [lo, hi] * lambda_max, theta = centre, delta = half-width of the interval.
+// xs_fresh_in: L.xs64 holds x as float pairs on entry (FP64, presplit levels);
+// xs_after: leave L.xs64 current with the smoothed x (an operator application
+// reads it next).
 template <typename T>
 static void smooth_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d, int steps, double lo, double hi,
-                           bool x_zero, int dtype, cudaStream_t s) {
+                           bool x_zero, int dtype, cudaStream_t s, bool xs_fresh_in = false, bool xs_after = false) {
   Level& L = h->L[l];
   const double a = lo * L.lmax, bmax = hi * L.lmax;
   const double theta = 0.5 * (bmax + a), delta = 0.5 * (bmax - a), sigma = theta / delta;
@@ -469,16 +513,21 @@ static void smooth_enqueue(fe_hierarchy* h, int l, const T* b, T* x, T* y, T* d,
     }
     return;
   }
+  float2* xs = nullptr;  // x's float pairs, written by each step whose x an operator application reads next
+  if constexpr (sizeof(T) == 8)
+    if (dtype == FE_F64 && presplit(h, l)) xs = L.xs64.p;
   for (int k = 0; k < steps; ++k) {
     const bool last = k + 1 == steps;  // its direction d is not used again
+    float2* xs_out = (!last || xs_after) ? xs : nullptr;
+    const float2* xs_in = (k > 0 || xs_fresh_in) ? xs : nullptr;
     if (k == 0) {
       if (x_zero)
-        launch_cheb_step<T>(L.n, b, nullptr, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, true, s, !last);
+        launch_cheb_step<T>(L.n, b, nullptr, lv_dinv<T>(L), x, d, 0.0, 1.0 / theta, true, s, !last, xs_out);
       else
-        apply_cheb_enqueue<T>(h, l, b, x, y, d, 0.0, 1.0 / theta, !last, dtype, s);
+        apply_cheb_enqueue<T>(h, l, b, x, y, d, 0.0, 1.0 / theta, !last, dtype, s, xs_in, xs_out);
     } else {
       const double rn = 1.0 / (2.0 * sigma - rho);
-      apply_cheb_enqueue<T>(h, l, b, x, y, d, rn * rho, 2.0 * rn / delta, !last, dtype, s);
+      apply_cheb_enqueue<T>(h, l, b, x, y, d, rn * rho, 2.0 * rn / delta, !last, dtype, s, xs_in, xs_out);
       rho = rn;
     }
   }
@@ -490,17 +539,34 @@ static void vcycle_level(fe_hierarchy* h, int l, int dtype, cudaStream_t s) {
   Level& L = h->L[l];
   T *b = lv_b<T>(L), *x = lv_x<T>(L), *y = lv_y<T>(L), *d = lv_d<T>(L);
   if (l == 0) {
+    PhaseScope ps(FE_PHASE_COARSE, 0, s);
     coarse_solve<T>(h, b, x, s);
     return;
   }
   const int rdt = (dtype == FE_BF16) ? FE_F32 : dtype;  // residuals in FP32 when smoothing in bf16
-  smooth_enqueue<T>(h, l, b, x, y, d, g_sp.steps, g_sp.lo, g_sp.hi, true, dtype, s);
-  apply_enqueue(h, l, x, y, rdt, s);
+  float2* xs = nullptr;  // x as float pairs on presplit FP64 levels (see smooth_enqueue)
+  if constexpr (sizeof(T) == 8)
+    if (dtype == FE_F64 && presplit(h, l)) xs = L.xs64.p;
+  {
+    PhaseScope ps(FE_PHASE_SMOOTH, l, s);
+    smooth_enqueue<T>(h, l, b, x, y, d, g_sp.steps, g_sp.lo, g_sp.hi, true, dtype, s, false, true);
+  }
+  {
+    PhaseScope ps(FE_PHASE_APPLY, l, s);
+    apply_enqueue(h, l, x, y, rdt, s, xs);
+  }
   Level& Lc = h->L[l - 1];
-  launch_restrict<T>(h, l, b, y, lv_b<T>(Lc), true, s);
+  {
+    PhaseScope ps(FE_PHASE_TRANSFER, l, s);
+    launch_restrict<T>(h, l, b, y, lv_b<T>(Lc), true, s);
+  }
   vcycle_level<T>(h, l - 1, dtype, s);
-  launch_prolong<T>(h, l, lv_x<T>(Lc), x, true, s);
-  smooth_enqueue<T>(h, l, b, x, y, d, g_sp.steps, g_sp.lo, g_sp.hi, false, dtype, s);
+  {
+    PhaseScope ps(FE_PHASE_TRANSFER, l, s);
+    launch_prolong<T>(h, l, lv_x<T>(Lc), x, true, s, xs);
+  }
+  PhaseScope ps(FE_PHASE_SMOOTH, l, s);
+  smooth_enqueue<T>(h, l, b, x, y, d, g_sp.steps, g_sp.lo, g_sp.hi, false, dtype, s, xs != nullptr, false);
 }
 
 // Enqueue one fine-level V-cycle (reads L.b of the finest level, writes
@@ -585,15 +651,31 @@ static void fmg_enqueue(fe_hierarchy* h, const double* b, int cycles, cudaStream
   const int top = h->nlev - 1;
   if (b != h->L[top].fb64.p)
     CUDA_CHECK(cudaMemcpyAsync(h->L[top].fb64, b, sizeof(double) * h->L[top].n, cudaMemcpyDeviceToDevice, s));
-  for (int l = top; l >= 1; --l) launch_restrict<double>(h, l, h->L[l].fb64, nullptr, h->L[l - 1].fb64, true, s);
-  coarse_solve<double>(h, h->L[0].fb64, h->L[0].fx64, s);
+  for (int l = top; l >= 1; --l) {
+    PhaseScope ps(FE_PHASE_TRANSFER, l, s);
+    launch_restrict<double>(h, l, h->L[l].fb64, nullptr, h->L[l - 1].fb64, true, s);
+  }
+  {
+    PhaseScope ps(FE_PHASE_COARSE, 0, s);
+    coarse_solve<double>(h, h->L[0].fb64, h->L[0].fx64, s);
+  }
   for (int l = 1; l <= top; ++l) {
     Level& L = h->L[l];
-    launch_prolong<double>(h, l, h->L[l - 1].fx64, L.fx64, false, s);
+    {
+      PhaseScope ps(FE_PHASE_TRANSFER, l, s);
+      launch_prolong<double>(h, l, h->L[l - 1].fx64, L.fx64, false, s);
+    }
     for (int c = 0; c < cycles; ++c) {
-      apply_enqueue(h, l, L.fx64, L.y64, FE_F64, s);
-      launch_sub64(L.n, L.fb64, L.y64, L.b64, s);
+      {
+        PhaseScope ps(FE_PHASE_APPLY, l, s);
+        apply_enqueue(h, l, L.fx64, L.y64, FE_F64, s);
+      }
+      {
+        PhaseScope ps(FE_PHASE_BLAS1, l, s);
+        launch_sub64(L.n, L.fb64, L.y64, L.b64, s);
+      }
       vcycle_level<double>(h, l, FE_F64, s);
+      PhaseScope ps(FE_PHASE_BLAS1, l, s);
       launch_axpy64(L.n, 1.0, L.x64, L.fx64, s);
     }
   }
@@ -733,10 +815,11 @@ static void build_cg_loop(fe_hierarchy* h) {
   CUDA_CHECK(cudaGraphAddNode(&loop, g, &test, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   capture(body, [&] {
+    float2* ps = presplit(h, h->nlev - 1) ? h->ps.p : nullptr;
     run_vcycle(h, FE_F64, false, cs);
     launch_cg_beta<double>(R, n, r, z, cs);
-    launch_cg_update_p<double>(R, n, p, z, cs);
-    apply_enqueue(h, h->nlev - 1, p, q, FE_F64, cs);
+    launch_cg_update_p<double>(R, n, p, z, cs, ps);
+    apply_enqueue(h, h->nlev - 1, p, q, FE_F64, cs, ps);
     launch_cg_alpha<double>(R, n, p, q, cs);
     launch_cg_update<double>(R, n, x, r, p, q, nullptr, z, cs);
     launch_cg_cond(cond, R.scal, h->cgp, h->cgctl, 1, cs);
@@ -763,7 +846,7 @@ static PcgResult pcg64_graph(fe_hierarchy* h, double* x, const fe_solver_opts& o
   if (!cl.exec) build_cg_loop(h);
   // first iteration from the host, then the loop
   CUDA_CHECK(cudaMemsetAsync(xw, 0, sizeof(double) * n, s));
-  apply_enqueue(h, h->nlev - 1, p, q, FE_F64, s);
+  apply_enqueue(h, h->nlev - 1, p, q, FE_F64, s, presplit(h, h->nlev - 1) ? h->ps.p : nullptr);
   launch_cg_alpha<double>(R, n, p, q, s);
   launch_cg_update<double>(R, n, xw, r, p, q, nullptr, z, s);
   launch_cg_set(h->cgp, h->cgctl, tol2, 1, o.max_it, s);
@@ -791,15 +874,29 @@ static PcgResult pcg64(fe_hierarchy* h, const double* b, double* x, const fe_sol
   double *r = F.b64, *z = F.x64, *p = h->p, *q = h->q;
   const bool gmg = o.precond == FE_PC_GMG && h->nlev > 1;
   PcgResult res;
-  CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-  CUDA_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  launch_dot<double>(R, n, b, b, S_BB, s);
-  if (gmg)
-    run_vcycle(h, FE_F64, o.use_graph != 0, s);
-  else
+  const int top = h->nlev - 1;
+  const bool graphs = o.use_graph != 0 && !o.profile;
+  {
+    PhaseScope ps(FE_PHASE_BLAS1, top, s);
+    CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    CUDA_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    launch_dot<double>(R, n, b, b, S_BB, s);
+  }
+  if (gmg) {
+    run_vcycle(h, FE_F64, graphs, s);
+  } else {
+    PhaseScope ps(FE_PHASE_SMOOTH, top, s);
     launch_cheb_step<double>(n, r, nullptr, F.dinv64, q, z, 0.0, 1.0, true, s);  // z = D^-1 r
-  launch_dot<double>(R, n, r, z, S_RZ, s);
-  CUDA_CHECK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  float2* psplit = presplit(h, top) ? h->ps.p : nullptr;  // p as float pairs for the operator
+  {
+    PhaseScope ps(FE_PHASE_BLAS1, top, s);
+    launch_dot<double>(R, n, r, z, S_RZ, s);
+    if (psplit)
+      launch_copy_split(n, z, p, psplit, s);
+    else
+      CUDA_CHECK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
   CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
   CUDA_CHECK(cudaStreamSynchronize(s));
   res.bb = R.h_scal[S_BB];
@@ -813,12 +910,18 @@ static PcgResult pcg64(fe_hierarchy* h, const double* b, double* x, const fe_sol
       res.status = FE_ERR_NO_CONVERGENCE;
       break;
     }
-    timer.start(s);
-    apply_enqueue(h, h->nlev - 1, p, q, FE_F64, s);
-    timer.stop(s);
+    {
+      PhaseScope ps(FE_PHASE_APPLY, top, s);
+      timer.start(s);
+      apply_enqueue(h, top, p, q, FE_F64, s, psplit);
+      timer.stop(s);
+    }
     ++res.applies;
-    launch_cg_alpha<double>(R, n, p, q, s);
-    launch_cg_update<double>(R, n, x, r, p, q, gmg ? nullptr : F.dinv64.p, z, s);
+    {
+      PhaseScope ps(FE_PHASE_BLAS1, top, s);
+      launch_cg_alpha<double>(R, n, p, q, s);
+      launch_cg_update<double>(R, n, x, r, p, q, gmg ? nullptr : F.dinv64.p, z, s);
+    }
     CUDA_CHECK(cudaMemcpyAsync(R.h_scal + S_RR, R.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_CHECK(cudaStreamSynchronize(s));
     timer.collect(res);
@@ -829,11 +932,10 @@ static PcgResult pcg64(fe_hierarchy* h, const double* b, double* x, const fe_sol
       break;
     }
     if (res.rr <= tol2) break;
-    if (gmg) {
-      run_vcycle(h, FE_F64, o.use_graph != 0, s);
-      launch_cg_beta<double>(R, n, r, z, s);
-    }
-    launch_cg_update_p<double>(R, n, p, z, s);
+    if (gmg) run_vcycle(h, FE_F64, graphs, s);
+    PhaseScope ps(FE_PHASE_BLAS1, top, s);
+    if (gmg) launch_cg_beta<double>(R, n, r, z, s);
+    launch_cg_update_p<double>(R, n, p, z, s, psplit);
   }
   return res;
 }
@@ -845,20 +947,34 @@ static PcgResult pcg_low(fe_hierarchy* h, int dtype, const fe_solver_opts& o, cu
   ReduceCtx& R = h->red;
   float *r = F.b32, *z = F.x32, *p = h->p32, *q = h->q32, *e = h->e32;
   PcgResult res;
-  CUDA_CHECK(cudaMemsetAsync(e, 0, sizeof(float) * n, s));
-  launch_dot<float>(R, n, r, r, S_BB, s);
-  run_vcycle(h, dtype, o.use_graph != 0, s);
-  launch_dot<float>(R, n, r, z, S_RZ, s);
-  CUDA_CHECK(cudaMemcpyAsync(p, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  const int top = h->nlev - 1;
+  const bool graphs = o.use_graph != 0 && !o.profile;
+  {
+    PhaseScope ps(FE_PHASE_BLAS1, top, s);
+    CUDA_CHECK(cudaMemsetAsync(e, 0, sizeof(float) * n, s));
+    launch_dot<float>(R, n, r, r, S_BB, s);
+  }
+  run_vcycle(h, dtype, graphs, s);
+  {
+    PhaseScope ps(FE_PHASE_BLAS1, top, s);
+    launch_dot<float>(R, n, r, z, S_RZ, s);
+    CUDA_CHECK(cudaMemcpyAsync(p, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  }
   CUDA_CHECK(cudaMemcpyAsync(R.h_scal, R.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
   CUDA_CHECK(cudaStreamSynchronize(s));
   res.bb = R.h_scal[S_BB];
   const double tol2 = o.inner_rtol * o.inner_rtol * res.bb;
   while (res.it < o.inner_max_it) {
-    launch_apply32(F, p, q, s);
+    {
+      PhaseScope ps(FE_PHASE_APPLY, top, s);
+      launch_apply32(F, p, q, s);
+    }
     ++res.applies;
-    launch_cg_alpha<float>(R, n, p, q, s);
-    launch_cg_update<float>(R, n, e, r, p, q, nullptr, z, s);
+    {
+      PhaseScope ps(FE_PHASE_BLAS1, top, s);
+      launch_cg_alpha<float>(R, n, p, q, s);
+      launch_cg_update<float>(R, n, e, r, p, q, nullptr, z, s);
+    }
     CUDA_CHECK(cudaMemcpyAsync(R.h_scal + S_RR, R.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_CHECK(cudaStreamSynchronize(s));
     ++res.it;
@@ -868,7 +984,8 @@ static PcgResult pcg_low(fe_hierarchy* h, int dtype, const fe_solver_opts& o, cu
       break;
     }
     if (res.rr <= tol2) break;
-    run_vcycle(h, dtype, o.use_graph != 0, s);
+    run_vcycle(h, dtype, graphs, s);
+    PhaseScope ps(FE_PHASE_BLAS1, top, s);
     launch_cg_beta<float>(R, n, r, z, s);
     launch_cg_update_p<float>(R, n, p, z, s);
   }
@@ -907,7 +1024,10 @@ static PcgResult refine(fe_hierarchy* h, const double* b, double* x, const fe_so
       // r32 = r / ||r||; ||r||^2 parked in S_TMP0 for the correction
       CUDA_CHECK(cudaMemcpyAsync(R.scal + S_TMP0, R.scal + (outer == 0 ? S_BB : S_DOT), sizeof(double),
                                  cudaMemcpyDeviceToDevice, s));
-      launch_scale_copy<float>(n, r, R.scal + S_TMP0, true, F.b32, s);
+      {
+        PhaseScope ps(FE_PHASE_BLAS1, h->nlev - 1, s);
+        launch_scale_copy<float>(n, r, R.scal + S_TMP0, true, F.b32, s);
+      }
       PcgResult in = pcg_low(h, dtype, o, s);
       inner_total += in.it;
       low_applies += in.applies;
@@ -915,9 +1035,16 @@ static PcgResult refine(fe_hierarchy* h, const double* b, double* x, const fe_so
         res.status = FE_ERR_NAN;
         break;
       }
-      launch_add_scaled<float>(n, h->e32, R.scal + S_TMP0, x, s);
-      apply_enqueue(h, h->nlev - 1, x, y, FE_F64, s);
+      {
+        PhaseScope ps(FE_PHASE_BLAS1, h->nlev - 1, s);
+        launch_add_scaled<float>(n, h->e32, R.scal + S_TMP0, x, s);
+      }
+      {
+        PhaseScope ps(FE_PHASE_APPLY, h->nlev - 1, s);
+        apply_enqueue(h, h->nlev - 1, x, y, FE_F64, s);
+      }
       ++res.applies;
+      PhaseScope ps(FE_PHASE_BLAS1, h->nlev - 1, s);
       launch_sub64(n, b, y, r, s);
       launch_dot<double>(R, n, r, r, S_DOT, s);
       CUDA_CHECK(cudaMemcpyAsync(R.h_scal + S_DOT, R.scal + S_DOT, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1060,6 +1187,7 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
     L.dinv64.alloc(L.n);
     L.dinv32.alloc(L.n);
     for (auto* v : {&L.b64, &L.x64, &L.y64, &L.d64, &L.w64, &L.fb64, &L.fx64}) v->alloc(L.n);
+    if (degree == 2) L.xs64.alloc(L.n);  // float pairs of x for the P2 float-pair operator
     for (auto* v : {&L.b32, &L.x32, &L.y32, &L.d32}) v->alloc(L.n);
     std::vector<int> bnd;
     bnd.reserve((size_t)6 * (m + 1) * (m + 1));
@@ -1098,6 +1226,7 @@ fe_hierarchy* hierarchy_create(int N0, int nrefine, int degree) {
   red_init(h->red, h->sms);
   const int nF = h->L.back().n;
   for (auto* v : {&h->x, &h->r, &h->z, &h->p, &h->q, &h->b, &h->e, &h->tmp, &h->xcg}) v->alloc(nF);
+  if (degree == 2) h->ps.alloc(nF);
   h->cgp.alloc(1);
   h->cgctl.alloc(2);
   for (auto* v : {&h->r32, &h->z32, &h->p32, &h->q32, &h->e32}) v->alloc(nF);
@@ -1483,8 +1612,8 @@ int fe_load_vector_quadrature(const fe_hierarchy* hc, const double* f_qp, double
   API_END
 }
 
-int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_solver_opts* opts, double* u,
-                     fe_solve_stats* stats, void* stream) {
+int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const double* bc_values,
+                     const fe_solver_opts* opts, double* u, fe_solve_stats* stats, void* stream) {
   API_BEGIN
   FE_REQUIRE(h && rhs && u, FE_ERR_ARG, "null argument");
   const fe_solver_opts o = resolve_opts(opts);
@@ -1498,14 +1627,28 @@ int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_
   const Level& F = h->L[h->nlev - 1];
   const auto t0 = std::chrono::steady_clock::now();
   g_sp = SmootherParams{o.cheb_steps, o.cheb_lo, o.cheb_hi};
+  // per-phase timers for this call (thread-local, cleared again on every exit path)
+  struct ProfGuard {
+    PhaseProf* p;
+    explicit ProfGuard(PhaseProf* q) : p(q) {
+      if (p) p->reset();
+      g_prof = p;
+    }
+    ~ProfGuard() { g_prof = nullptr; }
+  } prof_guard(o.profile ? &h->prof : nullptr);
   const double* b = rhs_to_load(h, rhs, rhs_kind, s);
+  const double* g = nullptr;
+  if (bc_values) {  // symmetric elimination of u = g on the boundary
+    g = stage_in<double>(h, 2, bc_values, F.n, s);
+    launch_bc_lift(F, g, h->b, s);
+  }
   double* ud = is_device_ptr(u) ? u : h->x.p;
   fe_solve_stats st{};
   st.outer_iterations = 1;
   PcgResult res;
   if (o.precond == FE_PC_FMG) {
     // one full-multigrid cycle, then the residual of its solution for the stats
-    run_fmg(h, b, o.max_it, o.use_graph != 0, s);
+    run_fmg(h, b, o.max_it, o.use_graph != 0 && !o.profile, s);
     Level& Ft = h->L[h->nlev - 1];
     CUDA_CHECK(cudaMemcpyAsync(ud, Ft.fx64, sizeof(double) * Ft.n, cudaMemcpyDeviceToDevice, s));
     apply_enqueue(h, h->nlev - 1, Ft.fx64, Ft.y64, FE_F64, s);
@@ -1528,6 +1671,9 @@ int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_
     res = refine(h, b, ud, o, o.precision == FE_PREC_MIXED_F32 ? FE_F32 : FE_BF16, &st, s);
     st.fine_applies_f64 = res.applies;
   }
+  // the boundary rows are the decoupled identity equations u_j = g_j: set them exactly (an iterative solve
+  // leaves them within its tolerance)
+  if (g) launch_set_boundary(F, g, ud, s);
   finish_out(u, ud, F.n, s);
   CUDA_CHECK(cudaStreamSynchronize(s));
   if (o.precision == FE_PREC_MIXED_BF16)
@@ -1536,6 +1682,7 @@ int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const fe_
   st.bnorm = std::sqrt(res.bb);
   st.rel_residual = res.bb > 0 ? std::sqrt(res.rr / res.bb) : 0.0;
   st.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (o.profile) h->prof.collect(st, h->nlev);
   if (stats) *stats = st;
   if (res.status == FE_ERR_NO_CONVERGENCE) FE_FAIL(FE_ERR_NO_CONVERGENCE, "iteration limit reached before rtol");
   if (res.status == FE_ERR_NAN) FE_FAIL(FE_ERR_NAN, "residual norm is not finite");

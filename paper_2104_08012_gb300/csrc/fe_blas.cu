@@ -8,6 +8,7 @@
 // and derives the CG scalars (alpha, beta, ...) in device memory, so the
 // recurrences never wait for the host.  Sums are accumulated in FP64 for
 // every vector type.
+#include "fe_df.cuh"
 #include "fe_internal.cuh"
 
 namespace {
@@ -135,9 +136,23 @@ __global__ void __launch_bounds__(kRedBlock) k_cg_beta(int n, const T* __restric
 }
 
 template <typename T>
-__global__ void k_cg_update_p(int n, T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ scal) {
+__global__ void k_cg_update_p(int n, T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ scal,
+                              float2* __restrict__ ps) {
   const T beta = (T)scal[S_BETA];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = z[i] + beta * p[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const T v = z[i] + beta * p[i];
+    p[i] = v;
+    if constexpr (sizeof(T) == 8)
+      if (ps) ps[i] = fe_df::split_pair(v);  // the operator's next input, ready as a float pair
+  }
+}
+
+__global__ void k_copy_split(int n, const double* __restrict__ z, double* __restrict__ p, float2* __restrict__ ps) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v = z[i];
+    p[i] = v;
+    ps[i] = fe_df::split_pair(v);
+  }
 }
 
 __global__ void k_axpy64(int n, double a, const double* __restrict__ x, double* __restrict__ y) {
@@ -217,8 +232,14 @@ void launch_cg_beta(ReduceCtx& R, int n, const T* r, const T* z, cudaStream_t s)
 }
 
 template <typename T>
-void launch_cg_update_p(ReduceCtx& R, int n, T* p, const T* z, cudaStream_t s) {
-  k_cg_update_p<T><<<vec_grid(n, R.grid / 2), 256, 0, s>>>(n, p, z, R.scal);
+void launch_cg_update_p(ReduceCtx& R, int n, T* p, const T* z, cudaStream_t s, float2* ps) {
+  k_cg_update_p<T><<<vec_grid(n, R.grid / 2), 256, 0, s>>>(n, p, z, R.scal, ps);
+  LAUNCH_CHECK();
+}
+
+void launch_copy_split(int n, const double* z, double* p, float2* ps, cudaStream_t s) {
+  const int g = ceil_div(n, 256);
+  k_copy_split<<<g < 8192 ? (g > 0 ? g : 1) : 8192, 256, 0, s>>>(n, z, p, ps);
   LAUNCH_CHECK();
 }
 
@@ -279,7 +300,7 @@ void launch_add_scaled(int n, const T* e, const double* slot, double* x, cudaStr
   template void launch_cg_update<T>(ReduceCtx&, int, T*, T*, const T*, const T*, const T*, T*,          \
                                     cudaStream_t);                                                      \
   template void launch_cg_beta<T>(ReduceCtx&, int, const T*, const T*, cudaStream_t);                   \
-  template void launch_cg_update_p<T>(ReduceCtx&, int, T*, const T*, cudaStream_t);                     \
+  template void launch_cg_update_p<T>(ReduceCtx&, int, T*, const T*, cudaStream_t, float2*);            \
   template void launch_scale_copy<T>(int, const double*, const double*, bool, T*, cudaStream_t);        \
   template void launch_add_scaled<T>(int, const T*, const double*, double*, cudaStream_t);
 FE_INST(double)

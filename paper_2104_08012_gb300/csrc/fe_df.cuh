@@ -198,8 +198,10 @@ __device__ __forceinline__ int block_exponent(const double (&xv)[ND]) {
   return emax == 0 ? 1023 : emax;
 }
 
-// exact float -> double of f * 2^(emax - 1023) by bit manipulation
-// (results below the double range flush to 0, above it give inf)
+// exact float -> double of f * 2^(emax - 1023) by bit manipulation; results
+// below the normal double range become subnormal doubles (gradual underflow:
+// the significand shifted right, bits below 2^-1074 truncated), results above
+// it give inf
 __device__ __forceinline__ double widen_scaled(float f, int emax) {
   const unsigned int b = __float_as_uint(f);
   const int ef = (int)((b >> 23) & 0xFFu);
@@ -207,9 +209,33 @@ __device__ __forceinline__ double widen_scaled(float f, int emax) {
   if (ef == 0) return __hiloint2double((int)sgn, 0);
   const int eh = ef + emax - 127;
   if (ef == 0xFF || eh >= 0x7FF) return __hiloint2double((int)(sgn | 0x7FF00000u | ((b & 0x7FFFFFu) >> 3)), 0);
-  if (eh <= 0) return __hiloint2double((int)sgn, 0);
+  if (eh <= 0) {
+    // value = m 2^(ef + emax - 1173) with the 24-bit significand m; as a
+    // subnormal it is k 2^-1074 with k = m 2^sh, sh = ef + emax - 99 = eh + 28
+    const unsigned long long m = 0x800000ull | (b & 0x7FFFFFu);
+    const int sh = eh + 28;
+    const unsigned long long k = sh >= 0 ? (m << sh) : (sh > -24 ? (m >> -sh) : 0ull);
+    return __longlong_as_double((long long)(((unsigned long long)sgn << 32) | k));
+  }
   return __hiloint2double((int)(sgn | ((unsigned int)eh << 20) | ((b & 0x7FFFFFu) >> 3)), (int)((b & 7u) << 29));
 }
 
+
+// Producer-side split of an FP64 value into the unscaled float pair that the
+// operator kernels gather (hi holds the leading 24 significant bits, lo the
+// next 24 rounded).  The pair is exact to 48 bits for 2^-64 <= |x| < 2^64; for
+// larger, smaller (nonzero), subnormal or non-finite x it is the marker
+// (NaN, 0), and a tet that gathers a marker splits its FP64 dofs itself with
+// its own power-of-two scaling.
+__device__ __forceinline__ float2 split_pair(double x) {
+  const unsigned int h32 = (unsigned int)__double2hiint(x), l32 = (unsigned int)__double2loint(x);
+  const unsigned int e = (h32 >> 20) & 0x7FFu;
+  if (e - 959u < 128u) {  // biased exponent 959..1086: 2^-64 <= |x| < 2^64
+    const DF p = split_scaled(x, 1023);
+    return make_float2(p.hi, p.lo);
+  }
+  if (((h32 & 0x7FFFFFFFu) | l32) == 0u) return make_float2(__uint_as_float(h32 & 0x80000000u), 0.0f);
+  return make_float2(__int_as_float(0x7fc00000), 0.0f);
+}
 
 }  // namespace fe_df

@@ -15,6 +15,7 @@
 // (their largest exponent) before the split, so the float pairs never leave
 // the FP32 exponent range whatever the magnitude of the vector.
 #include <algorithm>
+#include <type_traits>
 
 #include "fe_df.cuh"
 #include "fe_df2.cuh"
@@ -50,6 +51,13 @@ __device__ __forceinline__ void finish_dofs(const int* pidx, const unsigned* pre
 // map rows, dofs and geometric factors of the thread's next tet are already
 // in flight (the kernel is otherwise bound by the latency of its gathers).
 //
+// PRE: the dofs are gathered from xs, the input vector already split into
+// unscaled float pairs by the kernel that produced it (split_pair), so a tet
+// only finds its largest exponent and scales its ten pairs by a power of two
+// (exact) instead of splitting ten FP64 values.  A tet that gathers a marker
+// (a dof outside [2^-64, 2^64) or not finite) splits its FP64 dofs from x with
+// its own scaling, as without PRE; both paths feed the same element code.
+//
 // With FUSE the launch also performs the Chebyshev smoother step on its
 // input: each interior dof's countdown (its number of tets) is decremented
 // after the tet's contributions are issued and fenced; the thread that ends
@@ -58,12 +66,14 @@ __device__ __forceinline__ void finish_dofs(const int* pidx, const unsigned* pre
 // updates d_i and x_i in place.  Every tet
 // gathers x before it scatters, so x_i only changes once all its readers are
 // done.  Dirichlet rows (y = x) are updated by the threads that write them.
-template <int DEG, bool FUSE>
+template <int DEG, bool FUSE, bool PRE>
 __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
                                                         const float2* __restrict__ geo, const double* x,
-                                                        double* __restrict__ y, int nb, const int* __restrict__ bnd,
-                                                        ChebFuse<double> cf) {
+                                                        const float2* __restrict__ xs, double* __restrict__ y, int nb,
+                                                        const int* __restrict__ bnd, ChebFuse<double> cf) {
+  static_assert(!(FUSE && PRE), "the fused smoother changes x during the launch");
   constexpr int ND = DEG == 1 ? 4 : 10;
+  using XV = typename std::conditional<PRE, float2, double>::type;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   for (int i = tid; i < nb; i += stride) {  // Dirichlet rows: identity
     const int k = bnd[i];
@@ -72,40 +82,70 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int
     if constexpr (FUSE) cheb_update(k, xk, cf.b, cf.dinv, cf.x, cf.d, cf.c1, cf.c2, cf.store_d);
   }
   // with FUSE, x changes during the launch: plain loads instead of the read-only path
-  auto ldx = [&](int i) { return FUSE ? x[i] : __ldg(x + i); };
+  auto ldx = [&](int i) -> XV {
+    if constexpr (PRE)
+      return i >= 0 ? __ldg(xs + i) : make_float2(0.0f, 0.0f);
+    else
+      return i >= 0 ? (FUSE ? x[i] : __ldg(x + i)) : 0.0;
+  };
   int pidx[FUSE ? ND : 1];
   unsigned prev[FUSE ? ND : 1];
   bool have_prev = false;
   int c = tid;
   if (c >= C) return;
   int idx[ND];
-  double xv[ND];
+  XV xv[ND];
   float2 gv[6];
 #pragma unroll
   for (int j = 0; j < ND; ++j) idx[j] = __ldg(map + (size_t)j * Cs + c);
 #pragma unroll
-  for (int j = 0; j < ND; ++j) xv[j] = idx[j] >= 0 ? ldx(idx[j]) : 0.0;
+  for (int j = 0; j < ND; ++j) xv[j] = ldx(idx[j]);
 #pragma unroll
   for (int a = 0; a < 6; ++a) gv[a] = __ldg(geo + (size_t)a * Cs + c);
   while (true) {
     const int cn = c + stride;
     const bool more = cn < C;
     int idn[ND];
-    double xn[ND];
+    XV xn[ND];
     float2 gn[6];
     if (more) {
 #pragma unroll
       for (int j = 0; j < ND; ++j) idn[j] = __ldg(map + (size_t)j * Cs + cn);
 #pragma unroll
-      for (int j = 0; j < ND; ++j) xn[j] = idn[j] >= 0 ? ldx(idn[j]) : 0.0;
+      for (int j = 0; j < ND; ++j) xn[j] = ldx(idn[j]);
 #pragma unroll
       for (int a = 0; a < 6; ++a) gn[a] = __ldg(geo + (size_t)a * Cs + cn);
     }
     DF u[ND], g[6], out[ND];
-    const int emax = block_exponent<ND>(xv);  // the element map is linear: scale, contract, unscale
+    int emax;  // the element map is linear: scale by 2^(1023 - emax), contract, unscale
+    bool split_here = !PRE;
+    if constexpr (PRE) {
+      int ef = 0;  // largest float exponent of the pairs (0xFF: a marker)
 #pragma unroll
-    for (int j = 0; j < ND; ++j) u[j] = split_scaled(xv[j], emax);
-    if (emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
+      for (int j = 0; j < ND; ++j) ef = max(ef, (int)((__float_as_uint(xv[j].x) >> 23) & 0xFFu));
+      if (ef != 0xFF) {
+        const float f = __uint_as_float((unsigned int)(254 - ef) << 23);  // 2^(127 - ef)
+#pragma unroll
+        for (int j = 0; j < ND; ++j) u[j] = DF(__fmul_rn(xv[j].x, f), __fmul_rn(xv[j].y, f));
+        emax = ef + 896;
+      } else {
+        split_here = true;
+      }
+    }
+    if (split_here) {
+      double xd[ND];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        if constexpr (PRE)
+          xd[j] = idx[j] >= 0 ? __ldg(x + idx[j]) : 0.0;
+        else
+          xd[j] = xv[j];
+      }
+      emax = block_exponent<ND>(xd);
+#pragma unroll
+      for (int j = 0; j < ND; ++j) u[j] = split_scaled(xd[j], emax);
+      if (emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
+    }
 #pragma unroll
     for (int a = 0; a < 6; ++a) g[a] = DF(gv[a].x, gv[a].y);
     element_df<DEG>(u, g, out);
@@ -447,19 +487,34 @@ static void apply_cube_df(const Level& L, const double* x, double* y, const Cheb
   LAUNCH_CHECK();
 }
 
+template <int DEG, bool FUSE, bool PRE>
+static void apply_df_launch(const Level& L, const double* x, const float2* xs, double* y, const ChebFuse<double>& cf,
+                            cudaStream_t s) {
+  static int g = 0;
+  if (!g) g = resident_grid(k_apply_df<DEG, FUSE, PRE>, kBlock, 1 << 30);
+  k_apply_df<DEG, FUSE, PRE><<<std::min(g, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(
+      L.C, L.Cs, L.map, L.geodf, x, xs, y, L.nb, L.bnd, cf);
+}
+
 template <bool FUSE>
-static void apply_df(const Level& L, const double* x, double* y, const ChebFuse<double>& cf, cudaStream_t s) {
+static void apply_df(const Level& L, const double* x, const float2* xs, double* y, const ChebFuse<double>& cf,
+                     cudaStream_t s) {
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
-  if (L.deg == 1) {
-    static int g1 = 0;
-    if (!g1) g1 = resident_grid(k_apply_df<1, FUSE>, kBlock, 1 << 30);
-    k_apply_df<1, FUSE><<<std::min(g1, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(
-        L.C, L.Cs, L.map, L.geodf, x, y, L.nb, L.bnd, cf);
+  if constexpr (FUSE) {
+    if (L.deg == 1)
+      apply_df_launch<1, true, false>(L, x, nullptr, y, cf, s);
+    else
+      apply_df_launch<2, true, false>(L, x, nullptr, y, cf, s);
+  } else if (L.deg == 1) {
+    if (xs)
+      apply_df_launch<1, false, true>(L, x, xs, y, cf, s);
+    else
+      apply_df_launch<1, false, false>(L, x, nullptr, y, cf, s);
   } else {
-    static int g2 = 0;
-    if (!g2) g2 = resident_grid(k_apply_df<2, FUSE>, kBlock, 1 << 30);
-    k_apply_df<2, FUSE><<<std::min(g2, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(
-        L.C, L.Cs, L.map, L.geodf, x, y, L.nb, L.bnd, cf);
+    if (xs)
+      apply_df_launch<2, false, true>(L, x, xs, y, cf, s);
+    else
+      apply_df_launch<2, false, false>(L, x, nullptr, y, cf, s);
   }
   LAUNCH_CHECK();
 }
@@ -489,13 +544,14 @@ void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStre
   apply_cube_df<false>(L, x, y, ChebFuse<double>{}, s);
 }
 
-void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s) {
-  apply_df<false>(L, x, y, ChebFuse<double>{}, s);
+void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s, const float2* xs) {
+  apply_df<false>(L, x, xs, y, ChebFuse<double>{}, s);
 }
 
 void launch_apply_cheb64_df(const Level& L, const double* b, double* x, double* y, double* d, double c1, double c2,
                             bool store_d, cudaStream_t s) {
-  apply_df<true>(L, x, y, ChebFuse<double>{b, L.dinv64, x, d, L.val_tet, L.cnt_tet, c1, c2, store_d ? 1 : 0}, s);
+  apply_df<true>(L, x, nullptr, y, ChebFuse<double>{b, L.dinv64, x, d, L.val_tet, L.cnt_tet, c1, c2, store_d ? 1 : 0},
+                 s);
 }
 
 void launch_apply_cheb64_cube_df(const Level& L, const double* b, double* x, double* y, double* d, double c1,

@@ -210,6 +210,7 @@ struct Level {
   // V-cycle work vectors (level-owned so the cycle can be captured in a graph)
   DBuf<double> b64, x64, y64, d64, w64;
   DBuf<double> fb64, fx64;  // full multigrid: this level's right-hand side and solution
+  DBuf<float2> xs64;        // x64 as unscaled float pairs (split_pair), written with x64 for the FP64 operator
   // Transfer index tables (levels >= 1), one int4 per stencil entry of the
   // restriction to level-1 (fine dofs of this level around a coarse point) and
   // of the prolongation from level-1 (coarse dofs around a coarse cube): the
@@ -285,6 +286,40 @@ struct GraphCache {
   int extra = 0;  // another baked parameter (V-cycles per level of the full-multigrid graph)
 };
 
+// Per-phase, per-level CUDA-event timers of a profiled solve (fe_api.cu
+// brackets each phase; collect() sums the brackets into the stats).
+struct PhaseProf {
+  struct Rec {
+    int phase, level, e0, e1;
+  };
+  std::vector<cudaEvent_t> ev;  // pool, reused by later solves
+  std::vector<Rec> recs;
+  size_t used = 0;
+  ~PhaseProf() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  int take() {
+    if (used == ev.size()) {
+      cudaEvent_t e;
+      CUDA_CHECK(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+    return (int)used++;
+  }
+  void reset() {
+    used = 0;
+    recs.clear();
+  }
+  // after the stream has been synchronised
+  void collect(fe_solve_stats& st, int nlev) {
+    st.levels_timed = nlev < FE_MAX_LEVELS ? nlev : FE_MAX_LEVELS;
+    for (const Rec& r : recs) {
+      float ms = 0.f;
+      CUDA_CHECK(cudaEventElapsedTime(&ms, ev[r.e0], ev[r.e1]));
+      if (r.level >= 0 && r.level < FE_MAX_LEVELS) st.phase_ms[r.phase][r.level] += ms;
+    }
+  }
+};
 struct fe_hierarchy {
   int N0 = 0, nlev = 0, deg = 0;
   int sms = 148;
@@ -295,6 +330,7 @@ struct fe_hierarchy {
   DBuf<int> children;  // [6][8] coarse Kuhn type -> (subcube code * 8 + fine type)
   // fine-level Krylov vectors
   DBuf<double> x, r, z, p, q, b, e, tmp;
+  DBuf<float2> ps;  // CG's p as unscaled float pairs (split_pair), written with p for the FP64 operator
   DBuf<float> r32, z32, p32, q32, e32;
   // staging for host pointers
   DBuf<unsigned char> stage[4];
@@ -314,6 +350,7 @@ struct fe_hierarchy {
   int f64_mode = FE_F64_DOUBLE_FLOAT;  // arithmetic of FP64 operator applications
   int fuse_smoother = 0;               // Chebyshev update fused into the operator kernel (measured slower on GB300)
   int smoother = FE_SMOOTHER_JACOBI;   // preconditioner of the Chebyshev smoother
+  PhaseProf prof;                      // per-phase timers of profiled solves
 };
 
 // ------------------------------------------------------- launch wrappers ---
@@ -322,7 +359,8 @@ void launch_build_level(Level& L, cudaStream_t s);
 void launch_geometry(Level& L, cudaStream_t s);
 void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s);
-void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s);
+// xs (optional): x as unscaled float pairs (split_pair), gathered instead of x
+void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s, const float2* xs = nullptr);
 void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply64_df2(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply64_df3(const Level& L, const double* x, double* y, cudaStream_t s);
@@ -346,6 +384,8 @@ template <typename T>
 void launch_cheb_pc(int n, const T* z, T* x, T* d, double c1, double c2, bool first_from_zero, bool store_d,
                     cudaStream_t s);
 void launch_split_geometry(Level& L, cudaStream_t s);
+// b -= A g on interior rows and b = g on the boundary (inhomogeneous Dirichlet data, symmetric elimination)
+void launch_bc_lift(const Level& L, const double* g, double* b, cudaStream_t s);
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_mass_df(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_quad_points(const Level& L, double* xyz, cudaStream_t s);
@@ -358,15 +398,20 @@ void launch_bmask(const Level& L, unsigned char* m, cudaStream_t s);
 void launch_coarsen_kappa(const Level& Lc, const Level& Lf, const int* children, cudaStream_t s);
 int launch_check_positive(const double* v, int n, int* dflag, cudaStream_t s);
 // Transfers
+// xs (optional, FP64): also write the result as unscaled float pairs
 template <typename T>
-void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s);
+void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s,
+                    float2* xs = nullptr);
 template <typename T>
 void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, bool zero_bd, cudaStream_t s);
 
 // Vector kernels
+// xs (optional, FP64): also write the new x as unscaled float pairs
 template <typename T>
 void launch_cheb_step(int n, const T* b, const T* y, const T* dinv, T* x, T* d, double c1, double c2, bool first_from_zero,
-                      cudaStream_t s, bool store_d = true);
+                      cudaStream_t s, bool store_d = true, float2* xs = nullptr);
+// p = z and ps = split_pair(z)
+void launch_copy_split(int n, const double* z, double* p, float2* ps, cudaStream_t s);
 template <typename Ti, typename To>
 void launch_convert(int n, const Ti* in, To* out, cudaStream_t s);
 void launch_set_boundary(const Level& L, const double* src, double* dst, cudaStream_t s);
@@ -386,8 +431,9 @@ void launch_cg_update(ReduceCtx& R, int n, T* x, T* r, const T* p, const T* q, c
 // rznew = r.z; beta = rznew/rz; rz = rznew
 template <typename T>
 void launch_cg_beta(ReduceCtx& R, int n, const T* r, const T* z, cudaStream_t s);
+// ps (optional, FP64): also write the new p as unscaled float pairs
 template <typename T>
-void launch_cg_update_p(ReduceCtx& R, int n, T* p, const T* z, cudaStream_t s);
+void launch_cg_update_p(ReduceCtx& R, int n, T* p, const T* z, cudaStream_t s, float2* ps = nullptr);
 void launch_cg_cond(cudaGraphConditionalHandle hnd, const double* scal, const double* cgp, int* ctl, int inc,
                     cudaStream_t s);
 void launch_cg_set(double* cgp, int* ctl, double tol2, int it0, int max_it, cudaStream_t s);
@@ -408,7 +454,9 @@ void hierarchy_set_coefficient(fe_hierarchy* h, const double* kappa, cudaStream_
 void hierarchy_destroy(fe_hierarchy* h);
 template <typename T>
 void vcycle_enqueue(fe_hierarchy* h, int dtype, cudaStream_t s);  // reads L.b of the finest level, writes L.x
-void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s);
+// xs (optional): FP64 x as unscaled float pairs, current with x (the float-pair P2 kernel gathers it)
+void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s,
+                   const float2* xs = nullptr);
 void apply_bf16_enqueue(const Level& L, const float* x, float* y, cudaStream_t s);
 bool bf16_supported();
 int bf16_take_error(cudaStream_t s);      // nonzero if a tensor-core launch gave up a bounded wait

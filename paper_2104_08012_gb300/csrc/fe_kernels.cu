@@ -7,6 +7,7 @@
 #include <vector>
 #include <type_traits>
 
+#include "fe_df.cuh"
 #include "fe_internal.cuh"
 #include "fe_p3.cuh"
 #include "fe_reftables.h"
@@ -204,6 +205,38 @@ __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const
     const int i = bnd[t - Cpad];
     y[i] = x[i];
   }
+}
+
+// Lift of inhomogeneous Dirichlet data (symmetric elimination of u = g on the
+// boundary): b_i -= (A g)_i on every interior dof i, where g holds the
+// Dirichlet values on the boundary dofs and 0 inside.  Only tets with a
+// Dirichlet dof contribute; the others leave after reading their map rows.
+// FP64 FMAs: it runs once per solve, on the boundary layer of cells.
+template <int DEG>
+__global__ void __launch_bounds__(kBlock) k_bc_lift(int C, int Cs, const int* __restrict__ map,
+                                                    const double* __restrict__ geo, const double* __restrict__ g,
+                                                    double* __restrict__ b) {
+  constexpr int ND = tet_ndof(DEG);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C) return;
+  int idx[ND];
+  double u[ND];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    idx[j] = __ldg(map + (size_t)j * Cs + t);
+    any = any || idx[j] < 0;
+    u[j] = idx[j] < 0 ? __ldg(g + (-1 - idx[j])) : 0.0;
+  }
+  if (!any) return;
+  double gg[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) gg[a] = __ldg(geo + (size_t)a * Cs + t);
+  double out[ND];
+  tet_element<DEG, double>(u, gg, out);
+#pragma unroll
+  for (int j = 0; j < ND; ++j)
+    if (idx[j] >= 0) atomicAdd(b + idx[j], -out[j]);
 }
 
 // Cube-aggregated apply: one thread per cube gathers the cube's (k+1)^3 dofs
@@ -524,7 +557,8 @@ __global__ void k_check_positive(const double* __restrict__ v, int n, int* __res
 // t.x + cx + t.y cy + t.z cz (affine in the cube coordinates).
 template <int DEG, typename T>
 __global__ void k_prolong(Numbering nf, int n_f, const int* __restrict__ start, const int4* __restrict__ tab,
-                          const T* __restrict__ w, const T* __restrict__ xc, T* __restrict__ xf, int accumulate) {
+                          const T* __restrict__ w, const T* __restrict__ xc, T* __restrict__ xf, int accumulate,
+                          float2* __restrict__ xs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_f) return;
   int x, y, z;
@@ -548,7 +582,10 @@ __global__ void k_prolong(Numbering nf, int n_f, const int* __restrict__ start, 
       s += __ldg(w + e0 + k) * __ldg(xc + j);
     }
   }
-  xf[i] = accumulate ? xf[i] + s : s;
+  const T v = accumulate ? xf[i] + s : s;
+  xf[i] = v;
+  if constexpr (sizeof(T) == 8)
+    if (xs) xs[i] = fe_df::split_pair(v);  // the operator's next input, ready as a float pair
 }
 
 // Restriction = exact transpose: coarse point Lc gathers fine points
@@ -611,16 +648,23 @@ __global__ void __launch_bounds__(32 * TPC) k_restrict(int mf, Numbering nc, int
 // first_from_zero (x = 0, y unused): d = c2 D^-1 b; x = d.
 template <typename T>
 __global__ void k_cheb_step(int n, const T* __restrict__ b, const T* __restrict__ y, const T* __restrict__ dinv,
-                            T* __restrict__ x, T* __restrict__ d, T c1, T c2, int first_from_zero, int store_d) {
+                            T* __restrict__ x, T* __restrict__ d, T c1, T c2, int first_from_zero, int store_d,
+                            float2* __restrict__ xs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  T xn;
   if (first_from_zero) {
     const T dn = c2 * dinv[i] * b[i];
     if (store_d) d[i] = dn;
-    x[i] = dn;
+    xn = dn;
   } else {
-    cheb_update(i, y[i], b, dinv, x, d, c1, c2, store_d);
+    const T dn = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * dinv[i] * (b[i] - y[i]);
+    if (store_d) d[i] = dn;  // the last step of a sweep does not need d again
+    xn = x[i] + dn;
   }
+  x[i] = xn;
+  if constexpr (sizeof(T) == 8)
+    if (xs) xs[i] = fe_df::split_pair(xn);  // the operator's next input, ready as a float pair
 }
 
 template <typename Ti, typename To>
@@ -1014,12 +1058,13 @@ template <>
 const float* tt_weights<float>(const DBuf<double>&, const DBuf<float>& wf) { return wf.p; }
 
 template <typename T>
-void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s) {
+void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s, float2* xs) {
   const Level& F = h->L[lf];
   const TransferTables& t = h->tt;
   by_degree(h->deg, [&](auto D) {
     k_prolong<D.value, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, F.n, t.pro_start, F.ptab,
-                                                                  tt_weights<T>(t.pro_w, t.pro_wf), xc, xf, accumulate);
+                                                                  tt_weights<T>(t.pro_w, t.pro_wf), xc, xf, accumulate,
+                                                                  xs);
   });
   LAUNCH_CHECK();
 }
@@ -1044,23 +1089,23 @@ void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T*
   LAUNCH_CHECK();
 }
 
-template void launch_prolong<double>(const fe_hierarchy*, int, const double*, double*, bool, cudaStream_t);
-template void launch_prolong<float>(const fe_hierarchy*, int, const float*, float*, bool, cudaStream_t);
+template void launch_prolong<double>(const fe_hierarchy*, int, const double*, double*, bool, cudaStream_t, float2*);
+template void launch_prolong<float>(const fe_hierarchy*, int, const float*, float*, bool, cudaStream_t, float2*);
 template void launch_restrict<double>(const fe_hierarchy*, int, const double*, const double*, double*, bool,
                                       cudaStream_t);
 template void launch_restrict<float>(const fe_hierarchy*, int, const float*, const float*, float*, bool, cudaStream_t);
 
 template <typename T>
 void launch_cheb_step(int n, const T* b, const T* y, const T* dinv, T* x, T* d, double c1, double c2,
-                      bool first_from_zero, cudaStream_t s, bool store_d) {
+                      bool first_from_zero, cudaStream_t s, bool store_d, float2* xs) {
   k_cheb_step<T><<<ceil_div(n, kBlock), kBlock, 0, s>>>(n, b, y, dinv, x, d, (T)c1, (T)c2, first_from_zero ? 1 : 0,
-                                                        store_d ? 1 : 0);
+                                                        store_d ? 1 : 0, xs);
   LAUNCH_CHECK();
 }
 template void launch_cheb_step<double>(int, const double*, const double*, const double*, double*, double*, double,
-                                       double, bool, cudaStream_t, bool);
+                                       double, bool, cudaStream_t, bool, float2*);
 template void launch_cheb_step<float>(int, const float*, const float*, const float*, float*, float*, double, double,
-                                      bool, cudaStream_t, bool);
+                                      bool, cudaStream_t, bool, float2*);
 
 template <typename Ti, typename To>
 void launch_convert(int n, const Ti* in, To* out, cudaStream_t s) {
@@ -1077,6 +1122,14 @@ void launch_set_boundary(const Level& L, const double* src, double* dst, cudaStr
 }
 
 void launch_zero_boundary64(const Level& L, double* v, cudaStream_t s) { launch_set_boundary(L, nullptr, v, s); }
+
+void launch_bc_lift(const Level& L, const double* g, double* b, cudaStream_t s) {
+  by_degree(L.deg, [&](auto D) {
+    k_bc_lift<D.value><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.geo64, g, b);
+  });
+  LAUNCH_CHECK();
+  launch_set_boundary(L, g, b, s);
+}
 
 void launch_random(int n, uint64_t seed, double* v, cudaStream_t s) {
   k_random<<<ceil_div(n, kBlock), kBlock, 0, s>>>(n, seed, v);

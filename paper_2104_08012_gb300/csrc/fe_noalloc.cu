@@ -102,13 +102,18 @@ double* noalloc_scratch() {
   return g_na_ptr[dev];
 }
 
-bool na_is_device(const void* p) {
+// Where a pointer lives: 1 = device (or managed) memory of the current
+// device, 0 = host memory (pageable, pinned or unregistered), -1 = device
+// memory of another device (the kernel would fault or read the wrong GPU).
+int na_where(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice) return a.device == dev ? 1 : -1;
+  if (a.type == cudaMemoryTypeManaged) return 1;
+  return 0;
 }
 
 }  // namespace
@@ -119,11 +124,16 @@ extern "C" int fe_dot_noalloc(const double* x, const double* y, long long n, dou
     FE_REQUIRE(n >= 0, FE_ERR_ARG, "n must be >= 0");
     FE_REQUIRE(n <= kNaMaxN, FE_ERR_ARG,
                "n exceeds the no-alloc scratch capacity of " + std::to_string(kNaMaxN) + " elements");
-    FE_REQUIRE(na_is_device(x) && na_is_device(y), FE_ERR_ARG,
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    const int wx = na_where(x, dev), wy = na_where(y, dev), wo = na_where(out, dev);
+    FE_REQUIRE(wx >= 0 && wy >= 0 && wo >= 0, FE_ERR_ARG,
+               "x, y and out must be memory of the current device (or host memory for out)");
+    FE_REQUIRE(wx == 1 && wy == 1, FE_ERR_ARG,
                "x and y must be device pointers: the no-alloc entry point cannot stage host data");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double* scratch = noalloc_scratch();
-    const bool dev_out = na_is_device(out);
+    const bool dev_out = wo == 1;
     double* dst = dev_out ? out : scratch + kNaResultSlot;
     if (n == 0) {
       CUDA_CHECK(cudaMemsetAsync(dst, 0, sizeof(double), s));

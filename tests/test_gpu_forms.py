@@ -100,29 +100,39 @@ def test_adjoint_matches_oracle_assembled_adjoint(fe, k):
 
 
 def test_adjoint_vs_central_differences_8cubed(fe):
-    """P1 on 8^3 (3072 cells): gradient against central FD of J computed by GPU solves."""
+    """P1 on 8^3: the adjoint gradient against central finite differences of J on every one of the 3072 cells.
+
+    Step eps_K = 1e-4 kappa_K: the truncation error of the central difference is about (eps/kappa)^2 / 6 = 2e-9
+    relative, and J's rounding (both solves in native FP64 to rtol 1e-14) divided by eps stays below the floor.
+    Per cell: |FD - g_K| <= 1e-6 |g_K| + 1e-7 max|g|, i.e. 1e-6 relative wherever |g_K| >= 10% of max|g|, and an
+    absolute 1e-7 max|g| for the cells whose gradient is smaller than that."""
     h, kappa, f, ud = _setup_adjoint(fe, 2, 2, 1)
     with h:
+        h.set_f64_mode(fe.FE_F64_NATIVE)
         fd_f, fd_ud = dt(f), dt(ud)
         h.set_coefficient(dt(kappa))
         g = torch.empty(h.n_cells(), dtype=torch.float64, device=DEV)
-        h.adjoint_gradient(fd_f, fd_ud, g, rtol=1e-13)
+        h.adjoint_gradient(fd_f, fd_ud, g, rtol=1e-14, max_it=400)
         g = host(g)
         u = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+        kap = dt(kappa)
 
-        def J(kap):
-            h.set_coefficient(dt(kap))
-            h.solve(fd_f, u, rtol=1e-13)
+        def J(c, e):
+            kap[c] = kappa[c] + e
+            h.set_coefficient(kap)
+            kap[c] = kappa[c]
+            h.solve(fd_f, u, rtol=1e-14, max_it=400)
             return h.objective(u, fd_ud)
 
-        cells = np.random.default_rng(0).choice(h.n_cells(), 24, replace=False)
-        for c in cells:
-            eps = 1e-5 * kappa[c]
-            kp, km = kappa.copy(), kappa.copy()
-            kp[c] += eps
-            km[c] -= eps
-            fd = (J(kp) - J(km)) / (2 * eps)
-            assert abs(fd - g[c]) <= 1e-6 * np.abs(g).max(), (c, fd, g[c])
+        fd = np.empty(h.n_cells())
+        for c in range(h.n_cells()):
+            eps = 1e-4 * kappa[c]
+            fd[c] = (J(c, eps) - J(c, -eps)) / (2 * eps)
+        tol = 1e-6 * np.abs(g) + 1e-7 * np.abs(g).max()
+        bad = np.nonzero(np.abs(fd - g) > tol)[0]
+        assert bad.size == 0, (bad.size, bad[:5], fd[bad[:5]], g[bad[:5]])
+        big = np.abs(g) >= 0.1 * np.abs(g).max()
+        assert np.all(np.abs(fd - g)[big] <= 2e-6 * np.abs(g)[big])
 
 
 def test_autograd_function(fe):

@@ -164,13 +164,34 @@ def test_galerkin_identity(k):
     assert np.abs(Gi - c.A.toarray()[np.ix_(ic, ic)]).max() < 1e-13
 
 
-def test_coarsen_kappa_has_eight_children():
-    c, f = O.Mesh(2), O.Mesh(4)
-    parent, _ = O.locate_in_mesh(c, f.centroids())
+def _integer_parents(Nc):
+    """Parent coarse cell of every cell of the 2 Nc mesh from integer lattice coordinates alone: with the fine
+    tet's vertex lattice coordinates v_0..v_3 (fine lattice), its centroid is s / 8 in coarse cube units, s = sum
+    v_i; the coarse cube is q = s // 8 per axis and, with l = s - 8 q, the coarse Kuhn tet is the permutation
+    (p0, p1, p2) with l[p0] > l[p1] > l[p2] (a fine centroid is strictly inside one coarse tet)."""
+    fine = O.Mesh(2 * Nc)
+    s = fine.cell_vertex_lattice.sum(axis=1)
+    q = s // 8
+    loc = s - 8 * q
+    order = tuple(map(tuple, np.argsort(-loc, axis=1, kind="stable")))
+    assert np.all(np.diff(-np.sort(-loc, axis=1), axis=1) < 0)  # strict: no centroid on a coarse face
+    t = np.array([O.KUHN_PERMS.index(o) for o in order])
+    return 6 * (q[:, 0] + Nc * (q[:, 1] + Nc * q[:, 2])) + t
+
+
+@pytest.mark.parametrize("Nc", [1, 2, 3])
+def test_coarsen_kappa(Nc):
+    """Pinned without the oracle's point location: parents from integer lattice arithmetic; 8 children per coarse
+    cell; a kappa constant on each coarse cell comes back exactly; a random kappa gives the mean of the 8 children
+    of each coarse cell."""
+    c, f = O.Mesh(Nc), O.Mesh(2 * Nc)
+    parent = _integer_parents(Nc)
     assert np.all(np.bincount(parent, minlength=c.n_cells) == 8)
-    kf = I.grf_kappa(f.centroids())
-    kc = O.coarsen_kappa(c, f, kf)
-    assert np.allclose(kc, np.bincount(parent, kf) / 8)
+    K = 1.0 + np.arange(c.n_cells) * 0.25
+    assert np.array_equal(O.coarsen_kappa(c, f, K[parent]), K)
+    kf = np.random.default_rng(Nc).lognormal(size=f.n_cells)
+    want = np.array([kf[parent == p].sum() / 8 for p in range(c.n_cells)])
+    assert np.allclose(O.coarsen_kappa(c, f, kf), want, rtol=1e-15, atol=0)
 
 
 # ---------------------------------------------------- quadrature load vector
@@ -224,3 +245,22 @@ def test_p3_energies_of_polynomials():
     assert abs(np.ones(L.n) @ (M @ u) - 1 / 4) < 1e-13
     w = x * y * z
     assert abs(w @ (M @ w) - 1 / 27) < 1e-13
+
+
+@pytest.mark.parametrize("threads", [1, 3])
+def test_oracle_threaded_csr_product(threads):
+    """The solves' CSR product (rows split over threads) against a dense product of the same matrix, on a matrix
+    with empty rows, a ragged row-length mix and more rows than threads; it must also equal scipy's product."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(7)
+    n = 1001
+    A = sp.random(n, 733, density=0.01, format="csr", random_state=rng)
+    A = A.multiply(np.where(np.arange(n) % 17 == 0, 0.0, 1.0)[:, None]).tocsr()  # empty rows
+    x = rng.uniform(-1, 1, 733)
+    y = O.matvec(A, x, threads=threads)
+    dense = A.toarray() @ x
+    assert np.allclose(y, dense, rtol=0, atol=1e-14 * np.abs(A).toarray().sum(axis=1).max())
+    assert np.array_equal(y[::17], np.zeros_like(y[::17]))
+    assert np.allclose(y, A @ x, rtol=1e-15, atol=1e-15)
+    xt = rng.uniform(-1, 1, n)  # a transposed (CSC) operand takes scipy's product
+    assert np.allclose(O.matvec(A.T, xt), A.toarray().T @ xt, rtol=0, atol=1e-13)

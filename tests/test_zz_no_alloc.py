@@ -67,3 +67,49 @@ def test_dot_noalloc_large_and_limits(fe):
     with pytest.raises(fe.FeError) as err:
         fe.fe_dot_noalloc(x.cpu().numpy(), y)
     assert err.value.code == fe.FE_ERR_ARG
+
+
+def test_dot_noalloc_rejects_bad_buffers(fe):
+    """Buffers that do not hold what the call reads or writes are rejected before any launch."""
+    x = torch.rand(64, dtype=torch.float64, device="cuda")
+    y = torch.rand(64, dtype=torch.float64, device="cuda")
+    launches = fe.fe_kernel_launches()
+    bad = [
+        dict(x=x.float(), y=y.float()),                               # float32 vectors
+        dict(x=x, y=y, n=65),                                         # n beyond the vectors
+        dict(x=x, y=y[:32], n=64),                                    # n beyond y
+        dict(x=x, y=y, out=torch.zeros(1, dtype=torch.float32, device="cuda")),  # float32 out
+        dict(x=x, y=y, out=torch.zeros(0, dtype=torch.float64, device="cuda")),  # empty out
+        dict(x=x[::2], y=y[::2]),                                     # strided views
+        dict(x=x.cpu(), y=y),                                         # x on the host
+    ]
+    for kw in bad:
+        with pytest.raises(fe.FeError) as err:
+            fe.fe_dot_noalloc(**kw)
+        assert err.value.code == fe.FE_ERR_ARG, kw
+    assert fe.fe_kernel_launches() == launches
+
+
+def test_dot_noalloc_allocates_nothing(fe):
+    """The property the entry point exists for: after the first call on the device (which looks up the
+    static array's address), further calls change neither torch's allocations nor the device's free memory."""
+    n = 300_001
+    x = torch.rand(n, dtype=torch.float64, device="cuda")
+    y = torch.rand(n, dtype=torch.float64, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fe.fe_dot_noalloc(x, y, out=out)
+    fe.fe_dot_noalloc(x, y)
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    free0, _ = torch.cuda.mem_get_info()
+    vals = []
+    for _ in range(4):
+        fe.fe_dot_noalloc(x, y, out=out)
+        torch.cuda.synchronize()
+        vals.append(out.item())
+        vals.append(fe.fe_dot_noalloc(x, y))
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0
+    assert len(set(vals)) == 1
