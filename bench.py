@@ -41,16 +41,19 @@ F64_MODE = 1  # FE_F64_DOUBLE_FLOAT: the library default for FP64 operator appli
 # vertex coordinates (1/8 vertex per dof x 24 B = 3 B).
 BYTES_PER_DOF_P2 = {"f64": 49.0, "f32": 41.0}
 # DRAM bytes per launch of the FP64 operator kernel on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of the single-kernel P2 64^3 case, mean of 2 launches),
-# keyed by FP64 mode; None where the kernel changed after the last capture.
-TRAFFIC = {0: 182.4e6, 1: 181.9e6, 2: 181.9e6}
+# dram__bytes_write.sum from one ncu capture of the finest level's applications inside a V-cycle of the
+# P2 64^3 hierarchy, the kernel the CG iterations run; mean of 2 launches), keyed by FP64 mode; None where
+# the kernel changed after the last capture.
+TRAFFIC = {0: None, 1: 117.1e6, 2: None}
 # Arithmetic of one P2 element application (c, d, S, four G-products, transpose),
-# per tet: 151 flops in the FP64 formula (an FMA counts 2).  The float-pair form
-# of the same formula issues 976 FP32 operations (an add, mul or FMA counts 1):
-# 71 float-pair additions x 8, 12 three-term float-pair dot products x 28,
-# 8 small-integer scalings x 6, 12 power-of-two scalings x 2.
+# per tet: 151 flops in the FP64 formula with a general G (an FMA counts 2).  The
+# float-pair form with the geometric matrix shared by every Kuhn tet (G = c M)
+# issues 798 FP32 operations (an add, mul or FMA counts 1): 71 float-pair
+# additions x 8, the four products M t as 16 float-pair subtractions x 8,
+# 8 small-integer scalings x 6, 7 power-of-two scalings x 2 and ten products
+# by c x 4.
 FLOPS_PER_CELL_P2_F64 = 151
-OPS_PER_CELL_P2_DF = 976
+OPS_PER_CELL_P2_DF = 798
 # Operations of one P3 element application through the gradient at the P2 nodes (fe_p3.cuh; an FMA counts 1):
 # 206 additions, 165 multiplications, 284 FMAs, 22 negations (counted by tests/test_p3_element_host.py)
 OPS_PER_CELL_P3 = 677
@@ -715,7 +718,7 @@ def run_ours(args, rank, world, local_rank, oracle=None):
         kname = ("k_apply_df<2> (FP64 operator: float-pair element arithmetic on the FP32 pipes, persistent, one tet "
                  "per thread)")
         ops, opeak, ounit = OPS_PER_CELL_P2_DF * C, FP32_PEAK_TOPS, "T FP32 op/s"
-        oderiv = ("976 FP32 operations per tet of the float-pair element formula x cells / launch duration, against the "
+        oderiv = ("798 FP32 operations per tet of the float-pair element formula x cells / launch duration, against the "
                   "nominal FP32 issue rate 152 SMs x 128 lanes x 1 op/clk x 2.07 GHz = 40.3 T op/s (no measured FP32 "
                   "peak exists)")
     else:

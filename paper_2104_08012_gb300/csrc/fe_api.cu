@@ -1081,6 +1081,7 @@ static void set_coefficient_impl(fe_hierarchy* h, const double* kappa, cudaStrea
   for (int l = 0; l < h->nlev; ++l) {
     launch_geometry(h->L[l], s);
     launch_split_geometry(h->L[l], s);
+    launch_uniform_geometry(h->L[l], h->cs.flag, s);
     launch_diag(h->L[l], h->tmp, s);
   }
   if (h->smoother == FE_SMOOTHER_PATCH && h->deg >= 2)

@@ -39,6 +39,8 @@ struct BLevel {
   const int* map;
   const double* geo;
   const float2* geodf;  // geo as float pairs (double-float operator)
+  const float2* cdf;    // with `uniform`: c per cell as a float pair, G = c M (the Kuhn tets' shared matrix)
+  int uniform;
   const double* dinv;
   const double* detj;
   const int* bnd;
@@ -324,12 +326,17 @@ __device__ void apply_cells(const Params& A, const BProb& P, const BLevel& L, in
 #pragma unroll
       for (int j = 0; j < ND; ++j) ud[j] = fe_df::split_scaled(u[j], emax);
       if (emax == 0x7FF) ud[0] = fe_df::DF(__int_as_float(0x7fc00000), 0.0f);
+      if (L.uniform) {
+        const float2 v = L.cdf[c];
+        fe_df::element_df_m<DEG>(ud, fe_df::DF(v.x, v.y), od);
+      } else {
 #pragma unroll
-      for (int a = 0; a < 6; ++a) {
-        const float2 v = L.geodf[(size_t)a * L.Cs + c];
-        gd[a] = fe_df::DF(v.x, v.y);
+        for (int a = 0; a < 6; ++a) {
+          const float2 v = L.geodf[(size_t)a * L.Cs + c];
+          gd[a] = fe_df::DF(v.x, v.y);
+        }
+        fe_df::element_df<DEG>(ud, gd, od);
       }
-      fe_df::element_df<DEG>(ud, gd, od);
 #pragma unroll
       for (int j = 0; j < ND; ++j)
         if (idx[j] >= 0)
@@ -605,6 +612,8 @@ void fill_problems(fe_batch* B, double cheb_lo, double cheb_hi) {
       D.map = L.map;
       D.geo = L.geo64;
       D.geodf = L.geodf;
+      D.cdf = L.cdf;
+      D.uniform = L.uniform;
       D.dinv = L.dinv64;
       D.detj = L.detj;
       D.bnd = L.bnd;

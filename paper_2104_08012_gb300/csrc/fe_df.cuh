@@ -114,6 +114,59 @@ __device__ __forceinline__ void p2_element_df(const DF (&u)[10], const DF (&g)[6
   y[9] = scale2(b23 + b32, 4.f);
 }
 
+// h = M t for the geometric matrix shared by every Kuhn tet, M = U^-1 U^-T =
+// [[2,-1,0],[-1,2,-1],[0,-1,1]] (U the upper-triangular matrix of ones):
+// v = U^-T t = (t0, t1 - t0, t2 - t1), then h = U^-1 v = (v0 - v1, v1 - v2, v2).
+__device__ __forceinline__ void mmul(DF t0, DF t1, DF t2, DF& h0, DF& h1, DF& h2) {
+  const DF v1 = t1 - t0, v2 = t2 - t1;
+  h0 = t0 - v1;
+  h1 = v1 - v2;
+  h2 = v2;
+}
+
+// p2_element_df with G = c M (c = kappa h / 120 of the cell): the same vertex-
+// gradient formula with the three-term G products replaced by mmul, the ten
+// results multiplied by c at the end (the element map is linear).
+__device__ __forceinline__ void p2_element_df_m(const DF (&u)[10], DF c, DF (&y)[10]) {
+  const DF f01 = scale2(u[4], 4.f), f02 = scale2(u[5], 4.f), f03 = scale2(u[6], 4.f);
+  const DF f12 = scale2(u[7], 4.f), f13 = scale2(u[8], 4.f), f23 = scale2(u[9], 4.f);
+  const DF c00 = scalek(u[0], 3.f), c01 = f01 - u[1], c02 = f02 - u[2], c03 = f03 - u[3];
+  const DF c10 = f01 - u[0], c11 = scalek(u[1], 3.f), c12 = f12 - u[2], c13 = f13 - u[3];
+  const DF c20 = f02 - u[0], c21 = f12 - u[1], c22 = scalek(u[2], 3.f), c23 = f23 - u[3];
+  const DF c30 = f03 - u[0], c31 = f13 - u[1], c32 = f23 - u[2], c33 = scalek(u[3], 3.f);
+  const DF d00 = c01 - c00, d01 = c02 - c00, d02 = c03 - c00;
+  const DF d10 = c11 - c10, d11 = c12 - c10, d12 = c13 - c10;
+  const DF d20 = c21 - c20, d21 = c22 - c20, d22 = c23 - c20;
+  const DF d30 = c31 - c30, d31 = c32 - c30, d32 = c33 - c30;
+  const DF S0 = (d00 + d10) + (d20 + d30), S1 = (d01 + d11) + (d21 + d31), S2 = (d02 + d12) + (d22 + d32);
+  DF b01, b02, b03, b11, b12, b13, b21, b22, b23, b31, b32, b33;
+  mmul(S0 + d00, S1 + d01, S2 + d02, b01, b02, b03);
+  mmul(S0 + d10, S1 + d11, S2 + d12, b11, b12, b13);
+  mmul(S0 + d20, S1 + d21, S2 + d22, b21, b22, b23);
+  mmul(S0 + d30, S1 + d31, S2 + d32, b31, b32, b33);
+  const DF b00 = -(b01 + b02 + b03), b10 = -(b11 + b12 + b13), b20 = -(b21 + b22 + b23), b30 = -(b31 + b32 + b33);
+  y[0] = mul(c, scalek(b00, 3.f) - ((b10 + b20) + b30));
+  y[1] = mul(c, scalek(b11, 3.f) - ((b01 + b21) + b31));
+  y[2] = mul(c, scalek(b22, 3.f) - ((b02 + b12) + b32));
+  y[3] = mul(c, scalek(b33, 3.f) - ((b03 + b13) + b23));
+  const DF c4 = scale2(c, 4.f);
+  y[4] = mul(c4, b01 + b10);
+  y[5] = mul(c4, b02 + b20);
+  y[6] = mul(c4, b03 + b30);
+  y[7] = mul(c4, b12 + b21);
+  y[8] = mul(c4, b13 + b31);
+  y[9] = mul(c4, b23 + b32);
+}
+
+__device__ __forceinline__ void p1_element_df_m(const DF (&u)[4], DF c, DF (&y)[4]) {
+  DF h0, h1, h2;
+  mmul(u[1] - u[0], u[2] - u[0], u[3] - u[0], h0, h1, h2);
+  y[1] = mul(c, h0);
+  y[2] = mul(c, h1);
+  y[3] = mul(c, h2);
+  y[0] = -((y[1] + y[2]) + y[3]);
+}
+
 __device__ __forceinline__ void p1_element_df(const DF (&u)[4], const DF (&g)[6], DF (&y)[4]) {
   DF h0, h1, h2;
   gmul(g, u[1] - u[0], u[2] - u[0], u[3] - u[0], h0, h1, h2);
@@ -162,6 +215,14 @@ __device__ __forceinline__ void element_df(const DF (&u)[DEG == 1 ? 4 : 10], con
     p1_element_df(u, g, y);
   else
     p2_element_df(u, g, y);
+}
+
+template <int DEG>
+__device__ __forceinline__ void element_df_m(const DF (&u)[DEG == 1 ? 4 : 10], DF c, DF (&y)[DEG == 1 ? 4 : 10]) {
+  if constexpr (DEG == 1)
+    p1_element_df_m(u, c, y);
+  else
+    p2_element_df_m(u, c, y);
 }
 
 // Whether cube-local node l already received a contribution from one of the
@@ -220,6 +281,19 @@ __device__ __forceinline__ double widen_scaled(float f, int emax) {
   return __hiloint2double((int)(sgn | ((unsigned int)eh << 20) | ((b & 0x7FFFFFu) >> 3)), (int)((b & 7u) << 29));
 }
 
+
+// widen_scaled for a tet whose exponent emax lies in [127, 1918]: then every
+// normal float f maps to a normal double (biased exponent ef + emax - 127 in
+// [1, 2045]) and zero or subnormal f (negligible against the tet's largest
+// term) to +-0, so no range branches are needed.  kexp = (emax - 127) << 20.
+__device__ __forceinline__ double widen_in_range(float f, unsigned int kexp) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int mag = b & 0x7FFFFFFFu, sgn = b & 0x80000000u;
+  const bool normal = mag >= 0x00800000u;
+  const unsigned int hi = normal ? (((mag >> 3) + kexp) | sgn) : sgn;
+  const unsigned int lo = normal ? (b << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
 
 // Producer-side split of an FP64 value into the unscaled float pair that the
 // operator kernels gather (hi holds the leading 24 significant bits, lo the

@@ -30,6 +30,9 @@ namespace {
 using namespace fe_df;
 constexpr int kBlock = 256;
 constexpr int kBlockP3 = 128;
+#ifndef KDF_MINB
+#define KDF_MINB 2  // resident blocks per SM the pre-split, uniform-geometry float-pair kernel is compiled for
+#endif
 
 // The dofs whose countdown this thread ended (count returned 1): every other
 // contribution was fenced before its countdown, so after an acquiring fence
@@ -66,13 +69,17 @@ __device__ __forceinline__ void finish_dofs(const int* pidx, const unsigned* pre
 // updates d_i and x_i in place.  Every tet
 // gathers x before it scatters, so x_i only changes once all its readers are
 // done.  Dirichlet rows (y = x) are updated by the threads that write them.
-template <int DEG, bool FUSE, bool PRE>
-__global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
+//
+// UNI: geo is L.cdf, one float pair c per cell with G = c M (see Level), and
+// the element uses the fixed matrix M instead of six loaded factors.
+template <int DEG, bool FUSE, bool PRE, bool UNI>
+__global__ void __launch_bounds__(kBlock, UNI && PRE ? KDF_MINB : 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
                                                         const float2* __restrict__ geo, const double* x,
                                                         const float2* __restrict__ xs, double* __restrict__ y, int nb,
                                                         const int* __restrict__ bnd, ChebFuse<double> cf) {
   static_assert(!(FUSE && PRE), "the fused smoother changes x during the launch");
   constexpr int ND = DEG == 1 ? 4 : 10;
+  constexpr int NG = UNI ? 1 : 6;  // geometric values per cell
   using XV = typename std::conditional<PRE, float2, double>::type;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   for (int i = tid; i < nb; i += stride) {  // Dirichlet rows: identity
@@ -95,34 +102,35 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int
   if (c >= C) return;
   int idx[ND];
   XV xv[ND];
-  float2 gv[6];
+  float2 gv[NG];
 #pragma unroll
   for (int j = 0; j < ND; ++j) idx[j] = __ldg(map + (size_t)j * Cs + c);
 #pragma unroll
   for (int j = 0; j < ND; ++j) xv[j] = ldx(idx[j]);
 #pragma unroll
-  for (int a = 0; a < 6; ++a) gv[a] = __ldg(geo + (size_t)a * Cs + c);
+  for (int a = 0; a < NG; ++a) gv[a] = __ldg(geo + (size_t)a * Cs + c);
   while (true) {
     const int cn = c + stride;
     const bool more = cn < C;
     int idn[ND];
     XV xn[ND];
-    float2 gn[6];
+    float2 gn[NG];
     if (more) {
 #pragma unroll
       for (int j = 0; j < ND; ++j) idn[j] = __ldg(map + (size_t)j * Cs + cn);
 #pragma unroll
       for (int j = 0; j < ND; ++j) xn[j] = ldx(idn[j]);
 #pragma unroll
-      for (int a = 0; a < 6; ++a) gn[a] = __ldg(geo + (size_t)a * Cs + cn);
+      for (int a = 0; a < NG; ++a) gn[a] = __ldg(geo + (size_t)a * Cs + cn);
     }
-    DF u[ND], g[6], out[ND];
+    DF u[ND], out[ND];
     int emax;  // the element map is linear: scale by 2^(1023 - emax), contract, unscale
     bool split_here = !PRE;
     if constexpr (PRE) {
-      int ef = 0;  // largest float exponent of the pairs (0xFF: a marker)
+      unsigned int mb = 0u;  // largest magnitude bits of the leading floats (a marker NaN exceeds every finite one)
 #pragma unroll
-      for (int j = 0; j < ND; ++j) ef = max(ef, (int)((__float_as_uint(xv[j].x) >> 23) & 0xFFu));
+      for (int j = 0; j < ND; ++j) mb = max(mb, __float_as_uint(xv[j].x) & 0x7FFFFFFFu);
+      const int ef = (int)(mb >> 23);  // its exponent field (0xFF: a marker)
       if (ef != 0xFF) {
         const float f = __uint_as_float((unsigned int)(254 - ef) << 23);  // 2^(127 - ef)
 #pragma unroll
@@ -146,12 +154,24 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int
       for (int j = 0; j < ND; ++j) u[j] = split_scaled(xd[j], emax);
       if (emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
     }
+    if constexpr (UNI) {
+      element_df_m<DEG>(u, DF(gv[0].x, gv[0].y), out);
+    } else {
+      DF g[6];
 #pragma unroll
-    for (int a = 0; a < 6; ++a) g[a] = DF(gv[a].x, gv[a].y);
-    element_df<DEG>(u, g, out);
+      for (int a = 0; a < 6; ++a) g[a] = DF(gv[a].x, gv[a].y);
+      element_df<DEG>(u, g, out);
+    }
+    if (emax >= 127 && emax <= 1918) {  // every contribution widens without range checks
+      const unsigned int kexp = (unsigned int)(emax - 127) << 20;
 #pragma unroll
-    for (int j = 0; j < ND; ++j)
-      if (idx[j] >= 0) atomicAdd(y + idx[j], widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
+      for (int j = 0; j < ND; ++j)
+        if (idx[j] >= 0) atomicAdd(y + idx[j], widen_in_range(out[j].hi, kexp) + widen_in_range(out[j].lo, kexp));
+    } else {
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+        if (idx[j] >= 0) atomicAdd(y + idx[j], widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
+    }
     if constexpr (FUSE) {
       // the previous tet's countdowns have returned by now: finish its dofs
       if (have_prev) finish_dofs<ND>(pidx, prev, y, cf);
@@ -171,7 +191,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int
       xv[j] = xn[j];
     }
 #pragma unroll
-    for (int a = 0; a < 6; ++a) gv[a] = gn[a];
+    for (int a = 0; a < NG; ++a) gv[a] = gn[a];
   }
   if constexpr (FUSE)
     if (have_prev) finish_dofs<ND>(pidx, prev, y, cf);
@@ -247,7 +267,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_apply_df2(int P, int Cs, const in
 // P3, one tet per thread (persistent grid-stride loop): the element through
 // the gradient at the P2 nodes (fe_p3.cuh) in float pairs, on the geometric
 // factors kappa G / 161280 split once per tet; dofs split and contributions
-// widened per tet as in k_apply_df.
+// widened per tet as in k_apply_df.  UNI: geo is L.cdf (G = c M per cell).
+template <bool UNI>
 __global__ void __launch_bounds__(kBlockP3, 2) k_apply_df3(int C, int Cs, const int* __restrict__ map,
                                                            const float2* __restrict__ geo,
                                                            const double* __restrict__ x, double* __restrict__ y,
@@ -264,7 +285,7 @@ __global__ void __launch_bounds__(kBlockP3, 2) k_apply_df3(int C, int Cs, const 
     }
     DF g[6];
 #pragma unroll
-    for (int a = 0; a < 6; ++a) {
+    for (int a = 0; a < (UNI ? 1 : 6); ++a) {
       const float2 v = __ldg(geo + (size_t)a * Cs + c);
       g[a] = DF(v.x, v.y);
     }
@@ -273,7 +294,7 @@ __global__ void __launch_bounds__(kBlockP3, 2) k_apply_df3(int C, int Cs, const 
 #pragma unroll
     for (int j = 0; j < ND; ++j) u[j] = split_scaled(xv[j], emax);
     if (emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
-    fe_p3::p3_element_grad<fe_p3::DFOps>(u, g, out);
+    fe_p3::p3_element_grad<fe_p3::DFOps, UNI>(u, g, out);
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
       const int m = __ldg(map + (size_t)j * Cs + c);
@@ -487,13 +508,21 @@ static void apply_cube_df(const Level& L, const double* x, double* y, const Cheb
   LAUNCH_CHECK();
 }
 
-template <int DEG, bool FUSE, bool PRE>
+template <int DEG, bool FUSE, bool PRE, bool UNI>
 static void apply_df_launch(const Level& L, const double* x, const float2* xs, double* y, const ChebFuse<double>& cf,
                             cudaStream_t s) {
   static int g = 0;
-  if (!g) g = resident_grid(k_apply_df<DEG, FUSE, PRE>, kBlock, 1 << 30);
-  k_apply_df<DEG, FUSE, PRE><<<std::min(g, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(
-      L.C, L.Cs, L.map, L.geodf, x, xs, y, L.nb, L.bnd, cf);
+  if (!g) g = resident_grid(k_apply_df<DEG, FUSE, PRE, UNI>, kBlock, 1 << 30);
+  k_apply_df<DEG, FUSE, PRE, UNI><<<std::min(g, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(
+      L.C, L.Cs, L.map, UNI ? L.cdf.p : L.geodf.p, x, xs, y, L.nb, L.bnd, cf);
+}
+
+template <int DEG, bool PRE>
+static void apply_df_geo(const Level& L, const double* x, const float2* xs, double* y, cudaStream_t s) {
+  if (L.uniform)
+    apply_df_launch<DEG, false, PRE, true>(L, x, xs, y, ChebFuse<double>{}, s);
+  else
+    apply_df_launch<DEG, false, PRE, false>(L, x, xs, y, ChebFuse<double>{}, s);
 }
 
 template <bool FUSE>
@@ -502,19 +531,19 @@ static void apply_df(const Level& L, const double* x, const float2* xs, double* 
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
   if constexpr (FUSE) {
     if (L.deg == 1)
-      apply_df_launch<1, true, false>(L, x, nullptr, y, cf, s);
+      apply_df_launch<1, true, false, false>(L, x, nullptr, y, cf, s);
     else
-      apply_df_launch<2, true, false>(L, x, nullptr, y, cf, s);
+      apply_df_launch<2, true, false, false>(L, x, nullptr, y, cf, s);
   } else if (L.deg == 1) {
     if (xs)
-      apply_df_launch<1, false, true>(L, x, xs, y, cf, s);
+      apply_df_geo<1, true>(L, x, xs, y, s);
     else
-      apply_df_launch<1, false, false>(L, x, nullptr, y, cf, s);
+      apply_df_geo<1, false>(L, x, nullptr, y, s);
   } else {
     if (xs)
-      apply_df_launch<2, false, true>(L, x, xs, y, cf, s);
+      apply_df_geo<2, true>(L, x, xs, y, s);
     else
-      apply_df_launch<2, false, false>(L, x, nullptr, y, cf, s);
+      apply_df_geo<2, false>(L, x, nullptr, y, s);
   }
   LAUNCH_CHECK();
 }
@@ -534,9 +563,12 @@ void launch_apply64_df3(const Level& L, const double* x, double* y, cudaStream_t
   FE_REQUIRE(L.deg == 3, FE_ERR_UNSUPPORTED, "the float-pair P3 kernel needs a degree-3 level");
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)L.n, s));
   static int g = 0;
-  if (!g) g = resident_grid(k_apply_df3, kBlockP3, 1 << 30);
-  k_apply_df3<<<std::min(g, ceil_div(std::max(L.C, L.nb), kBlockP3)), kBlockP3, 0, s>>>(L.C, L.Cs, L.map, L.geodf, x,
-                                                                                       y, L.nb, L.bnd);
+  if (!g) g = resident_grid(k_apply_df3<true>, kBlockP3, 1 << 30);
+  const int grid = std::min(g, ceil_div(std::max(L.C, L.nb), kBlockP3));
+  if (L.uniform)
+    k_apply_df3<true><<<grid, kBlockP3, 0, s>>>(L.C, L.Cs, L.map, L.cdf, x, y, L.nb, L.bnd);
+  else
+    k_apply_df3<false><<<grid, kBlockP3, 0, s>>>(L.C, L.Cs, L.map, L.geodf, x, y, L.nb, L.bnd);
   LAUNCH_CHECK();
 }
 

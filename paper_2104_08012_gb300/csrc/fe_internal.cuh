@@ -200,6 +200,14 @@ struct Level {
   DBuf<double> geo64;     // [6][Cs] kappa*|detJ| J^-1 J^-T / w  (w = 6 for P1, 120 for P2)
   DBuf<float> geo32;
   DBuf<float2> geodf;     // [6][Cs] geo64 split into float pairs (hi, lo) for the double-float apply
+  // Every Kuhn tet of UnitCubeMesh has J = h P U (P a permutation, U the upper-triangular matrix of ones), so
+  // G = |det J| J^-1 J^-T = h U^-1 U^-T = h M, M = [[2,-1,0],[-1,2,-1],[0,-1,1]], the same for every cell:
+  // geo64 = c M with c = kappa h / w per cell.  Set-up checks this cell by cell against the G computed from the
+  // vertex coordinates (uniform = 1 when every cell agrees) and keeps c for the operator kernels that then read
+  // one value per cell instead of six.
+  int uniform = 0;
+  DBuf<float> c32;        // [C] c in FP32
+  DBuf<float2> cdf;       // [C] c as a float pair
   DBuf<float2> massdf;    // |det J| / 120 (P1) or / 2520 (P2) per cell as a float pair (double-float mass)
   DBuf<double> dinv64;    // 1/diag(A)
   DBuf<float> dinv32;
@@ -384,6 +392,8 @@ template <typename T>
 void launch_cheb_pc(int n, const T* z, T* x, T* d, double c1, double c2, bool first_from_zero, bool store_d,
                     cudaStream_t s);
 void launch_split_geometry(Level& L, cudaStream_t s);
+// Checks geo64 = c M cell by cell, fills c32 and cdf and sets L.uniform (synchronises s).
+void launch_uniform_geometry(Level& L, int* dflag, cudaStream_t s);
 // b -= A g on interior rows and b = g on the boundary (inhomogeneous Dirichlet data, symmetric elimination)
 void launch_bc_lift(const Level& L, const double* g, double* b, cudaStream_t s);
 void launch_mass(const Level& L, const double* x, double* y, cudaStream_t s);

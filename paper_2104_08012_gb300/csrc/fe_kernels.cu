@@ -63,6 +63,18 @@ __device__ __forceinline__ void tet_element(const T* u, const T* g, T* y) {
   }
 }
 
+// The same with G = c M (every Kuhn tet shares M = [[2,-1,0],[-1,2,-1],[0,-1,1]]).
+template <int DEG, typename T>
+__device__ __forceinline__ void tet_element_m(const T* u, T c, T* y) {
+  if constexpr (DEG == 3) {
+    const T gg[6] = {c, T(0), T(0), T(0), T(0), T(0)};
+    fe_p3::p3_element_grad<fe_p3::PlainOps<T>, true>(u, gg, y);
+  } else {
+    const T g[6] = {T(2) * c, -c, T(0), T(2) * c, -c, c};
+    element_apply<DEG, T>(u, g, y);
+  }
+}
+
 // Geometric factors are stored as kappa G / w: w = 6 (P1), 120 (P2) and
 // 161280 = 64 x 2520 (P3) fold the element formulas' reference integrals.
 template <int DEG>
@@ -174,12 +186,31 @@ __global__ void k_geometry(int C, int Cs, const int* __restrict__ map, const dou
   detj[c] = adet;
 }
 
+// geo64 = c M for every cell (M = [[2,-1,0],[-1,2,-1],[0,-1,1]] in the stored
+// order 00, 01, 02, 11, 12, 22), c = geo64[22]; a cell whose G differs from
+// c M by more than 1e-12 |c| sets the flag.
+__global__ void k_uniform_geometry(int C, int Cs, const double* __restrict__ geo64, float* __restrict__ c32,
+                                   float2* __restrict__ cdf, int* __restrict__ flag) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C) return;
+  const double c = geo64[(size_t)5 * Cs + t];
+  const double m[5] = {2.0, -1.0, 0.0, 2.0, -1.0};
+  bool ok = c > 0.0;
+#pragma unroll
+  for (int a = 0; a < 5; ++a) ok = ok && fabs(geo64[(size_t)a * Cs + t] - m[a] * c) <= 1e-12 * c;
+  if (!ok) atomicOr(flag, 1);
+  c32[t] = (float)c;
+  const float hi = (float)c;
+  cdf[t] = make_float2(hi, (float)(c - (double)hi));
+}
+
 // ------------------------------------------------------ operator apply
 // One thread per tet: gather the cell dofs through the cell->dof map
 // (coalesced: the map is stored [dof][cell]), contract with the cell's
 // geometric factors, scatter-add with atomics.  Extra threads past the last
 // cell copy x -> y on the Dirichlet dofs (identity rows).
-template <int DEG, typename T>
+// UNI: only row 5 of geo is read, c = G_22 with G = c M (see Level).
+template <int DEG, typename T, bool UNI>
 __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const int* __restrict__ map,
                                                   const T* __restrict__ geo, const T* __restrict__ x,
                                                   T* __restrict__ y, int nb, const int* __restrict__ bnd) {
@@ -193,11 +224,15 @@ __global__ void __launch_bounds__(kBlock) k_apply(int C, int Cs, int Cpad, const
       idx[j] = __ldg(map + (size_t)j * Cs + t);
       u[j] = idx[j] >= 0 ? __ldg(x + idx[j]) : T(0);
     }
-    T g[6];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) g[a] = __ldg(geo + (size_t)a * Cs + t);
     T out[ND];
-    tet_element<DEG, T>(u, g, out);
+    if constexpr (UNI) {
+      tet_element_m<DEG, T>(u, __ldg(geo + (size_t)5 * Cs + t), out);
+    } else {
+      T g[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) g[a] = __ldg(geo + (size_t)a * Cs + t);
+      tet_element<DEG, T>(u, g, out);
+    }
 #pragma unroll
     for (int j = 0; j < ND; ++j)
       if (idx[j] >= 0) atomicAdd(y + idx[j], out[j]);
@@ -244,7 +279,9 @@ __global__ void __launch_bounds__(kBlock) k_bc_lift(int C, int Cs, const int* __
 // (k+1)^3 atomics instead of 6 * nd (27 instead of 60 for P2).
 constexpr int kCubeBlock = 128;  // 4 blocks of 128 per SM at 128 registers: 5% faster than 2 of 256
 
-template <int DEG, bool FUSE>
+// UNI: geo is c32 (one value per cell, geometric factors c M, see Level)
+// instead of the six stored factors per cell.
+template <int DEG, bool FUSE, bool UNI>
 __global__ void __launch_bounds__(kCubeBlock, 4) k_apply_cube(int Q, int Qs, int Cs, int Qpad,
                                                             const int* __restrict__ cmap,
                                                             const float* __restrict__ geo, const float* x,
@@ -262,10 +299,11 @@ __global__ void __launch_bounds__(kCubeBlock, 4) k_apply_cube(int Q, int Qs, int
       acc[l] = 0.0f;
     }
     // The cube's six tets are cells 6q .. 6q+5, contiguous in every row of
-    // geo: one 8-byte load fetches G_a of two tets.
-    float2 gp[6][3];
+    // geo: one 8-byte load fetches G_a (or c) of two tets.
+    constexpr int NR = UNI ? 1 : 6;
+    float2 gp[NR][3];
 #pragma unroll
-    for (int a = 0; a < 6; ++a)
+    for (int a = 0; a < NR; ++a)
 #pragma unroll
       for (int h = 0; h < 3; ++h) gp[a][h] = __ldg(reinterpret_cast<const float2*>(geo + (size_t)a * Cs + 6 * q) + h);
 #pragma unroll
@@ -273,8 +311,13 @@ __global__ void __launch_bounds__(kCubeBlock, 4) k_apply_cube(int Q, int Qs, int
       float u[ND], g[6], o[ND];
 #pragma unroll
       for (int j = 0; j < ND; ++j) u[j] = xv[cube_local(DEG, t, j)];
+      if constexpr (UNI) {
+        const float c = (t & 1) ? gp[0][t >> 1].y : gp[0][t >> 1].x;
+        g[0] = 2.0f * c, g[1] = -c, g[2] = 0.0f, g[3] = 2.0f * c, g[4] = -c, g[5] = c;
+      } else {
 #pragma unroll
-      for (int a = 0; a < 6; ++a) g[a] = (t & 1) ? gp[a][t >> 1].y : gp[a][t >> 1].x;
+        for (int a = 0; a < 6; ++a) g[a] = (t & 1) ? gp[a][t >> 1].y : gp[a][t >> 1].x;
+      }
       element_apply<DEG, float>(u, g, o);
 #pragma unroll
       for (int j = 0; j < ND; ++j) acc[cube_local(DEG, t, j)] += o[j];
@@ -929,6 +972,20 @@ void launch_build_level(Level& L, cudaStream_t s) {
   LAUNCH_CHECK();
 }
 
+void launch_uniform_geometry(Level& L, int* dflag, cudaStream_t s) {
+  if (!L.c32.p) {
+    L.c32.alloc(L.C);
+    L.cdf.alloc(L.C);
+  }
+  CUDA_CHECK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+  k_uniform_geometry<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, L.c32, L.cdf, dflag);
+  LAUNCH_CHECK();
+  int hflag = 1;
+  CUDA_CHECK(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  L.uniform = hflag == 0 ? 1 : 0;
+}
+
 void launch_geometry(Level& L, cudaStream_t s) {
   by_degree(L.deg, [&](auto D) {
     k_geometry<D.value><<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.map, L.vx, L.vy, L.vz, L.kappa, L.geo64,
@@ -943,7 +1000,10 @@ static void apply_impl(const Level& L, const T* geo, const T* x, T* y, cudaStrea
   const int Cpad = ceil_div(L.C, kBlock) * kBlock;
   const int grid = ceil_div((long long)Cpad + L.nb, kBlock);
   by_degree(L.deg, [&](auto D) {
-    k_apply<D.value, T><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, geo, x, y, L.nb, L.bnd);
+    if (L.uniform)
+      k_apply<D.value, T, true><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, geo, x, y, L.nb, L.bnd);
+    else
+      k_apply<D.value, T, false><<<grid, kBlock, 0, s>>>(L.C, L.Cs, Cpad, L.map, geo, x, y, L.nb, L.bnd);
   });
   LAUNCH_CHECK();
 }
@@ -953,10 +1013,17 @@ static void apply_cube32(const Level& L, const float* x, float* y, const ChebFus
   CUDA_CHECK(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)L.n, s));
   const int Qpad = ceil_div(L.Q, kCubeBlock) * kCubeBlock;
   const int grid = ceil_div((long long)Qpad + L.nb, kCubeBlock);
-  if (L.deg == 1)
-    k_apply_cube<1, FUSE><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd, cf);
+  // c32 rows start at multiples of 24 bytes per cube: the UNI kernel's float2 loads stay 8-byte aligned
+  if (L.deg == 1 && L.uniform)
+    k_apply_cube<1, FUSE, true><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.c32, x, y, L.nb, L.bnd, cf);
+  else if (L.deg == 1)
+    k_apply_cube<1, FUSE, false><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd,
+                                                             cf);
+  else if (L.uniform)
+    k_apply_cube<2, FUSE, true><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.c32, x, y, L.nb, L.bnd, cf);
   else
-    k_apply_cube<2, FUSE><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd, cf);
+    k_apply_cube<2, FUSE, false><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd,
+                                                             cf);
   LAUNCH_CHECK();
 }
 

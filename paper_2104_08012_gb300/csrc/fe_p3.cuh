@@ -75,6 +75,14 @@ struct PlainOps {
     h1 = g[1] * t0 + g[3] * t1 + g[4] * t2;
     h2 = g[2] * t0 + g[4] * t1 + g[5] * t2;
   }
+  // M t for M = [[2,-1,0],[-1,2,-1],[0,-1,1]], the geometric matrix of every Kuhn tet (G = c M)
+  __host__ __device__ static void mmul(V t0, V t1, V t2, V& h0, V& h1, V& h2) {
+    const V v1 = t1 - t0, v2 = t2 - t1;
+    h0 = t0 - v1;
+    h1 = v1 - v2;
+    h2 = v2;
+  }
+  __host__ __device__ static V mul(V a, V b) { return a * b; }
 };
 
 struct DFOps {
@@ -92,6 +100,8 @@ struct DFOps {
   __device__ static void gmul(const V (&g)[6], V t0, V t1, V t2, V& h0, V& h1, V& h2) {
     fe_df::gmul(g, t0, t1, t2, h0, h1, h2);
   }
+  __device__ static void mmul(V t0, V t1, V t2, V& h0, V& h1, V& h2) { fe_df::mmul(t0, t1, t2, h0, h1, h2); }
+  __device__ static V mul(V a, V b) { return fe_df::mul(a, b); }
 };
 
 // ------------------------------------------------------- compile-time folds
@@ -186,8 +196,9 @@ __host__ __device__ __forceinline__ void p2_mass_int(const typename Ops::V (&x)[
   }
 }
 
-// y = A_K u for one P3 tet; g = kappa G / 161280 (symmetric, 00 01 02 11 12 22).
-template <typename Ops>
+// y = A_K u for one P3 tet; g = kappa G / 161280 (symmetric, 00 01 02 11 12 22),
+// or with UNI g[0] = c for G = c M (the Kuhn tets' shared matrix, see mmul).
+template <typename Ops, bool UNI = false>
 __host__ __device__ __forceinline__ void p3_element_grad(const typename Ops::V* u, const typename Ops::V (&g)[6],
                                                 typename Ops::V* y) {
   using V = typename Ops::V;
@@ -205,7 +216,10 @@ __host__ __device__ __forceinline__ void p3_element_grad(const typename Ops::V* 
 #pragma unroll
     for (int n = 0; n < 10; ++n) {
       V h0, h1, h2;
-      Ops::gmul(g, w[0][n], w[1][n], w[2][n], h0, h1, h2);
+      if constexpr (UNI)
+        Ops::mmul(w[0][n], w[1][n], w[2][n], h0, h1, h2);
+      else
+        Ops::gmul(g, w[0][n], w[1][n], w[2][n], h0, h1, h2);
       hh[n][0] = Ops::neg(Ops::add(Ops::add(h0, h1), h2));
       hh[n][1] = h0;
       hh[n][2] = h1;
@@ -213,6 +227,10 @@ __host__ __device__ __forceinline__ void p3_element_grad(const typename Ops::V* 
     }
   }
   outputs<Ops>(hh, y, std::make_integer_sequence<int, 20>{});
+  if constexpr (UNI) {
+#pragma unroll
+    for (int i = 0; i < 20; ++i) y[i] = Ops::mul(g[0], y[i]);
+  }
 }
 
 }  // namespace fe_p3

@@ -120,7 +120,7 @@ def test_double_float_value_range(fe, scale, mode):
         assert torch.isnan(y).any()
 
 
-@pytest.mark.parametrize("scale", [1.0, 1e-40, 1e40, 1e-200, 1e200])
+@pytest.mark.parametrize("scale", [1.0, 1e-40, 1e40, 1e-100, 1e100])
 def test_presplit_inputs_match_in_kernel_split(fe, scale):
     """Inside the solver the P2 float-pair operator gathers its input as float pairs written by the kernel that
     produced it (Chebyshev update, prolongation, CG direction); dofs outside [2^-64, 2^64) are markers and their
@@ -151,21 +151,24 @@ def test_presplit_inputs_match_in_kernel_split(fe, scale):
 
 
 def test_paired_float_pair_kernel_matches_per_tet(fe):
-    """The packed two-tets-per-thread kernel evaluates the per-tet kernel's element formula lane by lane (the
-    negations are arranged to be exact), so both give the same contributions; the sums differ only by the
-    order of the atomic additions."""
+    """The packed two-tets-per-thread kernel evaluates the element with the six stored geometric factors per cell,
+    the per-tet kernel with one factor per cell times the matrix M shared by every Kuhn tet; both are the same
+    operator in float-pair arithmetic, so they agree to the FP64 rounding scale of each row."""
     with fe.Hierarchy(12, 0, 2) as h:
         kappa = I.grf_kappa(h.cell_centroids(), seed=5)
         h.set_coefficient(dt(kappa))
-        x = dt(I.random_vector(h.n_dofs(), 21))
+        L = O.Level(12, 2, kappa)
+        xh = I.random_vector(h.n_dofs(), 21)
+        x = dt(xh)
         ys = {}
         for mode in (fe.FE_F64_DOUBLE_FLOAT_TET, fe.FE_F64_DOUBLE_FLOAT_PAIR):
             h.set_f64_mode(mode)
             ys[mode] = torch.empty_like(x)
             h.apply_operator(x, ys[mode])
         torch.cuda.synchronize()
-        d = (ys[fe.FE_F64_DOUBLE_FLOAT_TET] - ys[fe.FE_F64_DOUBLE_FLOAT_PAIR]).abs().max().item()
-        assert d <= 1e-15 * ys[fe.FE_F64_DOUBLE_FLOAT_TET].abs().max().item()
+        scale = abs(L.A) @ np.abs(xh)
+        assert_rowwise(host(ys[fe.FE_F64_DOUBLE_FLOAT_TET]), host(ys[fe.FE_F64_DOUBLE_FLOAT_PAIR]), scale, 2e-14,
+                       "per-tet vs paired kernels")
 
 
 def test_apply_host_pointers_match_device(fe):
