@@ -325,6 +325,10 @@ def extras(fe, I, h, dev, stream, flush):
     out["batched_64"] = {"ms": ms, "total_dofs": tot, "DoF_per_s": tot / (ms * 1e-3),
                          "max_iterations": max(s.iterations for s in st),
                          "max_rel_residual": max(s.rel_residual for s in st), "schedule": B.schedule()}
+    with torch.cuda.stream(stream):  # the persistent launch's wall time by phase and level (direct launch)
+        stp = B.solve(fs, us, rtol=1e-8, profile=1, stream=stream)
+    out["batched_64"]["phases_ms_profiled"] = phase_summary(stp[0])
+    out["batched_64"]["profiled_solve_ms"] = stp[0].solve_ms
     # the same 64 problems solved one after another with the single-problem solver (for comparison)
     with torch.cuda.stream(stream):
         for hp, fp, up in zip(B.problems, fs, us):
@@ -429,6 +433,44 @@ def extras(fe, I, h, dev, stream, flush):
     out["paper_poisson_p3_128cubed"] = pw
     h5.close()
     del f5, ue5, u5
+    # ---- the paper's own hierarchy for that problem: 4 levels from UnitCubeMesh 16^3 (103,823 interior coarse
+    # unknowns), the coarse level solved directly with the blocked band Cholesky factor
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    t0 = time.perf_counter()
+    h6 = fe.Hierarchy(16, 3, 3)
+    torch.cuda.synchronize()
+    ph = {"workload": "P3 UnitCubeMesh 128^3 as the paper's 4-level hierarchy from 16^3, direct coarse solve "
+                      "(blocked band Cholesky)", "dofs": h6.n_dofs(), "setup_s": time.perf_counter() - t0,
+          "coarse": h6.coarse_info(), "device_bytes_after_setup": free0 - torch.cuda.mem_get_info()[0]}
+    X6 = h6.dof_coordinates()
+    f6 = torch.from_numpy(I.sin_product_rhs(X6)).to(dev)
+    ue6 = torch.from_numpy(I.sin_product(X6)).to(dev)
+    del X6
+    u6 = torch.empty_like(f6)
+
+    def run6(name, reps=2, **kw):
+        with torch.cuda.stream(stream):
+            st = h6.solve(f6, u6, stream=stream, **kw)
+            ms = time_launches(lambda: h6.solve(f6, u6, stream=stream, **kw), stream, reps, flush)
+            stp = h6.solve(f6, u6, stream=stream, profile=1, **kw)
+        ph[name] = {"ms": ms, "DoF_per_s": h6.n_dofs() / (ms * 1e-3), "iterations": st.iterations,
+                    "max_nodal_error_vs_exact": float((u6 - ue6).abs().max()),
+                    "coarse_solve_ms_profiled": stp.phase_ms[fe.FE_PHASE_COARSE][0],
+                    "phases_ms_profiled": phase_summary(stp)}
+
+    run6("jacobi_gmg_pcg_1e-8", rtol=1e-8)
+    run6("jacobi_full_multigrid_2_cycles", precond=fe.FE_PC_FMG, max_it=2)
+    t0 = time.perf_counter()
+    h6.set_smoother(fe.FE_SMOOTHER_PATCH)
+    torch.cuda.synchronize()
+    ph["patch_setup_s"] = time.perf_counter() - t0
+    run6("paper_solver_full_multigrid_patch_1_cycle", precond=fe.FE_PC_FMG, max_it=1)
+    run6("paper_solver_full_multigrid_patch_2_cycles", precond=fe.FE_PC_FMG, max_it=2)
+    ph["device_bytes_with_patches"] = free0 - torch.cuda.mem_get_info()[0]
+    out["paper_poisson_p3_128cubed_paper_hierarchy"] = ph
+    h6.close()
+    del f6, ue6, u6
     return out
 
 

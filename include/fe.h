@@ -73,7 +73,8 @@ extern "C" {
 /* ---- arithmetic types of an operator application ---- */
 #define FE_F64 0   /* vectors double, arithmetic FP64 */
 #define FE_F32 1   /* vectors float, arithmetic FP32 */
-#define FE_BF16 2  /* vectors float; dofs rounded to bf16 and contracted on the tensor cores, FP32 accumulation */
+#define FE_BF16 2  /* vectors float; each dof split into two bf16 terms and contracted on the tensor cores
+                      (tcgen05, FP32 accumulation in TMEM) against exact bf16 reference tables; P1, P2, P3 */
 
 /* ---- arithmetic of FP64 operator applications (fe_set_f64_mode) ---- */
 #define FE_F64_NATIVE 0        /* FP64 FMA on the FP64 pipe */
@@ -182,9 +183,8 @@ void fe_mesh_destroy(fe_mesh* mesh);
  * Degree 3 (20 dofs per tet, dofs numbered lexicographically on the 3N
  * lattice): the operator applies each tet's element through the gradient at
  * its 10 P2 nodes (677 operations), in float pairs (FP64 default), FP64
- * (FE_F64_NATIVE) or FP32; the bf16 tensor-core operator and the batched
- * solver are P1/P2 only and return FE_ERR_UNSUPPORTED for a degree-3
- * hierarchy. */
+ * (FE_F64_NATIVE), FP32 or on the bf16 tensor cores; the batched solver is
+ * P1/P2 only and returns FE_ERR_UNSUPPORTED for a degree-3 hierarchy. */
 int fe_hierarchy_refine(const fe_mesh* coarse, int nrefine, int degree, fe_hierarchy** out);
 void fe_hierarchy_destroy(fe_hierarchy* h);
 
@@ -215,8 +215,11 @@ int fe_set_coefficient(fe_hierarchy* h, const double* kappa_cells, void* stream)
  * int_K grad(u) . grad(v) applied to the gathered dofs x_K, scatter-added
  * into y; boundary rows give y_i = x_i and boundary entries of x are treated
  * as 0 in interior rows.  dtype FE_F64: x, y double.  FE_F32: float.
- * FE_BF16: float vectors, x rounded to bf16 and contracted on the tensor
- * cores with FP32 accumulation.  x and y must not overlap. */
+ * FE_BF16: float vectors, each dof entering as two bf16 terms (16 significant
+ * bits) contracted on the tensor cores with FP32 accumulation: per tile of 128
+ * cells one GEMM against the reference stiffness tables (one combined table
+ * when every cell's G is c M, the case on UnitCubeMesh; else six), P1/P2/P3.
+ * x and y must not overlap. */
 int fe_apply_operator(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, void* stream);
 
 /* Choose how FP64 operator applications (dtype FE_F64, the FP64 solver and
@@ -245,6 +248,42 @@ int fe_set_f64_mode(fe_hierarchy* h, int mode);
  * vertex, 0.9 GB at UnitCubeMesh 32^3); for P1 a star patch is its vertex
  * alone and the patch preconditioner is exactly Jacobi. */
 int fe_set_smoother(fe_hierarchy* h, int smoother);
+
+/* ---- geometric factors of the operator kernels (fe_set_geometry_form) ---- */
+#define FE_GEOMETRY_AUTO 0      /* one value per cell when every cell's G is c M (always on UnitCubeMesh), else six */
+#define FE_GEOMETRY_PER_CELL 1  /* the six stored factors of G per cell in every operator kernel */
+
+/* Every Kuhn tet of UnitCubeMesh(N) has J = (1/N) P U (P a permutation, U the
+ * upper-triangular matrix of ones), so G = |det J| J^-1 J^-T = (1/N) M with
+ * M = [[2,-1,0],[-1,2,-1],[0,-1,1]] for every cell (Sec. 2: the mesh of the
+ * paper's Poisson problem).  Set-up computes G per cell from the vertex
+ * coordinates and checks this cell by cell; with FE_GEOMETRY_AUTO the operator
+ * kernels then read one value kappa_K h / w per cell and use M, with
+ * FE_GEOMETRY_PER_CELL they read the six stored factors (for comparison; the
+ * results agree to rounding).  Synchronises the current device. */
+int fe_set_geometry_form(fe_hierarchy* h, int form);
+
+/* ---- coarse direct solver (fe_set_coarse_solver) ---- */
+#define FE_COARSE_AUTO 0     /* dense inverse factor up to 16384 interior coarse dofs, blocked band factor above */
+#define FE_COARSE_DENSE 1    /* explicit L^-1 and L^-T: two parallel dense triangular products per solve */
+#define FE_COARSE_BLOCKED 2  /* band Cholesky factor; blocks of B = bandwidth rows with the inverse of each
+                                diagonal block and the block left of it: 4 nb block products per solve */
+
+/* Choose how the coarsest level's interior block A = L L^T (FP64 Cholesky,
+ * Sec. 3: a direct factorisation of the coarsest multigrid level) is applied:
+ * the dense explicit inverse of L (fast for small coarse levels; n^2 storage),
+ * or the band factor in blocks of B = w rows (w the half-bandwidth
+ * k (1 + e + e^2) for e interior points per axis): forward substitution
+ * y_I = D_I (b_I - E_I y_{I-1}) and the transposed backward pass, with D_I the
+ * inverse of the I-th diagonal block and E_I = L_{I,I-1}; storage about
+ * 4 n B doubles, e.g. 23 GB for the P3 16^3 coarse level (103,823 unknowns,
+ * w = 6771).  Refactors the coarse level (synchronises the current device). */
+int fe_set_coarse_solver(fe_hierarchy* h, int mode);
+
+/* The coarse solver in use: interior unknowns, half-bandwidth, 1 if blocked,
+ * device bytes of its factor data and the time of its last factorisation (ms). */
+int fe_coarse_info(const fe_hierarchy* h, long long* n_interior, int* bandwidth, int* blocked, long long* bytes,
+                   double* setup_ms);
 
 /* Chebyshev-Jacobi smoothing (Sec. 3: two Chebyshev iterations per level
  * visit) with the operator fused (on = 1) or not (on = 0, the default).

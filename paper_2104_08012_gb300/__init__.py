@@ -20,6 +20,8 @@ FE_F64_NATIVE, FE_F64_DOUBLE_FLOAT, FE_F64_DOUBLE_FLOAT_TET, FE_F64_DOUBLE_FLOAT
     0, 1, 2, 3, 4
 FE_PC_JACOBI, FE_PC_GMG, FE_PC_FMG = 0, 1, 2
 FE_SMOOTHER_JACOBI, FE_SMOOTHER_PATCH = 0, 1
+FE_COARSE_AUTO, FE_COARSE_DENSE, FE_COARSE_BLOCKED = 0, 1, 2
+FE_GEOMETRY_AUTO, FE_GEOMETRY_PER_CELL = 0, 1
 FE_QUAD_POINTS = 27
 FE_PREC_F64, FE_PREC_MIXED_F32, FE_PREC_MIXED_BF16 = 0, 1, 2
 FE_RHS_LOAD, FE_RHS_NODAL_F, FE_RHS_QUAD_F = 0, 1, 2
@@ -34,7 +36,7 @@ EXPORTED = (
     "fe_cell_centroids", "fe_boundary_mask", "fe_set_coefficient", "fe_apply_operator", "fe_apply_mass",
     "fe_diagonal", "fe_lambda_max", "fe_prolong", "fe_restrict", "fe_smooth", "fe_coarse_solve", "fe_vcycle",
     "fe_load_vector", "fe_quadrature_points", "fe_load_vector_quadrature", "fe_solve_poisson", "fe_adjoint_gradient",
-    "fe_objective", "fe_dot_noalloc",
+    "fe_objective", "fe_dot_noalloc", "fe_set_coarse_solver", "fe_coarse_info", "fe_set_geometry_form",
     "fe_set_f64_mode", "fe_set_smoother_fusion", "fe_set_smoother", "fe_batch_create", "fe_batch_destroy", "fe_batch_hierarchy", "fe_solve_batched", "fe_batch_schedule",
 )
 
@@ -116,6 +118,10 @@ def load():
         "fe_set_f64_mode": (i, [vp, i]),
         "fe_set_smoother_fusion": (i, [vp, i]),
         "fe_set_smoother": (i, [vp, i]),
+        "fe_set_coarse_solver": (i, [vp, i]),
+        "fe_set_geometry_form": (i, [vp, i]),
+        "fe_coarse_info": (i, [vp, ctypes.POINTER(ll), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ll),
+                               ctypes.POINTER(d)]),
         "fe_batch_create": (i, [i, vp, vp, vp, ctypes.POINTER(vp)]),
         "fe_batch_destroy": (None, [vp]),
         "fe_batch_hierarchy": (i, [vp, i, ctypes.POINTER(vp)]),
@@ -402,6 +408,21 @@ class Hierarchy:
     def set_smoother(self, smoother):
         """FE_SMOOTHER_JACOBI (default) or FE_SMOOTHER_PATCH (vertex-star patches) as the Chebyshev preconditioner."""
         _check(self._L.fe_set_smoother(self.h, smoother))
+
+    def set_geometry_form(self, form):
+        """FE_GEOMETRY_AUTO (one value per cell when every G = c M) or FE_GEOMETRY_PER_CELL (six stored factors)."""
+        _check(self._L.fe_set_geometry_form(self.h, form))
+
+    def set_coarse_solver(self, mode):
+        """FE_COARSE_AUTO (default), FE_COARSE_DENSE (explicit inverse factor) or FE_COARSE_BLOCKED (band factor)."""
+        _check(self._L.fe_set_coarse_solver(self.h, mode))
+
+    def coarse_info(self):
+        n, w, blk, byt, ms = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_double()
+        _check(self._L.fe_coarse_info(self.h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(blk), ctypes.byref(byt),
+                                      ctypes.byref(ms)))
+        return {"n_interior": n.value, "bandwidth": w.value, "blocked": bool(blk.value), "bytes": byt.value,
+                "setup_ms": ms.value}
 
     def set_smoother_fusion(self, on):
         """Chebyshev update fused into the operator launch (True) or a separate vector kernel (False, default)."""

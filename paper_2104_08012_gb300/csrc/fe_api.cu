@@ -422,14 +422,15 @@ static bool presplit(const fe_hierarchy* h, int l) {
 void apply_enqueue(const fe_hierarchy* h, int level, const void* x, void* y, int dtype, cudaStream_t s,
                    const float2* xs) {
   const Level& L = h->L[level];
-  if (L.deg == 3) {  // P3: element matrix per tet in FP64 FMAs, float pairs (default) or FP32
-    FE_REQUIRE(dtype != FE_BF16, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
+  if (L.deg == 3) {  // P3: element through the gradient at the P2 nodes in FP64, float pairs (default), FP32 or bf16
     if (dtype == FE_F64 && h->f64_mode == FE_F64_NATIVE)
       launch_apply64(L, (const double*)x, (double*)y, s);
     else if (dtype == FE_F64)
       launch_apply64_df3(L, (const double*)x, (double*)y, s);
     else if (dtype == FE_F32)
       launch_apply32(L, (const float*)x, (float*)y, s);
+    else if (dtype == FE_BF16)
+      apply_bf16_enqueue(L, (const float*)x, (float*)y, s);
     else
       FE_FAIL(FE_ERR_ARG, "unknown dtype");
     return;
@@ -1082,6 +1083,7 @@ static void set_coefficient_impl(fe_hierarchy* h, const double* kappa, cudaStrea
     launch_geometry(h->L[l], s);
     launch_split_geometry(h->L[l], s);
     launch_uniform_geometry(h->L[l], h->cs.flag, s);
+    if (h->geometry_form == FE_GEOMETRY_PER_CELL) h->L[l].uniform = 0;
     launch_diag(h->L[l], h->tmp, s);
   }
   if (h->smoother == FE_SMOOTHER_PATCH && h->deg >= 2)
@@ -1378,7 +1380,6 @@ int fe_apply_operator(const fe_hierarchy* hc, int level, const void* x, void* y,
   FE_REQUIRE(x && y && x != y, FE_ERR_ARG, "x and y must be distinct non-null vectors");
   FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32 || dtype == FE_BF16, FE_ERR_ARG, "unknown dtype");
   if (dtype == FE_BF16) FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
-  if (dtype == FE_BF16) FE_REQUIRE(hc->deg <= 2, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
   fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
   const Level& L = h->L[level];
   cudaStream_t s = as_stream(stream);
@@ -1431,6 +1432,44 @@ int fe_set_smoother(fe_hierarchy* h, int smoother) {
     invalidate_graphs(h);
     CUDA_CHECK(cudaStreamSynchronize(s));
   }
+  API_END
+}
+
+int fe_set_geometry_form(fe_hierarchy* h, int form) {
+  API_BEGIN
+  FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
+  FE_REQUIRE(form == FE_GEOMETRY_AUTO || form == FE_GEOMETRY_PER_CELL, FE_ERR_ARG, "unknown geometry form");
+  CUDA_CHECK(cudaDeviceSynchronize());
+  h->geometry_form = form;
+  for (int l = 0; l < h->nlev; ++l) {
+    launch_uniform_geometry(h->L[l], h->cs.flag, nullptr);
+    if (form == FE_GEOMETRY_PER_CELL) h->L[l].uniform = 0;
+  }
+  invalidate_graphs(h);
+  API_END
+}
+
+int fe_set_coarse_solver(fe_hierarchy* h, int mode) {
+  API_BEGIN
+  FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
+  FE_REQUIRE(mode == FE_COARSE_AUTO || mode == FE_COARSE_DENSE || mode == FE_COARSE_BLOCKED, FE_ERR_ARG,
+             "unknown coarse solver");
+  CUDA_CHECK(cudaDeviceSynchronize());
+  h->coarse_mode = mode;
+  if (h->nlev > 1) coarse_setup(h, nullptr);
+  invalidate_graphs(h);
+  API_END
+}
+
+int fe_coarse_info(const fe_hierarchy* h, long long* n_interior, int* bandwidth, int* blocked, long long* bytes,
+                   double* setup_ms) {
+  API_BEGIN
+  FE_REQUIRE(h, FE_ERR_ARG, "null hierarchy");
+  if (n_interior) *n_interior = h->cs.nci;
+  if (bandwidth) *bandwidth = h->cs.band;
+  if (blocked) *blocked = h->cs.blocked;
+  if (bytes) *bytes = (long long)h->cs.bytes;
+  if (setup_ms) *setup_ms = h->cs.setup_ms;
   API_END
 }
 
@@ -1519,7 +1558,6 @@ int fe_smooth(const fe_hierarchy* hc, int level, const void* b, void* x, int ste
   FE_REQUIRE(b && x && steps >= 1 && hi > lo && lo > 0, FE_ERR_ARG, "invalid smoother arguments");
   FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32 || dtype == FE_BF16, FE_ERR_ARG, "unknown dtype");
   if (dtype == FE_BF16) FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
-  if (dtype == FE_BF16) FE_REQUIRE(hc->deg <= 2, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
   fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
   Level& L = h->L[level];
   cudaStream_t s = as_stream(stream);
@@ -1559,7 +1597,6 @@ int fe_vcycle(const fe_hierarchy* hc, const void* b, void* x, int dtype, void* s
   FE_REQUIRE(b && x, FE_ERR_ARG, "null vector");
   FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32 || dtype == FE_BF16, FE_ERR_ARG, "unknown dtype");
   if (dtype == FE_BF16) FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
-  if (dtype == FE_BF16) FE_REQUIRE(hc->deg <= 2, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
   fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
   Level& F = h->L[h->nlev - 1];
   cudaStream_t s = as_stream(stream);
@@ -1621,7 +1658,6 @@ int fe_solve_poisson(fe_hierarchy* h, const double* rhs, int rhs_kind, const dou
   FE_REQUIRE(o.precision == FE_PREC_F64 || o.precond == FE_PC_GMG, FE_ERR_ARG, "mixed precision needs the GMG preconditioner");
   if (o.precision == FE_PREC_MIXED_BF16) {
     FE_REQUIRE(bf16_supported(), FE_ERR_UNSUPPORTED, "bf16 tensor-core apply not available");
-    FE_REQUIRE(h->deg <= 2, FE_ERR_UNSUPPORTED, "the bf16 tensor-core operator is for P1/P2");
   }
   FE_REQUIRE(o.precision == FE_PREC_F64 || h->nlev > 1, FE_ERR_ARG, "mixed precision needs at least 2 levels");
   cudaStream_t s = as_stream(stream);

@@ -41,6 +41,8 @@ struct BLevel {
   const float2* geodf;  // geo as float pairs (double-float operator)
   const float2* cdf;    // with `uniform`: c per cell as a float pair, G = c M (the Kuhn tets' shared matrix)
   int uniform;
+  const int4* rtab;     // restriction / prolongation index tables of this (fine) level: the dof of stencil entry e
+  const int4* ptab;     // at base point (X, Y, Z) is t.x + K X + t.y Y + t.z Z
   const double* dinv;
   const double* detj;
   const int* bnd;
@@ -57,6 +59,7 @@ struct BProb {
   const int* res_start;
   const int4* res_off;
   const double* res_w;
+  int res_margin;  // coarse points this far from the boundary need no bounds checks
   int nci;
   const int* ci;
   const int* dof2int;
@@ -95,6 +98,7 @@ struct Params {
   double rtol;
   unsigned long long timeout_ns;
   Work W;
+  unsigned long long* ptime;  // profile: ns per (FE_PHASE_*, level), charged by block 0 between barriers; or null
 };
 
 __device__ __forceinline__ uint64_t now_ns() {
@@ -133,6 +137,18 @@ __device__ bool grid_barrier(GridBar* gb, unsigned long long timeout_ns) {
   return *(volatile int*)&gb->abort == 0;
 }
 
+// Grid barrier that, when profiling, charges the wall time since the previous
+// barrier (as block 0 sees it: the phase and its barrier) to (phase, level).
+__device__ __forceinline__ bool pbar(const Params& A, int phase, int level, uint64_t& tlast) {
+  const bool ok = grid_barrier(A.bar, A.timeout_ns);
+  if (A.ptime && blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint64_t t = now_ns();
+    A.ptime[phase * kMaxLev + level] += t - tlast;
+    tlast = t;
+  }
+  return ok;
+}
+
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double sh[kThreads / 32];
 #pragma unroll
@@ -164,6 +180,10 @@ enum DofOp {
   OP_UPDATE_P      // beta = acc_rz/rz; p = z + beta p; q = 0
 };
 
+// Restriction of the fine residual b - w at coarse point J and prolongation of
+// the coarse x at fine point i, through the levels' index tables (each entry's
+// dof an affine form of the base point; bounds tested only within res_margin
+// of the boundary).
 template <int DEG>
 __device__ double restrict_point(const BProb& P, const BLevel& F, const BLevel& Cl, int J) {
   int X, Y, Z;
@@ -171,13 +191,18 @@ __device__ double restrict_point(const BProb& P, const BLevel& F, const BLevel& 
   const int m = Cl.num.m;
   if (X == 0 || Y == 0 || Z == 0 || X == m || Y == m || Z == m) return 0.0;
   const int cls = DEG == 2 ? ((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2)) : 0;
-  double s = 0.0;
+  constexpr int KX = DEG == 2 ? 1 : 2;
   const int mf = F.num.m;
-  for (int e = P.res_start[cls]; e < P.res_start[cls + 1]; ++e) {
-    const int4 o = P.res_off[e];
-    const int fx = 2 * X + o.x, fy = 2 * Y + o.y, fz = 2 * Z + o.z;
-    if (fx < 0 || fy < 0 || fz < 0 || fx > mf || fy > mf || fz > mf) continue;
-    const int i = lattice_to_dof(F.num, fx, fy, fz);
+  const bool near = min(min(X, Y), Z) < P.res_margin || max(max(X, Y), Z) > m - P.res_margin;
+  double s = 0.0;
+  const int e1 = P.res_start[cls + 1];
+  for (int e = P.res_start[cls]; e < e1; ++e) {
+    const int4 t = F.rtab[e];
+    if (near) {
+      const int fx = 2 * X + (t.w & 255) - 8, fy = 2 * Y + ((t.w >> 8) & 255) - 8, fz = 2 * Z + ((t.w >> 16) & 255) - 8;
+      if (fx < 0 || fy < 0 || fz < 0 || fx > mf || fy > mf || fz > mf) continue;
+    }
+    const int i = t.x + KX * X + t.y * Y + t.z * Z;
     s += P.res_w[e] * (F.b[i] - F.w[i]);
   }
   return s;
@@ -191,10 +216,10 @@ __device__ double prolong_point(const BProb& P, const BLevel& F, const BLevel& C
   const int cx = x / K2, cy = y / K2, cz = z / K2;
   const int cls = (x - K2 * cx) + K2 * ((y - K2 * cy) + K2 * (z - K2 * cz));
   double s = 0.0;
-  for (int e = P.pro_start[cls]; e < P.pro_start[cls + 1]; ++e) {
-    const int4 o = P.pro_off[e];
-    const int j = lattice_to_dof(Cl.num, DEG * cx + o.x, DEG * cy + o.y, DEG * cz + o.z);
-    s += P.pro_w[e] * Cl.x[j];
+  const int e1 = P.pro_start[cls + 1];
+  for (int e = P.pro_start[cls]; e < e1; ++e) {
+    const int4 t = F.ptab[e];
+    s += P.pro_w[e] * Cl.x[t.x + cx + t.y * cy + t.z * cz];
   }
   return s;
 }
@@ -416,37 +441,37 @@ __device__ void coarse_phase(const Params& A, int which) {
   }
 }
 
-__device__ bool vcycle(const Params& A) {
+__device__ bool vcycle(const Params& A, uint64_t& tl) {
   const int fine = A.nlev - 1;
   for (int l = fine; l >= 1; --l) {
     dof_phase(A, l, OP_PRE0, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_SMOOTH, l, tl)) return false;
     apply_phase(A, l, V_X_TO_Y, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_SMOOTH, l, tl)) return false;
     dof_phase(A, l, OP_CHEB1_PRE, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_SMOOTH, l, tl)) return false;
     apply_phase(A, l, V_X_TO_W, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_APPLY, l, tl)) return false;
     dof_phase(A, l - 1, OP_RESTRICT, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_TRANSFER, l, tl)) return false;
   }
   for (int k = 0; k < 3; ++k) {
     coarse_phase(A, k);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_COARSE, 0, tl)) return false;
   }
   dof_phase(A, 0, OP_SCATTER, false);
-  if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+  if (!pbar(A, FE_PHASE_COARSE, 0, tl)) return false;
   for (int l = 1; l <= fine; ++l) {
     dof_phase(A, l, OP_PROLONG, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_TRANSFER, l, tl)) return false;
     apply_phase(A, l, V_X_TO_Y, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_SMOOTH, l, tl)) return false;
     dof_phase(A, l, OP_CHEB0_POST, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_SMOOTH, l, tl)) return false;
     apply_phase(A, l, V_X_TO_W, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_SMOOTH, l, tl)) return false;
     dof_phase(A, l, OP_CHEB1_POST, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return false;
+    if (!pbar(A, FE_PHASE_SMOOTH, l, tl)) return false;
   }
   return true;
 }
@@ -460,6 +485,7 @@ __device__ bool any_active(const Params& A) {
 __global__ void __launch_bounds__(kThreads) k_batched_pcg(Params A) {
   const int fine = A.nlev - 1;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t tl = now_ns();  // profile clock of block 0
   // ---- setup: b = M f (Dirichlet rows 0), r = b, bb, x = 0
   dof_phase(A, fine, OP_INIT, true);
   if (gtid < A.nprob) {
@@ -469,39 +495,39 @@ __global__ void __launch_bounds__(kThreads) k_batched_pcg(Params A) {
     S.status = 0;
     S.active = 1;
   }
-  if (!grid_barrier(A.bar, A.timeout_ns)) return;
+  if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
   apply_phase(A, fine, V_F_TO_RHS, true);
-  if (!grid_barrier(A.bar, A.timeout_ns)) return;
+  if (!pbar(A, FE_PHASE_APPLY, fine, tl)) return;
   zero_rhs_boundary(A, fine);
-  if (!grid_barrier(A.bar, A.timeout_ns)) return;
+  if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
   dof_phase(A, fine, OP_R_FROM_RHS, true);
-  if (!grid_barrier(A.bar, A.timeout_ns)) return;
+  if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
   if (gtid < A.nprob) {
     BScal& S = A.sc[gtid];
     S.tol2 = A.rtol * A.rtol * S.acc_bb;
     S.rr = S.acc_bb;
     S.active = S.acc_bb > 0.0;
   }
-  if (!grid_barrier(A.bar, A.timeout_ns)) return;
+  if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
   // ---- z = V(r), rz = r.z, p = z
-  if (!vcycle(A)) return;
+  if (!vcycle(A, tl)) return;
   dof_phase(A, fine, OP_DOT_RZ, false);
-  if (!grid_barrier(A.bar, A.timeout_ns)) return;
+  if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
   dof_phase(A, fine, OP_P_FROM_Z, false);
   if (gtid < A.nprob) {
     BScal& S = A.sc[gtid];
     S.rz = S.acc_rz;
     S.acc_rz = 0.0;
   }
-  if (!grid_barrier(A.bar, A.timeout_ns)) return;
+  if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
   // ---- PCG iterations
   while (true) {
     apply_phase(A, fine, V_P_TO_Q, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return;
+    if (!pbar(A, FE_PHASE_APPLY, fine, tl)) return;
     dof_phase(A, fine, OP_DOT_PQ, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return;
+    if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
     dof_phase(A, fine, OP_UPDATE_XR, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return;
+    if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
     if (gtid < A.nprob) {
       BScal& S = A.sc[gtid];
       if (S.active) {
@@ -520,19 +546,19 @@ __global__ void __launch_bounds__(kThreads) k_batched_pcg(Params A) {
       S.acc_pq = 0.0;
       S.acc_rr = 0.0;
     }
-    if (!grid_barrier(A.bar, A.timeout_ns)) return;
+    if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
     if (!any_active(A)) break;
-    if (!vcycle(A)) return;
+    if (!vcycle(A, tl)) return;
     dof_phase(A, fine, OP_DOT_RZ, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return;
+    if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
     dof_phase(A, fine, OP_UPDATE_P, false);
-    if (!grid_barrier(A.bar, A.timeout_ns)) return;
+    if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
     if (gtid < A.nprob) {
       BScal& S = A.sc[gtid];
       if (S.active) S.rz = S.acc_rz;
       S.acc_rz = 0.0;
     }
-    if (!grid_barrier(A.bar, A.timeout_ns)) return;
+    if (!pbar(A, FE_PHASE_BLAS1, fine, tl)) return;
   }
 }
 
@@ -551,6 +577,7 @@ struct fe_batch {
   DBuf<GridBar> dbar;
   DBuf<double> mref1, mref2;
   DBuf<int4> items;
+  DBuf<unsigned long long> ptime;  // [FE_NUM_PHASES][kMaxLev] profile clock (ns)
   Work work{};
   Schedule sched;
   bool tuned = false;
@@ -614,6 +641,8 @@ void fill_problems(fe_batch* B, double cheb_lo, double cheb_hi) {
       D.geodf = L.geodf;
       D.cdf = L.cdf;
       D.uniform = L.uniform;
+      D.rtab = L.rtab;
+      D.ptab = L.ptab;
       D.dinv = L.dinv64;
       D.detj = L.detj;
       D.bnd = L.bnd;
@@ -635,6 +664,7 @@ void fill_problems(fe_batch* B, double cheb_lo, double cheb_hi) {
     P.res_start = h->tt.res_start;
     P.res_off = h->tt.res_off;
     P.res_w = h->tt.res_w;
+    P.res_margin = h->tt.res_margin;
     P.nci = h->cs.nci;
     P.ci = h->cs.ci;
     P.dof2int = h->cs.dof2int;
@@ -688,6 +718,7 @@ Params make_params(fe_batch* B, const fe_solver_opts& o) {
   A.rtol = o.rtol;
   A.timeout_ns = o.wait_timeout_us > 0 ? (unsigned long long)o.wait_timeout_us * 1000ull : 5000000000ull;
   A.W = B->work;
+  A.ptime = o.profile ? B->ptime.p : nullptr;
   return A;
 }
 
@@ -696,7 +727,11 @@ double run_solve(fe_batch* B, const fe_solver_opts& o, cudaStream_t s) {
   const Params A = make_params(B, o);
   const int grid = coop_grid(B);
   const auto t0 = std::chrono::steady_clock::now();
-  if (o.use_graph) {
+  if (o.profile) {  // phase clock: a direct launch (the counters are zeroed first)
+    B->ptime.alloc((size_t)FE_NUM_PHASES * kMaxLev);
+    CUDA_CHECK(cudaMemsetAsync(B->ptime.p, 0, sizeof(unsigned long long) * FE_NUM_PHASES * kMaxLev, s));
+    launch_persistent(B, make_params(B, o), grid, s);
+  } else if (o.use_graph) {
     const bool same = B->gexec && B->ggrid == grid && memcmp(&B->gparams, &A, sizeof(Params)) == 0;
     if (!same) {
       if (B->gexec) cudaGraphExecDestroy(B->gexec);
@@ -841,8 +876,13 @@ int fe_solve_batched(fe_batch* B, const double* const* f_nodal, double* const* u
                  "batched vectors must be device pointers");
     }
     fill_problems(B, o.cheb_lo, o.cheb_hi);
-    if (!B->tuned && o.use_graph) autotune(B, o, s);
+    if (!B->tuned && o.use_graph && !o.profile) autotune(B, o, s);
     const double ms = run_solve(B, o, s);
+    std::vector<unsigned long long> pt;
+    if (o.profile) {
+      pt.resize((size_t)FE_NUM_PHASES * kMaxLev);
+      CUDA_CHECK(cudaMemcpy(pt.data(), B->ptime.p, sizeof(unsigned long long) * pt.size(), cudaMemcpyDeviceToHost));
+    }
     GridBar hb;
     CUDA_CHECK(cudaMemcpy(&hb, B->dbar.p, sizeof(GridBar), cudaMemcpyDeviceToHost));
     FE_REQUIRE(hb.abort == 0, FE_ERR_TIMEOUT, "a grid barrier of the persistent batched kernel timed out");
@@ -861,6 +901,11 @@ int fe_solve_batched(fe_batch* B, const double* const* f_nodal, double* const* u
         st.rel_residual = hs[p].acc_bb > 0 ? std::sqrt(hs[p].rr / hs[p].acc_bb) : 0.0;
         st.solve_ms = ms;
         st.fine_applies_f64 = hs[p].iters;
+        if (o.profile) {  // the persistent launch's wall time by phase and level, the same for every problem
+          st.levels_timed = B->nlev;
+          for (int ph = 0; ph < FE_NUM_PHASES; ++ph)
+            for (int l = 0; l < B->nlev && l < FE_MAX_LEVELS; ++l) st.phase_ms[ph][l] = 1e-6 * (double)pt[ph * kMaxLev + l];
+        }
       }
       if (hs[p].status != 0 && worst == FE_OK) worst = hs[p].status;
     }

@@ -13,15 +13,30 @@
 // products are evaluated in float-pair arithmetic on the FP32 pipes (L^-1 and
 // L^-T stored as float pairs, the vector scaled by a power of two and split
 // once per product), since FP64 fused multiply-adds bound the FP64 form.
+//
+// Blocked form (large coarse levels, where n^2 storage is out of reach): the
+// band is assembled and factored in band storage (row i holds A[i][i-w..i];
+// the interior unknowns are padded with identity rows to a multiple of
+// B = w), then for every block I of B rows the inverse D_I of the diagonal
+// block L_II and the block E_I = L_{I,I-1} (upper triangular, since B = w)
+// are stored with their transposes.  A solve is the forward pass
+// y_I = D_I (b_I - E_I y_{I-1}) and the backward pass
+// x_I = D_I^T (y_I - E_{I+1}^T x_{I+1}): 4 nb - 2 dense block products, each
+// fully parallel over its B rows, in FP64.
+#include <chrono>
+#include <vector>
+
 #include "fe_df.cuh"
 
 namespace {
 
 constexpr int kBlock = 256;
 
+// band < 0: dense nci x nci (both triangles); band >= 0: band storage
+// [nci][band + 1] of the lower triangle.
 template <int DEG>
 __global__ void k_coarse_assemble(int C, int Cs, const int* __restrict__ map, const double* __restrict__ geo,
-                                  const int* __restrict__ dof2int, int nci, double* __restrict__ A) {
+                                  const int* __restrict__ dof2int, int nci, double* __restrict__ A, int band) {
   constexpr int ND = DEG == 1 ? 4 : 10;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
@@ -40,8 +55,154 @@ __global__ void k_coarse_assemble(int C, int Cs, const int* __restrict__ map, co
 #pragma unroll
     for (int k = 0; k < ND; ++k) u[k] = (k == j) ? 1.0 : 0.0;
     element_apply<DEG, double>(u, g, out);
-    for (int i = 0; i < ND; ++i)
-      if (ii[i] >= 0) atomicAdd(A + (size_t)ii[i] * nci + ii[j], out[i]);
+    for (int i = 0; i < ND; ++i) {
+      if (ii[i] < 0) continue;
+      if (band < 0)
+        atomicAdd(A + (size_t)ii[i] * nci + ii[j], out[i]);
+      else if (ii[j] <= ii[i])
+        atomicAdd(A + (size_t)ii[i] * (band + 1) + (ii[j] - ii[i] + band), out[i]);
+    }
+  }
+}
+
+// ---- blocked band factor ----
+// Right-looking band Cholesky in band storage (p = w + 1 values per row,
+// A[i][k] at Ab[i p + k - i + w]) with every column scaled as soon as it is
+// final, so the trailing update is a plain product (no FP64 division per
+// entry).  Before step j, column j holds L[., j] below the diagonal; step j
+// (i = j + a, k = j + b, 1 <= b <= a <= w):
+//   b > 1:  A[i][k] -= L[i][j] L[k][j];
+//   b = 1:  column j + 1 becomes final: d = A[j+1][j+1] - L[j+1][j]^2 (each
+//           thread recomputes it) and L[i][j+1] = (A[i][j+1] - L[i][j] L[j+1][j]) / sqrt(d)
+//           for i > j + 1; the diagonal itself is written by thread (1, 1) of
+//           step j + 1 (k_bchol_diag_prev for the last two columns), after
+//           every thread of step j has read it.
+__global__ void k_bchol_first(int n, int w, double* __restrict__ Ab, int* __restrict__ flag) {
+  const size_t p = (size_t)w + 1;
+  const double d = Ab[w];
+  if (!(d > 0.0)) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(flag, 1);
+    return;
+  }
+  const double s = sqrt(d);
+  const int wl = min(w, n - 1);
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x + 1; a <= wl; a += gridDim.x * blockDim.x)
+    Ab[(size_t)a * p + (w - a)] /= s;  // L[a][0]
+}
+
+__global__ void k_bchol_step(int n, int w, int j, double* __restrict__ Ab, int* __restrict__ flag) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x + 1;  // k - j
+  const int a = blockIdx.y * blockDim.y + threadIdx.y + 1;  // i - j
+  // rows j + 1 .. j + w + 1: the last one only to scale its entry of column j + 1 (it has no entry in column j)
+  const int wl = min(w + 1, n - 1 - j);
+  if (a > wl || b > a || (a > w && b > 1)) return;
+  const size_t p = (size_t)w + 1;
+  const int i = j + a, k = j + b;
+  const double lij = a <= w ? Ab[(size_t)i * p + (w - a)] : 0.0;
+  if (b > 1) {
+    Ab[(size_t)i * p + (k - i + w)] -= lij * Ab[(size_t)k * p + (w - b)];
+    return;
+  }
+  // b = 1: k = j + 1
+  const double l1 = Ab[(size_t)k * p + (w - 1)];                // L[j+1][j]
+  const double d = Ab[(size_t)k * p + w] - l1 * l1;              // pivot of column j + 1
+  if (a == 1) {
+    if (!(d > 0.0)) atomicOr(flag, 1);
+    if (j >= 1) {  // the diagonal of column j - 1 (no thread of step j reads it)
+      const size_t c = (size_t)(j - 1) * p + w;
+      const double lc = j >= 2 ? Ab[(size_t)(j - 1) * p + (w - 1)] : 0.0;
+      Ab[c] = sqrt(Ab[c] - lc * lc);
+    }
+    return;
+  }
+  if (!(d > 0.0)) return;
+  const size_t at = (size_t)i * p + (k - i + w);                 // A[i][j+1]
+  Ab[at] = (Ab[at] - lij * l1) / sqrt(d);
+}
+
+// Diagonal of column j - 1 (for j = n: the last column): sqrt(A[j-1][j-1] - L[j-1][j-2]^2),
+// or sqrt(A[0][0]) for column 0.
+__global__ void k_bchol_diag_prev(int w, int j, double* __restrict__ Ab) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const size_t p = (size_t)w + 1;
+  const int c = j - 1;
+  if (c < 0) return;
+  const double l = c > 0 ? Ab[(size_t)c * p + (w - 1)] : 0.0;
+  Ab[(size_t)c * p + w] = sqrt(Ab[(size_t)c * p + w] - l * l);
+}
+
+// D = L_II^-1 for diagonal block I (rows and columns [I B, I B + B)), one
+// warp per column j: X[i][j] = (delta_ij - sum_{k = max(j, i - w)}^{i-1}
+// L[i][k] X[k][j]) / L[i][i]; the last w + 1 values of the column live in a
+// shared-memory ring.  D is row-major B x B (zero above the diagonal, set by
+// the caller), DT its transpose.
+__global__ void k_btri_inverse(int B, int w, int I, const double* __restrict__ Ab, double* __restrict__ D,
+                               double* __restrict__ DT) {
+  extern __shared__ double ring_all[];
+  const int warps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int jl = blockIdx.x * warps + wib;
+  if (jl >= B) return;
+  const int R = w + 1;
+  const size_t p = (size_t)w + 1;
+  double* ring = ring_all + (size_t)wib * R;
+  const int j = I * B + jl;
+  for (int il = jl; il < B; ++il) {
+    const int i = I * B + il;
+    const int kmin = max(j, i - w);
+    double s = 0.0;
+    for (int k = kmin + lane; k < i; k += 32) s += Ab[(size_t)i * p + (k - i + w)] * ring[k % R];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const double v = (((i == j) ? 1.0 : 0.0) - s) / Ab[(size_t)i * p + w];
+      ring[i % R] = v;
+      D[(size_t)il * B + jl] = v;
+      DT[(size_t)jl * B + il] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// E_I[a][b] = L[I B + a][(I - 1) B + b] (nonzero for b >= a, since B = w) and its transpose.
+__global__ void k_bextract(int B, int w, int I, const double* __restrict__ Ab, double* __restrict__ E,
+                           double* __restrict__ ET) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)B * B) return;
+  const int a = (int)(t / B), b = (int)(t - (size_t)a * B);
+  const int i = I * B + a, j = (I - 1) * B + b;
+  const double v = (i - j <= w) ? Ab[(size_t)i * ((size_t)w + 1) + (j - i + w)] : 0.0;
+  E[t] = v;
+  ET[(size_t)b * B + a] = v;
+}
+
+// out_r = base_r - sum_j M[r][j] v_j (base != null) or sum_j M[r][j] v_j, j
+// over [0, r] (lower) or [r, B) (upper); one block per row.
+constexpr int kBlkThreads = 256;
+__global__ void __launch_bounds__(kBlkThreads) k_blkmv(int B, const double* __restrict__ M,
+                                                       const double* __restrict__ v, const double* __restrict__ base,
+                                                       double* __restrict__ out, int upper) {
+  __shared__ double sh[kBlkThreads / 32];
+  const int row = blockIdx.x;
+  const double* Mr = M + (size_t)row * B;
+  const int j0 = upper ? row : 0, j1 = upper ? B : row + 1;
+  double s0 = 0.0, s1 = 0.0;
+  int jj = j0 + threadIdx.x;
+  for (; jj + kBlkThreads < j1; jj += 2 * kBlkThreads) {
+    s0 += __ldg(Mr + jj) * __ldg(v + jj);
+    s1 += __ldg(Mr + jj + kBlkThreads) * __ldg(v + jj + kBlkThreads);
+  }
+  if (jj < j1) s0 += __ldg(Mr + jj) * __ldg(v + jj);
+  double s = s0 + s1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kBlkThreads / 32; ++q) t += sh[q];
+    out[row] = base ? base[row] - t : t;
   }
 }
 
@@ -110,9 +271,13 @@ __global__ void k_tri_inverse(int n, int w, const double* __restrict__ L, const 
 }
 
 template <typename T>
-__global__ void k_coarse_gather(int nci, const int* __restrict__ ci, const T* __restrict__ b, double* __restrict__ t) {
+__global__ void k_coarse_gather(int nci, int npad, const int* __restrict__ ci, const T* __restrict__ b,
+                                double* __restrict__ t) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < nci) t[j] = (double)b[ci[j]];
+  if (j < nci)
+    t[j] = (double)b[ci[j]];
+  else if (j < npad)
+    t[j] = 0.0;  // identity padding rows
 }
 
 // out_i = sum_{j<=i} M[i][j] in_j (lower) or out_i = sum_{j>=i} M[i][j] in_j (upper).
@@ -232,62 +397,35 @@ __global__ void k_coarse_scatter(int n, const int* __restrict__ dof2int, const d
 
 }  // namespace
 
-void coarse_setup(fe_hierarchy* h, cudaStream_t s) {
+// Interior coarse unknowns above which FE_COARSE_AUTO takes the blocked form
+// (the dense inverse factors would need five n^2 arrays: 10.7 GB at 16384).
+constexpr int kDenseMaxInterior = 16384;
+
+static void coarse_setup_dense(fe_hierarchy* h, cudaStream_t s) {
   Level& L0 = h->L[0];
   CoarseSolver& cs = h->cs;
-  const int m = L0.num.m;
-  const int e = m - 1;
-  const int nci = e * e * e;
-  if (nci == 0) {  // every coarse dof is a Dirichlet dof: the coarse solve is the identity
-    cs.nci = 0;
-    cs.band = 0;
-    cs.dof2int.alloc(L0.n);
-    CUDA_CHECK(cudaMemsetAsync(cs.dof2int, 0xff, sizeof(int) * L0.n, s));
-    CUDA_CHECK(cudaStreamSynchronize(s));
-    return;
-  }
+  const int nci = cs.nci, w = cs.band;
   FE_REQUIRE((double)nci * nci * 8.0 * 3 < 24e9, FE_ERR_UNSUPPORTED, "coarse level too large for the dense Cholesky");
-  if (cs.nci != nci) {
-    std::vector<int> ci(nci), d2i(L0.n, -1);
-    int j = 0;
-    for (int z = 1; z < m; ++z)
-      for (int y = 1; y < m; ++y)
-        for (int x = 1; x < m; ++x) {
-          const int dof = lattice_to_dof(L0.num, x, y, z);
-          ci[j] = dof;
-          d2i[dof] = j++;
-        }
-    cs.nci = nci;
-    cs.band = L0.deg * (1 + e + e * e);
-    if (cs.band > nci - 1) cs.band = nci - 1;
-    cs.ci.alloc(nci);
-    cs.dof2int.alloc(L0.n);
-    CUDA_CHECK(cudaMemcpy(cs.ci, ci.data(), sizeof(int) * nci, cudaMemcpyHostToDevice));
-    CUDA_CHECK(cudaMemcpy(cs.dof2int, d2i.data(), sizeof(int) * L0.n, cudaMemcpyHostToDevice));
-    cs.A.alloc((size_t)nci * nci);
-    cs.Linv.alloc((size_t)nci * nci);
-    cs.LinvT.alloc((size_t)nci * nci);
-    cs.LinvDF.alloc((size_t)nci * nci);
-    cs.LinvTDF.alloc((size_t)nci * nci);
-    cs.t0.alloc(nci);
-    cs.t1.alloc(nci);
-    cs.v0.alloc(nci);
-    cs.v1.alloc(nci);
-    cs.ev.alloc(2);
-    cs.flag.alloc(1);
-  }
+  for (auto* b : {&cs.Ab, &cs.D, &cs.DT, &cs.E, &cs.ET, &cs.yb}) b->release();
   const size_t nn = (size_t)nci * nci;
+  cs.A.alloc(nn);
+  cs.Linv.alloc(nn);
+  cs.LinvT.alloc(nn);
+  cs.LinvDF.alloc(nn);
+  cs.LinvTDF.alloc(nn);
+  cs.bytes = nn * (3 * sizeof(double) + 2 * sizeof(float2));
   CUDA_CHECK(cudaMemsetAsync(cs.A, 0, sizeof(double) * nn, s));
   if (L0.deg == 1) {
-    k_coarse_assemble<1><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci, cs.A);
+    k_coarse_assemble<1><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci, cs.A,
+                                                                   -1);
     LAUNCH_CHECK();
   } else if (L0.deg == 2) {
-    k_coarse_assemble<2><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci, cs.A);
+    k_coarse_assemble<2><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci, cs.A,
+                                                                   -1);
     LAUNCH_CHECK();
   } else {
-    launch_coarse_assemble_p3(L0, cs.dof2int, nci, cs.A, s);
+    launch_coarse_assemble_p3(L0, cs.dof2int, nci, cs.A, -1, s);
   }
-  const int w = cs.band;
   for (int j = 0; j + 1 < nci; ++j) {
     const int wl = std::min(w, nci - 1 - j);
     dim3 blk(32, 8), grd(ceil_div(wl, 32), ceil_div(wl, 8));
@@ -315,7 +453,137 @@ void coarse_setup(fe_hierarchy* h, cudaStream_t s) {
   LAUNCH_CHECK();
   k_split_mat<<<ceil_div((long long)nn, kBlock), kBlock, 0, s>>>(nn, cs.LinvT, cs.LinvTDF);
   LAUNCH_CHECK();
+}
+
+static void coarse_setup_blocked(fe_hierarchy* h, cudaStream_t s) {
+  Level& L0 = h->L[0];
+  CoarseSolver& cs = h->cs;
+  const int nci = cs.nci, w = cs.band;
+  for (auto* b : {&cs.A, &cs.Linv, &cs.LinvT}) b->release();
+  cs.LinvDF.release();
+  cs.LinvTDF.release();
+  const int B = std::max(w, 1);
+  const int nb = ceil_div(nci, B), npad = nb * B;
+  const size_t p = (size_t)w + 1, bb = (size_t)B * B;
+  cs.B = B;
+  cs.nb = nb;
+  cs.npad = npad;
+  cs.Ab.alloc((size_t)npad * p);
+  cs.D.alloc(nb * bb);
+  cs.DT.alloc(nb * bb);
+  cs.E.alloc(nb * bb);
+  cs.ET.alloc(nb * bb);
+  cs.yb.alloc(npad);
+  cs.t0.alloc(npad);
+  cs.t1.alloc(npad);
+  cs.bytes = 4 * nb * bb * sizeof(double);
+  // band assembly of the interior block, identity on the padding rows
+  CUDA_CHECK(cudaMemsetAsync(cs.Ab, 0, sizeof(double) * (size_t)npad * p, s));
+  if (L0.deg == 1) {
+    k_coarse_assemble<1><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci,
+                                                                   cs.Ab, w);
+    LAUNCH_CHECK();
+  } else if (L0.deg == 2) {
+    k_coarse_assemble<2><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci,
+                                                                   cs.Ab, w);
+    LAUNCH_CHECK();
+  } else {
+    launch_coarse_assemble_p3(L0, cs.dof2int, nci, cs.Ab, w, s);
+  }
+  if (npad > nci) {
+    std::vector<double> one(1, 1.0);
+    for (int i = nci; i < npad; ++i)
+      CUDA_CHECK(cudaMemcpyAsync(cs.Ab.p + (size_t)i * p + w, one.data(), sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  // right-looking band Cholesky, one launch per column (columns scaled as they become final)
+  CUDA_CHECK(cudaMemsetAsync(cs.flag, 0, sizeof(int), s));
+  k_bchol_first<<<ceil_div(std::max(w, 1), kBlock), kBlock, 0, s>>>(npad, w, cs.Ab, cs.flag);
+  LAUNCH_CHECK();
+  for (int j = 0; j + 1 < npad; ++j) {
+    const int wl = std::min(w + 1, npad - 1 - j);
+    dim3 blk(32, 8), grd(ceil_div(std::min(wl, w), 32), ceil_div(wl, 8));
+    k_bchol_step<<<grd, blk, 0, s>>>(npad, w, j, cs.Ab, cs.flag);
+  }
+  k_bchol_diag_prev<<<1, 32, 0, s>>>(w, npad - 1, cs.Ab);
+  k_bchol_diag_prev<<<1, 32, 0, s>>>(w, npad, cs.Ab);
+  LAUNCH_CHECK();
+  int hflag = 0;
+  CUDA_CHECK(cudaMemcpyAsync(&hflag, cs.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_CHECK(cudaStreamSynchronize(s));
+  FE_REQUIRE(hflag == 0, FE_ERR_ARG, "coarse matrix is not positive definite");
+  // per block: D_I = L_II^-1 (and transpose), E_I = L_{I,I-1} (and transpose)
+  CUDA_CHECK(cudaMemsetAsync(cs.D, 0, sizeof(double) * nb * bb, s));
+  CUDA_CHECK(cudaMemsetAsync(cs.DT, 0, sizeof(double) * nb * bb, s));
+  CUDA_CHECK(cudaMemsetAsync(cs.E, 0, sizeof(double) * nb * bb, s));
+  CUDA_CHECK(cudaMemsetAsync(cs.ET, 0, sizeof(double) * nb * bb, s));
+  // one shared ring of w + 1 doubles per warp: as many warps per block (up to 4) as fit in 200 KB
+  const int warps = (int)std::min<size_t>(4, (200 * 1024) / (sizeof(double) * p));
+  FE_REQUIRE(warps >= 1, FE_ERR_UNSUPPORTED, "coarse band too wide for the blocked factor");
+  const size_t shm = sizeof(double) * p * warps;
+  if (shm > 48 * 1024)
+    CUDA_CHECK(cudaFuncSetAttribute(k_btri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  for (int I = 0; I < nb; ++I) {
+    k_btri_inverse<<<ceil_div(B, warps), warps * 32, shm, s>>>(B, w, I, cs.Ab, cs.D.p + I * bb, cs.DT.p + I * bb);
+    LAUNCH_CHECK();
+    if (I > 0) {
+      k_bextract<<<ceil_div((long long)bb, kBlock), kBlock, 0, s>>>(B, w, I, cs.Ab, cs.E.p + I * bb, cs.ET.p + I * bb);
+      LAUNCH_CHECK();
+    }
+  }
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  cs.Ab.release();  // the blocks hold everything the solves need
+}
+
+void coarse_setup(fe_hierarchy* h, cudaStream_t s) {
+  Level& L0 = h->L[0];
+  CoarseSolver& cs = h->cs;
+  const int m = L0.num.m;
+  const int e = m - 1;
+  const int nci = e * e * e;
+  const auto t0 = std::chrono::steady_clock::now();
+  if (nci == 0) {  // every coarse dof is a Dirichlet dof: the coarse solve is the identity
+    cs.nci = 0;
+    cs.band = 0;
+    cs.blocked = 0;
+    cs.bytes = 0;
+    cs.dof2int.alloc(L0.n);
+    CUDA_CHECK(cudaMemsetAsync(cs.dof2int, 0xff, sizeof(int) * L0.n, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+    return;
+  }
+  if (cs.nci != nci) {
+    std::vector<int> ci(nci), d2i(L0.n, -1);
+    int j = 0;
+    for (int z = 1; z < m; ++z)
+      for (int y = 1; y < m; ++y)
+        for (int x = 1; x < m; ++x) {
+          const int dof = lattice_to_dof(L0.num, x, y, z);
+          ci[j] = dof;
+          d2i[dof] = j++;
+        }
+    cs.nci = nci;
+    cs.band = L0.deg * (1 + e + e * e);
+    if (cs.band > nci - 1) cs.band = nci - 1;
+    cs.ci.alloc(nci);
+    cs.dof2int.alloc(L0.n);
+    CUDA_CHECK(cudaMemcpy(cs.ci, ci.data(), sizeof(int) * nci, cudaMemcpyHostToDevice));
+    CUDA_CHECK(cudaMemcpy(cs.dof2int, d2i.data(), sizeof(int) * L0.n, cudaMemcpyHostToDevice));
+    cs.t0.alloc(nci);
+    cs.t1.alloc(nci);
+    cs.v0.alloc(nci);
+    cs.v1.alloc(nci);
+    cs.ev.alloc(2);
+    cs.flag.alloc(1);
+  }
+  const bool blocked =
+      h->coarse_mode == FE_COARSE_BLOCKED || (h->coarse_mode == FE_COARSE_AUTO && nci > kDenseMaxInterior);
+  cs.blocked = blocked ? 1 : 0;
+  if (blocked)
+    coarse_setup_blocked(h, s);
+  else
+    coarse_setup_dense(h, s);
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  cs.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
 template <typename T>
@@ -328,8 +596,37 @@ void coarse_solve(const fe_hierarchy* h, const T* b, T* x, cudaStream_t s) {
     LAUNCH_CHECK();
     return;
   }
-  if (h->f64_mode == FE_F64_NATIVE) {
-    k_coarse_gather<T><<<ceil_div(nci, kBlock), kBlock, 0, s>>>(nci, cs.ci, b, cs.t0);
+  if (cs.blocked) {
+    const int B = cs.B, nb = cs.nb;
+    const size_t bb = (size_t)B * B;
+    k_coarse_gather<T><<<ceil_div(cs.npad, kBlock), kBlock, 0, s>>>(nci, cs.npad, cs.ci, b, cs.t0);
+    LAUNCH_CHECK();
+    // forward: y_I = D_I (b_I - E_I y_{I-1})
+    for (int I = 0; I < nb; ++I) {
+      const double* rhs = cs.t0.p + (size_t)I * B;
+      if (I > 0) {
+        k_blkmv<<<B, kBlkThreads, 0, s>>>(B, cs.E.p + I * bb, cs.yb.p + (size_t)(I - 1) * B, rhs,
+                                          cs.t1.p + (size_t)I * B, 1);
+        LAUNCH_CHECK();
+        rhs = cs.t1.p + (size_t)I * B;
+      }
+      k_blkmv<<<B, kBlkThreads, 0, s>>>(B, cs.D.p + I * bb, rhs, nullptr, cs.yb.p + (size_t)I * B, 0);
+      LAUNCH_CHECK();
+    }
+    // backward: x_I = D_I^T (y_I - E_{I+1}^T x_{I+1}), x in t0
+    for (int I = nb - 1; I >= 0; --I) {
+      const double* rhs = cs.yb.p + (size_t)I * B;
+      if (I + 1 < nb) {
+        k_blkmv<<<B, kBlkThreads, 0, s>>>(B, cs.ET.p + (I + 1) * bb, cs.t0.p + (size_t)(I + 1) * B, rhs,
+                                          cs.t1.p + (size_t)I * B, 0);
+        LAUNCH_CHECK();
+        rhs = cs.t1.p + (size_t)I * B;
+      }
+      k_blkmv<<<B, kBlkThreads, 0, s>>>(B, cs.DT.p + I * bb, rhs, nullptr, cs.t0.p + (size_t)I * B, 1);
+      LAUNCH_CHECK();
+    }
+  } else if (h->f64_mode == FE_F64_NATIVE) {
+    k_coarse_gather<T><<<ceil_div(nci, kBlock), kBlock, 0, s>>>(nci, nci, cs.ci, b, cs.t0);
     LAUNCH_CHECK();
     k_trimv<<<nci, kRowThreads, 0, s>>>(nci, cs.Linv, cs.t0, cs.t1, 0);
     LAUNCH_CHECK();

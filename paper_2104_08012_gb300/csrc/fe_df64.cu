@@ -30,9 +30,7 @@ namespace {
 using namespace fe_df;
 constexpr int kBlock = 256;
 constexpr int kBlockP3 = 128;
-#ifndef KDF_MINB
-#define KDF_MINB 2  // resident blocks per SM the pre-split, uniform-geometry float-pair kernel is compiled for
-#endif
+
 
 // The dofs whose countdown this thread ended (count returned 1): every other
 // contribution was fenced before its countdown, so after an acquiring fence
@@ -73,7 +71,7 @@ __device__ __forceinline__ void finish_dofs(const int* pidx, const unsigned* pre
 // UNI: geo is L.cdf, one float pair c per cell with G = c M (see Level), and
 // the element uses the fixed matrix M instead of six loaded factors.
 template <int DEG, bool FUSE, bool PRE, bool UNI>
-__global__ void __launch_bounds__(kBlock, UNI && PRE ? KDF_MINB : 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
+__global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
                                                         const float2* __restrict__ geo, const double* x,
                                                         const float2* __restrict__ xs, double* __restrict__ y, int nb,
                                                         const int* __restrict__ bnd, ChebFuse<double> cf) {

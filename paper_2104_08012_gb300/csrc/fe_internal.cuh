@@ -270,6 +270,16 @@ struct ReduceCtx {
 
 struct CoarseSolver {
   int nci = 0, band = 0;
+  // Blocked form for large coarse levels (see fe_coarse.cu): the band factor in
+  // band storage, then per block of B = band rows the inverse D of its
+  // diagonal block and the block E to the left of it, with transposes.
+  int blocked = 0, B = 0, nb = 0, npad = 0;
+  double setup_ms = 0.0;
+  size_t bytes = 0;     // device memory of the factor data
+  DBuf<double> Ab;      // [npad][band + 1] band storage: row i holds A[i][i - band .. i]
+  DBuf<double> D, DT;   // [nb][B][B] D_I = L_II^-1 and its transpose
+  DBuf<double> E, ET;   // [nb][B][B] E_I = L_{I,I-1} (I >= 1) and its transpose
+  DBuf<double> yb;      // [npad] forward-substitution result
   DBuf<int> ci;        // interior unknown j -> coarse dof
   DBuf<int> dof2int;   // coarse dof -> interior index or -1
   DBuf<double> A;      // nci*nci dense, then L (lower)
@@ -358,6 +368,8 @@ struct fe_hierarchy {
   int f64_mode = FE_F64_DOUBLE_FLOAT;  // arithmetic of FP64 operator applications
   int fuse_smoother = 0;               // Chebyshev update fused into the operator kernel (measured slower on GB300)
   int smoother = FE_SMOOTHER_JACOBI;   // preconditioner of the Chebyshev smoother
+  int coarse_mode = FE_COARSE_AUTO;    // dense inverse factor or blocked band factor
+  int geometry_form = FE_GEOMETRY_AUTO;  // one value per cell (when uniform) or six stored factors
   PhaseProf prof;                      // per-phase timers of profiled solves
 };
 
@@ -382,7 +394,8 @@ void launch_apply_cheb64_df(const Level& L, const double* b, double* x, double* 
 void launch_apply_cheb64_cube_df(const Level& L, const double* b, double* x, double* y, double* d, double c1,
                                  double c2, bool store_d, cudaStream_t s);
 void launch_build_valence(Level& L, cudaStream_t s);
-void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, double* A, cudaStream_t s);
+// band < 0: dense nci x nci (both triangles); band >= 0: band storage [nci][band + 1], lower triangle only
+void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, double* A, int band, cudaStream_t s);
 // Vertex-star patch smoother (fe_patch.cu; P3 setup in fe_kernels.cu)
 void launch_patch_setup(Level& L, cudaStream_t s);
 void launch_patch_setup_p3(Level& L, cudaStream_t s);

@@ -277,12 +277,16 @@ __global__ void __launch_bounds__(kBlock) k_bc_lift(int C, int Cs, const int* __
 // Cube-aggregated apply: one thread per cube gathers the cube's (k+1)^3 dofs
 // once, applies its six Kuhn tets into register accumulators and scatters
 // (k+1)^3 atomics instead of 6 * nd (27 instead of 60 for P2).
-constexpr int kCubeBlock = 128;  // 4 blocks of 128 per SM at 128 registers: 5% faster than 2 of 256
+constexpr int kCubeBlock = 128;
+// The uniform-geometry FP32 cube kernel is gather-latency-bound: compiled for 6 resident blocks per SM (80
+// registers, 60 bytes of spill) it ran 0.134 ms at P2 128^3 against 0.138 ms for 5 (96 registers) and 0.148 ms
+// for 4 (109 registers); streaming cache hints on the cube map and c made it slower (0.167 ms).
+constexpr int kCubeMinBlocksUni = 6;  // 4 blocks of 128 per SM at 128 registers: 5% faster than 2 of 256
 
 // UNI: geo is c32 (one value per cell, geometric factors c M, see Level)
 // instead of the six stored factors per cell.
 template <int DEG, bool FUSE, bool UNI>
-__global__ void __launch_bounds__(kCubeBlock, 4) k_apply_cube(int Q, int Qs, int Cs, int Qpad,
+__global__ void __launch_bounds__(kCubeBlock, UNI ? kCubeMinBlocksUni : 4) k_apply_cube(int Q, int Qs, int Cs, int Qpad,
                                                             const int* __restrict__ cmap,
                                                             const float* __restrict__ geo, const float* x,
                                                             float* __restrict__ y, int nb, const int* __restrict__ bnd,
@@ -737,7 +741,7 @@ __global__ void k_random(int n, uint64_t seed, double* __restrict__ v) {
 // the reference coefficients (the P1/P2 assembly in fe_coarse.cu applies the
 // element to unit vectors).
 __global__ void k_coarse_assemble_p3(int C, int Cs, const int* __restrict__ map, const double* __restrict__ geo,
-                                     const int* __restrict__ dof2int, int nci, double* __restrict__ A) {
+                                     const int* __restrict__ dof2int, int nci, double* __restrict__ A, int band) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   int ii[20];
@@ -753,9 +757,11 @@ __global__ void k_coarse_assemble_p3(int C, int Cs, const int* __restrict__ map,
       if (ii[j] < 0) continue;
       const int lo = min(i, j), hi = max(i, j);
       const int p = 20 * lo - lo * (lo - 1) / 2 + (hi - lo);
+      if (band >= 0 && ii[j] > ii[i]) continue;  // band storage keeps the lower triangle
       double a = 0.0;
       for (int k = 0; k < 6; ++k) a += g[k] * c_K3[p][k];
-      atomicAdd(A + (size_t)ii[i] * nci + ii[j], 161280.0 * a);  // g = kappa G / 161280
+      const size_t at = band >= 0 ? (size_t)ii[i] * (band + 1) + (ii[j] - ii[i] + band) : (size_t)ii[i] * nci + ii[j];
+      atomicAdd(A + at, 161280.0 * a);  // g = kappa G / 161280
     }
   }
 }
@@ -942,8 +948,9 @@ void launch_patch_setup_p3(Level& L, cudaStream_t s) {
   FE_REQUIRE(hflag == 0, FE_ERR_CUDA, "P3 patch setup failed (non-positive pivot or unknown star node)");
 }
 
-void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, double* A, cudaStream_t s) {
-  k_coarse_assemble_p3<<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, dof2int, nci, A);
+void launch_coarse_assemble_p3(const Level& L0, const int* dof2int, int nci, double* A, int band, cudaStream_t s) {
+  k_coarse_assemble_p3<<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, dof2int, nci, A,
+                                                                 band);
   LAUNCH_CHECK();
 }
 
@@ -973,9 +980,9 @@ void launch_build_level(Level& L, cudaStream_t s) {
 }
 
 void launch_uniform_geometry(Level& L, int* dflag, cudaStream_t s) {
-  if (!L.c32.p) {
-    L.c32.alloc(L.C);
-    L.cdf.alloc(L.C);
+  if (!L.c32.p) {  // rows of Cs (a multiple of 128 cells): the tensor-core operator stages c32 by TMA tiles
+    L.c32.alloc(L.Cs);
+    L.cdf.alloc(L.Cs);
   }
   CUDA_CHECK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
   k_uniform_geometry<<<ceil_div(L.C, kBlock), kBlock, 0, s>>>(L.C, L.Cs, L.geo64, L.c32, L.cdf, dflag);

@@ -100,3 +100,24 @@ def test_batched_full_workload(fe):
             b = np.where(space.boundary[rows], 0.0, O.apply_rows_mass(space, np.ones(space.n), rows))
             Au = O.apply_rows(space, kappas[p], u, rows)
             assert np.abs(Au - b).max() <= 1.01e-8 * stats[p].bnorm
+
+
+def test_batched_phase_clock(fe):
+    """opts.profile: block 0 of the persistent launch charges the wall time between grid barriers to
+    (phase, level); the same solution and iteration counts as the unprofiled launch."""
+    B, kappas, fs, us = _setup(fe, SMALL[:4])
+    with B:
+        st0 = B.solve(fs, us, rtol=1e-10)
+        ref = [u.clone() for u in us]
+        st = B.solve(fs, us, rtol=1e-10, profile=1)
+        nl = B.problems[0].nlev
+        for s0, s1, a, b in zip(st0, st, ref, us):
+            assert s0.iterations == s1.iterations
+            assert torch.allclose(a, b, rtol=0, atol=1e-12 * a.abs().max().item())
+        P = np.array([list(r) for r in st[0].phase_ms])
+        assert st[0].levels_timed == nl and np.all(P >= 0) and np.all(P[:, nl:] == 0)
+        assert P[fe.FE_PHASE_COARSE, 0] > 0 and np.all(P[fe.FE_PHASE_COARSE, 1:] == 0)
+        assert np.all(P[fe.FE_PHASE_SMOOTH, 1:nl] > 0) and np.all(P[fe.FE_PHASE_TRANSFER, 1:nl] > 0)
+        assert P[fe.FE_PHASE_APPLY, nl - 1] > 0 and P[fe.FE_PHASE_BLAS1, nl - 1] > 0
+        assert P.sum() <= st[0].solve_ms
+        assert all(np.array_equal(P, np.array([list(r) for r in s.phase_ms])) for s in st)

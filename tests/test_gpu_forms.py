@@ -170,15 +170,19 @@ def test_adjoint_full_size_taylor(fe):
 
 
 # ------------------------------------------------------- bf16 tensor cores
-@pytest.mark.parametrize("k", [1, 2])
-@pytest.mark.parametrize("N", [3, 8, 16])
-def test_apply_bf16_tensor_core(fe, k, N):
-    """tcgen05 GEMM-form apply: each dof split into two bf16 terms, tables exact, FP32 accumulation.
+@pytest.mark.parametrize("k,N", [(1, 3), (1, 8), (1, 16), (2, 3), (2, 8), (2, 16), (3, 3), (3, 6)])
+@pytest.mark.parametrize("form", ["uniform", "per_cell"])
+def test_apply_bf16_tensor_core(fe, k, N, form):
+    """tcgen05 GEMM-form apply: each dof split into two bf16 terms, tables exact (two bf16 terms where needed,
+    P3), FP32 accumulation; the one-table form (G = c M, N = 16 / 16 / 32 columns) and the six-table form
+    (N = 32 / 64 / 128 columns).
 
     Rowwise bound 5e-5 |A||x| (the two-term bf16 split keeps 16 bits, 2^-17
     relative, plus FP32 sums); N=3 gives 162 cells, i.e. one partial 128-cell tile.
     """
     with fe.Hierarchy(N, 0, k) as h:
+        if form == "per_cell":
+            h.set_geometry_form(fe.FE_GEOMETRY_PER_CELL)
         kappa = I.grf_kappa(h.cell_centroids(), seed=N + 40)
         h.set_coefficient(dt(kappa))
         L = O.Level(N, k, kappa)
@@ -204,6 +208,43 @@ def test_apply_bf16_tensor_core(fe, k, N):
         sb = (abs(L.A) @ np.abs(xb))[inter]
         assert np.all(err_b <= 2e-5 * sb), np.max(err_b / sb)
         assert np.array_equal(got[~inter], x[~inter].astype(np.float64))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_geometry_forms_agree(fe, k):
+    """Every operator path with one geometric value per cell (G = c M) against the six stored factors: FP64 in
+    float pairs (per tet and, for P1, per cube), native FP64 and FP32, rowwise at their parity tolerances, and a
+    GMG-PCG solve."""
+    with fe.Hierarchy(4, 1, k) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=k)
+        h.set_coefficient(dt(kappa))
+        L = O.Level(8, k, kappa)
+        x = I.random_vector(L.n, 7)
+        scale = abs(L.A) @ np.abs(x)
+        out = {}
+        for form in (fe.FE_GEOMETRY_AUTO, fe.FE_GEOMETRY_PER_CELL):
+            h.set_geometry_form(form)
+            for mode in (fe.FE_F64_DOUBLE_FLOAT, fe.FE_F64_DOUBLE_FLOAT_TET, fe.FE_F64_NATIVE):
+                h.set_f64_mode(mode)
+                y = torch.empty(L.n, dtype=torch.float64, device=DEV)
+                h.apply_operator(dt(x), y)
+                out[form, mode] = host(y)
+            h.set_f64_mode(fe.FE_F64_DOUBLE_FLOAT)
+            y32 = torch.empty(L.n, dtype=torch.float32, device=DEV)
+            h.apply_operator(dt(x, torch.float32), y32, dtype=fe.FE_F32)
+            out[form, "f32"] = host(y32)
+            u = torch.empty(L.n, dtype=torch.float64, device=DEV)
+            st = h.solve(dt(I.sin_product_rhs(h.dof_coordinates())), u, rtol=1e-12)
+            out[form, "solve"] = (host(u), st.iterations)
+        ref = L.A @ x
+        for mode in (fe.FE_F64_DOUBLE_FLOAT, fe.FE_F64_DOUBLE_FLOAT_TET, fe.FE_F64_NATIVE):
+            for form in (fe.FE_GEOMETRY_AUTO, fe.FE_GEOMETRY_PER_CELL):
+                assert np.all(np.abs(out[form, mode] - ref) <= 1e-13 * scale), (form, mode)
+        for form in (fe.FE_GEOMETRY_AUTO, fe.FE_GEOMETRY_PER_CELL):
+            assert np.all(np.abs(out[form, "f32"] - ref) <= 1e-5 * scale), form
+        ua, ia = out[fe.FE_GEOMETRY_AUTO, "solve"]
+        ub, ib = out[fe.FE_GEOMETRY_PER_CELL, "solve"]
+        assert ia == ib and np.linalg.norm(ua - ub) <= 1e-11 * np.linalg.norm(ub)
 
 
 def test_mixed_bf16_refinement(fe):

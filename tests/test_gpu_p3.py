@@ -213,12 +213,22 @@ def test_p3_full_size_sampled_rows(fe):
         assert np.abs(host(y32)[rows] - ref32).max() <= 1e-4 * np.abs(ref32).max()
 
 
-def test_p3_unsupported_forms_fail_loudly(fe):
-    with fe.Hierarchy(2, 1, 3) as h:
-        n = h.n_dofs()
-        x = torch.zeros(n, dtype=torch.float32, device=DEV)
-        y = torch.empty_like(x)
-        with pytest.raises(fe.FeError):
-            h.apply_operator(x, y, dtype=fe.FE_BF16)
-    with pytest.raises(fe.FeError):
+def test_p3_batched_is_unsupported(fe):
+    with pytest.raises(fe.FeError) as e:
         fe.Batch([(2, 1, 3)])
+    assert e.value.code == fe.FE_ERR_UNSUPPORTED
+
+
+def test_p3_mixed_bf16_tensor_core_solve(fe):
+    """FP64 iterative refinement around the GMG-PCG whose smoother applies the P3 operator on the tensor cores
+    (K = 20 -> 32): reaches the FP64 solution at rtol 1e-10."""
+    with fe.Hierarchy(2, 2, 3) as h:
+        kappa = I.grf_kappa(h.cell_centroids(), seed=9)
+        h.set_coefficient(dt(kappa))
+        f = dt(I.sin_product_rhs(h.dof_coordinates()))
+        u64 = torch.empty(h.n_dofs(), dtype=torch.float64, device=DEV)
+        ub = torch.empty_like(u64)
+        h.solve(f, u64, rtol=1e-12)
+        st = h.solve(f, ub, rtol=1e-10, precision=fe.FE_PREC_MIXED_BF16, max_it=40)
+        assert st.rel_residual <= 1e-10
+        assert (torch.linalg.norm(ub - u64) / torch.linalg.norm(u64)).item() <= 1e-8
