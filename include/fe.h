@@ -153,7 +153,7 @@ typedef struct fe_solve_stats {
 } fe_solve_stats;
 
 /* Fill `opts` with the defaults: rtol 1e-8, max_it 500, GMG, FP64,
- * 2 Chebyshev steps on [0.1, 1.1] lambda_max, inner_rtol 1e-4, inner_max_it 60,
+ * 2 Chebyshev steps on [0.1, 1.1] lambda_max, inner_rtol 3e-5, inner_max_it 60,
  * graphs on, profiling off, default wait bound. */
 void fe_default_opts(fe_solver_opts* opts);
 

@@ -1254,7 +1254,7 @@ void fe_default_opts(fe_solver_opts* o) {
   o->cheb_steps = 2;
   o->cheb_lo = 0.1;
   o->cheb_hi = 1.1;
-  o->inner_rtol = 1e-4;
+  o->inner_rtol = 3e-5;  // P2 128^3: 2 refinement steps of 5 inner iterations (1e-4: 3 steps, 14 iterations, 40% slower)
   o->inner_max_it = 60;
   o->use_graph = 1;
   o->profile = 0;

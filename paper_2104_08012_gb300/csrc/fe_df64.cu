@@ -30,6 +30,13 @@ namespace {
 using namespace fe_df;
 constexpr int kBlock = 256;
 constexpr int kBlockP3 = 128;
+// Block shape of the pre-split, one-value-per-cell float-pair operator (the
+// FP64 solve's hot kernel): 128 threads, compiled for 5 resident blocks (96
+// registers, no spills).  Full P2 64^3 solves measured 7.80 / 7.40 / 7.75 /
+// 7.80 / 7.61 ms for (threads, blocks) = (256, 2) / (128, 5) / (192, 3) /
+// (128, 6: 80 registers, spills) / (128, 4).
+constexpr int kBlockDfU = 128;
+constexpr int kMinBlocksDfU = 5;
 
 
 // The dofs whose countdown this thread ended (count returned 1): every other
@@ -71,7 +78,7 @@ __device__ __forceinline__ void finish_dofs(const int* pidx, const unsigned* pre
 // UNI: geo is L.cdf, one float pair c per cell with G = c M (see Level), and
 // the element uses the fixed matrix M instead of six loaded factors.
 template <int DEG, bool FUSE, bool PRE, bool UNI>
-__global__ void __launch_bounds__(kBlock, 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
+__global__ void __launch_bounds__(UNI && PRE ? kBlockDfU : kBlock, UNI && PRE ? kMinBlocksDfU : 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
                                                         const float2* __restrict__ geo, const double* x,
                                                         const float2* __restrict__ xs, double* __restrict__ y, int nb,
                                                         const int* __restrict__ bnd, ChebFuse<double> cf) {
@@ -509,9 +516,10 @@ static void apply_cube_df(const Level& L, const double* x, double* y, const Cheb
 template <int DEG, bool FUSE, bool PRE, bool UNI>
 static void apply_df_launch(const Level& L, const double* x, const float2* xs, double* y, const ChebFuse<double>& cf,
                             cudaStream_t s) {
+  constexpr int blk = UNI && PRE ? kBlockDfU : kBlock;
   static int g = 0;
-  if (!g) g = resident_grid(k_apply_df<DEG, FUSE, PRE, UNI>, kBlock, 1 << 30);
-  k_apply_df<DEG, FUSE, PRE, UNI><<<std::min(g, ceil_div(std::max(L.C, L.nb), kBlock)), kBlock, 0, s>>>(
+  if (!g) g = resident_grid(k_apply_df<DEG, FUSE, PRE, UNI>, blk, 1 << 30);
+  k_apply_df<DEG, FUSE, PRE, UNI><<<std::min(g, ceil_div(std::max(L.C, L.nb), blk)), blk, 0, s>>>(
       L.C, L.Cs, L.map, UNI ? L.cdf.p : L.geodf.p, x, xs, y, L.nb, L.bnd, cf);
 }
 
