@@ -44,7 +44,7 @@ BYTES_PER_DOF_P2 = {"f64": 49.0, "f32": 41.0}
 # dram__bytes_write.sum from one ncu capture of the finest level's applications inside a V-cycle of the
 # P2 64^3 hierarchy, the kernel the CG iterations run; mean of 2 launches), keyed by FP64 mode; None where
 # the kernel changed after the last capture.
-TRAFFIC = {0: None, 1: 117.1e6, 2: None}
+TRAFFIC = {0: None, 1: None, 2: None}
 # Arithmetic of one P2 element application (c, d, S, four G-products, transpose),
 # per tet: 151 flops in the FP64 formula with a general G (an FMA counts 2).  The
 # float-pair form with the geometric matrix shared by every Kuhn tet (G = c M)

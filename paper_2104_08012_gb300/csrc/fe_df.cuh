@@ -6,6 +6,9 @@
 // power-of-two normalisation, so the FP64 pipe is not used for conversions.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "fe_internal.cuh"
 
 namespace fe_df {
@@ -223,6 +226,115 @@ __device__ __forceinline__ void element_df_m(const DF (&u)[DEG == 1 ? 4 : 10], D
     p1_element_df_m(u, c, y);
   else
     p2_element_df_m(u, c, y);
+}
+
+// ------------------------------------ P2 Kuhn tet by fixed-point limbs ---
+// Every Kuhn tet has G = c M, so its P2 element matrix (Eq. 4 with
+// phi_i, phi_j quadratic) is c K120 for one integer matrix:
+//   K120_ij = 120 int_ref grad phi_i^T M grad phi_j,
+// with grad phi_v = (4 lambda_v - 1) g_v, grad phi_ab = 4 (lambda_a g_b +
+// lambda_b g_a), g_a = grad lambda_a (constant) and the reference integrals
+// 120 int lambda_a lambda_b = 1 + delta_ab, 120 int lambda_a = 5, 120 vol = 20.
+// m_ab = g_a^T M g_b (g_0 = -(1, 1, 1), g_k = e_k).
+__host__ __device__ constexpr int kuhn_m(int a, int b) {
+  int s = 0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      const int mkl = k == l ? (k == 2 ? 1 : 2) : (k + l == 1 || k + l == 3 ? -1 : 0);
+      s += (a == 0 ? -1 : (a - 1 == k ? 1 : 0)) * mkl * (b == 0 ? -1 : (b - 1 == l ? 1 : 0));
+    }
+  return s;
+}
+__host__ __device__ constexpr int lam2(int a, int b) { return a == b ? 2 : 1; }
+__host__ __device__ constexpr int kuhn_p2_k120(int i, int j) {
+  return i < 4 && j < 4 ? kuhn_m(i, j) * (16 * lam2(i, j) - 20)
+         : i >= 4 && j >= 4
+             ? 16 * (lam2(edge_a(i), edge_a(j)) * kuhn_m(edge_b(i), edge_b(j)) +
+                     lam2(edge_a(i), edge_b(j)) * kuhn_m(edge_b(i), edge_a(j)) +
+                     lam2(edge_b(i), edge_a(j)) * kuhn_m(edge_a(i), edge_b(j)) +
+                     lam2(edge_b(i), edge_b(j)) * kuhn_m(edge_a(i), edge_a(j)))
+         : i >= 4 ? kuhn_p2_k120(j, i)
+                  : 4 * (kuhn_m(i, edge_b(j)) * (4 * lam2(i, edge_a(j)) - 5) +
+                         kuhn_m(i, edge_a(j)) * (4 * lam2(i, edge_b(j)) - 5));
+}
+// K120 = 4 K; the limb sums below rely on every row of |K| summing to at most 62.
+__host__ __device__ constexpr int kuhn_p2_k(int i, int j) { return kuhn_p2_k120(i, j) / 4; }
+__host__ __device__ constexpr bool kuhn_p2_k_ok() {
+  for (int i = 0; i < 10; ++i) {
+    int row = 0, absrow = 0;
+    for (int j = 0; j < 10; ++j) {
+      if (kuhn_p2_k120(i, j) % 4 != 0 || kuhn_p2_k120(i, j) != kuhn_p2_k120(j, i)) return false;
+      row += kuhn_p2_k(i, j);
+      absrow += kuhn_p2_k(i, j) < 0 ? -kuhn_p2_k(i, j) : kuhn_p2_k(i, j);
+    }
+    if (row != 0 || absrow > 62) return false;  // constants in the kernel: rows sum to 0
+  }
+  return kuhn_p2_k(0, 0) == 3 && kuhn_p2_k(5, 5) == 24;
+}
+static_assert(kuhn_p2_k_ok(), "P2 Kuhn stiffness: integer, symmetric, zero row sums, row abs sums <= 62");
+
+// Fixed-point limb evaluation of y = K x' for x'_j = cs u_j (float pairs,
+// |x'_j| < 2): p2_kuhn_split forms the limbs, p2_kuhn_apply the products.  Each x'_j, held as the unnormalised product (p, e), is cut
+// into three limbs by rounding against a magic constant (Dekker's splitting
+// with a fixed exponent instead of a relative one):
+//   A_j: a multiple of 2^-16, |A_j| <= 2;
+//   B_j: a multiple of 2^-33, |B_j| < 2^-16.9;
+//   C_j = x'_j - A_j - B_j, |C_j| < 2^-33.9.
+// Sums of K_ij A_j are integers below 62 * 2^17 < 2^23 times 2^-16, and of
+// K_ij B_j integers below 2^22.1 times 2^-33, so FP32 forms K A and K B
+// exactly in any order; only K C (below 2^-28) is rounded (about 2^-49
+// absolute).  Row i is handed to emit(i, y_i) as the float pair
+// (fl(KA + KB), err + KC) as soon as it is formed, so no output array stays
+// live.  The splitting costs 8 FP32 additions per dof and each limb product
+// 82 FMAs with immediate integer coefficients, against about 80 float-pair
+// additions of 8 instructions each for the same contraction through vertex
+// gradients.
+// One term K_ij (A_j, B_j, C_j) of row i, with K_ij a template argument so
+// that zero terms vanish and the coefficient is an immediate operand.
+template <int K>
+__device__ __forceinline__ void kuhn_term(float a, float b, float c, float& ya, float& yb, float& yc) {
+  if constexpr (K != 0) {
+    ya = __fmaf_rn((float)K, a, ya);
+    yb = __fmaf_rn((float)K, b, yb);
+    yc = __fmaf_rn((float)K, c, yc);
+  }
+}
+template <int I, int... J>
+__device__ __forceinline__ void kuhn_row(const float (&A)[10], const float (&B)[10], const float (&C)[10], float& ya,
+                                         float& yb, float& yc, std::integer_sequence<int, J...>) {
+  (kuhn_term<kuhn_p2_k(I, J)>(A[J], B[J], C[J], ya, yb, yc), ...);
+}
+template <int... I, typename Emit>
+__device__ __forceinline__ void kuhn_rows(const float (&A)[10], const float (&B)[10], const float (&C)[10],
+                                          Emit& emit, std::integer_sequence<int, I...>) {
+  auto row = [&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    float ya = 0.0f, yb = 0.0f, yc = 0.0f;
+    kuhn_row<i>(A, B, C, ya, yb, yc, std::make_integer_sequence<int, 10>{});
+    const DF t = two_sum(ya, yb);
+    emit(i, DF(t.hi, __fadd_rn(t.lo, yc)));
+  };
+  (row(std::integral_constant<int, I>{}), ...);
+}
+
+__device__ __forceinline__ void p2_kuhn_split(const DF (&u)[10], DF cs, float (&A)[10], float (&B)[10],
+                                              float (&C)[10]) {
+  constexpr float kMagA = 192.0f;      // 1.5 * 2^7: fl(v + kMagA) has ulp 2^-16 for |v| <= 2
+  constexpr float kMagB = 0x1.8p-10f;  // 1.5 * 2^-10: ulp 2^-33 for |v| < 2^-11
+#pragma unroll
+  for (int j = 0; j < 10; ++j) {
+    const float p = __fmul_rn(cs.hi, u[j].hi);
+    const float e = __fmaf_rn(cs.hi, u[j].lo, __fmaf_rn(cs.lo, u[j].hi, __fmaf_rn(cs.hi, u[j].hi, -p)));
+    A[j] = __fsub_rn(__fadd_rn(p, kMagA), kMagA);
+    const float r = __fsub_rn(p, A[j]);  // exact
+    B[j] = __fsub_rn(__fadd_rn(__fadd_rn(r, e), kMagB), kMagB);
+    C[j] = __fadd_rn(__fsub_rn(r, B[j]), e);  // r - B_j exact
+  }
+}
+template <typename Emit>
+__device__ __forceinline__ void p2_kuhn_apply(const float (&A)[10], const float (&B)[10], const float (&C)[10],
+                                              Emit&& emit) {
+  kuhn_rows(A, B, C, emit, std::make_integer_sequence<int, 10>{});
 }
 
 // Whether cube-local node l already received a contribution from one of the

@@ -30,11 +30,13 @@ namespace {
 using namespace fe_df;
 constexpr int kBlock = 256;
 constexpr int kBlockP3 = 128;
-// Block shape of the pre-split, one-value-per-cell float-pair operator (the
-// FP64 solve's hot kernel): 128 threads, compiled for 5 resident blocks (96
-// registers, no spills).  Full P2 64^3 solves measured 7.80 / 7.40 / 7.75 /
-// 7.80 / 7.61 ms for (threads, blocks) = (256, 2) / (128, 5) / (192, 3) /
-// (128, 6: 80 registers, spills) / (128, 4).
+// Block shape of the pre-split, one-value-per-cell operator (the FP64
+// solve's hot kernel): 128 threads, compiled for 5 resident blocks (96
+// registers, no spills).  With the fixed-point limb element, full P2 64^3
+// solves measured 6.46 / 6.63 / 6.60 ms for (threads, blocks) = (128, 5) /
+// (128, 4) / (256, 2); gathering the next tet's dofs after the limb split
+// instead of at the top of the iteration (so its map rows have arrived)
+// measured 6.53 ms at (128, 4) and spilled at (128, 5).
 constexpr int kBlockDfU = 128;
 constexpr int kMinBlocksDfU = 5;
 
@@ -76,7 +78,11 @@ __device__ __forceinline__ void finish_dofs(const int* pidx, const unsigned* pre
 // done.  Dirichlet rows (y = x) are updated by the threads that write them.
 //
 // UNI: geo is L.cdf, one float pair c per cell with G = c M (see Level), and
-// the element uses the fixed matrix M instead of six loaded factors.
+// the element uses the fixed matrix M instead of six loaded factors.  For P2
+// the element matrix is then c times one integer matrix, applied by exact
+// fixed-point limbs (p2_kuhn_limbs); the tet's power-of-two scaling goes into
+// c, so a pre-split tet uses its gathered pairs as they are, and a tet whose
+// dofs are all zero contributes nothing and is skipped.
 template <int DEG, bool FUSE, bool PRE, bool UNI>
 __global__ void __launch_bounds__(UNI && PRE ? kBlockDfU : kBlock, UNI && PRE ? kMinBlocksDfU : 2) k_apply_df(int C, int Cs, const int* __restrict__ map,
                                                         const float2* __restrict__ geo, const double* x,
@@ -84,6 +90,7 @@ __global__ void __launch_bounds__(UNI && PRE ? kBlockDfU : kBlock, UNI && PRE ? 
                                                         const int* __restrict__ bnd, ChebFuse<double> cf) {
   static_assert(!(FUSE && PRE), "the fused smoother changes x during the launch");
   constexpr int ND = DEG == 1 ? 4 : 10;
+  constexpr bool LIMBS = DEG == 2 && UNI;  // P2 on Kuhn tets: fixed-point limbs (p2_kuhn_limbs)
   constexpr int NG = UNI ? 1 : 6;  // geometric values per cell
   using XV = typename std::conditional<PRE, float2, double>::type;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -131,6 +138,8 @@ __global__ void __launch_bounds__(UNI && PRE ? kBlockDfU : kBlock, UNI && PRE ? 
     DF u[ND], out[ND];
     int emax;  // the element map is linear: scale by 2^(1023 - emax), contract, unscale
     bool split_here = !PRE;
+    float fsc = 1.0f;        // LIMBS: the tet's power-of-two scaling, applied to c instead of the dofs
+    bool zero_tet = false;   // LIMBS: every gathered dof is zero (no contribution)
     if constexpr (PRE) {
       unsigned int mb = 0u;  // largest magnitude bits of the leading floats (a marker NaN exceeds every finite one)
 #pragma unroll
@@ -138,8 +147,15 @@ __global__ void __launch_bounds__(UNI && PRE ? kBlockDfU : kBlock, UNI && PRE ? 
       const int ef = (int)(mb >> 23);  // its exponent field (0xFF: a marker)
       if (ef != 0xFF) {
         const float f = __uint_as_float((unsigned int)(254 - ef) << 23);  // 2^(127 - ef)
+        if constexpr (LIMBS) {
 #pragma unroll
-        for (int j = 0; j < ND; ++j) u[j] = DF(__fmul_rn(xv[j].x, f), __fmul_rn(xv[j].y, f));
+          for (int j = 0; j < ND; ++j) u[j] = DF(xv[j].x, xv[j].y);
+          fsc = f;
+          zero_tet = mb == 0u;
+        } else {
+#pragma unroll
+          for (int j = 0; j < ND; ++j) u[j] = DF(__fmul_rn(xv[j].x, f), __fmul_rn(xv[j].y, f));
+        }
         emax = ef + 896;
       } else {
         split_here = true;
@@ -159,23 +175,50 @@ __global__ void __launch_bounds__(UNI && PRE ? kBlockDfU : kBlock, UNI && PRE ? 
       for (int j = 0; j < ND; ++j) u[j] = split_scaled(xd[j], emax);
       if (emax == 0x7FF) u[0] = DF(__int_as_float(0x7fc00000), 0.0f);  // propagate NaN/inf dofs
     }
-    if constexpr (UNI) {
-      element_df_m<DEG>(u, DF(gv[0].x, gv[0].y), out);
+    if constexpr (LIMBS) {
+      float A[ND], B[ND], Cl[ND];
+      int w = 0;
+      if (!zero_tet) {
+        // x' = c 2^(126 - ec) x 2^(1023 - emax) stays below 2 (c.hi normalised to [0.5, 1)); the
+        // element matrix is 4 c K, so y = K x' 2^(ec + emax - 1147), widened with exponent w
+        const unsigned int cb = __float_as_uint(gv[0].x);
+        const int ec = (int)((cb >> 23) & 0xFFu);  // c in [2^-100, 2^100]: a normal float
+        const float chs = __uint_as_float((cb & 0x807FFFFFu) | (126u << 23));
+        const float cls = __fmul_rn(gv[0].y, __uint_as_float((unsigned int)(253 - ec) << 23));
+        p2_kuhn_split(u, DF(__fmul_rn(chs, fsc), __fmul_rn(cls, fsc)), A, B, Cl);
+        w = ec + emax - 124;
+      }
+      if (!zero_tet) {
+        if (w >= 127 && w <= 1918) {  // every contribution widens without range checks
+          const unsigned int kexp = (unsigned int)(w - 127) << 20;
+          p2_kuhn_apply(A, B, Cl, [&](int j, DF v) {
+            if (idx[j] >= 0) atomicAdd(y + idx[j], widen_in_range(v.hi, kexp) + widen_in_range(v.lo, kexp));
+          });
+        } else {
+          p2_kuhn_apply(A, B, Cl, [&](int j, DF v) {
+            if (idx[j] >= 0) atomicAdd(y + idx[j], widen_scaled(v.hi, w) + widen_scaled(v.lo, w));
+          });
+        }
+      }
     } else {
-      DF g[6];
+      if constexpr (UNI) {
+        element_df_m<DEG>(u, DF(gv[0].x, gv[0].y), out);
+      } else {
+        DF g[6];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) g[a] = DF(gv[a].x, gv[a].y);
-      element_df<DEG>(u, g, out);
-    }
-    if (emax >= 127 && emax <= 1918) {  // every contribution widens without range checks
-      const unsigned int kexp = (unsigned int)(emax - 127) << 20;
+        for (int a = 0; a < 6; ++a) g[a] = DF(gv[a].x, gv[a].y);
+        element_df<DEG>(u, g, out);
+      }
+      if (emax >= 127 && emax <= 1918) {  // every contribution widens without range checks
+        const unsigned int kexp = (unsigned int)(emax - 127) << 20;
 #pragma unroll
-      for (int j = 0; j < ND; ++j)
-        if (idx[j] >= 0) atomicAdd(y + idx[j], widen_in_range(out[j].hi, kexp) + widen_in_range(out[j].lo, kexp));
-    } else {
+        for (int j = 0; j < ND; ++j)
+          if (idx[j] >= 0) atomicAdd(y + idx[j], widen_in_range(out[j].hi, kexp) + widen_in_range(out[j].lo, kexp));
+      } else {
 #pragma unroll
-      for (int j = 0; j < ND; ++j)
-        if (idx[j] >= 0) atomicAdd(y + idx[j], widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
+        for (int j = 0; j < ND; ++j)
+          if (idx[j] >= 0) atomicAdd(y + idx[j], widen_scaled(out[j].hi, emax) + widen_scaled(out[j].lo, emax));
+      }
     }
     if constexpr (FUSE) {
       // the previous tet's countdowns have returned by now: finish its dofs

@@ -195,7 +195,7 @@ __global__ void k_uniform_geometry(int C, int Cs, const double* __restrict__ geo
   if (t >= C) return;
   const double c = geo64[(size_t)5 * Cs + t];
   const double m[5] = {2.0, -1.0, 0.0, 2.0, -1.0};
-  bool ok = c > 0.0;
+  bool ok = c >= 0x1p-100 && c <= 0x1p100;  // the float-pair kernels normalise c.hi by its exponent field
 #pragma unroll
   for (int a = 0; a < 5; ++a) ok = ok && fabs(geo64[(size_t)a * Cs + t] - m[a] * c) <= 1e-12 * c;
   if (!ok) atomicOr(flag, 1);
