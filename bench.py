@@ -44,16 +44,16 @@ BYTES_PER_DOF_P2 = {"f64": 49.0, "f32": 41.0}
 # dram__bytes_write.sum from one ncu capture of the finest level's applications inside a V-cycle of the
 # P2 64^3 hierarchy, the kernel the CG iterations run; mean of 2 launches), keyed by FP64 mode; None where
 # the kernel changed after the last capture.
-TRAFFIC = {0: None, 1: None, 2: None}
+TRAFFIC = {0: None, 1: 116.9e6, 2: None}
 # Arithmetic of one P2 element application (c, d, S, four G-products, transpose),
-# per tet: 151 flops in the FP64 formula with a general G (an FMA counts 2).  The
-# float-pair form with the geometric matrix shared by every Kuhn tet (G = c M)
-# issues 798 FP32 operations (an add, mul or FMA counts 1): 71 float-pair
-# additions x 8, the four products M t as 16 float-pair subtractions x 8,
-# 8 small-integer scalings x 6, 7 power-of-two scalings x 2 and ten products
-# by c x 4.
+# per tet: 151 flops in the FP64 formula with a general G (an FMA counts 2).  With
+# the geometric matrix shared by every Kuhn tet (G = c M) the element matrix is
+# c times one integer matrix K (82 nonzeros), applied by fixed-point limbs:
+# 436 FP32 operations (an add, mul or FMA counts 1) = ten products c x as float
+# pairs x 4, their cut into three limbs x 8 additions, 82 x 3 FMAs, and per row
+# one TwoSum (6) and one addition.
 FLOPS_PER_CELL_P2_F64 = 151
-OPS_PER_CELL_P2_DF = 798
+OPS_PER_CELL_P2_DF = 436
 # Operations of one P3 element application through the gradient at the P2 nodes (fe_p3.cuh; an FMA counts 1):
 # 206 additions, 165 multiplications, 284 FMAs, 22 negations (counted by tests/test_p3_element_host.py)
 OPS_PER_CELL_P3 = 677
@@ -757,10 +757,10 @@ def run_ours(args, rank, world, local_rank, oracle=None):
     byt = BYTES_PER_DOF_P2["f64"] * n
     achieved_gbs = byt / (apply_ms * 1e-3) / 1e9
     if F64_MODE == fe.FE_F64_DOUBLE_FLOAT:
-        kname = ("k_apply_df<2> (FP64 operator: float-pair element arithmetic on the FP32 pipes, persistent, one tet "
-                 "per thread)")
+        kname = ("k_apply_df<2> (FP64 operator on the FP32 pipes: exact fixed-point limbs of c x against the integer "
+                 "Kuhn-tet stiffness, persistent, one tet per thread)")
         ops, opeak, ounit = OPS_PER_CELL_P2_DF * C, FP32_PEAK_TOPS, "T FP32 op/s"
-        oderiv = ("798 FP32 operations per tet of the float-pair element formula x cells / launch duration, against the "
+        oderiv = ("436 FP32 operations per tet of the limb element x cells / launch duration, against the "
                   "nominal FP32 issue rate 152 SMs x 128 lanes x 1 op/clk x 2.07 GHz = 40.3 T op/s (no measured FP32 "
                   "peak exists)")
     else:
@@ -772,11 +772,12 @@ def run_ours(args, rank, world, local_rank, oracle=None):
         "metric": "Poisson GMG-CG solve DoF/s at 1e-8 residual",
         "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 (float-pair operator)" if F64_MODE == fe.FE_F64_DOUBLE_FLOAT else "f64",
+        "dtype": "f64 (operator on the FP32 pipes, ~47-bit)" if F64_MODE == fe.FE_F64_DOUBLE_FLOAT else "f64",
         "data": "synthetic (manufactured sin-product right-hand side, kappa = 1)",
         "config": dict(WORKLOAD, parallelism=f"replicas{world}",
-                       f64_operator="float-pair (double-float, ~47-bit) element arithmetic on the FP32 pipes; FP64 "
-                                    "vectors, reductions, transfers, smoother updates, coarse Cholesky"
+                       f64_operator="P2 element as exact fixed-point limbs of float-pair products on the FP32 "
+                                    "pipes (~47-bit); FP64 vectors, reductions, transfers, smoother updates, coarse "
+                                    "Cholesky"
                        if F64_MODE == 1 else "native FP64"),
         "iterations": stats[-1].iterations, "rel_residual": stats[-1].rel_residual,
         "max_nodal_error_vs_exact": nodal_err, "setup_s": setup_s,
@@ -791,7 +792,7 @@ def run_ours(args, rank, world, local_rank, oracle=None):
                                     "kappa = 1)",
                      "peak_source": f"{hsrc} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hsrc == "measured"
                      else "fallback 6.8 TB/s",
-                     "limiter": "instruction issue (float-pair arithmetic), not DRAM",
+                     "limiter": "instruction issue and gather latency, not DRAM (ncu: issue 66%, FP64 pipe 51%)",
                      "alu_issue_view_nominal": {"achieved": ops / (apply_ms * 1e-3) / 1e12, "peak": opeak,
                                                 "unit": ounit, "frac": ops / (apply_ms * 1e-3) / 1e12 / opeak,
                                                 "derivation": oderiv},
