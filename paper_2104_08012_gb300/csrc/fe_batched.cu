@@ -355,6 +355,23 @@ __device__ void apply_cells(const Params& A, const BProb& P, const BLevel& L, in
 #pragma unroll
       for (int j = 0; j < ND; ++j) ud[j] = fe_df::split_scaled(u[j], emax);
       if (emax == 0x7FF) ud[0] = fe_df::DF(__int_as_float(0x7fc00000), 0.0f);
+      if constexpr (DEG == 2) {
+        if (L.uniform) {
+          // the element matrix is 4 c K: exact fixed-point limbs of x' = c 2^(126 - ec) ud (as in k_apply_df)
+          const float2 v = L.cdf[c];
+          const unsigned int cb = __float_as_uint(v.x);
+          const int ec = (int)((cb >> 23) & 0xFFu);
+          const fe_df::DF cs(__uint_as_float((cb & 0x807FFFFFu) | (126u << 23)),
+                             __fmul_rn(v.y, __uint_as_float((unsigned int)(253 - ec) << 23)));
+          float la[10], lb[10], lc[10];
+          fe_df::p2_kuhn_split(ud, cs, la, lb, lc);
+          const int w = ec + emax - 124;
+          fe_df::p2_kuhn_apply(la, lb, lc, [&](int j, fe_df::DF t) {
+            if (idx[j] >= 0) atomicAdd(out + idx[j], fe_df::widen_scaled(t.hi, w) + fe_df::widen_scaled(t.lo, w));
+          });
+          continue;
+        }
+      }
       if (L.uniform) {
         const float2 v = L.cdf[c];
         fe_df::element_df_m<DEG>(ud, fe_df::DF(v.x, v.y), od);
