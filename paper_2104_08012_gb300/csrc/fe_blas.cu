@@ -70,12 +70,37 @@ __device__ bool grid_reduce(double (&v)[NV], double* __restrict__ partials, unsi
   return threadIdx.x == 0;
 }
 
+// The reductions run on a fixed grid of ReduceCtx::grid blocks (2 per SM), so
+// with one element per thread in flight they are bound by load latency, not
+// by HBM: each thread walks its grid-stride slice kUnroll elements at a time,
+// issuing their loads together, then the remainder one by one (a fixed order
+// per thread: the sums stay deterministic).
+constexpr int kUnroll = 4;
+
+// sum over this thread's slice of a[i] b[i]
+template <typename T>
+__device__ __forceinline__ double slice_dot(int n, const T* __restrict__ a, const T* __restrict__ b) {
+  const int G = gridDim.x * kRedBlock;
+  int i = blockIdx.x * kRedBlock + threadIdx.x;
+  double s = 0.0;
+  for (; i + (kUnroll - 1) * G < n; i += kUnroll * G) {
+    T av[kUnroll], bv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      av[u] = a[i + u * G];
+      bv[u] = b[i + u * G];
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) s += (double)av[u] * (double)bv[u];
+  }
+  for (; i < n; i += G) s += (double)a[i] * (double)b[i];
+  return s;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kRedBlock) k_dot(int n, const T* __restrict__ a, const T* __restrict__ b,
                                                    double* partials, unsigned int* counter, double* scal, int slot) {
-  double v[1] = {0.0};
-  for (int i = blockIdx.x * kRedBlock + threadIdx.x; i < n; i += gridDim.x * kRedBlock)
-    v[0] += (double)a[i] * (double)b[i];
+  double v[1] = {slice_dot(n, a, b)};
   double out[1];
   if (grid_reduce<1>(v, partials, counter, out)) scal[slot] = out[0];
 }
@@ -83,9 +108,7 @@ __global__ void __launch_bounds__(kRedBlock) k_dot(int n, const T* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(kRedBlock) k_cg_alpha(int n, const T* __restrict__ p, const T* __restrict__ q,
                                                         double* partials, unsigned int* counter, double* scal) {
-  double v[1] = {0.0};
-  for (int i = blockIdx.x * kRedBlock + threadIdx.x; i < n; i += gridDim.x * kRedBlock)
-    v[0] += (double)p[i] * (double)q[i];
+  double v[1] = {slice_dot(n, p, q)};
   double out[1];
   if (grid_reduce<1>(v, partials, counter, out)) {
     scal[S_PQ] = out[0];
@@ -99,9 +122,9 @@ __global__ void __launch_bounds__(kRedBlock)
                 const T* __restrict__ dinv, T* __restrict__ z, double* partials, unsigned int* counter, double* scal) {
   const T alpha = (T)scal[S_ALPHA];
   double v[2] = {0.0, 0.0};
-  for (int i = blockIdx.x * kRedBlock + threadIdx.x; i < n; i += gridDim.x * kRedBlock) {
-    x[i] += alpha * p[i];
-    const T ri = r[i] - alpha * q[i];
+  auto one = [&](int i, T xi, T pi, T ri0, T qi) {
+    x[i] = xi + alpha * pi;
+    const T ri = ri0 - alpha * qi;
     r[i] = ri;
     v[0] += (double)ri * (double)ri;
     if (dinv) {
@@ -109,7 +132,22 @@ __global__ void __launch_bounds__(kRedBlock)
       z[i] = zi;
       v[1] += (double)ri * (double)zi;
     }
+  };
+  const int G = gridDim.x * kRedBlock;
+  int i = blockIdx.x * kRedBlock + threadIdx.x;
+  for (; i + (kUnroll - 1) * G < n; i += kUnroll * G) {
+    T xv[kUnroll], pv[kUnroll], rv[kUnroll], qv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      xv[u] = x[i + u * G];
+      pv[u] = p[i + u * G];
+      rv[u] = r[i + u * G];
+      qv[u] = q[i + u * G];
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) one(i + u * G, xv[u], pv[u], rv[u], qv[u]);
   }
+  for (; i < n; i += G) one(i, x[i], p[i], r[i], q[i]);
   double out[2];
   if (grid_reduce<2>(v, partials, counter, out)) {
     scal[S_RR] = out[0];
@@ -124,9 +162,7 @@ __global__ void __launch_bounds__(kRedBlock)
 template <typename T>
 __global__ void __launch_bounds__(kRedBlock) k_cg_beta(int n, const T* __restrict__ r, const T* __restrict__ z,
                                                        double* partials, unsigned int* counter, double* scal) {
-  double v[1] = {0.0};
-  for (int i = blockIdx.x * kRedBlock + threadIdx.x; i < n; i += gridDim.x * kRedBlock)
-    v[0] += (double)r[i] * (double)z[i];
+  double v[1] = {slice_dot(n, r, z)};
   double out[1];
   if (grid_reduce<1>(v, partials, counter, out)) {
     scal[S_RZNEW] = out[0];
