@@ -369,7 +369,8 @@ def extras(fe, I, h, dev, stream, flush):
     p3["apply_f32"]["frac_of_fp32_issue_rate"] = p3["apply_f32"]["element_T_ops_per_s"] / FP32_PEAK_TOPS
     f4 = torch.from_numpy(I.sin_product_rhs(h4.dof_coordinates())).to(dev)
     u4 = torch.empty_like(f4)
-    for name, prec in (("solve_f64", fe.FE_PREC_F64), ("solve_mixed_f32", fe.FE_PREC_MIXED_F32)):
+    for name, prec in (("solve_f64", fe.FE_PREC_F64), ("solve_mixed_f32", fe.FE_PREC_MIXED_F32),
+                       ("solve_mixed_bf16_tensor_core", fe.FE_PREC_MIXED_BF16)):
         with torch.cuda.stream(stream):
             h4.solve(f4, u4, rtol=1e-8, precision=prec, stream=stream)
             ms = time_launches(lambda: h4.solve(f4, u4, rtol=1e-8, precision=prec, stream=stream), stream, 3, flush)
@@ -823,6 +824,11 @@ def summary(line):
         if "ms" in mp.get("f64", {}) and "ms" in mp.get(name, {}):
             out[key] = mp["f64"]["ms"] / mp[name]["ms"]
             out[key.replace("speedup_vs_f64", "rel_l2_vs_fp64")] = mp[name].get("rel_l2_diff_vs_fp64_gpu_solution")
+    p3 = ex.get("p3_32cubed", {})
+    for name, key in (("solve_mixed_f32", "p3_mixed_f32_speedup_vs_f64"),
+                      ("solve_mixed_bf16_tensor_core", "p3_mixed_bf16_speedup_vs_f64")):
+        if "ms" in p3.get("solve_f64", {}) and "ms" in p3.get(name, {}):
+            out[key] = p3["solve_f64"]["ms"] / p3[name]["ms"]
     cb = line.get("cpu_baseline", {})
     if "value" in cb:
         out["oracle_dofs_per_s"] = cb["value"]
