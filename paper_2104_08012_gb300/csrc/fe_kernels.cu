@@ -1143,6 +1143,13 @@ void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accu
   LAUNCH_CHECK();
 }
 
+// Coarse levels below this many dofs restrict with 32 warps per 32 coarse
+// points instead of 8: with fewer blocks than SMs there, a P2 vertex's 125
+// entries in chains of 16 per thread left them latency-bound (P2 16^3 -> 8^3,
+// 4,913 coarse dofs: 16.5 -> 9.1 us).  At 35,937 coarse dofs (32^3 -> 16^3)
+// the 1024-thread blocks were slower (14.0 -> 18.5 us).
+constexpr int kRestrictWideBelow = 1 << 14;
+
 template <typename T>
 void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, bool zero_bd, cudaStream_t s) {
   const Level& F = h->L[lf];
@@ -1152,6 +1159,10 @@ void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T*
     k_restrict<1, T, 4><<<ceil_div(Cc.n, 32), 32 * 4, 0, s>>>(F.num.m, Cc.num, Cc.n, t.res_margin, t.res_start,
                                                               F.rtab, tt_weights<T>(t.res_w, t.res_wf), bf,
                                                               yf, rc, zero_bd);
+  else if (h->deg == 2 && Cc.n < kRestrictWideBelow)
+    k_restrict<2, T, 32><<<ceil_div(Cc.n, 32), 32 * 32, 0, s>>>(F.num.m, Cc.num, Cc.n, t.res_margin, t.res_start,
+                                                                F.rtab, tt_weights<T>(t.res_w, t.res_wf), bf,
+                                                                yf, rc, zero_bd);
   else if (h->deg == 2)
     k_restrict<2, T, 8><<<ceil_div(Cc.n, 32), 32 * 8, 0, s>>>(F.num.m, Cc.num, Cc.n, t.res_margin, t.res_start,
                                                               F.rtab, tt_weights<T>(t.res_w, t.res_wf), bf,
