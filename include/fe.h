@@ -79,7 +79,9 @@ extern "C" {
 /* ---- arithmetic of FP64 operator applications (fe_set_f64_mode) ---- */
 #define FE_F64_NATIVE 0        /* FP64 FMA on the FP64 pipe */
 #define FE_F64_DOUBLE_FLOAT 1       /* float-pair (hi + lo, ~48-bit) arithmetic on the FP32 pipes, FP64 in and
-                                       out, with the faster layout per degree (P1: per cube, P2: per tet) */
+                                       out, with the faster layout per degree (P1: per cube, P2: per tet); on
+                                       Kuhn tets (G = c M) the P2 element is c times one integer matrix, applied
+                                       to exact fixed-point FP32 limbs of the float-pair products c x */
 #define FE_F64_DOUBLE_FLOAT_TET 2   /* the same arithmetic, one thread per tet (persistent, prefetching) */
 #define FE_F64_DOUBLE_FLOAT_CUBE 3  /* the same arithmetic, one thread per cube (27/8 dofs split and scattered once) */
 #define FE_F64_DOUBLE_FLOAT_PAIR 4  /* P2: the same arithmetic, two tets per thread in packed FP32x2 instructions */
@@ -224,10 +226,11 @@ int fe_apply_operator(const fe_hierarchy* h, int level, const void* x, void* y, 
 
 /* Choose how FP64 operator applications (dtype FE_F64, the FP64 solver and
  * V-cycle) compute the element contraction: FE_F64_NATIVE (FP64 FMAs) or
- * FE_F64_DOUBLE_FLOAT (default: the same formula in float-pair arithmetic with
- * error-free transformations, about 48 significant bits, several times faster
- * on GB300 whose FP64 pipe issues 2 FMAs/clk/SM).  Dofs, results and every
- * other step stay FP64. */
+ * FE_F64_DOUBLE_FLOAT (default: the same operator on the FP32 pipes, in
+ * float-pair arithmetic with error-free transformations or, for P2 on Kuhn
+ * tets, exact fixed-point limbs; about 47 significant bits, several times
+ * faster on GB300 whose FP64 pipe issues 2 FMAs/clk/SM).  Dofs, results and
+ * every other step stay FP64. */
 int fe_set_f64_mode(fe_hierarchy* h, int mode);
 
 /* ---- preconditioner of the Chebyshev level smoother (fe_set_smoother) ---- */
