@@ -10,6 +10,7 @@
 #include <utility>
 
 #include "fe_internal.cuh"
+#include "fe_kuhn.h"
 
 namespace fe_df {
 
@@ -229,49 +230,10 @@ __device__ __forceinline__ void element_df_m(const DF (&u)[DEG == 1 ? 4 : 10], D
 }
 
 // ------------------------------------ P2 Kuhn tet by fixed-point limbs ---
-// Every Kuhn tet has G = c M, so its P2 element matrix (Eq. 4 with
-// phi_i, phi_j quadratic) is c K120 for one integer matrix:
-//   K120_ij = 120 int_ref grad phi_i^T M grad phi_j,
-// with grad phi_v = (4 lambda_v - 1) g_v, grad phi_ab = 4 (lambda_a g_b +
-// lambda_b g_a), g_a = grad lambda_a (constant) and the reference integrals
-// 120 int lambda_a lambda_b = 1 + delta_ab, 120 int lambda_a = 5, 120 vol = 20.
-// m_ab = g_a^T M g_b (g_0 = -(1, 1, 1), g_k = e_k).
-__host__ __device__ constexpr int kuhn_m(int a, int b) {
-  int s = 0;
-  for (int k = 0; k < 3; ++k)
-    for (int l = 0; l < 3; ++l) {
-      const int mkl = k == l ? (k == 2 ? 1 : 2) : (k + l == 1 || k + l == 3 ? -1 : 0);
-      s += (a == 0 ? -1 : (a - 1 == k ? 1 : 0)) * mkl * (b == 0 ? -1 : (b - 1 == l ? 1 : 0));
-    }
-  return s;
-}
-__host__ __device__ constexpr int lam2(int a, int b) { return a == b ? 2 : 1; }
-__host__ __device__ constexpr int kuhn_p2_k120(int i, int j) {
-  return i < 4 && j < 4 ? kuhn_m(i, j) * (16 * lam2(i, j) - 20)
-         : i >= 4 && j >= 4
-             ? 16 * (lam2(edge_a(i), edge_a(j)) * kuhn_m(edge_b(i), edge_b(j)) +
-                     lam2(edge_a(i), edge_b(j)) * kuhn_m(edge_b(i), edge_a(j)) +
-                     lam2(edge_b(i), edge_a(j)) * kuhn_m(edge_a(i), edge_b(j)) +
-                     lam2(edge_b(i), edge_b(j)) * kuhn_m(edge_a(i), edge_a(j)))
-         : i >= 4 ? kuhn_p2_k120(j, i)
-                  : 4 * (kuhn_m(i, edge_b(j)) * (4 * lam2(i, edge_a(j)) - 5) +
-                         kuhn_m(i, edge_a(j)) * (4 * lam2(i, edge_b(j)) - 5));
-}
-// K120 = 4 K; the limb sums below rely on every row of |K| summing to at most 62.
-__host__ __device__ constexpr int kuhn_p2_k(int i, int j) { return kuhn_p2_k120(i, j) / 4; }
-__host__ __device__ constexpr bool kuhn_p2_k_ok() {
-  for (int i = 0; i < 10; ++i) {
-    int row = 0, absrow = 0;
-    for (int j = 0; j < 10; ++j) {
-      if (kuhn_p2_k120(i, j) % 4 != 0 || kuhn_p2_k120(i, j) != kuhn_p2_k120(j, i)) return false;
-      row += kuhn_p2_k(i, j);
-      absrow += kuhn_p2_k(i, j) < 0 ? -kuhn_p2_k(i, j) : kuhn_p2_k(i, j);
-    }
-    if (row != 0 || absrow > 62) return false;  // constants in the kernel: rows sum to 0
-  }
-  return kuhn_p2_k(0, 0) == 3 && kuhn_p2_k(5, 5) == 24;
-}
-static_assert(kuhn_p2_k_ok(), "P2 Kuhn stiffness: integer, symmetric, zero row sums, row abs sums <= 62");
+// The integer element matrix K of a P2 Kuhn tet (fe_kuhn.h) applied to exact
+// FP32 limbs of the float-pair products c x.
+static_assert(fe_kuhn::kuhn_p2_k_ok(), "P2 Kuhn stiffness: integer, symmetric, zero row sums, row abs sums <= 62");
+using fe_kuhn::kuhn_p2_k;
 
 // Fixed-point limb evaluation of y = K x' for x'_j = cs u_j (float pairs,
 // |x'_j| < 2): p2_kuhn_split forms the limbs, p2_kuhn_apply the products.  Each x'_j, held as the unnormalised product (p, e), is cut

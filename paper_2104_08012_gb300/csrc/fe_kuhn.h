@@ -1,0 +1,73 @@
+// The P2 element stiffness of a Kuhn tet as an integer matrix (host and
+// device code, no CUDA types, so that host tests compile it with g++).
+//
+// Every tet of the Kuhn split of UnitCubeMesh has J = h P U (P a permutation,
+// U the upper-triangular matrix of ones), hence G = |det J| J^-1 J^-T = h M
+// with M = U^-1 U^-T = [[2,-1,0],[-1,2,-1],[0,-1,1]] for every cell, and the P2
+// element matrix of the bilinear form (Section 2, Eq. 4, phi quadratic) is
+// kappa h / 120 times one integer matrix
+//   K120_ij = 120 int_ref grad phi_i^T M grad phi_j,
+// computed here from grad phi_v = (4 lambda_v - 1) g_v, grad phi_ab =
+// 4 (lambda_a g_b + lambda_b g_a) with g_a = grad lambda_a (constant:
+// g_0 = -(1, 1, 1), g_k = e_k) and the reference moments
+// 120 int lambda_a lambda_b = 1 + delta_ab, 120 int lambda_a = 5, 120 vol = 20.
+// Local dof order: vertices 0..3, then the edges (0,1), (0,2), (0,3), (1,2),
+// (1,3), (2,3) as dofs 4..9.
+#pragma once
+
+#ifdef __CUDACC__
+#define FE_KUHN_HD __host__ __device__
+#else
+#define FE_KUHN_HD
+#endif
+
+namespace fe_kuhn {
+
+// end points of the edge dof j (4..9)
+FE_KUHN_HD constexpr int edge_first(int j) { return j <= 6 ? 0 : (j <= 8 ? 1 : 2); }
+FE_KUHN_HD constexpr int edge_second(int j) { return j <= 6 ? j - 3 : (j <= 8 ? j - 5 : 3); }
+
+// m_ab = g_a^T M g_b
+FE_KUHN_HD constexpr int kuhn_m(int a, int b) {
+  int s = 0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      const int mkl = k == l ? (k == 2 ? 1 : 2) : (k + l == 1 || k + l == 3 ? -1 : 0);
+      s += (a == 0 ? -1 : (a - 1 == k ? 1 : 0)) * mkl * (b == 0 ? -1 : (b - 1 == l ? 1 : 0));
+    }
+  return s;
+}
+
+// 120 int lambda_a lambda_b over the reference tet
+FE_KUHN_HD constexpr int lam2(int a, int b) { return a == b ? 2 : 1; }
+
+FE_KUHN_HD constexpr int kuhn_p2_k120(int i, int j) {
+  return i < 4 && j < 4 ? kuhn_m(i, j) * (16 * lam2(i, j) - 20)
+         : i >= 4 && j >= 4
+             ? 16 * (lam2(edge_first(i), edge_first(j)) * kuhn_m(edge_second(i), edge_second(j)) +
+                     lam2(edge_first(i), edge_second(j)) * kuhn_m(edge_second(i), edge_first(j)) +
+                     lam2(edge_second(i), edge_first(j)) * kuhn_m(edge_first(i), edge_second(j)) +
+                     lam2(edge_second(i), edge_second(j)) * kuhn_m(edge_first(i), edge_first(j)))
+         : i >= 4 ? kuhn_p2_k120(j, i)
+                  : 4 * (kuhn_m(i, edge_second(j)) * (4 * lam2(i, edge_first(j)) - 5) +
+                         kuhn_m(i, edge_first(j)) * (4 * lam2(i, edge_second(j)) - 5));
+}
+
+// K120 = 4 K; the limb sums of the operator kernel rely on every row of |K|
+// summing to at most 62.
+FE_KUHN_HD constexpr int kuhn_p2_k(int i, int j) { return kuhn_p2_k120(i, j) / 4; }
+
+FE_KUHN_HD constexpr bool kuhn_p2_k_ok() {
+  for (int i = 0; i < 10; ++i) {
+    int row = 0, absrow = 0;
+    for (int j = 0; j < 10; ++j) {
+      if (kuhn_p2_k120(i, j) % 4 != 0 || kuhn_p2_k120(i, j) != kuhn_p2_k120(j, i)) return false;
+      row += kuhn_p2_k(i, j);
+      absrow += kuhn_p2_k(i, j) < 0 ? -kuhn_p2_k(i, j) : kuhn_p2_k(i, j);
+    }
+    if (row != 0 || absrow > 62) return false;  // constants in the kernel: rows sum to 0
+  }
+  return true;
+}
+
+}  // namespace fe_kuhn

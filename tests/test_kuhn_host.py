@@ -1,0 +1,49 @@
+"""The integer P2 stiffness of a Kuhn tet (fe_kuhn.h, compiled for the host) against the oracle, CPU only.
+
+The fixed-point limb operator applies every P2 element of UnitCubeMesh as (kappa h / 120) K120 with one integer
+matrix K120 derived in fe_kuhn.h from the basis gradients and the metric M shared by all Kuhn tets.  The oracle
+assembles each tet's matrix by quadrature from its own Jacobian, so agreement on all six tet types and at two mesh
+sizes pins both the integer matrix and the claim that every Kuhn tet has the same metric.  The properties the
+kernel's exactness argument needs (symmetry, divisibility by 4, zero row sums, |K120/4| row sums <= 62) are pinned
+here directly as well.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import fe_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def k120(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = str(tmp_path_factory.mktemp("kuhn") / "kuhn_host")
+    subprocess.check_call([cxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2104_08012_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "host", "kuhn_host.cpp"), "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    return np.array([[int(v) for v in line.split()] for line in out.splitlines()], dtype=np.int64)
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_k120_is_every_kuhn_element_matrix(k120, N):
+    mesh = O.Mesh(N)
+    A = O.element_stiffness(mesh, 2)  # (cells, 10, 10), kappa = 1
+    h = 1.0 / N
+    for c in range(6):  # the six tet types of the first cube
+        assert np.allclose(A[c] * 120.0 / h, k120, rtol=0, atol=1e-10), f"tet type {c}"
+
+
+def test_k120_properties(k120):
+    assert np.array_equal(k120, k120.T)
+    assert np.all(k120 % 4 == 0)
+    K = k120 // 4
+    assert np.all(K.sum(axis=1) == 0)
+    assert np.abs(K).sum(axis=1).max() == 62
+    assert np.count_nonzero(K) == 82
