@@ -44,7 +44,7 @@ BYTES_PER_DOF_P2 = {"f64": 49.0, "f32": 41.0}
 # dram__bytes_write.sum from one ncu capture of the finest level's applications inside a V-cycle of the
 # P2 64^3 hierarchy, the kernel the CG iterations run; mean of 2 launches), keyed by FP64 mode; None where
 # the kernel changed after the last capture.
-TRAFFIC = {0: None, 1: 116.9e6, 2: None}
+TRAFFIC = {0: None, 1: 116.6e6, 2: None}
 # Arithmetic of one P2 element application (c, d, S, four G-products, transpose),
 # per tet: 151 flops in the FP64 formula with a general G (an FMA counts 2).  With
 # the geometric matrix shared by every Kuhn tet (G = c M) the element matrix is
@@ -758,8 +758,8 @@ def run_ours(args, rank, world, local_rank, oracle=None):
     byt = BYTES_PER_DOF_P2["f64"] * n
     achieved_gbs = byt / (apply_ms * 1e-3) / 1e9
     if F64_MODE == fe.FE_F64_DOUBLE_FLOAT:
-        kname = ("k_apply_df<2> (FP64 operator on the FP32 pipes: exact fixed-point limbs of c x against the integer "
-                 "Kuhn-tet stiffness, persistent, one tet per thread)")
+        kname = ("k_apply_lp (FP64 operator on the FP32 pipes: exact fixed-point limbs of c x against the integer "
+                 "Kuhn-tet stiffness; persistent, one tet per thread, map rows staged in shared memory by cp.async)")
         ops, opeak, ounit = OPS_PER_CELL_P2_DF * C, FP32_PEAK_TOPS, "T FP32 op/s"
         oderiv = ("436 FP32 operations per tet of the limb element x cells / launch duration, against the "
                   "nominal FP32 issue rate 152 SMs x 128 lanes x 1 op/clk x 2.07 GHz = 40.3 T op/s (no measured FP32 "
