@@ -644,21 +644,6 @@ void launch_mass_df(const Level& L, const double* x, double* y, cudaStream_t s) 
   LAUNCH_CHECK();
 }
 
-// Resident blocks per SM of a kernel (cached per kernel).
-template <typename K>
-static int resident_grid(K kernel, int block, int work_items) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    CUDA_CHECK(cudaGetDevice(&dev));
-    CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
-  int occ = 1;
-  CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0));
-  const int g = sms * (occ > 0 ? occ : 1);
-  const int need = ceil_div(work_items, block);
-  return need < g ? (need > 0 ? need : 1) : g;
-}
 
 template <bool FUSE>
 static void apply_cube_df(const Level& L, const double* x, double* y, const ChebFuse<double>& cf, cudaStream_t s) {

@@ -187,6 +187,23 @@ struct ChebFuse {
   int store_d;
 };
 
+// Blocks of a persistent grid: resident blocks per SM of the kernel times the
+// SM count, or fewer when there are fewer work items.
+template <typename K>
+inline int resident_grid(K kernel, int block, int work_items) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  int occ = 1;
+  CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0));
+  const int g = sms * (occ > 0 ? occ : 1);
+  const int need = (int)(((long long)work_items + block - 1) / block);
+  return need < g ? (need > 0 ? need : 1) : g;
+}
+
 // ---------------------------------------------------------- level data ---
 struct Level {
   int N = 0, deg = 0, nd = 0;

@@ -352,6 +352,100 @@ __global__ void __launch_bounds__(kCubeBlock, UNI ? kCubeMinBlocksUni : 4) k_app
   }
 }
 
+// The uniform-geometry FP32 cube apply as a persistent loop over cubes: each
+// thread's cube map rows two cubes ahead are copied into shared memory by
+// cp.async ([buffer][node][thread], three buffers), and the next cube's dofs
+// and c values are gathered into registers while the current cube is
+// contracted, so the dependent map -> x gathers no longer stall every cube.
+// 128 threads, 4 resident blocks per SM (128 registers, 41 KB of staged map per
+// block): P2 applications measured 0.1305 / 0.0269 ms at 128^3 / 64^3, against
+// 0.1513 / 0.0287 ms at 5 blocks (96 registers, spills) and 0.131-0.134 /
+// 0.0297 ms for the one-cube-per-thread kernel without staging (k_apply_cube).
+constexpr int kCubeLpBlock = 128;
+constexpr int kCubeLpMinBlocks = 4;
+__device__ __forceinline__ void cp_async4_k(int* smem, const int* gmem) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_k() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_k() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int DEG>
+__global__ void __launch_bounds__(kCubeLpBlock, DEG == 1 ? 8 : kCubeLpMinBlocks)
+    k_apply_cube_lp32(int Q, int Qs, int Cs, const int* __restrict__ cmap, const float* __restrict__ c32,
+                      const float* __restrict__ x, float* __restrict__ y, int nb, const int* __restrict__ bnd) {
+  constexpr int NL = DEG == 1 ? 8 : 27, ND = DEG == 1 ? 4 : 10;
+  __shared__ int smap[3][NL][kCubeLpBlock];
+  const int tx = threadIdx.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (int i = tid; i < nb; i += stride) y[bnd[i]] = x[bnd[i]];  // Dirichlet rows: identity
+  int q = tid;
+  if (q >= Q) return;
+  auto copy_map = [&](int cube, int buf) {
+    if (cube < Q) {
+#pragma unroll
+      for (int l = 0; l < NL; ++l) cp_async4_k(&smap[buf][l][tx], cmap + (size_t)l * Qs + cube);
+    }
+    cp_async_commit_k();
+  };
+  auto gather = [&](int cube, int buf, float (&xv)[NL], float2 (&cv)[3]) {
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const int i = smap[buf][l][tx];
+      xv[l] = i >= 0 ? __ldg(x + i) : 0.0f;
+    }
+    // the cube's six tets are cells 6q .. 6q+5: three 8-byte loads of c
+#pragma unroll
+    for (int h = 0; h < 3; ++h) cv[h] = __ldg(reinterpret_cast<const float2*>(c32 + 6 * (size_t)cube) + h);
+  };
+  copy_map(q, 0);
+  copy_map(q + stride, 1);
+  cp_async_wait_all_k();
+  float xv[NL];
+  float2 cv[3];
+  gather(q, 0, xv, cv);
+  int b = 0;
+  while (true) {
+    const int qn = q + stride;
+    const bool more = qn < Q;
+    const int bn = b == 2 ? 0 : b + 1, bnn = bn == 2 ? 0 : bn + 1;
+    float xn[NL];
+    float2 cn[3];
+    if (more) {
+      cp_async_wait_all_k();  // the next cube's map rows (copied one iteration ago)
+      gather(qn, bn, xn, cn);
+      copy_map(qn + stride, bnn);
+    }
+    float acc[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) acc[l] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      float u[ND], g[6], o[ND];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) u[j] = xv[cube_local(DEG, t, j)];
+      const float c = (t & 1) ? cv[t >> 1].y : cv[t >> 1].x;
+      g[0] = 2.0f * c, g[1] = -c, g[2] = 0.0f, g[3] = 2.0f * c, g[4] = -c, g[5] = c;
+      element_apply<DEG, float>(u, g, o);
+#pragma unroll
+      for (int j = 0; j < ND; ++j) acc[cube_local(DEG, t, j)] += o[j];
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const int i = smap[b][l][tx];
+      if (i >= 0) atomicAdd(y + i, acc[l]);
+    }
+    if (!more) break;
+    q = qn;
+    b = bn;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) xv[l] = xn[l];
+#pragma unroll
+    for (int h = 0; h < 3; ++h) cv[h] = cn[h];
+  }
+  cp_async_wait_all_k();
+}
+
 // Contributors per interior dof: cells (nd map rows) or cubes (cube map rows).
 __global__ void k_valence(int C, int Cs, int rows, const int* __restrict__ map, unsigned* __restrict__ v) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1026,7 +1120,12 @@ static void apply_cube32(const Level& L, const float* x, float* y, const ChebFus
   else if (L.deg == 1)
     k_apply_cube<1, FUSE, false><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd,
                                                              cf);
-  else if (L.uniform)
+  else if (L.uniform && !FUSE) {
+    static int g2 = 0;
+    if (!g2) g2 = resident_grid(k_apply_cube_lp32<2>, kCubeLpBlock, 1 << 30);
+    k_apply_cube_lp32<2><<<std::min(g2, ceil_div(std::max(L.Q, L.nb), kCubeLpBlock)), kCubeLpBlock, 0, s>>>(
+        L.Q, L.Qs, L.Cs, L.cmap, L.c32, x, y, L.nb, L.bnd);
+  } else if (L.uniform)
     k_apply_cube<2, FUSE, true><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.c32, x, y, L.nb, L.bnd, cf);
   else
     k_apply_cube<2, FUSE, false><<<grid, kCubeBlock, 0, s>>>(L.Q, L.Qs, L.Cs, Qpad, L.cmap, L.geo32, x, y, L.nb, L.bnd,
