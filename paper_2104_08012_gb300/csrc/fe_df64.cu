@@ -30,9 +30,9 @@ namespace {
 using namespace fe_df;
 constexpr int kBlock = 256;
 constexpr int kBlockP3 = 128;
-// Block shape of the pre-split, one-value-per-cell operator (the FP64
-// solve's hot kernel): 128 threads, compiled for 5 resident blocks (96
-// registers, no spills).  With the fixed-point limb element, full P2 64^3
+// Block shape of the pre-split, one-value-per-cell variants of k_apply_df
+// (the P2 solver path has moved to k_apply_lp): 128 threads, compiled for 5
+// resident blocks (96 registers, no spills).  With the fixed-point limb element, full P2 64^3
 // solves measured 6.46 / 6.63 / 6.60 ms for (threads, blocks) = (128, 5) /
 // (128, 4) / (256, 2); gathering the next tet's dofs after the limb split
 // instead of at the top of the iteration (so its map rows have arrived)
@@ -260,12 +260,6 @@ __global__ void __launch_bounds__(UNI && PRE ? kBlockDfU : kBlock, UNI && PRE ? 
 // 6.40 ms for the same element with register-held map rows (k_apply_df).
 constexpr int kBlockLp = 128;
 constexpr int kMinBlocksLp = 6;
-__device__ __forceinline__ void cp_async4(int* smem, const int* gmem) {
-  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kBlockLp, kMinBlocksLp)
     k_apply_lp(int C, int Cs, const int* __restrict__ map, const float2* __restrict__ cdf,

@@ -187,6 +187,15 @@ struct ChebFuse {
   int store_d;
 };
 
+// Asynchronous 4-byte global -> shared copies (cp.async, completed by
+// cp_async_wait_all in the issuing thread; no other thread reads the slots).
+__device__ __forceinline__ void cp_async4(int* smem, const int* gmem) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Blocks of a persistent grid: resident blocks per SM of the kernel times the
 // SM count, or fewer when there are fewer work items.
 template <typename K>

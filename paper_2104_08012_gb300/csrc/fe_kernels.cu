@@ -363,12 +363,6 @@ __global__ void __launch_bounds__(kCubeBlock, UNI ? kCubeMinBlocksUni : 4) k_app
 // 0.0297 ms for the one-cube-per-thread kernel without staging (k_apply_cube).
 constexpr int kCubeLpBlock = 128;
 constexpr int kCubeLpMinBlocks = 4;
-__device__ __forceinline__ void cp_async4_k(int* smem, const int* gmem) {
-  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_k() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all_k() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int DEG>
 __global__ void __launch_bounds__(kCubeLpBlock, DEG == 1 ? 8 : kCubeLpMinBlocks)
@@ -384,9 +378,9 @@ __global__ void __launch_bounds__(kCubeLpBlock, DEG == 1 ? 8 : kCubeLpMinBlocks)
   auto copy_map = [&](int cube, int buf) {
     if (cube < Q) {
 #pragma unroll
-      for (int l = 0; l < NL; ++l) cp_async4_k(&smap[buf][l][tx], cmap + (size_t)l * Qs + cube);
+      for (int l = 0; l < NL; ++l) cp_async4(&smap[buf][l][tx], cmap + (size_t)l * Qs + cube);
     }
-    cp_async_commit_k();
+    cp_async_commit();
   };
   auto gather = [&](int cube, int buf, float (&xv)[NL], float2 (&cv)[3]) {
 #pragma unroll
@@ -400,7 +394,7 @@ __global__ void __launch_bounds__(kCubeLpBlock, DEG == 1 ? 8 : kCubeLpMinBlocks)
   };
   copy_map(q, 0);
   copy_map(q + stride, 1);
-  cp_async_wait_all_k();
+  cp_async_wait_all();
   float xv[NL];
   float2 cv[3];
   gather(q, 0, xv, cv);
@@ -412,7 +406,7 @@ __global__ void __launch_bounds__(kCubeLpBlock, DEG == 1 ? 8 : kCubeLpMinBlocks)
     float xn[NL];
     float2 cn[3];
     if (more) {
-      cp_async_wait_all_k();  // the next cube's map rows (copied one iteration ago)
+      cp_async_wait_all();  // the next cube's map rows (copied one iteration ago)
       gather(qn, bn, xn, cn);
       copy_map(qn + stride, bnn);
     }
@@ -443,7 +437,7 @@ __global__ void __launch_bounds__(kCubeLpBlock, DEG == 1 ? 8 : kCubeLpMinBlocks)
 #pragma unroll
     for (int h = 0; h < 3; ++h) cv[h] = cn[h];
   }
-  cp_async_wait_all_k();
+  cp_async_wait_all();
 }
 
 // Contributors per interior dof: cells (nd map rows) or cubes (cube map rows).
