@@ -8,6 +8,7 @@
 #include <type_traits>
 
 #include "fe_df.cuh"
+#include "fe_kuhn.h"
 #include "fe_internal.cuh"
 #include "fe_p3.cuh"
 #include "fe_reftables.h"
@@ -723,6 +724,106 @@ __global__ void k_prolong(Numbering nf, int n_f, const int* __restrict__ start, 
     if (xs) xs[i] = fe_df::split_pair(v);  // the operator's next input, ready as a float pair
 }
 
+// P2 prolongation per coarse cube and fine row: a thread takes coarse cube
+// (cx, cy, cz) and one row (OY, OZ) of the cube's fine points (4 per row, 5 in
+// the last cube along x; rows OY = 4 or OZ = 4 only in the last cube along y
+// or z), loads the coarse values the row needs once, and forms each fine value
+// with the compile-time weights of fe_kuhn.h (pro_w8: about 3.8 terms per
+// point).  The table-driven kernel above spent some 250 instructions per fine
+// point on recovering lattice coordinates and classes from the dof index and
+// on loading stencil entries; here the indices are affine in the cube
+// coordinates (the P2 numbering is class-major by lattice parity) and the
+// weights are immediates.  Blocks of 32 x 4 cubes share one row, so the row's
+// template instance is chosen by a uniform branch.
+// Compile-time weights (template constants, so that nothing of pro_w8 is left
+// to run on the device) and the coarse nodes a row needs.
+template <int OX, int OY, int OZ, int N>
+struct ProW8 {
+  static constexpr int v = fe_kuhn::pro_w8(OX, OY, OZ, N % 3, (N / 3) % 3, N / 9);
+};
+template <int OY, int OZ, int N>
+struct ProNeed {
+  static constexpr bool v = ProW8<0, OY, OZ, N>::v != 0 || ProW8<1, OY, OZ, N>::v != 0 ||
+                            ProW8<2, OY, OZ, N>::v != 0 || ProW8<3, OY, OZ, N>::v != 0 || ProW8<4, OY, OZ, N>::v != 0;
+};
+
+__host__ __device__ constexpr int p2_class(int px, int py, int pz) {
+  return (px | (py << 1) | (pz << 2)) == 3 ? 4 : ((px | (py << 1) | (pz << 2)) == 4 ? 3 : (px | (py << 1) | (pz << 2)));
+}
+
+template <int OY, int OZ, int N, typename T>
+__device__ __forceinline__ void pro_load(const Numbering& nc, int cx, int cy, int cz, const T* __restrict__ xc,
+                                         T (&v)[27]) {
+  if constexpr (ProNeed<OY, OZ, N>::v) {
+    constexpr int a = N % 3, b = (N / 3) % 3, d = N / 9, c = p2_class(a & 1, b & 1, d & 1);
+    v[N] = __ldg(xc + nc.off[c] + (cx + (a >> 1)) + nc.sx[c] * ((cy + (b >> 1)) + nc.sy[c] * (cz + (d >> 1))));
+  }
+}
+template <int OX, int OY, int OZ, int N, typename T>
+__device__ __forceinline__ void pro_term(const T (&v)[27], T& s) {
+  if constexpr (ProW8<OX, OY, OZ, N>::v != 0) s += T(ProW8<OX, OY, OZ, N>::v * 0.125) * v[N];
+}
+template <int OX, int OY, int OZ, typename T, int... N>
+__device__ __forceinline__ T pro_sum(const T (&v)[27], std::integer_sequence<int, N...>) {
+  T s = T(0);
+  (pro_term<OX, OY, OZ, N>(v, s), ...);
+  return s;
+}
+template <int OX, int OY, int OZ, typename T>
+__device__ __forceinline__ void pro_point(const T (&v)[27], int base0, int base1, T* __restrict__ xf, int accumulate,
+                                          float2* __restrict__ xs) {
+  const T s = pro_sum<OX, OY, OZ, T>(v, std::make_integer_sequence<int, 27>{});
+  const int i = (OX & 1 ? base1 : base0) + (OX >> 1);
+  const T r = accumulate ? xf[i] + s : s;
+  xf[i] = r;
+  if constexpr (sizeof(T) == 8)
+    if (xs) xs[i] = fe_df::split_pair(r);  // the operator's next input, ready as a float pair
+}
+template <int OY, int OZ, typename T, int... N>
+__device__ __forceinline__ void pro_loads(const Numbering& nc, int cx, int cy, int cz, const T* __restrict__ xc,
+                                          T (&v)[27], std::integer_sequence<int, N...>) {
+  (pro_load<OY, OZ, N>(nc, cx, cy, cz, xc, v), ...);
+}
+
+template <int OY, int OZ, typename T>
+__device__ __forceinline__ void pro_row(const Numbering& nc, const Numbering& nf, int Nc, int cx, int cy, int cz,
+                                        const T* __restrict__ xc, T* __restrict__ xf, int accumulate,
+                                        float2* __restrict__ xs) {
+  T v[27];
+  pro_loads<OY, OZ>(nc, cx, cy, cz, xc, v, std::make_integer_sequence<int, 27>{});
+  // fine dofs of the row: parity class by ox & 1, the y and z parts fixed
+  const int fy = 2 * cy + (OY >> 1), fz = 2 * cz + (OZ >> 1);
+  constexpr int c0 = p2_class(0, OY & 1, OZ & 1), c1 = p2_class(1, OY & 1, OZ & 1);
+  const int base0 = nf.off[c0] + 2 * cx + nf.sx[c0] * (fy + nf.sy[c0] * fz);
+  const int base1 = nf.off[c1] + 2 * cx + nf.sx[c1] * (fy + nf.sy[c1] * fz);
+  pro_point<0, OY, OZ>(v, base0, base1, xf, accumulate, xs);
+  pro_point<1, OY, OZ>(v, base0, base1, xf, accumulate, xs);
+  pro_point<2, OY, OZ>(v, base0, base1, xf, accumulate, xs);
+  pro_point<3, OY, OZ>(v, base0, base1, xf, accumulate, xs);
+  if (cx == Nc - 1) pro_point<4, OY, OZ>(v, base0, base1, xf, accumulate, xs);
+}
+
+template <int R, typename T>
+__device__ __forceinline__ void pro_row_dispatch(int row, const Numbering& nc, const Numbering& nf, int Nc, int cx,
+                                                 int cy, int cz, const T* xc, T* xf, int accumulate, float2* xs) {
+  if (row == R)
+    pro_row<R % 5, R / 5, T>(nc, nf, Nc, cx, cy, cz, xc, xf, accumulate, xs);
+  else if constexpr (R + 1 < 25)
+    pro_row_dispatch<R + 1, T>(row, nc, nf, Nc, cx, cy, cz, xc, xf, accumulate, xs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_prolong_cube(Numbering nc, Numbering nf, int Nc, int nby,
+                                                      const T* __restrict__ xc, T* __restrict__ xf, int accumulate,
+                                                      float2* __restrict__ xs) {
+  const int row = blockIdx.y / nby;  // uniform per block
+  const int cx = blockIdx.x * 32 + threadIdx.x, cy = (blockIdx.y - row * nby) * 4 + threadIdx.y, cz = blockIdx.z;
+  if (cx >= Nc || cy >= Nc) return;
+  const int oy = row % 5, oz = row / 5;
+  if ((oy == 4 && cy != Nc - 1) || (oz == 4 && cz != Nc - 1)) return;
+  pro_row_dispatch<0, T>(row, nc, nf, Nc, cx, cy, cz, xc, xf, accumulate, xs);
+}
+
 // Restriction = exact transpose: coarse point Lc gathers fine points
 // 2 Lc + o for the stencil entries of its class (Lc mod k per axis); the index
 // table gives the fine dof as t.x + KX X + t.y Y + t.z Z (KX = 1 for P2, whose
@@ -1228,6 +1329,17 @@ template <typename T>
 void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s, float2* xs) {
   const Level& F = h->L[lf];
   const TransferTables& t = h->tt;
+  // the per-cube kernel's blocks span 32 cubes along x: on coarse levels with
+  // fewer cubes the table-driven kernel keeps every lane busy (P2 16^3 -> 32^3:
+  // 10.5 against 12.5 us; 32^3 -> 64^3: 48.8 against 31.1 us)
+  if (h->deg == 2 && h->L[lf - 1].N >= 32) {
+    const Level& Cl = h->L[lf - 1];
+    const int Nc = Cl.N, nby = ceil_div(Nc, 4);
+    const dim3 grid(ceil_div(Nc, 32), nby * 25, Nc), block(32, 4);
+    k_prolong_cube<T><<<grid, block, 0, s>>>(Cl.num, F.num, Nc, nby, xc, xf, accumulate, xs);
+    LAUNCH_CHECK();
+    return;
+  }
   by_degree(h->deg, [&](auto D) {
     k_prolong<D.value, T><<<ceil_div(F.n, kBlock), kBlock, 0, s>>>(F.num, F.n, t.pro_start, F.ptab,
                                                                   tt_weights<T>(t.pro_w, t.pro_wf), xc, xf, accumulate,

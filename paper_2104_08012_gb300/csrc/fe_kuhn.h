@@ -1,5 +1,7 @@
-// The P2 element stiffness of a Kuhn tet as an integer matrix (host and
-// device code, no CUDA types, so that host tests compile it with g++).
+// Integer tables of P2 on Kuhn tets, computed at compile time (host and
+// device code, no CUDA types, so that host tests compile it with g++): the
+// element stiffness of a Kuhn tet and the prolongation weights between nested
+// Kuhn meshes.
 //
 // Every tet of the Kuhn split of UnitCubeMesh has J = h P U (P a permutation,
 // U the upper-triangular matrix of ones), hence G = |det J| J^-1 J^-T = h M
@@ -68,6 +70,40 @@ FE_KUHN_HD constexpr bool kuhn_p2_k_ok() {
     if (row != 0 || absrow > 62) return false;  // constants in the kernel: rows sum to 0
   }
   return true;
+}
+
+// P2 prolongation weights on nested Kuhn meshes, times 8 (integers): the
+// coarse P2 function of a cube evaluated at the fine P2 node o / 4 of that
+// cube (o in [0, 4]^3, fine lattice units), as the sum over the basis
+// functions of the Kuhn tet containing the point: the tet follows the
+// descending order of the coordinates (ties resolved by axis order; the
+// basis functions of the shared face agree there), its barycentrics are
+// L / 4 with integer L, a vertex function is L (L - 2) / 8 and an edge
+// function 2 L_i L_j / 8.  (a, b, d) in [0, 2]^3 is the coarse node, in
+// coarse P2 lattice units from the cube's corner.
+FE_KUHN_HD constexpr int pro_w8(int ox, int oy, int oz, int a, int b, int d) {
+  const int s[3] = {ox, oy, oz};
+  int sg[3] = {0, 1, 2};
+  // stable descending sort of the three coordinates
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j + 1 < 3 - i; ++j)
+      if (s[sg[j + 1]] > s[sg[j]]) {
+        const int t = sg[j];
+        sg[j] = sg[j + 1];
+        sg[j + 1] = t;
+      }
+  const int L[4] = {4 - s[sg[0]], s[sg[0]] - s[sg[1]], s[sg[1]] - s[sg[2]], s[sg[2]]};
+  int v[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {1, 1, 1}};
+  v[1][sg[0]] = 1;
+  v[2][sg[0]] = 1;
+  v[2][sg[1]] = 1;
+  const int n[3] = {a, b, d};
+  for (int k = 0; k < 4; ++k)
+    if (n[0] == 2 * v[k][0] && n[1] == 2 * v[k][1] && n[2] == 2 * v[k][2]) return L[k] * (L[k] - 2);
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j)
+      if (n[0] == v[i][0] + v[j][0] && n[1] == v[i][1] + v[j][1] && n[2] == v[i][2] + v[j][2]) return 2 * L[i] * L[j];
+  return 0;
 }
 
 }  // namespace fe_kuhn

@@ -229,6 +229,28 @@ def test_prolong_restrict(fe, k, N0):
         assert_rowwise(host(rc0), ref, abs(P.T) @ np.abs(rf), 1e-14, "restrict (zero bd)")
 
 
+def test_prolong_p2_per_cube_kernel_full_size(fe):
+    """From 32^3 up the P2 prolongation runs per coarse cube with compile-time weights (k_prolong_cube); the level
+    pair 32^3 -> 64^3 of the benchmark hierarchy against the oracle's P row by row, with and without accumulation,
+    at the FP64 bound of test_prolong_restrict (4 m 2^-53 of |P| |x|, m = 10)."""
+    import types
+    with fe.Hierarchy(8, 3, 2) as h:
+        sc, sf = O.Space(O.Mesh(32), 2), O.Space(O.Mesh(64), 2)
+        c = types.SimpleNamespace(mesh=sc.mesh, space=sc, n=sc.n)
+        f = types.SimpleNamespace(mesh=sf.mesh, space=sf, n=sf.n)
+        P = O.prolongation(c, f)
+        xc = I.random_vector(c.n, 31)
+        x0 = I.random_vector(f.n, 32)
+        xf = torch.empty(f.n, dtype=torch.float64, device=DEV)
+        h.prolong(dt(xc), xf, 3)
+        xa = dt(x0)
+        h.prolong(dt(xc), xa, 3, accumulate=True)
+        torch.cuda.synchronize()
+        tol = 4 * 10 * 2.0 ** -53
+        assert_rowwise(host(xf), P @ xc, abs(P) @ np.abs(xc), tol, "prolong (per cube)")
+        assert_rowwise(host(xa), x0 + P @ xc, np.abs(x0) + abs(P) @ np.abs(xc), tol, "prolong (per cube, accumulate)")
+
+
 # ------------------------------------------------------------ smoother
 @pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("steps", [1, 2, 3])

@@ -5,7 +5,8 @@ matrix K120 derived in fe_kuhn.h from the basis gradients and the metric M share
 assembles each tet's matrix by quadrature from its own Jacobian, so agreement on all six tet types and at two mesh
 sizes pins both the integer matrix and the claim that every Kuhn tet has the same metric.  The properties the
 kernel's exactness argument needs (symmetry, divisibility by 4, zero row sums, |K120/4| row sums <= 62) are pinned
-here directly as well.
+here directly as well.  The compile-time P2 prolongation weights (pro_w8, times 8) are compared entry by entry with
+the host stencil tables of fe_stencils.h, which test_transfer_stencils_host.py pins against the oracle's P.
 """
 import os
 import shutil
@@ -47,3 +48,16 @@ def test_k120_properties(k120):
     assert np.all(K.sum(axis=1) == 0)
     assert np.abs(K).sum(axis=1).max() == 62
     assert np.count_nonzero(K) == 82
+
+
+def test_prolongation_weights_match_the_stencil_tables(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = str(tmp_path_factory.mktemp("kuhnpro") / "kuhn_pro_host")
+    subprocess.check_call([cxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2104_08012_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "host", "kuhn_pro_host.cpp"), "-o", exe])
+    bad, compared, maxsum = (int(v) for v in subprocess.run([exe], capture_output=True, text=True,
+                                                               check=True).stdout.split())
+    assert bad == 0 and compared == 64 * 27 + 61 * 27
+    assert maxsum == 16  # the largest sum of |8 w| over one fine point's stencil
