@@ -451,6 +451,7 @@ int launch_check_positive(const double* v, int n, int* dflag, cudaStream_t s);
 template <typename T>
 void launch_prolong(const fe_hierarchy* h, int lf, const T* xc, T* xf, bool accumulate, cudaStream_t s,
                     float2* xs = nullptr);
+// rc = P^T (bf - yf), or P^T bf when yf is null
 template <typename T>
 void launch_restrict(const fe_hierarchy* h, int lf, const T* bf, const T* yf, T* rc, bool zero_bd, cudaStream_t s);
 

@@ -229,10 +229,11 @@ def test_prolong_restrict(fe, k, N0):
         assert_rowwise(host(rc0), ref, abs(P.T) @ np.abs(rf), 1e-14, "restrict (zero bd)")
 
 
-def test_prolong_p2_per_cube_kernel_full_size(fe):
-    """From 32^3 up the P2 prolongation runs per coarse cube with compile-time weights (k_prolong_cube); the level
-    pair 32^3 -> 64^3 of the benchmark hierarchy against the oracle's P row by row, with and without accumulation,
-    at the FP64 bound of test_prolong_restrict (4 m 2^-53 of |P| |x|, m = 10)."""
+def test_transfers_p2_full_size(fe):
+    """On large P2 levels the prolongation runs per coarse cube with compile-time weights (k_prolong_cube); the level
+    pair 32^3 -> 64^3 of the benchmark hierarchy against the oracle's P and P^T row by row, prolongation with and
+    without accumulation, restriction with and without zeroed boundary rows, at the FP64 bounds of
+    test_prolong_restrict."""
     import types
     with fe.Hierarchy(8, 3, 2) as h:
         sc, sf = O.Space(O.Mesh(32), 2), O.Space(O.Mesh(64), 2)
@@ -246,9 +247,19 @@ def test_prolong_p2_per_cube_kernel_full_size(fe):
         xa = dt(x0)
         h.prolong(dt(xc), xa, 3, accumulate=True)
         torch.cuda.synchronize()
+        rf = I.random_vector(f.n, 33)
+        rc = torch.empty(c.n, dtype=torch.float64, device=DEV)
+        h.restrict(dt(rf), rc, 3)
+        rc0 = torch.empty(c.n, dtype=torch.float64, device=DEV)
+        h.restrict(dt(rf), rc0, 3, zero_boundary=True)
+        torch.cuda.synchronize()
         tol = 4 * 10 * 2.0 ** -53
         assert_rowwise(host(xf), P @ xc, abs(P) @ np.abs(xc), tol, "prolong (per cube)")
         assert_rowwise(host(xa), x0 + P @ xc, np.abs(x0) + abs(P) @ np.abs(xc), tol, "prolong (per cube, accumulate)")
+        ref = P.T @ rf
+        assert_rowwise(host(rc), ref, abs(P.T) @ np.abs(rf), 1e-14, "restrict (full size)")
+        ref[sc.boundary] = 0
+        assert_rowwise(host(rc0), ref, abs(P.T) @ np.abs(rf), 1e-14, "restrict (full size, zero bd)")
 
 
 # ------------------------------------------------------------ smoother

@@ -61,3 +61,4 @@ def test_prolongation_weights_match_the_stencil_tables(tmp_path_factory):
                                                                check=True).stdout.split())
     assert bad == 0 and compared == 64 * 27 + 61 * 27
     assert maxsum == 16  # the largest sum of |8 w| over one fine point's stencil
+
