@@ -216,7 +216,9 @@ int fe_set_coefficient(fe_hierarchy* h, const double* kappa_cells, void* stream)
 /* y = A_l x on `level`, matrix-free: for every tet K, y_K += kappa_K
  * int_K grad(u) . grad(v) applied to the gathered dofs x_K, scatter-added
  * into y; boundary rows give y_i = x_i and boundary entries of x are treated
- * as 0 in interior rows.  dtype FE_F64: x, y double.  FE_F32: float.
+ * as 0 in interior rows.  dtype FE_F64: x, y double (P2 in the default FP64
+ * mode: x is first split into the float pairs that the solver's operator
+ * gathers, held by the hierarchy, then applied by that operator).  FE_F32: float.
  * FE_BF16: float vectors, each dof entering as two bf16 terms (16 significant
  * bits) contracted on the tensor cores with FP32 accumulation: per tile of 128
  * cells one GEMM against the reference stiffness tables (one combined table

@@ -1386,7 +1386,12 @@ int fe_apply_operator(const fe_hierarchy* hc, int level, const void* x, void* y,
   if (dtype == FE_F64) {
     const double* xd = stage_in<double>(h, 0, (const double*)x, L.n, s);
     double* yd = stage_out<double>(h, 1, (double*)y, L.n);
-    apply_enqueue(h, level, xd, yd, dtype, s);
+    if (presplit(h, level)) {  // the solver's operator: x split into float pairs first
+      launch_split_pairs(L, xd, s);
+      apply_enqueue(h, level, xd, yd, dtype, s, L.xs64.p);
+    } else {
+      apply_enqueue(h, level, xd, yd, dtype, s);
+    }
     finish_out((double*)y, yd, L.n, s);
   } else {
     const float* xd = stage_in<float>(h, 0, (const float*)x, L.n, s);

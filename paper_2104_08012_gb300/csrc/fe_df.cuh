@@ -245,7 +245,8 @@ using fe_kuhn::kuhn_p2_k;
 // Sums of K_ij A_j are integers below 62 * 2^17 < 2^23 times 2^-16, and of
 // K_ij B_j integers below 2^22.1 times 2^-33, so FP32 forms K A and K B
 // exactly in any order; only K C (below 2^-28) is rounded (about 2^-49
-// absolute).  Row i is handed to emit(i, y_i) as the float pair
+// absolute).  The same holds for the stiffness of two tets that share a face
+// (rows of |K| summing to at most 124: below 2^24 and 2^23.1 units).  Row i is handed to emit(i, y_i) as the float pair
 // (fl(KA + KB), err + KC) as soon as it is formed, so no output array stays
 // live.  The splitting costs 8 FP32 additions per dof and each limb product
 // 82 FMAs with immediate integer coefficients, against about 80 float-pair
@@ -261,30 +262,49 @@ __device__ __forceinline__ void kuhn_term(float a, float b, float c, float& ya, 
     yc = __fmaf_rn((float)K, c, yc);
   }
 }
-template <int I, int... J>
-__device__ __forceinline__ void kuhn_row(const float (&A)[10], const float (&B)[10], const float (&C)[10], float& ya,
+// The integer matrices applied by the limbs: one P2 Kuhn tet (10 dofs) and a
+// pair of Kuhn tets with the same first axis (14 dofs, fe_kuhn.h).
+// cells: consecutive cells of one unit; cell(n), local(n): the cell (0 or 1)
+// and its local dof that unit dof n is read from.
+struct KuhnTet {
+  static constexpr int nd = 10, cells = 1;
+  __host__ __device__ static constexpr int k(int i, int j) { return kuhn_p2_k(i, j); }
+  __host__ __device__ static constexpr int cell(int) { return 0; }
+  __host__ __device__ static constexpr int local(int n) { return n; }
+};
+struct KuhnPair {
+  static constexpr int nd = 14, cells = 2;
+  __host__ __device__ static constexpr int k(int i, int j) { return fe_kuhn::kuhn_pair_k(i, j); }
+  __host__ __device__ static constexpr int cell(int n) { return n >= 10 ? 1 : 0; }
+  __host__ __device__ static constexpr int local(int n) { return n >= 10 ? fe_kuhn::pair_second_local(n) : n; }
+};
+static_assert(fe_kuhn::kuhn_pair_k_ok(), "P2 Kuhn pair stiffness: symmetric, zero row sums, row abs sums <= 127");
+
+template <typename Km, int I, int ND, int... J>
+__device__ __forceinline__ void kuhn_row(const float (&A)[ND], const float (&B)[ND], const float (&C)[ND], float& ya,
                                          float& yb, float& yc, std::integer_sequence<int, J...>) {
-  (kuhn_term<kuhn_p2_k(I, J)>(A[J], B[J], C[J], ya, yb, yc), ...);
+  (kuhn_term<Km::k(I, J)>(A[J], B[J], C[J], ya, yb, yc), ...);
 }
-template <int... I, typename Emit>
-__device__ __forceinline__ void kuhn_rows(const float (&A)[10], const float (&B)[10], const float (&C)[10],
+template <typename Km, int ND, int... I, typename Emit>
+__device__ __forceinline__ void kuhn_rows(const float (&A)[ND], const float (&B)[ND], const float (&C)[ND],
                                           Emit& emit, std::integer_sequence<int, I...>) {
   auto row = [&](auto ic) {
     constexpr int i = decltype(ic)::value;
     float ya = 0.0f, yb = 0.0f, yc = 0.0f;
-    kuhn_row<i>(A, B, C, ya, yb, yc, std::make_integer_sequence<int, 10>{});
+    kuhn_row<Km, i>(A, B, C, ya, yb, yc, std::make_integer_sequence<int, ND>{});
     const DF t = two_sum(ya, yb);
     emit(i, DF(t.hi, __fadd_rn(t.lo, yc)));
   };
   (row(std::integral_constant<int, I>{}), ...);
 }
 
-__device__ __forceinline__ void p2_kuhn_split(const DF (&u)[10], DF cs, float (&A)[10], float (&B)[10],
-                                              float (&C)[10]) {
+template <int ND>
+__device__ __forceinline__ void p2_kuhn_split(const DF (&u)[ND], DF cs, float (&A)[ND], float (&B)[ND],
+                                              float (&C)[ND]) {
   constexpr float kMagA = 192.0f;      // 1.5 * 2^7: fl(v + kMagA) has ulp 2^-16 for |v| <= 2
   constexpr float kMagB = 0x1.8p-10f;  // 1.5 * 2^-10: ulp 2^-33 for |v| < 2^-11
 #pragma unroll
-  for (int j = 0; j < 10; ++j) {
+  for (int j = 0; j < ND; ++j) {
     const float p = __fmul_rn(cs.hi, u[j].hi);
     const float e = __fmaf_rn(cs.hi, u[j].lo, __fmaf_rn(cs.lo, u[j].hi, __fmaf_rn(cs.hi, u[j].hi, -p)));
     A[j] = __fsub_rn(__fadd_rn(p, kMagA), kMagA);
@@ -293,10 +313,10 @@ __device__ __forceinline__ void p2_kuhn_split(const DF (&u)[10], DF cs, float (&
     C[j] = __fadd_rn(__fsub_rn(r, B[j]), e);  // r - B_j exact
   }
 }
-template <typename Emit>
-__device__ __forceinline__ void p2_kuhn_apply(const float (&A)[10], const float (&B)[10], const float (&C)[10],
-                                              Emit&& emit) {
-  kuhn_rows(A, B, C, emit, std::make_integer_sequence<int, 10>{});
+template <typename Km = KuhnTet, typename Emit>
+__device__ __forceinline__ void p2_kuhn_apply(const float (&A)[Km::nd], const float (&B)[Km::nd],
+                                              const float (&C)[Km::nd], Emit&& emit) {
+  kuhn_rows<Km>(A, B, C, emit, std::make_integer_sequence<int, Km::nd>{});
 }
 
 // Whether cube-local node l already received a contribution from one of the

@@ -247,35 +247,47 @@ __global__ void __launch_bounds__(UNI && PRE ? kBlockDfU : kBlock, UNI && PRE ? 
 
 // The default FP64 operator of the solver (P2, pre-split input, one c per
 // Kuhn tet, fixed-point limbs) with its map rows staged in shared memory by
-// asynchronous copies (cp.async): a thread's tet two iterations ahead has its
-// ten map entries copied while the current tet is contracted, so the gathers
-// of the next tet's dofs only wait for a shared-memory read, and the map
-// entries of the current tet are re-read from shared memory for the scatter
+// asynchronous copies (cp.async): a thread's unit two iterations ahead has its
+// map entries copied while the current unit is contracted, so the gathers
+// of the next unit's dofs only wait for a shared-memory read, and the map
+// entries of the current unit are re-read from shared memory for the scatter
 // instead of occupying registers.  Three buffers per thread ([buffer][dof]
-// [thread]): the current tet (scatter), the next (gathers issued this
+// [thread]): the current unit (scatter), the next (gathers issued this
 // iteration) and the one after (copies in flight).
-// 128 threads, 6 resident blocks per SM (79 registers, no spills; the staged map
-// frees the registers that held map entries).  Full P2 64^3 solves measured
-// 6.34 / 6.30 / 6.33 / 6.72 ms at 5 / 6 / 7 (spills) / 8 blocks per SM, against
-// 6.40 ms for the same element with register-held map rows (k_apply_df).
+// A unit (Km) is one tet (KuhnTet) or, on a level where the two tets of every
+// pair with the same first axis have the same c, such a pair (KuhnPair): the
+// tets 2p and 2p + 1 share a face, so the pair's 14 dofs are gathered, split
+// and scattered once (14 gathers and 14 FP64 atomics for two tets instead of
+// 20) and the pair stiffness (136 nonzero integers against 2 x 82) is applied
+// by the same exact limbs.
+// 128 threads.  One tet: 6 resident blocks per SM (79 registers, no spills; the
+// staged map frees the registers that held map entries); full P2 64^3 solves
+// measured 6.34 / 6.30 / 6.33 / 6.72 ms at 5 / 6 / 7 (spills) / 8 blocks per
+// SM, against 6.40 ms for the same element with register-held map rows
+// (k_apply_df).
 constexpr int kBlockLp = 128;
-constexpr int kMinBlocksLp = 6;
+template <typename Km>
+constexpr int lp_min_blocks() {
+  return Km::cells == 1 ? 6 : 5;
+}
 
-__global__ void __launch_bounds__(kBlockLp, kMinBlocksLp)
-    k_apply_lp(int C, int Cs, const int* __restrict__ map, const float2* __restrict__ cdf,
+template <typename Km>
+__global__ void __launch_bounds__(kBlockLp, lp_min_blocks<Km>())
+    k_apply_lp(int U, int Cs, const int* __restrict__ map, const float2* __restrict__ cdf,
                const double* __restrict__ x, const float2* __restrict__ xs, double* __restrict__ y, int nb,
                const int* __restrict__ bnd) {
-  constexpr int ND = 10;
+  constexpr int ND = Km::nd;
   __shared__ int smap[3][ND][kBlockLp];
   const int tx = threadIdx.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   for (int i = tid; i < nb; i += stride) y[bnd[i]] = x[bnd[i]];  // Dirichlet rows: identity
-  int c = tid;
-  if (c >= C) return;
-  auto copy_map = [&](int cell, int buf) {
-    if (cell < C) {
+  int c = tid;  // the current unit
+  if (c >= U) return;
+  auto copy_map = [&](int u, int buf) {
+    if (u < U) {
 #pragma unroll
-      for (int j = 0; j < ND; ++j) cp_async4(&smap[buf][j][tx], map + (size_t)j * Cs + cell);
+      for (int j = 0; j < ND; ++j)
+        cp_async4(&smap[buf][j][tx], map + (size_t)Km::local(j) * Cs + (size_t)Km::cells * u + Km::cell(j));
     }
     cp_async_commit();
   };
@@ -288,28 +300,28 @@ __global__ void __launch_bounds__(kBlockLp, kMinBlocksLp)
     const int i = smap[0][j][tx];
     xv[j] = i >= 0 ? __ldg(xs + i) : make_float2(0.0f, 0.0f);
   }
-  gv = __ldg(cdf + c);
-  int b = 0;  // buffer of the current tet
+  gv = __ldg(cdf + (size_t)Km::cells * c);
+  int b = 0;  // buffer of the current unit
   while (true) {
     const int cn = c + stride;
-    const bool more = cn < C;
+    const bool more = cn < U;
     const int bn = b == 2 ? 0 : b + 1, bnn = bn == 2 ? 0 : bn + 1;
     float2 xn[ND], gn = make_float2(0.0f, 0.0f);
     if (more) {
-      cp_async_wait_all();  // the next tet's map entries (copied one iteration ago)
+      cp_async_wait_all();  // the next unit's map entries (copied one iteration ago)
 #pragma unroll
       for (int j = 0; j < ND; ++j) {
         const int i = smap[bn][j][tx];
         xn[j] = i >= 0 ? __ldg(xs + i) : make_float2(0.0f, 0.0f);
       }
-      gn = __ldg(cdf + cn);
+      gn = __ldg(cdf + (size_t)Km::cells * cn);
       copy_map(cn + stride, bnn);
     }
     unsigned int mb = 0u;  // largest magnitude bits of the leading floats (a marker NaN exceeds every finite one)
 #pragma unroll
     for (int j = 0; j < ND; ++j) mb = max(mb, __float_as_uint(xv[j].x) & 0x7FFFFFFFu);
     const int ef = (int)(mb >> 23);
-    if (mb != 0u) {  // a tet whose dofs are all zero contributes nothing
+    if (mb != 0u) {  // a unit whose dofs are all zero contributes nothing
       DF u[ND];
       int emax;
       float fsc = 1.0f;
@@ -318,7 +330,7 @@ __global__ void __launch_bounds__(kBlockLp, kMinBlocksLp)
         for (int j = 0; j < ND; ++j) u[j] = DF(xv[j].x, xv[j].y);
         fsc = __uint_as_float((unsigned int)(254 - ef) << 23);  // 2^(127 - ef), applied to c
         emax = ef + 896;
-      } else {  // a marker: the tet's FP64 dofs split with their own scaling
+      } else {  // a marker: the unit's FP64 dofs split with their own scaling
         double xd[ND];
 #pragma unroll
         for (int j = 0; j < ND; ++j) {
@@ -339,12 +351,12 @@ __global__ void __launch_bounds__(kBlockLp, kMinBlocksLp)
       const int w = ec + emax - 124;
       if (w >= 127 && w <= 1918) {  // every contribution widens without range checks
         const unsigned int kexp = (unsigned int)(w - 127) << 20;
-        p2_kuhn_apply(A, B, Cl, [&](int j, DF v) {
+        p2_kuhn_apply<Km>(A, B, Cl, [&](int j, DF v) {
           const int i = smap[b][j][tx];
           if (i >= 0) atomicAdd(y + i, widen_in_range(v.hi, kexp) + widen_in_range(v.lo, kexp));
         });
       } else {
-        p2_kuhn_apply(A, B, Cl, [&](int j, DF v) {
+        p2_kuhn_apply<Km>(A, B, Cl, [&](int j, DF v) {
           const int i = smap[b][j][tx];
           if (i >= 0) atomicAdd(y + i, widen_scaled(v.hi, w) + widen_scaled(v.lo, w));
         });
@@ -669,10 +681,17 @@ static void apply_df_launch(const Level& L, const double* x, const float2* xs, d
 template <int DEG, bool PRE>
 static void apply_df_geo(const Level& L, const double* x, const float2* xs, double* y, cudaStream_t s) {
   if constexpr (DEG == 2 && PRE) {
+    if (L.uniform && L.pair_uniform) {
+      static int g = 0;
+      if (!g) g = resident_grid(k_apply_lp<KuhnPair>, kBlockLp, 1 << 30);
+      k_apply_lp<KuhnPair><<<std::min(g, ceil_div(std::max(L.C / 2, L.nb), kBlockLp)), kBlockLp, 0, s>>>(
+          L.C / 2, L.Cs, L.map, L.cdf, x, xs, y, L.nb, L.bnd);
+      return;
+    }
     if (L.uniform) {
       static int g = 0;
-      if (!g) g = resident_grid(k_apply_lp, kBlockLp, 1 << 30);
-      k_apply_lp<<<std::min(g, ceil_div(std::max(L.C, L.nb), kBlockLp)), kBlockLp, 0, s>>>(
+      if (!g) g = resident_grid(k_apply_lp<KuhnTet>, kBlockLp, 1 << 30);
+      k_apply_lp<KuhnTet><<<std::min(g, ceil_div(std::max(L.C, L.nb), kBlockLp)), kBlockLp, 0, s>>>(
           L.C, L.Cs, L.map, L.cdf, x, xs, y, L.nb, L.bnd);
       return;
     }
@@ -736,6 +755,18 @@ void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStre
 
 void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s, const float2* xs) {
   apply_df<false>(L, x, xs, y, ChebFuse<double>{}, s);
+}
+
+__global__ void k_split_pairs(int n, const double* __restrict__ x, float2* __restrict__ xs) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) xs[i] = split_pair(x[i]);
+}
+
+void launch_split_pairs(const Level& L, const double* x, cudaStream_t s) {
+  FE_REQUIRE(L.xs64.p, FE_ERR_UNSUPPORTED, "this level keeps no float-pair copy of x");
+  static int g = 0;
+  if (!g) g = resident_grid(k_split_pairs, kBlock, 1 << 30);
+  k_split_pairs<<<std::min(g, std::max(1, ceil_div(L.n, kBlock))), kBlock, 0, s>>>(L.n, x, L.xs64.p);
+  LAUNCH_CHECK();
 }
 
 void launch_apply_cheb64_df(const Level& L, const double* b, double* x, double* y, double* d, double c1, double c2,

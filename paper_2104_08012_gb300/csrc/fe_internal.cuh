@@ -232,6 +232,9 @@ struct Level {
   // vertex coordinates (uniform = 1 when every cell agrees) and keeps c for the operator kernels that then read
   // one value per cell instead of six.
   int uniform = 0;
+  // 1 when also the two tets of every pair with the same first axis (cells 6q + 2k, 6q + 2k + 1: they share a face)
+  // have the same c, so that the FP64 P2 operator applies such pairs as one unit
+  int pair_uniform = 0;
   DBuf<float> c32;        // [C] c in FP32
   DBuf<float2> cdf;       // [C] c as a float pair
   DBuf<float2> massdf;    // |det J| / 120 (P1) or / 2520 (P2) per cell as a float pair (double-float mass)
@@ -407,6 +410,9 @@ void launch_apply64(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s);
 // xs (optional): x as unscaled float pairs (split_pair), gathered instead of x
 void launch_apply64_df(const Level& L, const double* x, double* y, cudaStream_t s, const float2* xs = nullptr);
+// x as the float pairs the pre-split P2 operator gathers (into L.xs64), for an application whose input no vector
+// kernel has split.
+void launch_split_pairs(const Level& L, const double* x, cudaStream_t s);
 void launch_apply64_cube_df(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply64_df2(const Level& L, const double* x, double* y, cudaStream_t s);
 void launch_apply64_df3(const Level& L, const double* x, double* y, cudaStream_t s);
@@ -431,7 +437,7 @@ template <typename T>
 void launch_cheb_pc(int n, const T* z, T* x, T* d, double c1, double c2, bool first_from_zero, bool store_d,
                     cudaStream_t s);
 void launch_split_geometry(Level& L, cudaStream_t s);
-// Checks geo64 = c M cell by cell, fills c32 and cdf and sets L.uniform (synchronises s).
+// Checks geo64 = c M cell by cell, fills c32 and cdf and sets L.uniform and L.pair_uniform (synchronises s).
 void launch_uniform_geometry(Level& L, int* dflag, cudaStream_t s);
 // b -= A g on interior rows and b = g on the boundary (inhomogeneous Dirichlet data, symmetric elimination)
 void launch_bc_lift(const Level& L, const double* g, double* b, cudaStream_t s);

@@ -189,7 +189,8 @@ __global__ void k_geometry(int C, int Cs, const int* __restrict__ map, const dou
 
 // geo64 = c M for every cell (M = [[2,-1,0],[-1,2,-1],[0,-1,1]] in the stored
 // order 00, 01, 02, 11, 12, 22), c = geo64[22]; a cell whose G differs from
-// c M by more than 1e-12 |c| sets the flag.
+// c M by more than 1e-12 |c| sets bit 0 of the flag, an odd cell whose c
+// differs from that of the cell before it (the other tet of its pair) bit 1.
 __global__ void k_uniform_geometry(int C, int Cs, const double* __restrict__ geo64, float* __restrict__ c32,
                                    float2* __restrict__ cdf, int* __restrict__ flag) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -200,6 +201,7 @@ __global__ void k_uniform_geometry(int C, int Cs, const double* __restrict__ geo
 #pragma unroll
   for (int a = 0; a < 5; ++a) ok = ok && fabs(geo64[(size_t)a * Cs + t] - m[a] * c) <= 1e-12 * c;
   if (!ok) atomicOr(flag, 1);
+  if ((t & 1) && c != geo64[(size_t)5 * Cs + t - 1]) atomicOr(flag, 2);
   c32[t] = (float)c;
   const float hi = (float)c;
   cdf[t] = make_float2(hi, (float)(c - (double)hi));
@@ -1179,7 +1181,8 @@ void launch_uniform_geometry(Level& L, int* dflag, cudaStream_t s) {
   int hflag = 1;
   CUDA_CHECK(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_CHECK(cudaStreamSynchronize(s));
-  L.uniform = hflag == 0 ? 1 : 0;
+  L.uniform = (hflag & 1) == 0 ? 1 : 0;
+  L.pair_uniform = hflag == 0 ? 1 : 0;
 }
 
 void launch_geometry(Level& L, cudaStream_t s) {

@@ -72,6 +72,48 @@ FE_KUHN_HD constexpr bool kuhn_p2_k_ok() {
   return true;
 }
 
+// Two Kuhn tets of a cube whose permutations share the first axis, (p0, p1,
+// p2) and (p0, p2, p1) (cells 6q + 2k and 6q + 2k + 1), share the vertices
+// v0, v1 = v0 + e_p0 and v3 and the edges (0,1), (0,3), (1,3): the face that
+// separates them.  Their 14 distinct P2 dofs, as a pair: pair dof n < 10 is
+// local dof n of the first tet; the second tet's vertex 2 and its edges
+// (0,2), (1,2), (2,3) (local dofs 2, 5, 7, 9) are pair dofs 10..13, and its
+// other local dofs are the first tet's with the same number.
+FE_KUHN_HD constexpr int pair_second_local(int n) {  // the second tet's local dof at pair dof n, -1 if none
+  return n >= 10 ? (n == 10 ? 2 : n == 11 ? 5 : n == 12 ? 7 : 9)
+                 : (n == 2 || n == 5 || n == 7 || n == 9 ? -1 : n);
+}
+
+// The stiffness of such a pair with one c for both tets, divided by 4 c: the
+// two integer element matrices K added on the 14 pair dofs.
+FE_KUHN_HD constexpr int kuhn_pair_k(int m, int n) {
+  const int sm = pair_second_local(m), sn = pair_second_local(n);
+  return (m < 10 && n < 10 ? kuhn_p2_k(m, n) : 0) + (sm >= 0 && sn >= 0 ? kuhn_p2_k(sm, sn) : 0);
+}
+
+// The pair's limb sums stay exact while every row of |K_pair| sums to at most
+// 127 (127 * 2^17 < 2^24, the integers FP32 holds exactly).
+FE_KUHN_HD constexpr int kuhn_pair_k_absrow_max() {
+  int mx = 0;
+  for (int m = 0; m < 14; ++m) {
+    int absrow = 0;
+    for (int n = 0; n < 14; ++n) absrow += kuhn_pair_k(m, n) < 0 ? -kuhn_pair_k(m, n) : kuhn_pair_k(m, n);
+    mx = absrow > mx ? absrow : mx;
+  }
+  return mx;
+}
+FE_KUHN_HD constexpr bool kuhn_pair_k_ok() {
+  for (int m = 0; m < 14; ++m) {
+    int row = 0;
+    for (int n = 0; n < 14; ++n) {
+      if (kuhn_pair_k(m, n) != kuhn_pair_k(n, m)) return false;
+      row += kuhn_pair_k(m, n);
+    }
+    if (row != 0) return false;
+  }
+  return kuhn_pair_k_absrow_max() <= 127;
+}
+
 // P2 prolongation weights on nested Kuhn meshes, times 8 (integers): the
 // coarse P2 function of a cube evaluated at the fine P2 node o / 4 of that
 // cube (o in [0, 4]^3, fine lattice units), as the sum over the basis

@@ -59,16 +59,23 @@ def test_mesh_queries_match_oracle(fe, k, N):
 # ------------------------------------------------------------ operator
 @pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("N", [1, 2, 3, 5, 8])
-@pytest.mark.parametrize("coef", ["one", "grf"])
-@pytest.mark.parametrize("mode", ["native", "double_float_tet", "double_float_cube", "double_float_pair"])
+@pytest.mark.parametrize("coef", ["one", "grf", "grf_per_pair"])
+@pytest.mark.parametrize("mode", ["native", "double_float", "double_float_tet", "double_float_cube",
+                                  "double_float_pair"])
 def test_apply_f64(fe, k, N, coef, mode):
     """FP64 operator in both arithmetics: FP64 FMAs and float-pair (~48-bit) on the FP32 pipes
-    (per cube, per tet, and two tets per thread in packed FP32x2 instructions)."""
+    (per cube, per tet, and two tets per thread in packed FP32x2 instructions).  In the default mode the P2
+    operator is the solver's: pre-split input, fixed-point limbs, one tet per unit under a coefficient that varies
+    from tet to tet ("grf"), the two tets that share a face as one unit where they have the same coefficient ("one",
+    and "grf_per_pair": the value of the pair's first tet on both)."""
     with fe.Hierarchy(N, 0, k) as h:
-        h.set_f64_mode({"native": fe.FE_F64_NATIVE, "double_float_cube": fe.FE_F64_DOUBLE_FLOAT_CUBE,
+        h.set_f64_mode({"native": fe.FE_F64_NATIVE, "double_float": fe.FE_F64_DOUBLE_FLOAT,
+                        "double_float_cube": fe.FE_F64_DOUBLE_FLOAT_CUBE,
                         "double_float_tet": fe.FE_F64_DOUBLE_FLOAT_TET,
                         "double_float_pair": fe.FE_F64_DOUBLE_FLOAT_PAIR}[mode])
         kappa = None if coef == "one" else I.grf_kappa(h.cell_centroids(), seed=N)
+        if coef == "grf_per_pair":
+            kappa[1::2] = kappa[0::2]
         h.set_coefficient(None if kappa is None else dt(kappa))
         L = O.Level(N, k, kappa)
         x = I.random_vector(L.n, 10 + N)
@@ -98,13 +105,14 @@ def test_apply_f32(fe, k, N, variable_kappa):
 
 
 @pytest.mark.parametrize("scale", [1e-300, 1e-250, 1e-30, 1e-8, 1.0, 1e8, 1e30, 1e250, 1e300])
-@pytest.mark.parametrize("mode", ["double_float_cube", "double_float_tet", "double_float_pair"])
+@pytest.mark.parametrize("mode", ["double_float", "double_float_cube", "double_float_tet", "double_float_pair"])
 def test_double_float_value_range(fe, scale, mode):
     """The float-pair split/widen keep FP64-class accuracy from 1e-300 to 1e300 (each tet's dofs are scaled by a
     power of two first; contributions below the normal FP64 range widen to subnormal doubles), with exact zeros
     and sign changes, and NaN dofs propagate."""
     with fe.Hierarchy(3, 0, 2) as h:
-        h.set_f64_mode({"double_float_cube": fe.FE_F64_DOUBLE_FLOAT_CUBE, "double_float_tet": fe.FE_F64_DOUBLE_FLOAT_TET,
+        h.set_f64_mode({"double_float": fe.FE_F64_DOUBLE_FLOAT, "double_float_cube": fe.FE_F64_DOUBLE_FLOAT_CUBE,
+                        "double_float_tet": fe.FE_F64_DOUBLE_FLOAT_TET,
                         "double_float_pair": fe.FE_F64_DOUBLE_FLOAT_PAIR}[mode])
         L = O.Level(3, 2)
         x = I.random_vector(L.n, 77) * scale
@@ -374,9 +382,17 @@ def test_coarse_blocked_matches_oracle(fe, k, N0):
 
 
 @pytest.mark.parametrize("k", [1, 2])
-def test_vcycle_matches_oracle(fe, k):
+@pytest.mark.parametrize("coef", ["grf", "grf_per_pair", "one"])
+def test_vcycle_matches_oracle(fe, k, coef):
+    """One V-cycle against the oracle's; at P2 the operator units are single tets ("grf"), pairs of tets on the
+    fine level ("grf_per_pair"; below it, single tets wherever the coarsened coefficient differs between the tets
+    of a pair), or pairs on every level ("one")."""
     with fe.Hierarchy(2, 2, k) as h:
         kappa = I.grf_kappa(h.cell_centroids(), seed=4)
+        if coef == "grf_per_pair":
+            kappa[1::2] = kappa[0::2]
+        elif coef == "one":
+            kappa[:] = 1.0
         h.set_coefficient(dt(kappa))
         oh = O.Hierarchy(2, 2, k, kappa)
         oh.lmax = [h.lambda_max(l) for l in range(3)]  # same Chebyshev intervals
