@@ -44,16 +44,17 @@ BYTES_PER_DOF_P2 = {"f64": 49.0, "f32": 41.0}
 # dram__bytes_write.sum from one ncu capture of the finest level's applications inside a V-cycle of the
 # P2 64^3 hierarchy, the kernel the CG iterations run; mean of 2 launches), keyed by FP64 mode; None where
 # the kernel changed after the last capture.
-TRAFFIC = {0: None, 1: 116.6e6, 2: None}
+TRAFFIC = {0: None, 1: 116.4e6, 2: None}
 # Arithmetic of one P2 element application (c, d, S, four G-products, transpose),
 # per tet: 151 flops in the FP64 formula with a general G (an FMA counts 2).  With
 # the geometric matrix shared by every Kuhn tet (G = c M) the element matrix is
-# c times one integer matrix K (82 nonzeros), applied by fixed-point limbs:
-# 436 FP32 operations (an add, mul or FMA counts 1) = ten products c x as float
-# pairs x 4, their cut into three limbs x 8 additions, 82 x 3 FMAs, and per row
-# one TwoSum (6) and one addition.
+# c times one integer matrix K (82 nonzeros), applied by fixed-point limbs to
+# the two tets that share a face as one unit (14 dofs, 136 nonzero integers):
+# per pair 674 FP32 operations (an add, mul or FMA counts 1) = 14 products c x
+# as float pairs x 4, their cut into three limbs x 8 additions, 136 x 3 FMAs,
+# and per row one TwoSum (6) and one addition; 337 per tet.
 FLOPS_PER_CELL_P2_F64 = 151
-OPS_PER_CELL_P2_DF = 436
+OPS_PER_CELL_P2_DF = 337
 # Operations of one P3 element application through the gradient at the P2 nodes (fe_p3.cuh; an FMA counts 1):
 # 206 additions, 165 multiplications, 284 FMAs, 22 negations (counted by tests/test_p3_element_host.py)
 OPS_PER_CELL_P3 = 677
@@ -758,10 +759,11 @@ def run_ours(args, rank, world, local_rank, oracle=None):
     byt = BYTES_PER_DOF_P2["f64"] * n
     achieved_gbs = byt / (apply_ms * 1e-3) / 1e9
     if F64_MODE == fe.FE_F64_DOUBLE_FLOAT:
-        kname = ("k_apply_lp (FP64 operator on the FP32 pipes: exact fixed-point limbs of c x against the integer "
-                 "Kuhn-tet stiffness; persistent, one tet per thread, map rows staged in shared memory by cp.async)")
+        kname = ("k_apply_lp<KuhnPair> (FP64 operator on the FP32 pipes: exact fixed-point limbs of c x against the "
+                 "integer stiffness of the two Kuhn tets that share a face, applied as one unit of 14 dofs; "
+                 "persistent, map rows staged in shared memory by cp.async)")
         ops, opeak, ounit = OPS_PER_CELL_P2_DF * C, FP32_PEAK_TOPS, "T FP32 op/s"
-        oderiv = ("436 FP32 operations per tet of the limb element x cells / launch duration, against the "
+        oderiv = ("337 FP32 operations per tet of the limb element (674 per pair) x cells / launch duration, against the "
                   "nominal FP32 issue rate 152 SMs x 128 lanes x 1 op/clk x 2.07 GHz = 40.3 T op/s (no measured FP32 "
                   "peak exists)")
     else:
@@ -793,7 +795,7 @@ def run_ours(args, rank, world, local_rank, oracle=None):
                                     "kappa = 1)",
                      "peak_source": f"{hsrc} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hsrc == "measured"
                      else "fallback 6.8 TB/s",
-                     "limiter": "instruction issue and gather latency, not DRAM (ncu: issue 66%, FP64 pipe 51%)",
+                     "limiter": "instruction issue and gather latency, not DRAM (ncu: issue 65%, FP64 pipe 48%)",
                      "alu_issue_view_nominal": {"achieved": ops / (apply_ms * 1e-3) / 1e12, "peak": opeak,
                                                 "unit": ounit, "frac": ops / (apply_ms * 1e-3) / 1e12 / opeak,
                                                 "derivation": oderiv},

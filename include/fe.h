@@ -270,7 +270,9 @@ int fe_set_geometry_form(fe_hierarchy* h, int form);
 
 /* ---- coarse direct solver (fe_set_coarse_solver) ---- */
 #define FE_COARSE_AUTO 0     /* dense inverse factor up to 16384 interior coarse dofs, blocked band factor above */
-#define FE_COARSE_DENSE 1    /* explicit L^-1 and L^-T: two parallel dense triangular products per solve */
+#define FE_COARSE_DENSE 1    /* explicit L^-1 and L^-T: two parallel dense triangular products per solve
+                                (native FP64), or one dense product with A^-1 = L^-T L^-1 held as float
+                                pairs (the float-pair FP64 modes and FP32) */
 #define FE_COARSE_BLOCKED 2  /* band Cholesky factor; blocks of B = bandwidth rows with the inverse of each
                                 diagonal block and the block left of it: 4 nb block products per solve */
 
@@ -333,7 +335,8 @@ int fe_smooth(const fe_hierarchy* h, int level, const void* b, void* x, int step
               int dtype, void* stream);
 
 /* x = A_0^-1 b on the coarsest level with the FP64 Cholesky factor of its
- * interior block (x_bd = b_bd). */
+ * interior block (x_bd = b_bd).  b and x must not overlap (FE_ERR_ARG when
+ * they are the same vector). */
 int fe_coarse_solve(const fe_hierarchy* h, const double* b, double* x, void* stream);
 
 /* x = V(b): one V-cycle on the finest level (pre-smoothing from 0, residual,

@@ -1585,7 +1585,7 @@ int fe_smooth(const fe_hierarchy* hc, int level, const void* b, void* x, int ste
 int fe_coarse_solve(const fe_hierarchy* hc, const double* b, double* x, void* stream) {
   API_BEGIN
   FE_REQUIRE(hc && hc->nlev > 1, FE_ERR_ARG, "coarse solve needs a hierarchy with at least 2 levels");
-  FE_REQUIRE(b && x, FE_ERR_ARG, "null vector");
+  FE_REQUIRE(b && x && (const void*)b != (const void*)x, FE_ERR_ARG, "b and x must be distinct non-null vectors");
   fe_hierarchy* h = const_cast<fe_hierarchy*>(hc);
   cudaStream_t s = as_stream(stream);
   const Level& L0 = h->L[0];

@@ -9,10 +9,12 @@
 // warp per column, forward substitution over the band).
 // Solve (every V-cycle): x = L^-T (L^-1 b) as two dense triangular
 // matrix-vector products, which are fully parallel instead of 2 n
-// dependent substitution steps.  Unless the hierarchy runs native FP64, the
-// products are evaluated in float-pair arithmetic on the FP32 pipes (L^-1 and
-// L^-T stored as float pairs, the vector scaled by a power of two and split
-// once per product), since FP64 fused multiply-adds bound the FP64 form.
+// dependent substitution steps (native FP64 hierarchies).  Otherwise the
+// setup also forms A^-1 = L^-T L^-1 (FP64 sums, stored as float pairs) and a
+// solve is one launch: the vector scaled by a power of two and split into
+// float pairs in each block's shared memory, one dense product with A^-1 in
+// float-pair arithmetic on the FP32 pipes (FP64 fused multiply-adds would
+// bound it), the result written straight to the interior dofs.
 //
 // Blocked form (large coarse levels, where n^2 storage is out of reach): the
 // band is assembled and factored in band storage (row i holds A[i][i-w..i];
@@ -312,78 +314,177 @@ __global__ void __launch_bounds__(kRowThreads) k_trimv(int n, const double* __re
   }
 }
 
-// Row kernel of y = M v in float pairs: M row-major n x n (float pairs), v
-// split by k_split_vec with exponent *ev; y in FP64.
-__global__ void __launch_bounds__(kRowThreads) k_trimv_df(int n, const float2* __restrict__ M,
-                                                          const float2* __restrict__ v, const int* __restrict__ ev,
-                                                          double* __restrict__ out, int upper) {
-  using namespace fe_df;
-  __shared__ float2 sh[kRowThreads / 32];
-  const int row = blockIdx.x;
-  const float2* Mr = M + (size_t)row * n;
-  const int j0 = upper ? row : 0, j1 = upper ? n : row + 1;
-  DF s0, s1;
-  int jj = j0 + threadIdx.x;
-  for (; jj + kRowThreads < j1; jj += 2 * kRowThreads) {
-    const float2 a = __ldg(Mr + jj), b = __ldg(v + jj), c = __ldg(Mr + jj + kRowThreads),
-                 d = __ldg(v + jj + kRowThreads);
-    s0 = s0 + mul(DF(a.x, a.y), DF(b.x, b.y));
-    s1 = s1 + mul(DF(c.x, c.y), DF(d.x, d.y));
-  }
-  if (jj < j1) {
-    const float2 a = __ldg(Mr + jj), b = __ldg(v + jj);
-    s0 = s0 + mul(DF(a.x, a.y), DF(b.x, b.y));
-  }
-  DF s = s0 + s1;
+// The coarse inverse A^-1 = L^-T L^-1 from the inverse factor (row-major,
+// lower triangular): entry (i, j) is the sum over k >= max(i, j) of
+// Linv[k][i] Linv[k][j], in FP64 (n x n, row-major).  One 32 x 32 tile per
+// block, tiles above the diagonal only, each mirrored.
+constexpr int kGramTile = 32;
+__global__ void __launch_bounds__(kGramTile * 8) k_inv_gram(int n, const double* __restrict__ Linv,
+                                                            double* __restrict__ Ainv) {
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (I > J) return;
+  __shared__ double si[kGramTile][kGramTile + 1], sj[kGramTile][kGramTile + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int i0 = I * kGramTile, j0 = J * kGramTile;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k0 = j0; k0 < n; k0 += kGramTile) {  // Linv[k][i] = 0 for k < i: k starts at the tile's larger index
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-    s = s + DF(__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_float2(s.hi, s.lo);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    DF t;
+    for (int r = 0; r < 4; ++r) {
+      const int k = k0 + ty + 8 * r;
+      si[ty + 8 * r][tx] = k < n && i0 + tx < n ? Linv[(size_t)k * n + i0 + tx] : 0.0;
+      sj[ty + 8 * r][tx] = k < n && j0 + tx < n ? Linv[(size_t)k * n + j0 + tx] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kGramTile; ++kk) {
+      const double b = sj[kk][tx];
 #pragma unroll
-    for (int w = 0; w < kRowThreads / 32; ++w) t = t + DF(sh[w].x, sh[w].y);
-    const int e = *ev;
-    out[row] = widen_scaled(t.hi, e) + widen_scaled(t.lo, e);
+      for (int r = 0; r < 4; ++r) acc[r] = fma(si[kk][ty + 8 * r], b, acc[r]);
+    }
+    __syncthreads();
+  }
+  const int j = j0 + tx;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty + 8 * r;
+    if (i < n && j < n) {
+      Ainv[(size_t)i * n + j] = acc[r];
+      Ainv[(size_t)j * n + i] = acc[r];
+    }
   }
 }
 
-// One block: v (gathered through idx when idx != null) -> float pairs scaled by
-// 2^(1023 - e), e = the largest biased exponent of v (0x7FF: a non-finite
-// entry, which is propagated as NaN).
+// The largest biased exponent on the diagonal of A^-1 (an SPD matrix: its
+// largest entry lies on the diagonal).
+__global__ void k_diag_exponent(int n, const double* __restrict__ Ainv, int* __restrict__ e) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicMax(e, (int)(((unsigned int)__double2hiint(Ainv[(size_t)i * n + i]) >> 20) & 0x7FFu));
+}
+
+// A^-1 * 2^(1023 - ea) as float pairs in rows of the even length ld (every row
+// starts on 16 bytes; the padding is zero).
+__global__ void k_split_rows(int n, int ld, const double* __restrict__ Ainv, const int* __restrict__ ea,
+                             float2* __restrict__ out) {
+  const size_t nn = (size_t)n * ld;
+  const double sc = __hiloint2double((2046 - *ea) << 20, 0);  // 2^(1023 - ea), ea in [1, 2045]
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / ld), j = (int)(t - (size_t)i * ld);
+    const double x = j < n ? Ainv[(size_t)i * n + j] * sc : 0.0;
+    const float hi = (float)x;
+    out[t] = make_float2(hi, (float)(x - (double)hi));
+  }
+}
+
+// The whole coarse solve x = A^-1 b in one launch (float pairs on the FP32
+// pipes).  Each warp streams its rows of A^-1 2^(1023 - ea) (float pairs) in
+// chunks of 128 16-byte words through a three-stage ring in shared memory,
+// filled by cp.async (no registers held by the copies in flight; each lane
+// contracts exactly the words it copied, so the ring needs no barrier).  The
+// first two chunks go out before the block prepares v: the interior entries
+// of b gathered into shared memory as float pairs scaled by 2^(1023 - e), e
+// the largest biased exponent among them (0x7FF: a non-finite entry,
+// propagated as NaN).  Each row is scaled back by 2^(e + ea - 2046) and
+// written to its interior dof of x; the boundary dofs copy b.  The matrix is
+// read once per solve (n_interior * ld * 8 bytes); b and x must not overlap.
+constexpr int kInvThreads = 256;
+constexpr int kInvStages = 3;
+constexpr int kInvWords = 4;                      // 16-byte words per lane per chunk
+constexpr int kInvChunkWords = 32 * kInvWords;    // per warp: 2 KB
+__host__ __device__ constexpr size_t coarse_inv_smem(int ld) {  // ring of every warp, then v
+  return sizeof(float4) * ((size_t)(kInvThreads / 32) * kInvStages * kInvChunkWords + (size_t)(ld / 2));
+}
+
 template <typename T>
-__global__ void k_split_vec(int n, const int* __restrict__ idx, const T* __restrict__ v, double* __restrict__ vd,
-                            float2* __restrict__ vs, int* __restrict__ ev) {
+__global__ void __launch_bounds__(kInvThreads, 3) k_coarse_inv_df(int n, int nci, int ld, const int* __restrict__ ci,
+                                                                  const int* __restrict__ dof2int,
+                                                                  const float2* __restrict__ Ainv, int ea,
+                                                                  const T* __restrict__ b, T* __restrict__ x) {
   using namespace fe_df;
+  extern __shared__ float4 sm4[];
   __shared__ int smax;
+  const int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  float4* ring = sm4 + (threadIdx.x >> 5) * (kInvStages * kInvChunkWords);
+  float4* vs4 = sm4 + (kInvThreads / 32) * kInvStages * kInvChunkWords;  // [ld / 2]
+  float2* vs = reinterpret_cast<float2*>(vs4);
+  const int q1 = ld / 2;                                      // 16-byte words (two float pairs) per row
+  const int nch = (q1 + kInvChunkWords - 1) / kInvChunkWords;  // chunks per row
+  const int nrows = wid < nci ? (nci - wid + nw - 1) / nw : 0;  // rows wid, wid + nw, ...
+  const int ctot = nrows * nch;
+  // chunk c of this warp: row wid + nw (c / nch), words (c % nch) kInvChunkWords + 32 u + lane, into slot c % 3
+  auto issue = [&](int c) {
+    if (c < ctot) {
+      const int rr = c / nch, k = c - rr * nch;
+      const float4* Ar = reinterpret_cast<const float4*>(Ainv + (size_t)(wid + nw * rr) * ld);
+      float4* dst = ring + (c % kInvStages) * kInvChunkWords;
+#pragma unroll
+      for (int u = 0; u < kInvWords; ++u) {
+        const int q = k * kInvChunkWords + 32 * u + lane;
+        cp_async16(dst + 32 * u + lane, Ar + min(q, q1 - 1), q < q1 ? 16 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int c = 0; c < kInvStages - 1; ++c) issue(c);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (dof2int[i] < 0) x[i] = b[i];
   if (threadIdx.x == 0) smax = 0;
   __syncthreads();
+  // b is gathered once, eight loads in flight per thread: the doubles are parked in the float-pair slots
+  // (8 bytes each) until e is known
+  double* vd = reinterpret_cast<double*>(vs4);
   int e = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double x = (double)v[idx ? idx[i] : i];
-    if (vd) vd[i] = x;
-    e = max(e, (int)(((unsigned int)__double2hiint(x) >> 20) & 0x7FFu));
+  for (int j0 = threadIdx.x; j0 < nci; j0 += 8 * kInvThreads) {
+    int idx[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) idx[u] = j0 + kInvThreads * u < nci ? ci[j0 + kInvThreads * u] : -1;
+    double d[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) d[u] = idx[u] >= 0 ? (double)b[idx[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (idx[u] >= 0) {
+        vd[j0 + kInvThreads * u] = d[u];
+        e = max(e, (int)(((unsigned int)__double2hiint(d[u]) >> 20) & 0x7FFu));
+      }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
   if ((threadIdx.x & 31) == 0) atomicMax(&smax, e);
   __syncthreads();
   const int E = smax == 0 ? 1023 : smax;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    DF d = split_scaled((double)v[idx ? idx[i] : i], E);
-    if (E == 0x7FF) d = DF(__int_as_float(0x7fc00000), 0.0f);
-    vs[i] = make_float2(d.hi, d.lo);
+  for (int j = threadIdx.x; j < ld; j += blockDim.x) {  // each thread converts the slots it filled
+    DF d(0.0f, 0.0f);
+    if (j < nci) d = E == 0x7FF ? DF(__int_as_float(0x7fc00000), 0.0f) : split_scaled(vd[j], E);
+    vs[j] = make_float2(d.hi, d.lo);
   }
-  if (threadIdx.x == 0) *ev = E;
-}
-
-__global__ void k_split_mat(size_t nn, const double* __restrict__ a, float2* __restrict__ b) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nn) return;
-  const double x = a[i];
-  const float hi = (float)x;
-  b[i] = make_float2(hi, (float)(x - (double)hi));
+  __syncthreads();
+  DF s0, s1;
+  for (int c = 0; c < ctot; ++c) {
+    issue(c + kInvStages - 1);
+    cp_async_wait<kInvStages - 1>();  // this lane's words of chunk c have landed
+    const float4* src = ring + (c % kInvStages) * kInvChunkWords;
+    const int rr = c / nch, k = c - rr * nch;
+#pragma unroll
+    for (int u = 0; u < kInvWords; ++u) {
+      const float4 a = src[32 * u + lane];  // zero past the row end
+      const float4 v = vs4[min(k * kInvChunkWords + 32 * u + lane, q1 - 1)];
+      s0 = s0 + mul(DF(a.x, a.y), DF(v.x, v.y));
+      s1 = s1 + mul(DF(a.z, a.w), DF(v.z, v.w));
+    }
+    if (k == nch - 1) {  // the row is complete
+      DF t = s0 + s1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        t = t + DF(__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o));
+      if (lane == 0)
+        x[ci[wid + nw * rr]] = (T)(widen_scaled(t.hi, E + ea - 1023) + widen_scaled(t.lo, E + ea - 1023));
+      s0 = DF(0.0f, 0.0f);
+      s1 = DF(0.0f, 0.0f);
+    }
+  }
+  cp_async_wait_all();
 }
 
 template <typename T>
@@ -411,9 +512,9 @@ static void coarse_setup_dense(fe_hierarchy* h, cudaStream_t s) {
   cs.A.alloc(nn);
   cs.Linv.alloc(nn);
   cs.LinvT.alloc(nn);
-  cs.LinvDF.alloc(nn);
-  cs.LinvTDF.alloc(nn);
-  cs.bytes = nn * (3 * sizeof(double) + 2 * sizeof(float2));
+  cs.ld = nci + (nci & 1);
+  cs.AinvDF.alloc((size_t)nci * cs.ld);
+  cs.bytes = nn * 3 * sizeof(double) + (size_t)nci * cs.ld * sizeof(float2);
   CUDA_CHECK(cudaMemsetAsync(cs.A, 0, sizeof(double) * nn, s));
   if (L0.deg == 1) {
     k_coarse_assemble<1><<<ceil_div(L0.C, kBlock), kBlock, 0, s>>>(L0.C, L0.Cs, L0.map, L0.geo64, cs.dof2int, nci, cs.A,
@@ -449,10 +550,34 @@ static void coarse_setup_dense(fe_hierarchy* h, cudaStream_t s) {
   if (shm > 48 * 1024) CUDA_CHECK(cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   k_tri_inverse<<<ceil_div(nci, warps), warps * 32, shm, s>>>(nci, w, cs.A, cs.t0, cs.Linv, cs.LinvT);
   LAUNCH_CHECK();
-  k_split_mat<<<ceil_div((long long)nn, kBlock), kBlock, 0, s>>>(nn, cs.Linv, cs.LinvDF);
+  // A^-1 = L^-T L^-1 in FP64 into cs.A (the factor is no longer needed), then as scaled float pairs
+  const int tiles = ceil_div(nci, kGramTile);
+  k_inv_gram<<<dim3(tiles, tiles), dim3(kGramTile, 8), 0, s>>>(nci, cs.Linv, cs.A);
   LAUNCH_CHECK();
-  k_split_mat<<<ceil_div((long long)nn, kBlock), kBlock, 0, s>>>(nn, cs.LinvT, cs.LinvTDF);
+  CUDA_CHECK(cudaMemsetAsync(cs.flag, 0, sizeof(int), s));
+  k_diag_exponent<<<ceil_div(nci, kBlock), kBlock, 0, s>>>(nci, cs.A, cs.flag);
   LAUNCH_CHECK();
+  CUDA_CHECK(cudaMemcpyAsync(&cs.ainv_exp, cs.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_CHECK(cudaStreamSynchronize(s));
+  FE_REQUIRE(cs.ainv_exp >= 1 && cs.ainv_exp <= 2045, FE_ERR_ARG, "coarse inverse out of the FP64 range");
+  k_split_rows<<<std::min(ceil_div((long long)nci * cs.ld, kBlock), 1 << 20), kBlock, 0, s>>>(nci, cs.ld, cs.A,
+                                                                                             cs.flag, cs.AinvDF);
+  LAUNCH_CHECK();
+  // the fused solve: v in dynamic shared memory, a persistent grid of the resident blocks (at most one warp per row)
+  cs.inv_smem = coarse_inv_smem(cs.ld);
+  FE_REQUIRE(cs.inv_smem <= 200 * 1024, FE_ERR_UNSUPPORTED, "coarse level too large for the fused dense solve");
+  int dev = 0, sms = 0;
+  CUDA_CHECK(cudaGetDevice(&dev));
+  CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  auto grid_of = [&](auto kernel) {
+    if (cs.inv_smem > 48 * 1024)
+      CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs.inv_smem));
+    int per_sm = 0;
+    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kInvThreads, cs.inv_smem));
+    return std::max(1, std::min(std::max(1, per_sm) * sms, ceil_div(nci, kInvThreads / 32)));
+  };
+  cs.inv_grid64 = grid_of(k_coarse_inv_df<double>);
+  cs.inv_grid32 = grid_of(k_coarse_inv_df<float>);
 }
 
 static void coarse_setup_blocked(fe_hierarchy* h, cudaStream_t s) {
@@ -460,8 +585,7 @@ static void coarse_setup_blocked(fe_hierarchy* h, cudaStream_t s) {
   CoarseSolver& cs = h->cs;
   const int nci = cs.nci, w = cs.band;
   for (auto* b : {&cs.A, &cs.Linv, &cs.LinvT}) b->release();
-  cs.LinvDF.release();
-  cs.LinvTDF.release();
+  cs.AinvDF.release();
   const int B = std::max(w, 1);
   const int nb = ceil_div(nci, B), npad = nb * B;
   const size_t p = (size_t)w + 1, bb = (size_t)B * B;
@@ -570,9 +694,6 @@ void coarse_setup(fe_hierarchy* h, cudaStream_t s) {
     CUDA_CHECK(cudaMemcpy(cs.dof2int, d2i.data(), sizeof(int) * L0.n, cudaMemcpyHostToDevice));
     cs.t0.alloc(nci);
     cs.t1.alloc(nci);
-    cs.v0.alloc(nci);
-    cs.v1.alloc(nci);
-    cs.ev.alloc(2);
     cs.flag.alloc(1);
   }
   const bool blocked =
@@ -633,14 +754,11 @@ void coarse_solve(const fe_hierarchy* h, const T* b, T* x, cudaStream_t s) {
     k_trimv<<<nci, kRowThreads, 0, s>>>(nci, cs.LinvT, cs.t1, cs.t0, 1);
     LAUNCH_CHECK();
   } else {
-    k_split_vec<T><<<1, 1024, 0, s>>>(nci, cs.ci, b, nullptr, cs.v0, cs.ev);
+    constexpr bool f64 = sizeof(T) == 8;
+    k_coarse_inv_df<T><<<f64 ? cs.inv_grid64 : cs.inv_grid32, kInvThreads, cs.inv_smem, s>>>(
+        L0.n, nci, cs.ld, cs.ci, cs.dof2int, cs.AinvDF, cs.ainv_exp, b, x);
     LAUNCH_CHECK();
-    k_trimv_df<<<nci, kRowThreads, 0, s>>>(nci, cs.LinvDF, cs.v0, cs.ev, cs.t1, 0);
-    LAUNCH_CHECK();
-    k_split_vec<double><<<1, 1024, 0, s>>>(nci, nullptr, cs.t1, nullptr, cs.v1, cs.ev + 1);
-    LAUNCH_CHECK();
-    k_trimv_df<<<nci, kRowThreads, 0, s>>>(nci, cs.LinvTDF, cs.v1, cs.ev + 1, cs.t0, 1);
-    LAUNCH_CHECK();
+    return;
   }
   k_coarse_scatter<T><<<ceil_div(L0.n, kBlock), kBlock, 0, s>>>(L0.n, cs.dof2int, cs.t0, b, x);
   LAUNCH_CHECK();

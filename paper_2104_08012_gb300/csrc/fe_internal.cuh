@@ -193,8 +193,19 @@ __device__ __forceinline__ void cp_async4(int* smem, const int* gmem) {
   const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
+// 16 bytes (both addresses 16-byte aligned), L2 only; with bytes = 0 the slot is
+// zero-filled and gmem is not read.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Until at most N of this thread's most recent groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Blocks of a persistent grid: resident blocks per SM of the kernel times the
 // SM count, or fewer when there are fewer work items.
@@ -313,10 +324,13 @@ struct CoarseSolver {
   DBuf<int> dof2int;   // coarse dof -> interior index or -1
   DBuf<double> A;      // nci*nci dense, then L (lower)
   DBuf<double> Linv, LinvT;
-  DBuf<float2> LinvDF, LinvTDF;  // the same as float pairs (float-pair triangular products)
+  // A^-1 = L^-T L^-1 times 2^(1023 - ainv_exp) (ainv_exp: the largest biased exponent of its diagonal) as float
+  // pairs, rows padded to the even length ld: the dense coarse solve of the float-pair modes is one product with
+  // it (k_coarse_inv_df: inv_smem bytes of shared memory, inv_grid64/32 blocks)
+  DBuf<float2> AinvDF;
+  int ld = 0, ainv_exp = 1023, inv_grid64 = 1, inv_grid32 = 1;
+  size_t inv_smem = 0;
   DBuf<double> t0, t1;  // nci
-  DBuf<float2> v0, v1;  // nci, scaled float pairs of the product inputs
-  DBuf<int> ev;         // their scaling exponents
   DBuf<int> flag;
 };
 
