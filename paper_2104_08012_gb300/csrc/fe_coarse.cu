@@ -564,14 +564,17 @@ static void coarse_setup_dense(fe_hierarchy* h, cudaStream_t s) {
                                                                                              cs.flag, cs.AinvDF);
   LAUNCH_CHECK();
   // the fused solve: v in dynamic shared memory, a persistent grid of the resident blocks (at most one warp per row)
+  // The shared-memory limit is a process-wide attribute of the kernel: it is set to the cap checked here, the
+  // largest size the kernel is ever launched with, not to this hierarchy's size, so that setting up a smaller coarse
+  // level later cannot invalidate the launches of a larger one.
+  constexpr int kInvSmemMax = 200 * 1024;
   cs.inv_smem = coarse_inv_smem(cs.ld);
-  FE_REQUIRE(cs.inv_smem <= 200 * 1024, FE_ERR_UNSUPPORTED, "coarse level too large for the fused dense solve");
+  FE_REQUIRE(cs.inv_smem <= kInvSmemMax, FE_ERR_UNSUPPORTED, "coarse level too large for the fused dense solve");
   int dev = 0, sms = 0;
   CUDA_CHECK(cudaGetDevice(&dev));
   CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   auto grid_of = [&](auto kernel) {
-    if (cs.inv_smem > 48 * 1024)
-      CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs.inv_smem));
+    CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmemMax));
     int per_sm = 0;
     CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kInvThreads, cs.inv_smem));
     return std::max(1, std::min(std::max(1, per_sm) * sms, ceil_div(nci, kInvThreads / 32)));

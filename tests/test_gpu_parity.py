@@ -381,6 +381,28 @@ def test_coarse_blocked_matches_oracle(fe, k, N0):
         assert np.linalg.norm(host(u) - uo) <= 1e-10 * np.linalg.norm(uo)
 
 
+def test_dense_coarse_solve_after_a_smaller_coarse_level(fe):
+    """The one-launch dense coarse solve keeps its shared-memory limit when a hierarchy with a smaller coarse level is
+    set up after it (the limit is a process-wide attribute of the kernel): P2 8^3 (3375 interior unknowns, 76 KB of
+    shared memory per block), then P1 12^3 (1331 unknowns, 60 KB), then the first hierarchy's coarse solve against the
+    oracle's and a whole solve to 1e-10."""
+    with fe.Hierarchy(8, 1, 2) as big:
+        oh = O.Hierarchy(8, 1, 2)
+        c = oh.levels[0]
+        b = I.random_vector(c.n, 13)
+        ref = oh.coarse_solve(b)
+        with fe.Hierarchy(12, 1, 1) as small:
+            assert small.coarse_info()["n_interior"] == 11 ** 3 and not small.coarse_info()["blocked"]
+            x = torch.empty(c.n, dtype=torch.float64, device=DEV)
+            big.coarse_solve(dt(b), x)
+            torch.cuda.synchronize()
+            assert np.linalg.norm(host(x) - ref) <= 1e-11 * np.linalg.norm(ref)
+            f = dt(I.sin_product_rhs(big.dof_coordinates()))
+            u = torch.empty_like(f)
+            st = big.solve(f, u, rtol=1e-10, max_it=100)
+            assert st.rel_residual <= 1e-10 and st.iterations <= 15
+
+
 @pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("coef", ["grf", "grf_per_pair", "one"])
 def test_vcycle_matches_oracle(fe, k, coef):
