@@ -101,6 +101,19 @@ def test_pair_stiffness_properties(pair120):
     assert np.count_nonzero(K) == 136
 
 
+def test_limb_sums_exact_at_the_worst_case(kuhn_exe):
+    """The operator's exactness argument, run in FP32 on the host: every row of K and of the pair matrix, summed by
+    single-precision FMAs in column order over limbs of the largest magnitude with odd unit counts and the row's signs
+    (A_j = +-(2 - 2^-16), B_j = +-(2^-17 + 2^-22 + 2^-33)), equals the exact integer sum; the largest |sum A| is
+    124 (2^17 - 1) units of 2^-16, below 2^24.  (With the coefficients' magnitudes raised so that rows exceed 127 the
+    same check reports inexact rows.)"""
+    inexact, max_a, max_b = (int(v) for v in subprocess.run([kuhn_exe, "limbs"], capture_output=True, text=True,
+                                                             check=True).stdout.split())
+    assert inexact == 0
+    assert max_a == 124 * (2 ** 17 - 1) and max_a < 2 ** 24
+    assert max_b < 2 ** 24
+
+
 def test_prolongation_weights_match_the_stencil_tables(tmp_path_factory):
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:
